@@ -1,0 +1,159 @@
+"""CCFD (two-point flux) discretisation and BDF1/BDF2 residual, Section 2.
+
+Oracle; test infrastructure only.
+
+Residual of cell i (Eq. gover_sys integrated over the cell, times its volume V,
+time derivative by Eq. implicit-method-bdf1 / implicit-method-bdf2, gravity off):
+
+    F_i = V phi_i c(p_i) D_t p_i + sum_faces T_f mbar_f (p_i - p_j)
+          + sum_conns T_q mbar_q (p_i - p_q)
+
+with c(p) = (p/Z)(1/p - Z'/Z) evaluated at the new level, m(p) = p / (mu Z),
+D_t p = (p - p^l)/dt (BDF1) or (3p - 4p^l + p^{l-1})/(2 dt) (BDF2).
+
+Readings (the paper defers CCFD details to its references):
+* geometric face transmissibility T_f = A_f / (h/(2 k_i) + h/(2 k_j)) (harmonic);
+* mbar_f = (m_i + m_j)/2 (arithmetic mean of the two cells);
+* wells and Dirichlet faces are fixed-pressure connections with a half-cell
+  transmissibility and mbar = (m_i + m(p_q))/2; faces without one are no-flow.
+The source term -qRT/W of Eq. gover_sys is carried by the connections.
+
+Jacobian storage: seven arrays (centre, -x, +x, -y, +y, -z, +z) of length N,
+J[s][i] = dF_i / dp_{neighbour s of i}, zero where the neighbour is absent.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+
+from . import eos
+
+STENCIL = ("c", "-x", "+x", "-y", "+y", "-z", "+z")
+
+
+def face_transmissibilities(grid, kx, ky, kz):
+    """Harmonic-average geometric transmissibility of every +x/+y/+z face.
+
+    Tx[i] joins cell i to cell i+1 (0 on the last x layer), likewise Ty, Tz.
+    """
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    K = [np.asarray(k, dtype=np.float64).reshape(nz, ny, nx) for k in (kx, ky, kz)]
+    hx, hy, hz = grid.hx, grid.hy, grid.hz
+    Tx = np.zeros((nz, ny, nx))
+    Ty = np.zeros((nz, ny, nx))
+    Tz = np.zeros((nz, ny, nx))
+    Ax, Ay, Az = hy * hz, hx * hz, hx * hy
+    Tx[:, :, :-1] = Ax / (hx / (2 * K[0][:, :, :-1]) + hx / (2 * K[0][:, :, 1:]))
+    Ty[:, :-1, :] = Ay / (hy / (2 * K[1][:, :-1, :]) + hy / (2 * K[1][:, 1:, :]))
+    Tz[:-1, :, :] = Az / (hz / (2 * K[2][:-1, :, :]) + hz / (2 * K[2][1:, :, :]))
+    return Tx.reshape(-1), Ty.reshape(-1), Tz.reshape(-1)
+
+
+class Problem:
+    """A reservoir with its static discretisation data."""
+
+    def __init__(self, res):
+        self.res = res
+        self.grid = res.grid
+        self.fluid = res.fluid
+        self.a, self.b = eos.pr_constants(res.fluid)
+        self.Tx, self.Ty, self.Tz = face_transmissibilities(res.grid, res.kx, res.ky, res.kz)
+        g = res.grid
+        self.V = g.hx * g.hy * g.hz
+        self.phi = np.asarray(res.phi, dtype=np.float64)
+        self.conn_cell = res.conns.cell.astype(np.int64)
+        self.conn_p = res.conns.p
+        self.conn_T = res.conns.T
+        _, _, _, _, self.conn_m, _ = eos.eos_state(self.conn_p, self.fluid, self.a, self.b)
+
+    def _shifts(self):
+        g = self.grid
+        return (1, g.nx, g.nx * g.ny)
+
+
+def bdf_terms(p, p_l, p_lm1, dt, order):
+    """(D_t p, dD_t/dp) of Eq. implicit-method-bdf1 (order 1) or -bdf2 (order 2)."""
+    if order == 1:
+        return (p - p_l) / dt, 1.0 / dt
+    return (3.0 * p - 4.0 * p_l + p_lm1) / (2.0 * dt), 1.5 / dt
+
+
+def residual(prob: Problem, p, p_l, p_lm1, dt, order, want_jac=False):
+    """F(p) and, optionally, the seven Jacobian arrays."""
+    g = prob.grid
+    N = g.n
+    p = np.asarray(p, dtype=np.float64)
+    _, _, c, dc, m, dm = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    Dt, dDt = bdf_terms(p, p_l, p_lm1, dt, order)
+    F = prob.V * prob.phi * c * Dt
+    Jc = prob.V * prob.phi * (dc * Dt + c * dDt)
+    J = {s: np.zeros(N) for s in STENCIL}
+    # interior faces, one axis at a time (+ side of cell i joins i and i+shift)
+    for T, sh, minus, plus in ((prob.Tx, 1, "-x", "+x"),
+                               (prob.Ty, g.nx, "-y", "+y"),
+                               (prob.Tz, g.nx * g.ny, "-z", "+z")):
+        i = np.nonzero(T > 0)[0]
+        j = i + sh
+        mbar = 0.5 * (m[i] + m[j])
+        dp = p[i] - p[j]
+        flux = T[i] * mbar * dp
+        np.add.at(F, i, flux)
+        np.add.at(F, j, -flux)
+        # d flux / d p_i and d flux / d p_j
+        dfi = T[i] * (0.5 * dm[i] * dp + mbar)
+        dfj = T[i] * (0.5 * dm[j] * dp - mbar)
+        np.add.at(Jc, i, dfi)
+        np.add.at(Jc, j, -dfj)
+        J[plus][i] += dfj
+        J[minus][j] += -dfi
+    # fixed-pressure connections (wells, Dirichlet faces)
+    q = prob.conn_cell
+    if q.size:
+        mbar = 0.5 * (m[q] + prob.conn_m)
+        dp = p[q] - prob.conn_p
+        np.add.at(F, q, prob.conn_T * mbar * dp)
+        np.add.at(Jc, q, prob.conn_T * (0.5 * dm[q] * dp + mbar))
+    J["c"] = Jc
+    if want_jac:
+        return F, J
+    return F
+
+
+def jacobian_csr(grid, J):
+    """Assemble the seven stencil arrays into a scipy CSR matrix."""
+    N = grid.n
+    nx, ny, nz = grid.nx, grid.ny, grid.nz
+    idx = np.arange(N)
+    ii = idx % nx
+    jj = (idx // nx) % ny
+    kk = idx // (nx * ny)
+    rows, cols, vals = [idx], [idx], [J["c"]]
+    for s, sh, ok in (("-x", -1, ii > 0), ("+x", 1, ii < nx - 1),
+                      ("-y", -nx, jj > 0), ("+y", nx, jj < ny - 1),
+                      ("-z", -nx * ny, kk > 0), ("+z", nx * ny, kk < nz - 1)):
+        rows.append(idx[ok])
+        cols.append(idx[ok] + sh)
+        vals.append(J[s][ok])
+    A = sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                      shape=(N, N))
+    A.sort_indices()
+    return A
+
+
+def stencil_matvec(grid, J, x):
+    """y = J x with the seven stencil arrays (plain definition)."""
+    return jacobian_csr(grid, J) @ x
+
+
+def storage(prob: Problem, p, p_l, p_lm1, dt, order):
+    """The accumulation part V phi c D_t p of each cell."""
+    _, _, c, _, _, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    Dt, _ = bdf_terms(p, p_l, p_lm1, dt, order)
+    return prob.V * prob.phi * c * Dt
+
+
+def connection_flux(prob: Problem, p):
+    """Per-connection outflow T mbar (p_i - p_q) (positive out of the cell)."""
+    _, _, _, _, m, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    q = prob.conn_cell
+    return prob.conn_T * 0.5 * (m[q] + prob.conn_m) * (p[q] - prob.conn_p)

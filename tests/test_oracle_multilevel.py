@@ -1,0 +1,116 @@
+"""Pins of the oracle's interpolation and multilevel preconditioners (Section 3.2)."""
+import numpy as np
+import pytest
+import scipy.sparse as sp
+
+from oracle import discretization as disc
+from oracle import multilevel as ml
+from oracle import schwarz
+from paper_2007_13966_gb300 import synthetic as syn
+
+
+@pytest.mark.parametrize("order", [1, 2, 3])
+@pytest.mark.parametrize("n,r", [(16, 2), (32, 4), (20, 4), (13, 2), (24, 8)])
+def test_interp_rows_sum_to_one(order, n, r):
+    P = ml.interp_1d(n, r, order)
+    assert np.allclose(P.sum(axis=1), 1.0, atol=1e-14)
+
+
+def test_ratio_two_linear_weights():
+    P = ml.interp_1d(16, 2, 2)
+    # interior fine cells sit at 1/4 and 3/4 between coarse centres
+    assert np.allclose(P[3, 1:3], [0.75, 0.25])
+    assert np.allclose(P[4, 1:3], [0.25, 0.75])
+
+
+@pytest.mark.parametrize("n,r", [(32, 4), (24, 2), (40, 8)])
+def test_polynomial_reproduction(n, r):
+    xc = ml.coarse_centres(n, r)
+    x = np.arange(n) + 0.5
+    inside = (x >= xc[0]) & (x <= xc[-1])
+    P1, P2, P3 = (ml.interp_1d(n, r, o) for o in (1, 2, 3))
+    assert np.allclose(P1 @ np.full(xc.size, 3.0), 3.0)
+    lin = lambda t: 2.0 * t - 1.0
+    assert np.allclose((P2 @ lin(xc))[inside], lin(x)[inside], atol=1e-12)
+    # cubic convolution (a = -1/2) reproduces quadratics away from the clamped ends
+    quad = lambda t: 0.3 * t * t - t + 2.0
+    far = (x >= xc[1]) & (x <= xc[-2])
+    assert np.allclose((P3 @ quad(xc))[far], quad(x)[far], rtol=1e-12)
+
+
+def setup_two_level(nx=6, ny=6, nz=1, seed=2, r=2):
+    res = syn.small_3d(nx, ny, nz, seed=seed)
+    prob = disc.Problem(res)
+    p = syn.random_pressure(res, seed)
+    _, J = disc.residual(prob, p, 0.98 * p, 0.97 * p, 8640.0, 2, want_jac=True)
+    A = disc.jacobian_csr(res.grid, J)
+    dims = (nx, ny, nz)
+    ratios = (r, r, 1 if nz == 1 else r)
+    P = ml.interpolation(dims, ratios, 2)
+    M = schwarz.Schwarz(A, dims, (2, 2, 1), 1)
+    Ac = ml.galerkin(A, P)
+    return A, M, P, Ac, dims, ratios
+
+
+def _dense(op, n):
+    return np.column_stack([op(e) for e in np.eye(n)])
+
+
+def test_vcycle_three_steps_equal_closed_form():
+    A, M, P, Ac, dims, _ = setup_two_level()
+    n = A.shape[0]
+    Ad = A.toarray()
+    Md = M.dense()
+    C = P.toarray() @ np.linalg.inv(Ac.toarray()) @ P.T.toarray()
+    I = np.eye(n)
+    for kind, mu, nu in ((ml.VCYCLE, 1, 1), (ml.LEFT_KASKADE, 0, 1), (ml.RIGHT_KASKADE, 1, 0)):
+        T = ml.TwoLevel(A, M, P, ml.DenseCoarse(Ac), kind)
+        # Eq. two_level_preconditioner with the given mu, nu
+        S = np.linalg.matrix_power(I - Ad @ Md, nu) @ (I - Ad @ C) @ np.linalg.matrix_power(I - Ad @ Md, mu)
+        ref = np.linalg.solve(Ad, I - S)
+        assert np.abs(_dense(T, n) - ref).max() <= 1e-11 * np.abs(ref).max(), kind
+    add = ml.TwoLevel(A, M, P, ml.DenseCoarse(Ac), ml.ADDITIVE)
+    assert np.allclose(_dense(add, n), C + Md, rtol=1e-12, atol=1e-12 * np.abs(Md).max())
+
+
+def test_algorithm1_two_levels_equals_vcycle():
+    A, M, P, Ac, dims, _ = setup_two_level(8, 6, 1)
+    mg = ml.MultiLevel([Ac, A], [None, M], [None, P], ml.DenseCoarse(Ac))
+    T = ml.TwoLevel(A, M, P, ml.DenseCoarse(Ac), ml.VCYCLE)
+    r = syn.random_vector(A.shape[0], 1)
+    assert np.allclose(mg(r), T(r), rtol=1e-13, atol=1e-13 * np.abs(T(r)).max())
+
+
+def test_galerkin_symmetric_for_symmetric_A():
+    A, M, P, Ac, dims, _ = setup_two_level(8, 8, 4, r=2)
+    S = ((A + A.T) * 0.5).tocsr()
+    Sc = ml.galerkin(S, P)
+    assert abs(Sc - Sc.T).max() <= 1e-14 * abs(Sc).max()
+
+
+def test_galerkin_pattern_is_125_point():
+    A, M, P, Ac, dims, _ = setup_two_level(16, 16, 8, r=4)
+    cdims = ml.coarse_dims(dims, (4, 4, 4))
+    nc = np.prod(cdims)
+    C = Ac.tocoo()
+    ci = np.stack(np.unravel_index(C.row, cdims[::-1]))
+    cj = np.stack(np.unravel_index(C.col, cdims[::-1]))
+    assert np.abs(ci - cj).max() <= 2
+    interior = [i for i in range(nc)
+                if all(2 <= c < d - 2 for c, d in zip(np.unravel_index(i, cdims[::-1]), cdims[::-1]))]
+    if interior:
+        assert Ac[interior[0]].nnz <= 125
+
+
+def test_coarse_only_is_weaker_than_vcycle():
+    """The paper reports the coarse-only preconditioner diverging (Table 6);
+    here: many more FGMRES iterations than the V-cycle on the same system."""
+    from oracle import krylov
+    A, M, P, Ac, dims, _ = setup_two_level(16, 16, 1, r=2)
+    b = syn.random_vector(A.shape[0], 4)
+    its = {}
+    for kind in (ml.VCYCLE, ml.COARSE_ONLY):
+        T = ml.TwoLevel(A, M, P, ml.DenseCoarse(Ac), kind)
+        _, info = krylov.fgmres(lambda v: A @ v, T, b, rtol=1e-8, restart=30, maxit=300)
+        its[kind] = info["iters"]
+    assert its[ml.COARSE_ONLY] > 3 * its[ml.VCYCLE]
