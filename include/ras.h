@@ -1,0 +1,227 @@
+/*
+ * ras.h - C ABI of the GB300 multilevel restricted-additive-Schwarz
+ * Newton-Krylov solver for compressible gas flow with the Peng-Robinson EOS
+ * (Li, Yang, Yang, arXiv 2007.13966).
+ *
+ * Conventions (every entry point):
+ *  - Arrays are DEVICE pointers owned by the caller unless stated otherwise;
+ *    FP64; cell n = i + nx*(j + ny*k) (x fastest). The library never frees
+ *    them and never keeps them past the call, except where a create function
+ *    says it copies them.
+ *  - Handles (ras_problem, ras_precond) own their device workspaces; they are
+ *    created by *_create / ras_setup and released by *_destroy.
+ *  - `stream` is a cudaStream_t passed as void* (NULL = legacy default stream).
+ *    Calls are asynchronous on that stream unless they return a convergence
+ *    result (gmres_solve, newton_step, ras_factor's pivot check), which
+ *    synchronise it.
+ *  - Return value: RAS_OK (0); > 0 did not converge; < 0 error. No exception
+ *    crosses the ABI. ras_status_string() describes a code.
+ */
+#ifndef RAS_H
+#define RAS_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum ras_status {
+    RAS_OK = 0,
+    RAS_GMRES_MAXIT = 1,       /* linear solve hit maxit without Eq. equ:linear_stop */
+    RAS_NEWTON_MAXIT = 2,      /* Newton hit maxit without Eq. equ:nonlinear_stop   */
+    RAS_LINESEARCH_FAIL = 3,   /* step length fell below ls_min_lambda               */
+    RAS_EINVAL = -1,           /* invalid argument (NULL, size, option out of range) */
+    RAS_ECUDA = -2,            /* a CUDA runtime call failed                         */
+    RAS_ENOMEM = -3,           /* device allocation failed                           */
+    RAS_ENAN = -4,             /* NaN/Inf in a norm                                  */
+    RAS_EZEROPIVOT = -5,       /* zero or non-finite ILU / LU pivot                  */
+    RAS_ENOROOT = -6,          /* no admissible EOS root                             */
+    RAS_ETIMEOUT = -7          /* a bounded device wait gave up                      */
+};
+
+/* Structured cell-centred grid (Section 2; Fig. 1). nz = 1 for 2D
+ * (the thickness hz is then the cell depth). Spacing in metres. */
+typedef struct {
+    int nx, ny, nz;
+    double hx, hy, hz;
+} ras_grid;
+
+/* Fluid (Section 2, Eq. attrfactor and the m(omega), omega(T_br) fits;
+ * constants of Section 4). SI units: K, Pa, J/(mol K), kg/mol, Pa s.
+ * If omega_from_Tb != 0, omega is computed from Tb by the Section 2
+ * correlation; otherwise `omega` is used. */
+typedef struct {
+    double Tc, pc, omega, Tb;
+    int omega_from_Tb;
+    double T, R, W, mu;
+} ras_eos;
+
+/* Rock and fixed-pressure connections. kx, ky, kz (m^2) and phi are device
+ * arrays of N cells. Connections (wells and Dirichlet faces) join cell
+ * conn_cell[q] to pressure conn_p[q] (Pa) through geometric transmissibility
+ * conn_T[q] (m^3); they must be sorted by cell (several per cell allowed).
+ * conn_* are device arrays of nconn entries. ras_problem_create copies all of
+ * it; the caller may free these arrays afterwards. */
+typedef struct {
+    const double *kx, *ky, *kz, *phi;
+    int nconn;
+    const int *conn_cell;
+    const double *conn_p, *conn_T;
+} ras_rock;
+
+/* Jacobian (or any 7-point operator) as seven device arrays of N entries:
+ * c[0] centre, c[1] -x, c[2] +x, c[3] -y, c[4] +y, c[5] -z, c[6] +z;
+ * c[s][n] = dF_n / dp_{neighbour s of n}, zero where the neighbour is absent. */
+typedef struct {
+    double *c[7];
+} ras_stencil;
+
+/* Schwarz preconditioner options (Sections 3.1-3.2). */
+typedef struct {
+    int px, py, pz;        /* subdomain counts per axis (Omega_i, Fig. 1)             */
+    int overlap;           /* delta >= 0 (cells per side, cut at the boundary)       */
+    int ras_type;          /* 1 = left-RAS, Eq. equ:as-left (only value implemented) */
+    int ilu_k;             /* 0 = ILU(0) subdomain solver (only value implemented)   */
+    int factor_prec;       /* 64 = FP64 factors and solves; 32 = FP32 factors, FP32
+                              solves; 16 = BF16-stored factors, FP32 solves          */
+    int nlevels;           /* 1 = one-level; 2 = two-level (Eq. equ:v-cycle)          */
+    int coarsen[3];        /* coarse:fine ratio per axis for nlevels = 2 (Table 7)    */
+    int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second (only value)  */
+    int mlevel_type;       /* 0 = V-cycle, 1 = left-Kaskade, 2 = right-Kaskade,
+                              3 = additive, 4 = coarse-only (Eqs. equ:v-cycle ..
+                              equ:coarse-level)                                      */
+    int coarse_prec;       /* 64 or 32: precision of the dense banded coarse LU       */
+} ras_opts;
+
+typedef struct {
+    int restart;           /* GMRES(m) restart length (30 in Section 4)              */
+    int maxit;             /* total iteration cap                                     */
+    double rtol, atol;     /* Eq. equ:linear_stop, read as max(rtol ||b||, atol)      */
+} ras_krylov_opts;
+
+typedef struct {
+    int iters;             /* FGMRES iterations done                                  */
+    int converged;         /* 1 if the stop test was met                              */
+    double r0, rfinal;     /* ||b|| and the final true residual norm                  */
+    double *history;       /* HOST buffer (may be NULL): residual estimates, one per
+                              iteration plus the initial and each restart's value    */
+    int history_cap;       /* capacity of history                                     */
+    int history_len;       /* entries written                                         */
+} ras_krylov_stats;
+
+typedef struct {
+    int maxit;             /* Newton iteration cap (50)                               */
+    double rtol, atol;     /* Eq. equ:nonlinear_stop: eps_r, eps_a                    */
+    double ls_alpha;       /* sufficient-decrease alpha (1e-4, Section 3)             */
+    double ls_min_lambda;  /* smallest step length before failure (1e-8)              */
+    ras_krylov_opts lin;   /* inner FGMRES options                                    */
+} ras_newton_opts;
+
+typedef struct {
+    int iters;             /* Newton iterations                                       */
+    int lin_iters;         /* FGMRES iterations summed over the Newton iterations     */
+    int residual_evals;    /* residual evaluations (incl. line-search trials)         */
+    double f0, ffinal;     /* ||F(X^0)|| and the final ||F||                          */
+    double *fhistory;      /* HOST buffer (may be NULL): ||F|| after each iteration   */
+    int fhistory_cap, fhistory_len;
+    int *lin_history;      /* HOST buffer (may be NULL): FGMRES iterations per Newton */
+    int lin_history_cap;
+    double *lambdas;       /* HOST buffer (may be NULL): accepted step lengths        */
+} ras_newton_stats;
+
+typedef struct ras_problem ras_problem;
+typedef struct ras_precond ras_precond;
+
+/* Creates the discrete problem: computes the PR constants a, b
+ * (Eq. attrfactor), the harmonic-average face transmissibilities of the
+ * two-point flux scheme (Section 2, CCFD) and copies phi and the connections.
+ * The grid must have nx, ny >= 1, nz >= 1 and positive spacings; N = nx*ny*nz
+ * must fit in int32. Returns RAS_EINVAL on bad arguments. */
+int ras_problem_create(const ras_grid *grid, const ras_eos *eos, const ras_rock *rock,
+                       void *stream, ras_problem **out);
+void ras_problem_destroy(ras_problem *prob);
+
+/* Residual of Eq. implicit-method-bdf1 (bdf_order = 1) or
+ * Eq. implicit-method-bdf2 (bdf_order = 2) integrated over each cell:
+ *   F_n = V phi_n c(p_n) D_t p_n + sum_faces T_f mbar_f (p_n - p_m)
+ *         + sum_conns T_q mbar_q (p_n - p_q),
+ * c(p) = (p/Z)(1/p - Z'/Z) (Eq. gover_sys), m = p/(mu Z), mbar the arithmetic
+ * mean of the two sides; Z is the largest real root of Eq. equ:PR, Z' the
+ * closed form under Eq. gover_sys. p, p_l, p_lm1: device [N] (p_lm1 unused
+ * for bdf_order 1). F: device [N] output. J: if non-NULL, its seven arrays
+ * (device [N] each) receive the exact Jacobian. normF: if non-NULL, HOST
+ * pointer that receives ||F||_2 (the call then synchronises the stream). */
+int residual_eval(ras_problem *prob, const double *p, const double *p_l, const double *p_lm1,
+                  double dt, int bdf_order, double *F, const ras_stencil *J, double *normF,
+                  void *stream);
+
+/* y = J x for a 7-point operator (the Jacobian-vector product of the Krylov
+ * solve, Eq. jacobian). x, y: device [N], must not alias. */
+int ras_stencil_matvec(const ras_problem *prob, const ras_stencil *J, const double *x,
+                       double *y, void *stream);
+
+/* Symbolic set-up, once per grid: the P_x x P_y x P_z partition with overlap
+ * (Section 3.1, Fig. 1), per-subdomain boxes, the wavefront (level) schedule of
+ * the natural-order ILU(0) triangular solves, factor storage, and for
+ * nlevels = 2 the interpolation (Eq. equ:inter-second), the coarse grid and the
+ * banded coarse-LU layout. Returns RAS_EINVAL for unsupported options. */
+int ras_setup(const ras_problem *prob, const ras_opts *opts, ras_precond **out);
+void ras_precond_destroy(ras_precond *pc);
+
+/* Numeric factorisation, once per Newton iteration: A_i = R_i^delta J
+ * (R_i^delta)^T (Eq. equ:as-class), ILU(0) without pivoting in natural order
+ * inside each overlapped subdomain, stored at factor_prec; for nlevels = 2 also
+ * the Galerkin coarse operator R J P (R = P^T) and its banded LU.
+ * Synchronises the stream to check pivots: RAS_EZEROPIVOT on a zero or
+ * non-finite pivot. */
+int ras_factor(ras_precond *pc, const ras_stencil *J, void *stream);
+
+/* z = M^{-1} r. One level: left-RAS, Eq. equ:as-left,
+ *   z = sum_i (R_i^0)^T (L_i U_i)^{-1} R_i^delta r.
+ * Two levels: the configured two-level combination (Eq. equ:v-cycle by
+ * default). r, z: device [N], must not alias. Requires a prior ras_factor. */
+int ras_apply(ras_precond *pc, const double *r, double *z, void *stream);
+
+/* Right-preconditioned flexible GMRES(m) (Section 3, Eq. jacobian, Remark 2)
+ * for J x = b from x = 0, classical Gram-Schmidt applied twice, Givens
+ * rotations; stops when the residual estimate satisfies
+ * ||b - J x|| <= max(rtol ||b||, atol). b, x: device [N]. stats may be NULL.
+ * Returns RAS_OK or RAS_GMRES_MAXIT (x then holds the last iterate). */
+int gmres_solve(ras_problem *prob, const ras_stencil *J, ras_precond *pc, const double *b,
+                double *x, const ras_krylov_opts *opts, ras_krylov_stats *stats, void *stream);
+
+/* One implicit time step (Sections 2-3): inexact Newton X^{k+1} = X^k +
+ * lambda s^k (Eq. newton_iterate) from X^0 = p (normally p_l), J s = -F by
+ * gmres_solve with pc refactored every iteration, cubic backtracking line
+ * search with sufficient decrease ||F(X + lambda s)|| <= (1 - alpha lambda)||F||,
+ * stop on Eq. equ:nonlinear_stop. p: device [N], in: initial guess, out:
+ * p^{l+1}. stats may be NULL. */
+int newton_step(ras_problem *prob, ras_precond *pc, double *p, const double *p_l,
+                const double *p_lm1, double dt, int bdf_order, const ras_newton_opts *opts,
+                ras_newton_stats *stats, void *stream);
+
+/* Human-readable description of a status code (static storage). */
+const char *ras_status_string(int status);
+
+/* Text of the last CUDA runtime failure seen by the library (static storage,
+ * empty if none); diagnostic only. */
+const char *ras_last_error(void);
+
+/* Number of CUDA kernels this library has launched since it was loaded. */
+long long ras_kernel_launches(void);
+
+/* Per-kernel-class device timing of ras_apply's subdomain-solve kernel:
+ * when enabled, every launch is bracketed by CUDA events on its stream;
+ * ras_timing_read returns the summed milliseconds and the launch count since
+ * the last reset (synchronises the events). */
+int ras_timing_enable(ras_precond *pc, int enable);
+int ras_timing_read(ras_precond *pc, double *total_ms, long long *launches, int reset);
+
+/* Algorithmic bytes of one subdomain-solve launch of ras_apply (factors read
+ * once, r read over the overlapped boxes, z written once), for roofline
+ * reporting. */
+double ras_apply_bytes(const ras_precond *pc);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* RAS_H */

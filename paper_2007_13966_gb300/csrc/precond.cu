@@ -1,0 +1,141 @@
+// ras_setup / ras_factor / ras_apply: the one-level left-RAS preconditioner of
+// Eq. equ:as-left and the two-level combinations of Section 3.2.1.
+#include "precond.cuh"
+
+namespace ras {
+
+static int fine_apply(ras_precond *pc, const double *r, double *z, int accumulate, cudaStream_t st) {
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    if (pc->timing) {
+        if (pc->ev_used + 2 > pc->ev.size()) {
+            for (int i = 0; i < 64; ++i) {
+                cudaEvent_t e;
+                RAS_CK(cudaEventCreate(&e));
+                pc->ev.push_back(e);
+            }
+        }
+        e0 = pc->ev[pc->ev_used++];
+        e1 = pc->ev[pc->ev_used++];
+        RAS_CK(cudaEventRecord(e0, st));
+    }
+    RAS_TRY(ras1_apply(pc->fine, r, z, accumulate, st));
+    if (pc->timing) RAS_CK(cudaEventRecord(e1, st));
+    return RAS_OK;
+}
+
+int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
+    Stencil7 A;
+    for (int s = 0; s < 7; ++s) A.c[s] = J->c[s];
+    pc->A = A;
+    RAS_TRY(ras1_factor(pc->fine, A, st));
+    if (pc->coarse) RAS_TRY(coarse_factor(pc->coarse, A, st));
+    return ras1_check(pc->fine, st);
+}
+
+// z = M^{-1} r for the configured preconditioner
+int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st) {
+    const ras_problem *P = pc->prob;
+    if (!pc->coarse) return fine_apply(pc, r, z, 0, st);
+    const int nx = P->nx, ny = P->ny, nz = P->nz;
+    double *t = pc->t1;
+    switch (pc->opts.mlevel_type) {
+        case 0:  // V-cycle, Eq. equ:v-cycle
+            RAS_TRY(fine_apply(pc, r, z, 0, st));                       // e1 = M r
+            RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));   // t = r - A e1
+            RAS_TRY(coarse_correct(pc->coarse, t, z, 1, st));            // e2 = e1 + P Ac^-1 R t
+            RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));   // t = r - A e2
+            RAS_TRY(fine_apply(pc, t, z, 1, st));                        // e = e2 + M t
+            return RAS_OK;
+        case 1:  // left-Kaskade, Eq. equ:left-Kas: c + M (r - A c)
+            RAS_TRY(coarse_correct(pc->coarse, r, z, 0, st));
+            RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));
+            RAS_TRY(fine_apply(pc, t, z, 1, st));
+            return RAS_OK;
+        case 2:  // right-Kaskade, Eq. equ:right-Kas: e + C (r - A e)
+            RAS_TRY(fine_apply(pc, r, z, 0, st));
+            RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));
+            RAS_TRY(coarse_correct(pc->coarse, t, z, 1, st));
+            return RAS_OK;
+        case 3:  // additive, Eq. equ:two-additive
+            RAS_TRY(fine_apply(pc, r, z, 0, st));
+            RAS_TRY(coarse_correct(pc->coarse, r, z, 1, st));
+            return RAS_OK;
+        case 4:  // coarse only, Eq. equ:coarse-level
+            return coarse_correct(pc->coarse, r, z, 0, st);
+        default:
+            return RAS_EINVAL;
+    }
+}
+
+}  // namespace ras
+
+using namespace ras;
+
+extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **out) {
+    if (!P || !o || !out) return RAS_EINVAL;
+    *out = nullptr;
+    if (o->ras_type != 1 || o->ilu_k != 0) return RAS_EINVAL;
+    if (o->nlevels != 1 && o->nlevels != 2) return RAS_EINVAL;
+    if (o->mlevel_type < 0 || o->mlevel_type > 4) return RAS_EINVAL;
+    ras_precond *pc = new ras_precond();
+    pc->prob = P;
+    pc->opts = *o;
+    int rc = ras1_setup(pc->fine, P->nx, P->ny, P->nz, o->px, o->py, o->pz, o->overlap,
+                        o->factor_prec);
+    if (rc) { ras_precond_destroy(pc); return rc; }
+    if (o->nlevels == 2) {
+        rc = coarse_setup(&pc->coarse, P, *o);
+        if (!rc) rc = dalloc(&pc->t1, P->N);
+        if (!rc) rc = dalloc(&pc->t2, P->N);
+        if (!rc) rc = dalloc(&pc->t3, P->N);
+        if (rc) { ras_precond_destroy(pc); return rc; }
+    }
+    *out = pc;
+    return RAS_OK;
+}
+
+extern "C" void ras_precond_destroy(ras_precond *pc) {
+    if (!pc) return;
+    ras1_free(pc->fine);
+    if (pc->coarse) coarse_free(pc->coarse);
+    dfree(pc->t1); dfree(pc->t2); dfree(pc->t3);
+    for (auto e : pc->ev) cudaEventDestroy(e);
+    delete pc;
+}
+
+extern "C" int ras_factor(ras_precond *pc, const ras_stencil *J, void *stream) {
+    if (!pc || !J) return RAS_EINVAL;
+    for (int s = 0; s < 7; ++s) if (!J->c[s]) return RAS_EINVAL;
+    return precond_factor(pc, J, S(stream));
+}
+
+extern "C" int ras_apply(ras_precond *pc, const double *r, double *z, void *stream) {
+    if (!pc || !r || !z || r == z) return RAS_EINVAL;
+    return precond_apply(pc, r, z, S(stream));
+}
+
+extern "C" int ras_timing_enable(ras_precond *pc, int enable) {
+    if (!pc) return RAS_EINVAL;
+    pc->timing = enable != 0;
+    return RAS_OK;
+}
+
+extern "C" int ras_timing_read(ras_precond *pc, double *total_ms, long long *launches, int reset) {
+    if (!pc) return RAS_EINVAL;
+    for (size_t i = 0; i + 1 < pc->ev_used; i += 2) {
+        RAS_CK(cudaEventSynchronize(pc->ev[i + 1]));
+        float ms = 0.f;
+        RAS_CK(cudaEventElapsedTime(&ms, pc->ev[i], pc->ev[i + 1]));
+        pc->acc_ms += ms;
+        pc->acc_n += 1;
+    }
+    pc->ev_used = 0;
+    if (total_ms) *total_ms = pc->acc_ms;
+    if (launches) *launches = pc->acc_n;
+    if (reset) { pc->acc_ms = 0.0; pc->acc_n = 0; }
+    return RAS_OK;
+}
+
+extern "C" double ras_apply_bytes(const ras_precond *pc) {
+    return pc ? ras1_bytes(pc->fine) : 0.0;
+}

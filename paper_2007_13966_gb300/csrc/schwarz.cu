@@ -1,0 +1,518 @@
+// One-level restricted additive Schwarz (Section 3.1) on sm_103a.
+//
+// The paper's subdomains (one per MPI rank on Tianhe-2) become one CTA each.
+// Inside a subdomain the natural-order ILU(0) triangular solves are run as a
+// wavefront: cells with equal i + j + k form a level, levels are separated by
+// CTA barriers, and the working vector lives in shared memory. Factor records
+// are stored in level order so that each staged chunk of consecutive levels is
+// one contiguous range, streamed into a shared-memory ring with cp.async ahead
+// of the sweep that consumes it.
+#include "schwarz.cuh"
+
+#include <algorithm>
+#include <map>
+#include <tuple>
+
+namespace ras {
+
+// ---------------------------------------------------------------------------
+// factor record types
+// ---------------------------------------------------------------------------
+
+struct RecF64 { double a, b, c, d; };
+struct __align__(16) RecF32 { float a, b, c, d; };
+struct __align__(8) RecB16 { __nv_bfloat16 a, b, c, d; };
+
+template <int PREC> struct RecT;
+template <> struct RecT<64> { using T = RecF64; using Acc = double; };
+template <> struct RecT<32> { using T = RecF32; using Acc = float; };
+template <> struct RecT<16> { using T = RecB16; using Acc = float; };
+
+__device__ __forceinline__ RecF64 make_rec64(double a, double b, double c, double d) {
+    return RecF64{a, b, c, d};
+}
+
+template <int PREC>
+__device__ __forceinline__ void store_rec(void *base, long long idx, double a, double b, double c,
+                                          double d) {
+    if constexpr (PREC == 64) {
+        reinterpret_cast<RecF64 *>(base)[idx] = RecF64{a, b, c, d};
+    } else if constexpr (PREC == 32) {
+        reinterpret_cast<RecF32 *>(base)[idx] = RecF32{(float)a, (float)b, (float)c, (float)d};
+    } else {
+        // FP64 -> FP32 -> BF16, each round to nearest even
+        RecB16 r;
+        r.a = __float2bfloat16_rn((float)a);
+        r.b = __float2bfloat16_rn((float)b);
+        r.c = __float2bfloat16_rn((float)c);
+        r.d = __float2bfloat16_rn((float)d);
+        reinterpret_cast<RecB16 *>(base)[idx] = r;
+    }
+}
+
+template <typename Acc, typename R>
+__device__ __forceinline__ void load_rec(const unsigned char *p, Acc &a, Acc &b, Acc &c, Acc &d) {
+    if constexpr (sizeof(R) == 32) {
+        const double2 *q = reinterpret_cast<const double2 *>(p);
+        const double2 u = q[0], v = q[1];
+        a = u.x; b = u.y; c = v.x; d = v.y;
+    } else if constexpr (sizeof(R) == 16) {
+        const float4 u = *reinterpret_cast<const float4 *>(p);
+        a = u.x; b = u.y; c = u.z; d = u.w;
+    } else {
+        const RecB16 u = *reinterpret_cast<const RecB16 *>(p);
+        a = __bfloat162float(u.a); b = __bfloat162float(u.b);
+        c = __bfloat162float(u.c); d = __bfloat162float(u.d);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// cp.async staging
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() {
+    asm volatile("cp.async.commit_group;\n" ::: "memory");
+}
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// copy the 16-byte-aligned window around global bytes [b0, b1) of `base`
+// into `dst`; the data of byte b0 lands at dst + (b0 & 15)
+__device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned char *base,
+                                            long long b0, long long b1) {
+    const long long a0 = b0 & ~15LL;
+    const long long a1 = (b1 + 15) & ~15LL;
+    for (long long o = a0 + 16LL * threadIdx.x; o < a1; o += 16LL * blockDim.x)
+        cp_async16(dst + (o - a0), base + o);
+}
+
+// ---------------------------------------------------------------------------
+// kernels
+// ---------------------------------------------------------------------------
+
+struct ApplyParams {
+    const SubInfo *subs;
+    const ShapeInfo *shapes;
+    const int *lvl, *chunk;
+    const unsigned *cells;
+    const unsigned char *fwd, *bwd;
+    const double *r;
+    double *z;
+    int nx, ny, nz;
+    int accumulate;
+    int ycap, lcap, nbuf, chunk_cells;
+};
+
+template <int PREC, int NBUF>
+__global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
+    using R = typename RecT<PREC>::T;
+    using Acc = typename RecT<PREC>::Acc;
+    constexpr int RB = (int)sizeof(R);
+    extern __shared__ __align__(16) unsigned char smem[];
+    Acc *Y = reinterpret_cast<Acc *>(smem);
+    int *lvl_s = reinterpret_cast<int *>(smem + ((size_t)P.ycap * sizeof(Acc)));
+    unsigned char *ring = smem + ((size_t)P.ycap * sizeof(Acc)) + (size_t)P.lcap * sizeof(int);
+    const int rcap = ((P.chunk_cells * RB + 32) + 15) & ~15;
+    const int ccap = ((P.chunk_cells * 4 + 32) + 15) & ~15;
+    unsigned char *ring_rec = ring;
+    unsigned char *ring_cell = ring + (size_t)NBUF * rcap;
+
+    const SubInfo si = P.subs[blockIdx.x];
+    const ShapeInfo sh = P.shapes[si.shape];
+    const int *chunk_lev = P.chunk + sh.chunk_off;
+    for (int t = threadIdx.x; t <= sh.nlev; t += blockDim.x) lvl_s[t] = P.lvl[sh.lvl_off + t];
+    __syncthreads();
+
+    const int nstage = 2 * sh.nchunk;
+    auto issue = [&](int t) {
+        if (t < nstage) {
+            const bool fw = t < sh.nchunk;
+            const int c = fw ? t : nstage - 1 - t;
+            const int qa = lvl_s[chunk_lev[c]], qb = lvl_s[chunk_lev[c + 1]];
+            const int slot = t % NBUF;
+            stage_bytes(ring_rec + (size_t)slot * rcap, fw ? P.fwd : P.bwd,
+                        (si.foff + qa) * (long long)RB, (si.foff + qb) * (long long)RB);
+            stage_bytes(ring_cell + (size_t)slot * ccap,
+                        reinterpret_cast<const unsigned char *>(P.cells),
+                        (sh.cell_off + (long long)qa) * 4, (sh.cell_off + (long long)qb) * 4);
+        }
+        cp_async_commit();
+    };
+#pragma unroll
+    for (int t = 0; t < NBUF - 1; ++t) issue(t);
+
+    // gather R_i^delta r into shared memory
+    const int bx = sh.bx, by = sh.by, bxy = sh.bx * sh.by;
+    const int nx = P.nx, nxy = P.nx * P.ny;
+    const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
+    for (int idx = threadIdx.x; idx < sh.ncell; idx += blockDim.x) {
+        const int i = idx % bx, j = (idx / bx) % by, k = idx / bxy;
+        Y[idx] = (Acc)P.r[g0 + i + (long long)nx * j + (long long)nxy * k];
+    }
+
+    for (int t = 0; t < nstage; ++t) {
+        cp_async_wait<NBUF - 2>();
+        __syncthreads();
+        issue(t + NBUF - 1);
+        const bool fw = t < sh.nchunk;
+        const int c = fw ? t : nstage - 1 - t;
+        const int l0 = chunk_lev[c], l1 = chunk_lev[c + 1];
+        const int qa = lvl_s[l0];
+        const int slot = t % NBUF;
+        const unsigned char *rec = ring_rec + (size_t)slot * rcap +
+                                   (int)(((si.foff + qa) * (long long)RB) & 15);
+        const unsigned char *cel = ring_cell + (size_t)slot * ccap +
+                                   (int)(((sh.cell_off + (long long)qa) * 4) & 15);
+        if (fw) {
+            // forward: w_n = (r_n - sum_{m<n} a_nm w_m) / d_n, w = D^{-1} L^{-1} r
+            for (int l = l0; l < l1; ++l) {
+                const int q1 = lvl_s[l + 1];
+                for (int q = lvl_s[l] + threadIdx.x; q < q1; q += blockDim.x) {
+                    const unsigned e = *reinterpret_cast<const unsigned *>(cel + 4 * (q - qa));
+                    Acc ax, ay, az, dinv;
+                    load_rec<Acc, R>(rec + (size_t)RB * (q - qa), ax, ay, az, dinv);
+                    const int n = (int)(e & 255u) + bx * (int)((e >> 8) & 255u) +
+                                  bxy * (int)((e >> 16) & 255u);
+                    const unsigned fl = e >> 24;
+                    Acc s = Y[n];
+                    if (fl & F_MZ) s -= az * Y[n - bxy];
+                    if (fl & F_MY) s -= ay * Y[n - bx];
+                    if (fl & F_MX) s -= ax * Y[n - 1];
+                    Y[n] = s * dinv;
+                }
+                __syncthreads();
+            }
+        } else {
+            // backward: z_n = w_n - d_n^{-1} sum_{m>n} a_nm z_m
+            for (int l = l1 - 1; l >= l0; --l) {
+                const int q1 = lvl_s[l + 1];
+                for (int q = lvl_s[l] + threadIdx.x; q < q1; q += blockDim.x) {
+                    const unsigned e = *reinterpret_cast<const unsigned *>(cel + 4 * (q - qa));
+                    Acc ax, ay, az, dinv;
+                    load_rec<Acc, R>(rec + (size_t)RB * (q - qa), ax, ay, az, dinv);
+                    const int n = (int)(e & 255u) + bx * (int)((e >> 8) & 255u) +
+                                  bxy * (int)((e >> 16) & 255u);
+                    const unsigned fl = e >> 24;
+                    Acc s = 0;
+                    if (fl & F_PX) s += ax * Y[n + 1];
+                    if (fl & F_PY) s += ay * Y[n + bx];
+                    if (fl & F_PZ) s += az * Y[n + bxy];
+                    Y[n] = Y[n] - dinv * s;
+                }
+                __syncthreads();
+            }
+        }
+    }
+    cp_async_wait<0>();
+
+    // (R_i^0)^T: write the owned cells
+    for (int idx = threadIdx.x; idx < sh.ncell; idx += blockDim.x) {
+        const int i = idx % bx, j = (idx / bx) % by, k = idx / bxy;
+        if (i < si.ox0 || i >= si.ox1 || j < si.oy0 || j >= si.oy1 || k < si.oz0 || k >= si.oz1)
+            continue;
+        const long long g = g0 + i + (long long)nx * j + (long long)nxy * k;
+        const double v = (double)Y[idx];
+        if (P.accumulate) P.z[g] += v; else P.z[g] = v;
+    }
+}
+
+struct FactorParams {
+    const SubInfo *subs;
+    const ShapeInfo *shapes;
+    const int *lvl;
+    const unsigned *cells;
+    Stencil7 A;
+    void *fwd, *bwd;
+    int nx, ny, nz;
+    int *err;
+};
+
+// ILU(0) of A_i in natural order: only the diagonal changes,
+// d_n = a_nn - sum_{m<n neighbour} (a_nm / d_m) a_mn   (m: -z, -y, -x).
+template <int PREC>
+__global__ void __launch_bounds__(512) k_ras_factor(FactorParams P) {
+    extern __shared__ __align__(16) unsigned char smem[];
+    double *D = reinterpret_cast<double *>(smem);
+    const SubInfo si = P.subs[blockIdx.x];
+    const ShapeInfo sh = P.shapes[si.shape];
+    const int *lvl = P.lvl + sh.lvl_off;
+    const unsigned *cells = P.cells + sh.cell_off;
+    const int bx = sh.bx, by = sh.by, bxy = bx * by;
+    const int nx = P.nx, nxy = P.nx * P.ny;
+    const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
+    const double *Ac = P.A.c[0], *Amx = P.A.c[1], *Apx = P.A.c[2], *Amy = P.A.c[3],
+                 *Apy = P.A.c[4], *Amz = P.A.c[5], *Apz = P.A.c[6];
+    for (int l = 0; l < sh.nlev; ++l) {
+        const int q1 = lvl[l + 1];
+        for (int q = lvl[l] + threadIdx.x; q < q1; q += blockDim.x) {
+            const unsigned e = cells[q];
+            const int i = e & 255u, j = (e >> 8) & 255u, k = (e >> 16) & 255u;
+            const unsigned fl = e >> 24;
+            const int n = i + bx * j + bxy * k;
+            const long long g = g0 + i + (long long)nx * j + (long long)nxy * k;
+            double d = Ac[g];
+            if (fl & F_MZ) { const double lm = Amz[g] / D[n - bxy]; d -= lm * Apz[g - nxy]; }
+            if (fl & F_MY) { const double lm = Amy[g] / D[n - bx]; d -= lm * Apy[g - nx]; }
+            if (fl & F_MX) { const double lm = Amx[g] / D[n - 1]; d -= lm * Apx[g - 1]; }
+            if (!(d != 0.0) || !isfinite(d)) atomicExch(P.err, 1);
+            D[n] = d;
+        }
+        __syncthreads();
+    }
+    for (int q = threadIdx.x; q < sh.ncell; q += blockDim.x) {
+        const unsigned e = cells[q];
+        const int i = e & 255u, j = (e >> 8) & 255u, k = (e >> 16) & 255u;
+        const unsigned fl = e >> 24;
+        const int n = i + bx * j + bxy * k;
+        const long long g = g0 + i + (long long)nx * j + (long long)nxy * k;
+        const double dinv = 1.0 / D[n];
+        store_rec<PREC>(P.fwd, si.foff + q, (fl & F_MX) ? Amx[g] : 0.0, (fl & F_MY) ? Amy[g] : 0.0,
+                        (fl & F_MZ) ? Amz[g] : 0.0, dinv);
+        store_rec<PREC>(P.bwd, si.foff + q, (fl & F_PX) ? Apx[g] : 0.0, (fl & F_PY) ? Apy[g] : 0.0,
+                        (fl & F_PZ) ? Apz[g] : 0.0, dinv);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// host set-up
+// ---------------------------------------------------------------------------
+
+static std::vector<int> split_axis(int n, int parts) {
+    std::vector<int> s(parts + 1);
+    const int q = n / parts, r = n % parts;
+    for (int p = 0; p <= parts; ++p) s[p] = p * q + std::min(p, r);
+    return s;
+}
+
+// The opt-in limit is raised to the per-CTA maximum once: a later set-up with
+// a smaller need must not lower it under a handle that needs more.
+constexpr int SMEM_OPTIN = 227 * 1024;
+template <int PREC, int NBUF>
+static int set_apply_attr(size_t) {
+    RAS_CK(cudaFuncSetAttribute(k_ras_apply<PREC, NBUF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
+    return RAS_OK;
+}
+template <int PREC>
+static int set_factor_attr(size_t) {
+    RAS_CK(cudaFuncSetAttribute(k_ras_factor<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_OPTIN));
+    return RAS_OK;
+}
+
+int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec) {
+    if (px < 1 || py < 1 || pz < 1 || overlap < 0) return RAS_EINVAL;
+    if (px > nx || py > ny || pz > nz) return RAS_EINVAL;
+    if (prec != 64 && prec != 32 && prec != 16) return RAS_EINVAL;
+    R.nx = nx; R.ny = ny; R.nz = nz; R.N = nx * ny * nz;
+    R.prec = prec;
+    R.rec_bytes = prec == 64 ? 32 : (prec == 32 ? 16 : 8);
+    const int dims[3] = {nx, ny, nz};
+    const int parts[3] = {px, py, pz};
+    std::vector<int> cuts[3];
+    for (int a = 0; a < 3; ++a) cuts[a] = split_axis(dims[a], parts[a]);
+
+    std::map<std::tuple<int, int, int>, int> shape_id;
+    std::vector<int> lvl_tab, chunk_tab;
+    std::vector<unsigned> cell_tab;
+    R.subs.clear();
+    R.shapes.clear();
+    long long foff = 0;
+    int maxw_all = 0, ycap = 0, lcap = 0;
+    for (int kz = 0; kz < pz; ++kz)
+        for (int jy = 0; jy < py; ++jy)
+            for (int ix = 0; ix < px; ++ix) {
+                const int p[3] = {ix, jy, kz};
+                int o0[3], o1[3], e0[3], e1[3];
+                for (int a = 0; a < 3; ++a) {
+                    o0[a] = cuts[a][p[a]];
+                    o1[a] = cuts[a][p[a] + 1];
+                    e0[a] = dims[a] > 1 ? std::max(o0[a] - overlap, 0) : 0;
+                    e1[a] = dims[a] > 1 ? std::min(o1[a] + overlap, dims[a]) : 1;
+                }
+                const int bx = e1[0] - e0[0], by = e1[1] - e0[1], bz = e1[2] - e0[2];
+                if (bx > 256 || by > 256 || bz > 256) return RAS_EINVAL;
+                const int ncell = bx * by * bz;
+                if (ncell > 16384) return RAS_EINVAL;  // shared-memory pivots in the factor
+                auto key = std::make_tuple(bx, by, bz);
+                auto it = shape_id.find(key);
+                int sid;
+                if (it == shape_id.end()) {
+                    sid = (int)R.shapes.size();
+                    shape_id[key] = sid;
+                    ShapeInfo sh{};
+                    sh.bx = bx; sh.by = by; sh.bz = bz; sh.ncell = ncell;
+                    sh.nlev = bx + by + bz - 2;
+                    // level schedule: cells ordered by (i + j + k, natural index)
+                    std::vector<std::vector<unsigned>> levels(sh.nlev);
+                    for (int k = 0; k < bz; ++k)
+                        for (int j = 0; j < by; ++j)
+                            for (int i = 0; i < bx; ++i) {
+                                unsigned fl = 0;
+                                if (i > 0) fl |= F_MX;
+                                if (j > 0) fl |= F_MY;
+                                if (k > 0) fl |= F_MZ;
+                                if (i < bx - 1) fl |= F_PX;
+                                if (j < by - 1) fl |= F_PY;
+                                if (k < bz - 1) fl |= F_PZ;
+                                levels[i + j + k].push_back((unsigned)i | ((unsigned)j << 8) |
+                                                            ((unsigned)k << 16) | (fl << 24));
+                            }
+                    // natural order inside a level: sort by n = i + bx (j + by k)
+                    for (auto &L : levels)
+                        std::sort(L.begin(), L.end(), [&](unsigned a, unsigned b) {
+                            auto nat = [&](unsigned e) {
+                                return (int)(e & 255u) + bx * ((int)((e >> 8) & 255u) +
+                                                               by * (int)((e >> 16) & 255u));
+                            };
+                            return nat(a) < nat(b);
+                        });
+                    while (cell_tab.size() % 4) cell_tab.push_back(0);
+                    sh.cell_off = (int)cell_tab.size();
+                    sh.lvl_off = (int)lvl_tab.size();
+                    int pos = 0, maxw = 0;
+                    for (auto &L : levels) {
+                        lvl_tab.push_back(pos);
+                        for (unsigned e : L) cell_tab.push_back(e);
+                        pos += (int)L.size();
+                        maxw = std::max(maxw, (int)L.size());
+                    }
+                    lvl_tab.push_back(pos);
+                    sh.maxw = maxw;
+                    maxw_all = std::max(maxw_all, maxw);
+                    ycap = std::max(ycap, ncell);
+                    lcap = std::max(lcap, sh.nlev + 1);
+                    R.shapes.push_back(sh);
+                    sid = (int)R.shapes.size() - 1;
+                }
+                SubInfo si{};
+                si.e0x = e0[0]; si.e0y = e0[1]; si.e0z = e0[2];
+                si.shape = sid;
+                si.ox0 = o0[0] - e0[0]; si.oy0 = o0[1] - e0[1]; si.oz0 = o0[2] - e0[2];
+                si.ox1 = o1[0] - e0[0]; si.oy1 = o1[1] - e0[1]; si.oz1 = o1[2] - e0[2];
+                si.foff = foff;
+                foff += (ncell + 3) & ~3;
+                R.ncell_total += ncell;
+                R.nown += (long long)(o1[0] - o0[0]) * (o1[1] - o0[1]) * (o1[2] - o0[2]);
+                R.subs.push_back(si);
+            }
+    R.nsub = (int)R.subs.size();
+    R.nshape = (int)R.shapes.size();
+    R.nrec = foff;
+    // chunks of consecutive levels with at most chunk_cells cells
+    const int base_chunk = prec == 64 ? 384 : 1024;
+    R.chunk_cells = std::max(base_chunk, maxw_all);
+    R.nbuf = 3;
+    for (auto &sh : R.shapes) {
+        sh.chunk_off = (int)chunk_tab.size();
+        const int *lv = &lvl_tab[sh.lvl_off];
+        int l = 0;
+        chunk_tab.push_back(0);
+        int nch = 0;
+        while (l < sh.nlev) {
+            int l1 = l + 1;
+            while (l1 < sh.nlev && lv[l1 + 1] - lv[l] <= R.chunk_cells) ++l1;
+            chunk_tab.push_back(l1);
+            ++nch;
+            l = l1;
+        }
+        sh.nchunk = nch;
+    }
+    R.block = std::min(512, std::max(64, ((maxw_all + 31) / 32) * 32));
+    if (R.block > 256 && maxw_all < 384) R.block = 256;
+    R.ycap = (ycap + 3) & ~3;
+    R.lcap = (lcap + 3) & ~3;
+    const size_t acc = prec == 64 ? 8 : 4;
+    const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
+    const size_t ccap = ((R.chunk_cells * 4 + 32) + 15) & ~15;
+    R.smem_apply = R.ycap * acc + R.lcap * sizeof(int) + R.nbuf * (rcap + ccap);
+    R.smem_factor = (size_t)R.ycap * sizeof(double);
+    if (R.smem_apply > 227 * 1024 || R.smem_factor > 227 * 1024) return RAS_EINVAL;
+
+    RAS_TRY(dalloc(&R.d_subs, R.subs.size()));
+    RAS_TRY(dalloc(&R.d_shapes, R.shapes.size()));
+    RAS_TRY(dalloc(&R.d_lvl, lvl_tab.size()));
+    RAS_TRY(dalloc(&R.d_chunk, chunk_tab.size()));
+    RAS_TRY(dalloc(&R.d_cells, cell_tab.size() + 16));
+    RAS_TRY(dalloc(&R.d_err, 1));
+    unsigned char *fw = nullptr, *bw = nullptr;
+    RAS_TRY(dalloc(&fw, (size_t)R.nrec * R.rec_bytes + 64));
+    RAS_TRY(dalloc(&bw, (size_t)R.nrec * R.rec_bytes + 64));
+    R.d_fwd = fw; R.d_bwd = bw;
+    RAS_CK(cudaMemcpy(R.d_subs, R.subs.data(), R.subs.size() * sizeof(SubInfo), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(R.d_shapes, R.shapes.data(), R.shapes.size() * sizeof(ShapeInfo),
+                      cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(R.d_lvl, lvl_tab.data(), lvl_tab.size() * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(R.d_chunk, chunk_tab.data(), chunk_tab.size() * sizeof(int),
+                      cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemset(R.d_cells, 0, (cell_tab.size() + 16) * sizeof(unsigned)));
+    RAS_CK(cudaMemcpy(R.d_cells, cell_tab.data(), cell_tab.size() * sizeof(unsigned),
+                      cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemset(R.d_err, 0, sizeof(int)));
+    RAS_CK(cudaMemset(R.d_fwd, 0, (size_t)R.nrec * R.rec_bytes + 64));
+    RAS_CK(cudaMemset(R.d_bwd, 0, (size_t)R.nrec * R.rec_bytes + 64));
+    if (prec == 64) { RAS_TRY(set_apply_attr<64, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<64>(R.smem_factor)); }
+    if (prec == 32) { RAS_TRY(set_apply_attr<32, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<32>(R.smem_factor)); }
+    if (prec == 16) { RAS_TRY(set_apply_attr<16, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<16>(R.smem_factor)); }
+    return RAS_OK;
+}
+
+void ras1_free(Ras1 &R) {
+    dfree(R.d_subs); dfree(R.d_shapes); dfree(R.d_lvl); dfree(R.d_chunk); dfree(R.d_cells);
+    dfree(R.d_err);
+    if (R.d_fwd) cudaFree(R.d_fwd);
+    if (R.d_bwd) cudaFree(R.d_bwd);
+    R.d_fwd = R.d_bwd = nullptr;
+}
+
+int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st) {
+    FactorParams P;
+    P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.cells = R.d_cells;
+    P.A = A; P.fwd = R.d_fwd; P.bwd = R.d_bwd;
+    P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.err = R.d_err;
+    const int block = std::min(R.block, 256);
+    if (R.prec == 64) k_ras_factor<64><<<R.nsub, block, R.smem_factor, st>>>(P);
+    else if (R.prec == 32) k_ras_factor<32><<<R.nsub, block, R.smem_factor, st>>>(P);
+    else k_ras_factor<16><<<R.nsub, block, R.smem_factor, st>>>(P);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+int ras1_check(Ras1 &R, cudaStream_t st) {
+    int h = 0;
+    RAS_CK(cudaMemcpyAsync(&h, R.d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+    RAS_CK(cudaStreamSynchronize(st));
+    if (h) {
+        RAS_CK(cudaMemsetAsync(R.d_err, 0, sizeof(int), st));
+        return RAS_EZEROPIVOT;
+    }
+    return RAS_OK;
+}
+
+int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st) {
+    ApplyParams P;
+    P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.chunk = R.d_chunk;
+    P.cells = R.d_cells;
+    P.fwd = (const unsigned char *)R.d_fwd; P.bwd = (const unsigned char *)R.d_bwd;
+    P.r = r; P.z = z; P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.accumulate = accumulate;
+    P.ycap = R.ycap; P.lcap = R.lcap; P.nbuf = R.nbuf; P.chunk_cells = R.chunk_cells;
+    if (R.prec == 64) k_ras_apply<64, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
+    else if (R.prec == 32) k_ras_apply<32, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
+    else k_ras_apply<16, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+// algorithmic bytes of one apply: both factor record sets once, r over the
+// overlapped boxes (FP64), z over the owned cells (FP64)
+double ras1_bytes(const Ras1 &R) {
+    return 2.0 * (double)R.ncell_total * R.rec_bytes + 8.0 * (double)R.ncell_total + 8.0 * (double)R.nown;
+}
+
+}  // namespace ras

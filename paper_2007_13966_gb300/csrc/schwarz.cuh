@@ -1,0 +1,66 @@
+// One-level restricted additive Schwarz on the GPU: set-up tables, ILU(0)
+// factorisation and the level-scheduled subdomain solves (Section 3.1).
+#pragma once
+
+#include "common.cuh"
+
+namespace ras {
+
+// One distinct overlapped-box shape: its wavefront (level) schedule is shared
+// by every subdomain of that shape.
+struct ShapeInfo {
+    int bx, by, bz, ncell;
+    int nlev, nchunk;
+    int lvl_off;     // into lvl_tab: nlev + 1 level starts (cell positions)
+    int cell_off;    // into cell_tab: ncell packed entries (multiple of 4 aligned)
+    int chunk_off;   // into chunk_tab: nchunk + 1 level indices
+    int maxw;        // widest level
+};
+
+// One subdomain: overlapped box origin, its shape, owned box (relative to the
+// overlapped origin) and the offset of its factor records.
+struct SubInfo {
+    int e0x, e0y, e0z, shape;
+    int ox0, oy0, oz0, ox1, oy1, oz1;
+    long long foff;
+};
+
+// cell entry: i | j << 8 | k << 16 | flags << 24 (local coordinates)
+enum : unsigned {
+    F_MX = 1u, F_MY = 2u, F_MZ = 4u, F_PX = 8u, F_PY = 16u, F_PZ = 32u
+};
+
+struct Ras1 {
+    int nx, ny, nz, N;
+    int nsub = 0, nshape = 0;
+    int prec = 64;          // 64, 32, 16
+    int rec_bytes = 32;     // bytes of one factor record (4 values)
+    int block = 128;        // threads per subdomain CTA
+    int chunk_cells = 1024; // max cells per staged chunk
+    int nbuf = 3;           // staged chunks in flight
+    int ycap = 0, lcap = 0; // smem capacities (cells, levels + 1)
+    size_t smem_apply = 0, smem_factor = 0;
+    long long nrec = 0;     // factor records (incl. padding)
+    long long ncell_total = 0;  // sum of overlapped cells
+    long long nown = 0;
+    SubInfo *d_subs = nullptr;
+    ShapeInfo *d_shapes = nullptr;
+    int *d_lvl = nullptr, *d_chunk = nullptr;
+    unsigned *d_cells = nullptr;
+    void *d_fwd = nullptr, *d_bwd = nullptr;
+    int *d_err = nullptr;
+    std::vector<SubInfo> subs;
+    std::vector<ShapeInfo> shapes;
+};
+
+int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec);
+void ras1_free(Ras1 &R);
+// numeric ILU(0) of every A_i = R_i^delta A (R_i^delta)^T; no synchronisation
+int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st);
+// reads and clears the pivot flag (synchronises)
+int ras1_check(Ras1 &R, cudaStream_t st);
+// z = M^{-1} r (accumulate = 0) or z += M^{-1} r (accumulate = 1)
+int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st);
+double ras1_bytes(const Ras1 &R);
+
+}  // namespace ras
