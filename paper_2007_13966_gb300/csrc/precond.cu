@@ -29,7 +29,9 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
     pc->A = A;
     RAS_TRY(ras1_factor(pc->fine, A, st));
     if (pc->coarse) RAS_TRY(coarse_factor(pc->coarse, A, st));
-    return ras1_check(pc->fine, st);
+    RAS_TRY(ras1_check(pc->fine, st));
+    if (pc->coarse) RAS_TRY(coarse_check(pc->coarse, st));
+    return RAS_OK;
 }
 
 // z = M^{-1} r for the configured preconditioner

@@ -9,6 +9,10 @@ struct Coarse;
 int coarse_setup(Coarse **out, const ras_problem *P, const ras_opts &o);
 void coarse_free(Coarse *c);
 int coarse_factor(Coarse *c, const Stencil7 &A, cudaStream_t st);
+// reads and clears the coarse pivot / layout flag (synchronises)
+int coarse_check(Coarse *c, cudaStream_t st);
+// bytes of the dense block factors read by one coarse solve
+double coarse_bytes(const Coarse *c);
 // ec = A_c^{-1} R t, then z (+)= P ec  (accumulate selects += )
 int coarse_correct(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st);
 }  // namespace ras

@@ -342,8 +342,8 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
                 if (ncell > 16384) return RAS_EINVAL;  // shared-memory pivots in the factor
                 auto key = std::make_tuple(bx, by, bz);
                 auto it = shape_id.find(key);
-                int sid;
-                if (it == shape_id.end()) {
+                int sid = it == shape_id.end() ? -1 : it->second;
+                if (sid < 0) {
                     sid = (int)R.shapes.size();
                     shape_id[key] = sid;
                     ShapeInfo sh{};
@@ -404,6 +404,17 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
             }
     R.nsub = (int)R.subs.size();
     R.nshape = (int)R.shapes.size();
+    // every overlapped box must lie inside the grid and match its shape
+    for (const SubInfo &si : R.subs) {
+        if (si.shape < 0 || si.shape >= R.nshape) return RAS_EINVAL;
+        const ShapeInfo &sh = R.shapes[si.shape];
+        if (si.e0x < 0 || si.e0y < 0 || si.e0z < 0 || si.e0x + sh.bx > nx ||
+            si.e0y + sh.by > ny || si.e0z + sh.bz > nz)
+            return RAS_EINVAL;
+        if (si.ox0 < 0 || si.oy0 < 0 || si.oz0 < 0 || si.ox1 > sh.bx || si.oy1 > sh.by ||
+            si.oz1 > sh.bz)
+            return RAS_EINVAL;
+    }
     R.nrec = foff;
     // chunks of consecutive levels with at most chunk_cells cells
     const int base_chunk = prec == 64 ? 384 : 1024;
