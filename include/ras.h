@@ -89,7 +89,7 @@ typedef struct {
     int mlevel_type;       /* 0 = V-cycle, 1 = left-Kaskade, 2 = right-Kaskade,
                               3 = additive, 4 = coarse-only (Eqs. equ:v-cycle ..
                               equ:coarse-level)                                      */
-    int coarse_prec;       /* 64 or 32: precision of the dense banded coarse LU       */
+    int coarse_prec;       /* 64 or 32: precision of the dense block coarse LU        */
 } ras_opts;
 
 typedef struct {
@@ -163,14 +163,16 @@ int ras_stencil_matvec(const ras_problem *prob, const ras_stencil *J, const doub
  * (Section 3.1, Fig. 1), per-subdomain boxes, the wavefront (level) schedule of
  * the natural-order ILU(0) triangular solves, factor storage, and for
  * nlevels = 2 the interpolation (Eq. equ:inter-second), the coarse grid and the
- * banded coarse-LU layout. Returns RAS_EINVAL for unsupported options. */
+ * dense block-LU layout. Returns RAS_EINVAL for unsupported options. */
 int ras_setup(const ras_problem *prob, const ras_opts *opts, ras_precond **out);
 void ras_precond_destroy(ras_precond *pc);
 
 /* Numeric factorisation, once per Newton iteration: A_i = R_i^delta J
  * (R_i^delta)^T (Eq. equ:as-class), ILU(0) without pivoting in natural order
  * inside each overlapped subdomain, stored at factor_prec; for nlevels = 2 also
- * the Galerkin coarse operator R J P (R = P^T) and its banded LU.
+ * the Galerkin coarse operator R J P (R = P^T) and its dense block LU; the
+ * two-level preconditioner also keeps a private copy of J for the fine-level
+ * residuals of the multilevel combination, so J may be freed after the call.
  * Synchronises the stream to check pivots: RAS_EZEROPIVOT on a zero or
  * non-finite pivot. */
 int ras_factor(ras_precond *pc, const ras_stencil *J, void *stream);

@@ -26,7 +26,15 @@ static int fine_apply(ras_precond *pc, const double *r, double *z, int accumulat
 int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
     Stencil7 A;
     for (int s = 0; s < 7; ++s) A.c[s] = J->c[s];
-    pc->A = A;
+    if (pc->coarse) {
+        // the multilevel combinations apply J again inside ras_apply: keep a copy
+        const int N = pc->prob->N;
+        for (int s = 0; s < 7; ++s) {
+            RAS_CK(cudaMemcpyAsync(pc->Acopy[s], J->c[s], (size_t)N * sizeof(double),
+                                   cudaMemcpyDeviceToDevice, st));
+            pc->A.c[s] = pc->Acopy[s];
+        }
+    }
     RAS_TRY(ras1_factor(pc->fine, A, st));
     if (pc->coarse) RAS_TRY(coarse_factor(pc->coarse, A, st));
     RAS_TRY(ras1_check(pc->fine, st));
@@ -90,6 +98,7 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
         if (!rc) rc = dalloc(&pc->t1, P->N);
         if (!rc) rc = dalloc(&pc->t2, P->N);
         if (!rc) rc = dalloc(&pc->t3, P->N);
+        for (int s = 0; s < 7 && !rc; ++s) rc = dalloc(&pc->Acopy[s], P->N);
         if (rc) { ras_precond_destroy(pc); return rc; }
     }
     *out = pc;
@@ -101,6 +110,7 @@ extern "C" void ras_precond_destroy(ras_precond *pc) {
     ras1_free(pc->fine);
     if (pc->coarse) coarse_free(pc->coarse);
     dfree(pc->t1); dfree(pc->t2); dfree(pc->t3);
+    for (int s = 0; s < 7; ++s) dfree(pc->Acopy[s]);
     for (auto e : pc->ev) cudaEventDestroy(e);
     delete pc;
 }

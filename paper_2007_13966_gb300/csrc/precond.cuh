@@ -22,7 +22,8 @@ struct ras_precond {
     ras_opts opts{};
     ras::Ras1 fine;
     ras::Coarse *coarse = nullptr;
-    ras::Stencil7 A{};          // operator of the last ras_factor (for the V-cycle residuals)
+    ras::Stencil7 A{};          // copy of the operator of the last ras_factor (fine residuals)
+    double *Acopy[7] = {};      // owned storage of that copy (two-level only)
     double *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;  // multilevel scratch [N]
     bool timing = false;
     std::vector<cudaEvent_t> ev;
