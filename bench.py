@@ -1,0 +1,450 @@
+#!/usr/bin/env python
+"""Benchmark: seconds per implicit step of the multilevel-RAS Newton-Krylov
+Peng-Robinson solver on GB300, with the RAS subdomain-solve kernel's HBM
+roofline.
+
+Workload (default): 3D 128 x 128 x 64 cell-centred grid (1,048,576 cells), seeded
+log-normal permeability (sigma 1.5, correlated over 8 cells), methane PR-EOS,
+corner-column injector/producer, dt = 0.1 day, BDF1 then BDF2; inexact Newton
+to 1e-6 relative with FGMRES(30) (rtol 1e-6), two-level V-cycle RAS: 8 x 8 x 4
+subdomains with overlap 2, ILU(0) factors in FP32, coarse grid coarsened 4x per
+axis (32 x 32 x 16) solved by an FP32 dense block LU; Newton, residual,
+Jacobian, SpMV and Krylov in FP64.
+
+One step = one full implicit time step (all Newton iterations, every FGMRES
+iteration, every preconditioner factorisation and application) on state that
+is resident in HBM. `e2e` repeats the steps through the same public API with
+the step's inputs copied from pinned host memory and the new state copied
+back, inside the timed region.
+
+Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
+path has no data exchange between them.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import threading
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "sec per implicit step and ras_apply HBM GB/s, FP32-RAS vs FP64, at 1e-6 rel residual"
+WORKLOAD = ("3d 128x128x64 lognormal (1.05M cells), two-level V-cycle RAS 8x8x4 overlap 2, "
+            "ILU(0) FP32 factors, coarse 4x (32x32x16) FP32 dense block LU, FP64 FGMRES(30) "
+            "rtol 1e-6, Newton rtol 1e-6, dt 0.1 day")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--factor-prec", type=int, default=32)
+    ap.add_argument("--coarse-prec", type=int, default=32)
+    ap.add_argument("--no-fp64-form", action="store_true",
+                    help="skip the all-FP64 comparison run")
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--small", action="store_true", help="32x32x16 case (profiling / smoke)")
+    ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    return ap.parse_args()
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+
+def make_reservoir(small=False):
+    from paper_2007_13966_gb300 import synthetic as syn
+    if small:
+        return syn.lognormal_reservoir(32, 32, 16, 25.0, 25.0, 12.5, sigma=1.5, corr=8.0,
+                                       seed_k=3, seed_phi=4, name="3d 32x32x16 lognormal")
+    return syn.config_3d_1m()
+
+
+def precond_opts(small=False):
+    parts = (2, 2, 1) if small else (8, 8, 4)
+    return dict(parts=parts, overlap=2, nlevels=2, coarsen=(4, 4, 4), mlevel_type=0)
+
+
+NEWTON = dict(rtol=1e-6, atol=1e-10, maxit=50, lin_rtol=1e-6, lin_atol=1e-8, restart=30,
+              lin_maxit=3000)
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+
+class ClockSampler:
+    FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.gpu = gpu_index
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        self.thread.join(timeout=2)
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 8:
+                continue
+            try:
+                sm.append(float(parts[0]))
+                mx.append(float(parts[1]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, parts[4:8]):
+                if v.lower() == "active":
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"], "samples": 0}
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2], "sm_max_mhz": max(mx), "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# GB300 arm
+# ---------------------------------------------------------------------------
+
+def run_steps(gp, pc, res, state, nsteps, torch, stream_sync=True, e2e_host=None):
+    """Advance `nsteps` implicit steps. state = dict(p_l, p_lm1, step)."""
+    outs = []
+    for _ in range(nsteps):
+        order = 1 if state["step"] == 0 else 2
+        if e2e_host is not None:
+            # inputs from pinned host memory, result back to host
+            state["p_l"].copy_(e2e_host["p_l"], non_blocking=True)
+            state["p_lm1"].copy_(e2e_host["p_lm1"], non_blocking=True)
+        p = state["p_l"].clone()
+        out = gp.newton_step(pc, p, state["p_l"], state["p_lm1"], res.dt, order, **NEWTON)
+        if out["status"] != 0:
+            raise RuntimeError(f"newton_step status {out['status']}")
+        if e2e_host is not None:
+            e2e_host["p_lm1"].copy_(e2e_host["p_l"])
+            e2e_host["p_l"].copy_(p, non_blocking=False)
+        state["p_lm1"], state["p_l"] = state["p_l"], p
+        state["step"] += 1
+        outs.append(out)
+    return outs
+
+
+def timed(fn, torch, dist_on):
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record()
+    r = fn()
+    e1.record()
+    torch.cuda.synchronize()
+    if dist_on:
+        import torch.distributed as dist
+        dist.barrier()
+    return e0.elapsed_time(e1) / 1e3, r
+
+
+def max_over_ranks(v, dist_on):
+    if not dist_on:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def load_peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    except Exception:
+        return 6800.0, "fallback"
+
+
+def load_traffic(key):
+    """Per-launch DRAM bytes of the kernel from the committed ncu summary, if it
+    was taken on the current kernel (the summary records the source hash)."""
+    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+    try:
+        with open(path) as f:
+            d = json.load(f)
+        ent = d.get(key)
+        if not ent:
+            return None
+        from paper_2007_13966_gb300 import build_lib
+        if ent.get("source_hash") != build_lib.source_hash():
+            return None
+        return float(ent["bytes_per_launch"])
+    except Exception:
+        return None
+
+
+def gb300_arm(args):
+    import numpy as np
+    import torch
+
+    ws, rank, local = dist_env()
+    dist_on = ws > 1
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2007_13966_gb300 import ras
+
+    res = make_reservoir(args.small)
+    N = res.grid.n
+    gp = ras.Problem(res)
+    po = precond_opts(args.small)
+    pc = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=args.factor_prec,
+                     nlevels=po["nlevels"], coarsen=po["coarsen"], mlevel_type=po["mlevel_type"],
+                     coarse_prec=args.coarse_prec)
+    p0 = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
+    state = {"p_l": p0.clone(), "p_lm1": p0.clone(), "step": 0}
+
+    # warm-up (also the first, BDF1, step)
+    run_steps(gp, pc, res, state, args.warmup, torch)
+    torch.cuda.synchronize()
+
+    # timed region: K implicit steps on resident state
+    sampler = ClockSampler(local)
+    sampler.start()
+    pc.timing(True)
+    pc.timing_read(reset=True)
+    n0 = ras.kernel_launches()
+    t, outs = timed(lambda: run_steps(gp, pc, res, state, args.steps, torch), torch, dist_on)
+    launches = ras.kernel_launches() - n0
+    apply_ms, apply_n = pc.timing_read(reset=True)
+    pc.timing(False)
+    clocks = sampler.stop()
+    t = max_over_ranks(t, dist_on)
+    sec_per_step = t / args.steps
+
+    # e2e: same steps through the public API with host-resident inputs
+    pin = {"p_l": state["p_l"].cpu().pin_memory(), "p_lm1": state["p_lm1"].cpu().pin_memory()}
+    te, _ = timed(lambda: run_steps(gp, pc, res, state, args.steps, torch, e2e_host=pin), torch,
+                  dist_on)
+    te = max_over_ranks(te, dist_on)
+
+    # the all-FP64 form on the same step sequence, for the FP32-vs-FP64 comparison
+    fp64 = None
+    if not args.no_fp64_form and (args.factor_prec != 64 or args.coarse_prec != 64):
+        pc64 = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=64, nlevels=po["nlevels"],
+                           coarsen=po["coarsen"], mlevel_type=po["mlevel_type"], coarse_prec=64)
+        st64 = {"p_l": state["p_l"].clone(), "p_lm1": state["p_lm1"].clone(), "step": state["step"]}
+        run_steps(gp, pc64, res, st64, 1, torch)
+        k64 = max(1, min(args.steps, 2))
+        t64, outs64 = timed(lambda: run_steps(gp, pc64, res, st64, k64, torch), torch, dist_on)
+        t64 = max_over_ranks(t64, dist_on)
+        fp64 = {"sec_per_step": t64 / k64, "steps": k64,
+                "newton_iters": [o["newton_iters"] for o in outs64],
+                "fgmres_iters": [o["lin_total"] for o in outs64],
+                "fp32_speedup": (t64 / k64) / sec_per_step}
+        del pc64
+
+    if rank != 0:
+        if dist_on:
+            import torch.distributed as dist
+            dist.destroy_process_group()
+        return
+
+    peak, peak_kind = load_peaks()
+    bytes_per_launch = pc.apply_bytes()
+    avg_s = (apply_ms / 1e3) / max(apply_n, 1)
+    achieved = bytes_per_launch / avg_s / 1e9 if apply_n else None
+    traffic = load_traffic("k_ras_apply_fp32_1m" if args.factor_prec == 32 else
+                           f"k_ras_apply_fp{args.factor_prec}_1m")
+    line = {
+        "metric": METRIC,
+        "value": sec_per_step,
+        "unit": "s/step",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": sec_per_step * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64+f32",
+        "data": "synthetic",
+        "config": {
+            "workload": WORKLOAD if not args.small else "3d 32x32x16 lognormal (profiling case)",
+            "cells": N, "subdomains": list(po["parts"]), "overlap": po["overlap"],
+            "coarse": [c for c in (32, 32, 16)] if not args.small else [8, 8, 4],
+            "factor_prec": args.factor_prec, "coarse_prec": args.coarse_prec,
+            "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
+            "l2": "working set ~1 GB > 129 MB L2 (no flush needed)",
+        },
+        "newton_iters": [o["newton_iters"] for o in outs],
+        "fgmres_iters": [o["lin_total"] for o in outs],
+        "clocks": clocks,
+        "e2e": {"value": te / args.steps, "unit": "s/step",
+                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
+        "gpu_launches": int(launches),
+        "roofline": {
+            "kernel": "k_ras_apply (fine-level subdomain ILU(0) solves, FP32 factors)",
+            "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+            "frac": (achieved / peak) if achieved else None,
+            "traffic": traffic,
+            "peak_kind": peak_kind,
+            "bytes_per_launch": bytes_per_launch,
+            "avg_launch_us": avg_s * 1e6, "launches": int(apply_n),
+        },
+        "fp64_form": fp64,
+    }
+    if ws == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline_subprocess(args)
+    print(json.dumps(line), flush=True)
+    if dist_on:
+        import torch.distributed as dist
+        dist.destroy_process_group()
+
+
+# ---------------------------------------------------------------------------
+# oracle on the host cores (CPU baseline leg and the reference arm)
+# ---------------------------------------------------------------------------
+
+SAMPLE = ("one implicit step (BDF1, Newton to 1e-6 with FGMRES(30) and the two-level V-cycle "
+          "left-RAS / ILU(0) / dense coarse LU of the oracle) on a 32x32x16 sub-grid of the same "
+          "recipe (2x2x1 subdomains of 16^3, overlap 2, coarse 8x8x4), scaled by the cell ratio "
+          "1048576/16384 = 64")
+
+
+def oracle_step_seconds():
+    """Times the oracle (as it stands) on the bounded sample; returns scaled s/step."""
+    import numpy as np
+    from oracle import discretization as disc
+    from oracle import multilevel as ml
+    from oracle import newton, schwarz
+    from paper_2007_13966_gb300 import synthetic as syn
+
+    res = syn.lognormal_reservoir(32, 32, 16, 25.0, 25.0, 12.5, sigma=1.5, corr=8.0,
+                                  seed_k=3, seed_phi=4)
+    g = res.grid
+    dims = (g.nx, g.ny, g.nz)
+    prob = disc.Problem(res)
+    P = ml.interpolation(dims, (4, 4, 4), 2)
+
+    def fac(A, J):
+        M = schwarz.Schwarz(A, dims, (2, 2, 1), 2)
+        return ml.TwoLevel(A, M, P, ml.DenseCoarse(ml.galerkin(A, P)), ml.VCYCLE)
+
+    p0 = np.full(g.n, res.p0)
+    t0 = time.perf_counter()
+    newton.newton_solve(prob, fac, p0, p0, res.dt, 1, rtol=1e-6, atol=1e-10, lin_rtol=1e-6,
+                        lin_atol=1e-8, restart=30)
+    dt = time.perf_counter() - t0
+    return dt * (1048576 / g.n), dt
+
+
+def cpu_baseline_subprocess(args):
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    try:
+        r = subprocess.run([sys.executable, os.path.abspath(__file__), "--cpu-sample"],
+                           capture_output=True, text=True, env=env, timeout=600)
+        d = json.loads(r.stdout.strip().splitlines()[-1])
+    except Exception as e:  # the baseline is reported, never required
+        return {"value": None, "unit": "s/step", "cores": 1, "kind": "oracle",
+                "sample": SAMPLE, "error": str(e)[:200]}
+    return {"value": d["value"], "unit": "s/step", "cores": 1, "kind": "oracle",
+            "sample": SAMPLE, "sample_seconds": d["raw"]}
+
+
+def cpu_sample_main():
+    v, raw = oracle_step_seconds()
+    print(json.dumps({"value": v, "raw": raw}))
+
+
+def reference_arm(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return
+    vals = []
+    for _ in range(args.warmup):
+        oracle_step_seconds()
+    for _ in range(args.steps):
+        v, _raw = oracle_step_seconds()
+        vals.append(v)
+    value = sum(vals) / len(vals)
+    line = {
+        "impl": "reference",
+        "metric": METRIC,
+        "value": value,
+        "unit": "s/step",
+        "n_gpus": ws,
+        "steps": args.steps,
+        "warmup": args.warmup,
+        "ms_per_step": value * 1e3,
+        "higher_is_better": False,
+        "scaling": "weak",
+        "vs_baseline": None,
+        "dtype": "f64",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD, "cells": 1048576},
+        "cpu_baseline": {"value": value, "unit": "s/step", "cores": 1, "kind": "oracle",
+                         "sample": SAMPLE},
+        "e2e": {"value": value, "unit": "s/step", "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    args = parse()
+    if args.cpu_sample:
+        cpu_sample_main()
+        return
+    if args.impl == "reference":
+        for var in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS"):
+            os.environ.setdefault(var, "1")
+        reference_arm(args)
+        return
+    gb300_arm(args)
+
+
+if __name__ == "__main__":
+    main()

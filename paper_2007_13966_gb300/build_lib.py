@@ -20,6 +20,19 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["problem.cu", "schwarz.cu", "precond.cu", "krylov.cu", "coarse.cu"]
 
 
+def source_hash() -> str:
+    """Hash of the CUDA sources and the ABI header (identifies a kernel build)."""
+    import hashlib
+    h = hashlib.sha256()
+    for fn in sorted(os.listdir(CSRC)) + ["../../include/ras.h"]:
+        path = os.path.normpath(os.path.join(CSRC, fn))
+        if path.endswith((".cu", ".cuh", ".h")) and os.path.isfile(path):
+            h.update(os.path.basename(path).encode())
+            with open(path, "rb") as f:
+                h.update(f.read())
+    return h.hexdigest()[:16]
+
+
 def nvcc() -> str:
     for cand in (os.environ.get("NVCC"), shutil.which("nvcc"), "/usr/local/cuda/bin/nvcc"):
         if cand and os.path.exists(cand):
