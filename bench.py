@@ -53,6 +53,10 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="32x32x16 case (profiling / smoke)")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
+    ap.add_argument("--kernel", choices=["ras_apply", "vcycle"], default=None,
+                    help="kernel-only mode: factor once, then time REPS applications "
+                         "(used for the ncu captures)")
+    ap.add_argument("--reps", type=int, default=20)
     return ap.parse_args()
 
 
@@ -433,8 +437,42 @@ def reference_arm(args):
     print(json.dumps(line), flush=True)
 
 
+def kernel_mode(args):
+    """Set up the workload, factor once, time `reps` preconditioner applications."""
+    import torch
+    from paper_2007_13966_gb300 import ras
+    res = make_reservoir(args.small)
+    N = res.grid.n
+    gp = ras.Problem(res)
+    po = precond_opts(args.small)
+    nl = 1 if args.kernel == "ras_apply" else 2
+    pc = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=args.factor_prec, nlevels=nl,
+                     coarsen=po["coarsen"], mlevel_type=0, coarse_prec=args.coarse_prec)
+    from paper_2007_13966_gb300 import synthetic as syn
+    p = torch.tensor(syn.random_pressure(res, 3, 1.0, 3.0), device="cuda")
+    p0 = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
+    F = torch.zeros(N, dtype=torch.float64, device="cuda")
+    gp.residual_eval(p, p0, p0, res.dt, 1, F, gp.J)
+    pc.factor(gp.J)
+    r = torch.randn(N, dtype=torch.float64, device="cuda")
+    z = torch.zeros_like(r)
+    for _ in range(3):
+        pc.apply(r, z)
+    pc.timing(True)
+    pc.timing_read(reset=True)
+    t, _ = timed(lambda: [pc.apply(r, z) for _ in range(args.reps)], torch, False)
+    ms, n = pc.timing_read(reset=True)
+    B = pc.apply_bytes()
+    print(json.dumps({"kernel": args.kernel, "reps": args.reps, "apply_us": t / args.reps * 1e6,
+                      "subdomain_kernel_us": ms / max(n, 1) * 1e3, "bytes": B,
+                      "GBps": B / (ms / max(n, 1) / 1e3) / 1e9 if n else None}))
+
+
 def main():
     args = parse()
+    if args.kernel:
+        kernel_mode(args)
+        return
     if args.cpu_sample:
         cpu_sample_main()
         return

@@ -213,7 +213,9 @@ def test_newton_step_history_matches_oracle(ras):
     assert out["lin_iters"] == info["lin_iters"]
     assert np.allclose(out["lambdas"], info["lambdas"], rtol=1e-9)
     fh = np.array(out["fnorm_history"])
-    assert np.max(np.abs(fh - info["fnorm_history"]) / np.array(info["fnorm_history"])) < 1e-9
+    ref = np.array(info["fnorm_history"])
+    # 1e-9 relative, with the FP64 noise floor of ||F|| (~1e-13 ||F0||) allowed
+    assert np.all(np.abs(fh - ref) <= 1e-9 * ref + 1e-12 * ref[0])
     assert rel_err(host(p), x_ref) < 1e-10
 
 

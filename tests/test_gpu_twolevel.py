@@ -123,7 +123,8 @@ def test_two_level_newton_step_matches_oracle(ras):
     assert out["lin_iters"] == info["lin_iters"]
     fh = np.array(out["fnorm_history"])
     ref = np.array(info["fnorm_history"])
-    assert np.max(np.abs(fh - ref) / ref) < 1e-9
+    # 1e-9 relative, with the FP64 noise floor of ||F|| (~1e-13 ||F0||) allowed
+    assert np.all(np.abs(fh - ref) <= 1e-9 * ref + 1e-12 * ref[0])
     assert rel_err(host(p), x_ref) < 1e-10
 
 
