@@ -13,6 +13,10 @@
 // Solve: g_k -= C_{k-1} g_{k-1} (forward), x_k = E_k g_k - F_k x_{k+1}.
 // Each E_k is computed in place by a blocked Gauss-Jordan inversion without
 // pivoting (64 x 64 tiles); Lo_k / Up_k are sparse and stored in ELL form.
+//
+// The factorisation and the solve each run as ONE cooperative persistent
+// kernel whose phases are separated by a grid barrier; the barrier gives up
+// after a bounded number of polls and reports RAS_ETIMEOUT instead of hanging.
 #include "precond.cuh"
 
 #include <algorithm>
@@ -21,12 +25,21 @@
 namespace ras {
 
 constexpr int TILE = 64;
-constexpr int ELLW = 64;   // max couplings of one cell into the neighbouring block (<= 50)
+constexpr int ELLW = 64;    // max couplings of one cell into the neighbouring block (<= 50)
+constexpr int FROWS = 8;    // rows of a dense block staged per CTA in the sparse products
+constexpr int ERR_PIVOT = 1, ERR_ELL = 2, ERR_TIMEOUT = 7;
+constexpr long long BAR_POLLS = 1LL << 22;   // ~1-2 s of polling before a barrier gives up
+
+struct GridBar {
+    unsigned count;
+    unsigned gen;
+};
 
 struct Coarse {
     int prec = 64;
     int nx, ny, nz, N;
     int n[3], r[3], c[3], Nc;
+    int wmax[3];                    // widest fine support of a coarse cell per axis
     int *d_ia[3] = {}, *d_ib[3] = {};
     double *d_wa[3] = {}, *d_wb[3] = {};
     int *d_lo[3] = {}, *d_hi[3] = {};
@@ -40,7 +53,10 @@ struct Coarse {
     void *lo_v = nullptr, *up_v = nullptr;           // ELL values
     void *g = nullptr, *x = nullptr;                 // [nb*T]
     int *d_err = nullptr;
+    GridBar *d_bar = nullptr;
     size_t esz = 8;
+    size_t rap_smem = 0, fac_smem = 0, sol_smem = 0;
+    int fac_grid = 0, sol_grid = 0;
 };
 
 // ---------------------------------------------------------------------------
@@ -53,11 +69,12 @@ struct Interp {
     const int *lo[3], *hi[3];
 };
 
+// P(a, I) along one axis (ia == ib only where the second weight is zero, so
+// a selection suffices: no floating-point arithmetic)
 __device__ __forceinline__ double w1(const Interp &P, int ax, int a, int I) {
-    double w = 0.0;
-    if (P.ia[ax][a] == I) w += P.wa[ax][a];
-    if (P.ib[ax][a] == I) w += P.wb[ax][a];
-    return w;
+    if (P.ia[ax][a] == I) return P.wa[ax][a];
+    if (P.ib[ax][a] == I) return P.wb[ax][a];
+    return 0.0;
 }
 
 struct CGeom {
@@ -67,49 +84,98 @@ struct CGeom {
 };
 
 // ---------------------------------------------------------------------------
-// Galerkin product A_c[I][I + d] = sum_s sum_a P(a,I) A_s(a) P(a + e_s, I + d)
+// Galerkin product, sum-factorised per coarse row I:
+//   A_c[I][I+d] = sum_s sum_a P(a,I) A_s(a) P(a + e_s, I + d),
+// P = Px Py Pz, contracted z, then y, then x inside shared memory.
 // ---------------------------------------------------------------------------
 
+struct RapDims {
+    int wx, wy, wz;   // maximum support widths (shared-memory capacity)
+};
+
 template <typename AT>
-__global__ void __launch_bounds__(128) k_rap(Stencil7 A, Interp P, CGeom G, AT *__restrict__ Ac) {
+__global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapDims W,
+                                             AT *__restrict__ Ac) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AT *sm = reinterpret_cast<AT *>(smem_raw);
+    const int WX = W.wx, WY = W.wy, WZ = W.wz;
+    const int WM = max(WX, max(WY, WZ));
+    AT *Abox = sm;                              // [7][WZ][WY][WX]
+    AT *Wt = Abox + 7 * WX * WY * WZ;           // [3][5][3][WM]
+    AT *U = Wt + 45 * WM;                       // [5][WY][WX]
+    AT *V = U + 5 * WY * WX;                    // [25][WX]
+    AT *out = V + 25 * WX;                      // [125]
+
     const int I = blockIdx.x;
-    const int t = threadIdx.x;
-    if (t >= 125) return;
-    const int dx = t % 5 - 2, dy = (t / 5) % 5 - 2, dz = t / 25 - 2;
-    const int Ix = I % G.cx, Iy = (I / G.cx) % G.cy, Iz = I / (G.cx * G.cy);
-    const int Jx = Ix + dx, Jy = Iy + dy, Jz = Iz + dz;
-    AT acc = 0;
-    if (Jx >= 0 && Jx < G.cx && Jy >= 0 && Jy < G.cy && Jz >= 0 && Jz < G.cz) {
-        const int nx = G.nx, nxy = G.nx * G.ny;
-#pragma unroll 1
-        for (int s = 0; s < 7; ++s) {
-            // stencil term s: 0 centre, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z
-            const int sgn = (s & 1) ? -1 : 1;
-            const int sx = (s == 1 || s == 2) ? sgn : 0;
-            const int sy = (s == 3 || s == 4) ? sgn : 0;
-            const int sz = (s == 5 || s == 6) ? sgn : 0;
-            const int x0 = max(P.lo[0][Ix], P.lo[0][Jx] - sx), x1 = min(P.hi[0][Ix], P.hi[0][Jx] - sx);
-            const int y0 = max(P.lo[1][Iy], P.lo[1][Jy] - sy), y1 = min(P.hi[1][Iy], P.hi[1][Jy] - sy);
-            const int z0 = max(P.lo[2][Iz], P.lo[2][Jz] - sz), z1 = min(P.hi[2][Iz], P.hi[2][Jz] - sz);
-            if (x0 >= x1 || y0 >= y1 || z0 >= z1) continue;
-            const double *As = A.c[s];
-            for (int az = z0; az < z1; ++az) {
-                const AT wz = (AT)(w1(P, 2, az, Iz) * w1(P, 2, az + sz, Jz));
-                for (int ay = y0; ay < y1; ++ay) {
-                    const AT wyz = wz * (AT)(w1(P, 1, ay, Iy) * w1(P, 1, ay + sy, Jy));
-                    const long long rowb = (long long)nx * ay + (long long)nxy * az;
-                    for (int ax = x0; ax < x1; ++ax) {
-                        const AT wx = (AT)(w1(P, 0, ax, Ix) * w1(P, 0, ax + sx, Jx));
-                        acc += wyz * wx * (AT)As[rowb + ax];
-                    }
-                }
-            }
-        }
+    const int Ic[3] = {I % G.cx, (I / G.cx) % G.cy, I / (G.cx * G.cy)};
+    const int cdim[3] = {G.cx, G.cy, G.cz};
+    const int ndim[3] = {G.nx, G.ny, G.nz};
+    const int lo[3] = {P.lo[0][Ic[0]], P.lo[1][Ic[1]], P.lo[2][Ic[2]]};
+    const int wx = P.hi[0][Ic[0]] - lo[0], wy = P.hi[1][Ic[1]] - lo[1], wz = P.hi[2][Ic[2]] - lo[2];
+    const int box = wx * wy * wz;
+    const long long nxy = (long long)G.nx * G.ny;
+
+    for (int e = threadIdx.x; e < 7 * box; e += blockDim.x) {
+        const int s = e / box, q = e % box;
+        const int ax = q % wx, ay = (q / wx) % wy, az = q / (wx * wy);
+        const long long g = (lo[0] + ax) + (long long)G.nx * (lo[1] + ay) + nxy * (lo[2] + az);
+        Abox[((s * WZ + az) * WY + ay) * WX + ax] = (AT)A.c[s][g];
     }
-    Ac[(long long)t * G.Nc + I] = acc;
+    // pair weights W[axis][d][s][a] = P(a, I) P(a + s, I + d)
+    for (int e = threadIdx.x; e < 45 * WM; e += blockDim.x) {
+        const int q = e % WM, si = (e / WM) % 3, d = (e / (3 * WM)) % 5, axis = e / (15 * WM);
+        const int wa = axis == 0 ? wx : (axis == 1 ? wy : wz);
+        double w = 0.0;
+        if (q < wa) {
+            const int a = lo[axis] + q, as = a + si - 1, J = Ic[axis] + d - 2;
+            if (J >= 0 && J < cdim[axis] && as >= 0 && as < ndim[axis])
+                w = w1(P, axis, a, Ic[axis]) * w1(P, axis, as, J);
+        }
+        Wt[e] = (AT)w;
+    }
+    if (threadIdx.x < 125) out[threadIdx.x] = 0;
+    __syncthreads();
+
+    for (int s = 0; s < 7; ++s) {
+        // stencil term s: 0 centre, 1 -x, 2 +x, 3 -y, 4 +y, 5 -z, 6 +z
+        const int sgn = (s & 1) ? -1 : 1;
+        const int sx = (s == 1 || s == 2) ? sgn : 0;
+        const int sy = (s == 3 || s == 4) ? sgn : 0;
+        const int sz = (s == 5 || s == 6) ? sgn : 0;
+        const AT *As = Abox + s * WZ * WY * WX;
+        const AT *Wz = Wt + (2 * 15) * WM + (sz + 1) * WM;   // + dz * 3 * WM
+        const AT *Wy = Wt + (1 * 15) * WM + (sy + 1) * WM;
+        const AT *Wx = Wt + (0 * 15) * WM + (sx + 1) * WM;
+        for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
+            const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
+            const AT *wz_ = Wz + dz * 3 * WM;
+            AT acc = 0;
+            for (int az = 0; az < wz; ++az) acc += wz_[az] * As[(az * WY + ay) * WX + ax];
+            U[(dz * WY + ay) * WX + ax] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
+            const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
+            const AT *wy_ = Wy + dy * 3 * WM;
+            AT acc = 0;
+            for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * U[(dz * WY + ay) * WX + ax];
+            V[(dz * 5 + dy) * WX + ax] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < 125) {
+            const int e = threadIdx.x;
+            const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
+            const AT *wx_ = Wx + dx * 3 * WM;
+            AT acc = 0;
+            for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
+            out[e] += acc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
 }
 
-// natural coarse index -> coordinates, offset helpers
+// natural coarse index -> neighbour at offset o (or -1)
 __device__ __forceinline__ int nbr_index(const CGeom &G, int I, int o) {
     const int dx = o % 5 - 2, dy = (o / 5) % 5 - 2, dz = o / 25 - 2;
     const int x = I % G.cx + dx, y = (I / G.cx) % G.cy + dy, z = I / (G.cx * G.cy) + dz;
@@ -159,71 +225,85 @@ __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
                 if (J < 0) continue;
                 const int pj = pos[J];
                 if (pj / G.T != k) continue;
-                // Lo_k[I][J] = A_c[I][J] (offset o of row I)
-                if (nl < ELLW) {
+                if (nl < ELLW) {   // Lo_k[I][J] = A_c[I][J] (offset o of row I)
                     lo_q[p * ELLW + nl] = pj % G.T;
                     lo_v[p * ELLW + nl] = Ac[(long long)o * G.Nc + I];
                 }
                 ++nl;
-                // Up_k[J][I] = A_c[J][I] (offset 124 - o of row J)
-                if (nu < ELLW) {
+                if (nu < ELLW) {   // Up_k[J][I] = A_c[J][I] (offset -d of row J)
                     up_q[p * ELLW + nu] = pj % G.T;
                     up_v[p * ELLW + nu] = Ac[(long long)(124 - o) * G.Nc + J];
                 }
                 ++nu;
             }
         }
-        if (nl > ELLW || nu > ELLW) atomicExch(err, 2);
+        if (nl > ELLW || nu > ELLW) atomicExch(err, ERR_ELL);
         for (int e = min(nl, ELLW); e < ELLW; ++e) { lo_q[p * ELLW + e] = 0; lo_v[p * ELLW + e] = 0; }
         for (int e = min(nu, ELLW); e < ELLW; ++e) { up_q[p * ELLW + e] = 0; up_v[p * ELLW + e] = 0; }
     }
 }
 
 // ---------------------------------------------------------------------------
-// blocked Gauss-Jordan inversion (in place, no pivoting) of one T x T block
+// bounded grid barrier (all CTAs are co-resident: cooperative launch)
+// ---------------------------------------------------------------------------
+
+__device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
+    unsigned v;
+    asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+    return v;
+}
+
+// returns false if this or another CTA has recorded an error (then callers
+// stop doing work but still return from the kernel promptly)
+__device__ bool grid_barrier(GridBar *bar, int *err) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int ok = (ld_acquire((const unsigned *)err) == 0);
+        if (ok) {
+            const unsigned g = ld_acquire(&bar->gen);
+            __threadfence();
+            if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
+                atomicExch(&bar->count, 0u);
+                __threadfence();
+                atomicAdd(&bar->gen, 1u);
+            } else {
+                long long it = 0;
+                while (ld_acquire(&bar->gen) == g) {
+                    if (++it > BAR_POLLS) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
+                    if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
+                    __nanosleep(32);
+                }
+            }
+            __threadfence();
+        }
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// ---------------------------------------------------------------------------
+// 64 x 64 tile helpers (256 threads; thread t owns rows tr..tr+3, cols tc..tc+3)
 // ---------------------------------------------------------------------------
 
 template <typename AT>
-__device__ void tile_load(AT (*s)[TILE + 1], const AT *M, int ld, int ti, int tj) {
-    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-        const int i = e / TILE, j = e % TILE;
-        s[i][j] = M[(long long)(ti * TILE + i) * ld + tj * TILE + j];
-    }
-}
+struct TileSmem {
+    AT X[TILE][TILE + 1];
+    AT Y[TILE][TILE + 1];
+    AT rowb[2][TILE];
+    AT colb[2][TILE];
+};
+
 template <typename AT>
-__device__ void tile_store(AT (*s)[TILE + 1], AT *M, int ld, int ti, int tj) {
+__device__ __forceinline__ void tile_to_smem(AT (*s)[TILE + 1], const AT *M, int ld, int ti, int tj) {
     for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
         const int i = e / TILE, j = e % TILE;
-        M[(long long)(ti * TILE + i) * ld + tj * TILE + j] = s[i][j];
+        s[i][j] = __ldcg(M + (long long)(ti * TILE + i) * ld + tj * TILE + j);
     }
 }
 
-// in-place inverse of the 64 x 64 tile held in shared memory
-template <typename AT>
-__device__ void tile_invert(AT (*a)[TILE + 1], AT *col, int *err) {
-    for (int kk = 0; kk < TILE; ++kk) {
-        const AT p = a[kk][kk];
-        if (threadIdx.x == 0 && (!(p != (AT)0) || !isfinite((double)p))) atomicExch(err, 1);
-        const AT ip = (AT)1 / p;
-        __syncthreads();
-        for (int j = threadIdx.x; j < TILE; j += blockDim.x) {
-            col[j] = a[j][kk];
-            if (j != kk) a[kk][j] *= ip;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-            const int i = e / TILE, j = e % TILE;
-            if (i == kk) continue;
-            if (j == kk) a[i][j] = -col[i] * ip;
-            else a[i][j] -= col[i] * a[kk][j];
-        }
-        __syncthreads();
-        if (threadIdx.x == 0) a[kk][kk] = ip;
-        __syncthreads();
-    }
-}
-
-// out = (sign) * X * Y (+ base), all 64 x 64 tiles in shared memory, 256 threads
+// acc = X * Y (both in shared memory)
 template <typename AT>
 __device__ __forceinline__ void tile_mma(AT (*X)[TILE + 1], AT (*Y)[TILE + 1], AT acc[4][4]) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
@@ -239,223 +319,268 @@ __device__ __forceinline__ void tile_mma(AT (*X)[TILE + 1], AT (*Y)[TILE + 1], A
     }
 }
 
-struct GJArgs {
-    void *D;
-    int ld, nt, p;
-    int *err;
-};
-
-// job 0: invert the diagonal tile p (one CTA)
-// shared-memory carve-up of the Gauss-Jordan kernels (dynamic: the FP64 tiles
-// exceed the 48 KB static limit)
+// in-place Gauss-Jordan inverse of tile (ti, ti) of M, no pivoting; the tile
+// lives in registers, pivot row / column are exchanged through double-buffered
+// shared vectors (one barrier per pivot)
 template <typename AT>
-struct GJSmem {
-    AT X[TILE][TILE + 1];
-    AT Y[TILE][TILE + 1];
-    AT col[TILE];
-};
-
-template <typename AT>
-__device__ __forceinline__ GJSmem<AT> &gj_smem() {
-    extern __shared__ __align__(16) unsigned char smem_raw[];
-    return *reinterpret_cast<GJSmem<AT> *>(smem_raw);
-}
-
-template <typename AT>
-__global__ void __launch_bounds__(256) k_gj_diag(GJArgs a) {
-    GJSmem<AT> &sm = gj_smem<AT>();
-    auto &t = sm.X;
-    auto &col = sm.col;
-    AT *D = (AT *)a.D;
-    tile_load(t, D, a.ld, a.p, a.p);
-    __syncthreads();
-    tile_invert(t, col, a.err);
-    tile_store(t, D, a.ld, a.p, a.p);
-}
-
-// row panel: D_pj = Dpp^{-1} D_pj for j != p (CTA per j)
-template <typename AT>
-__global__ void __launch_bounds__(256) k_gj_row(GJArgs a) {
-    GJSmem<AT> &sm = gj_smem<AT>();
-    auto &X = sm.X;
-    auto &Y = sm.Y;
-    AT *D = (AT *)a.D;
-    const int j = blockIdx.x < a.p ? blockIdx.x : blockIdx.x + 1;
-    tile_load(X, D, a.ld, a.p, a.p);
-    tile_load(Y, D, a.ld, a.p, j);
-    __syncthreads();
-    AT acc[4][4] = {};
-    tile_mma(X, Y, acc);
+__device__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
+    AT a[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v)
-            D[(long long)(a.p * TILE + tr + u) * a.ld + j * TILE + tc + v] = acc[u][v];
+            a[u][v] = __ldcg(M + (long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v);
+    for (int kk = 0; kk < TILE; ++kk) {
+        const int par = kk & 1;
+        if (tr <= kk && kk < tr + 4) {
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sm.rowb[par][tc + v] = a[kk - tr][v];
+        }
+        if (tc <= kk && kk < tc + 4) {
+#pragma unroll
+            for (int u = 0; u < 4; ++u) sm.colb[par][tr + u] = a[u][kk - tc];
+        }
+        __syncthreads();
+        const AT piv = sm.rowb[par][kk];
+        if (threadIdx.x == 0 && (!(piv != (AT)0) || !isfinite((double)piv))) atomicExch(err, ERR_PIVOT);
+        const AT ip = (AT)1 / piv;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const int i = tr + u;
+            const AT ci = sm.colb[par][i] * ip;
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const int j = tc + v;
+                if (i == kk) a[u][v] = (j == kk) ? ip : a[u][v] * ip;
+                else if (j == kk) a[u][v] = -ci;
+                else a[u][v] -= ci * sm.rowb[par][j];
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            M[(long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v] = a[u][v];
 }
 
-// trailing update: D_ij -= D_ip D_pj for i, j != p (CTA per (i, j))
+// out tile (oi, oj) = sign * tile(xi, xj) * tile(yi, yj)  (+ tile(oi,oj) if accumulate)
 template <typename AT>
-__global__ void __launch_bounds__(256) k_gj_update(GJArgs a) {
-    GJSmem<AT> &sm = gj_smem<AT>();
-    auto &X = sm.X;
-    auto &Y = sm.Y;
-    AT *D = (AT *)a.D;
-    const int bi = blockIdx.x / (a.nt - 1), bj = blockIdx.x % (a.nt - 1);
-    const int i = bi < a.p ? bi : bi + 1, j = bj < a.p ? bj : bj + 1;
-    tile_load(X, D, a.ld, i, a.p);
-    tile_load(Y, D, a.ld, a.p, j);
+__device__ void tile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj, int yi, int yj,
+                             int oi, int oj, AT sign, bool accumulate) {
+    tile_to_smem(sm.X, M, ld, xi, xj);
+    tile_to_smem(sm.Y, M, ld, yi, yj);
     __syncthreads();
     AT acc[4][4] = {};
-    tile_mma(X, Y, acc);
+    tile_mma(sm.X, sm.Y, acc);
+    __syncthreads();   // the output tile may alias an input tile
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
         for (int v = 0; v < 4; ++v) {
-            const long long e = (long long)(i * TILE + tr + u) * a.ld + j * TILE + tc + v;
-            D[e] -= acc[u][v];
+            AT *o = M + (long long)(oi * TILE + tr + u) * ld + oj * TILE + tc + v;
+            *o = accumulate ? __ldcg(o) + sign * acc[u][v] : sign * acc[u][v];
         }
 }
 
-// column panel for step p (D_ip = -D_ip Dpp^{-1}, CTA per i != p) and, in the
-// last CTA, the inversion of the next diagonal tile p + 1
+// ---------------------------------------------------------------------------
+// cooperative factorisation: block Thomas with in-place Gauss-Jordan inverses
+// ---------------------------------------------------------------------------
+
 template <typename AT>
-__global__ void __launch_bounds__(256) k_gj_col(GJArgs a, int do_next) {
-    GJSmem<AT> &sm = gj_smem<AT>();
-    auto &X = sm.X;
-    auto &Y = sm.Y;
-    auto &col = sm.col;
-    AT *D = (AT *)a.D;
-    if ((int)blockIdx.x == a.nt - 1) {
-        if (!do_next) return;
-        tile_load(X, D, a.ld, a.p + 1, a.p + 1);
-        __syncthreads();
-        tile_invert(X, col, a.err);
-        tile_store(X, D, a.ld, a.p + 1, a.p + 1);
-        return;
-    }
-    const int i = blockIdx.x < a.p ? blockIdx.x : blockIdx.x + 1;
-    tile_load(X, D, a.ld, i, a.p);
-    tile_load(Y, D, a.ld, a.p, a.p);
+struct FacArgs {
+    AT *D, *C, *F;
+    const int *lo_q, *up_q;
+    const AT *lo_v, *up_v;
+    int T, nt, nb;
+    GridBar *bar;
+    int *err;
+};
+
+// Out[r0+i][c] (=, -=) sum_e M[r0+i][uq[c][e]] uv[c][e] for a chunk of FROWS rows
+template <typename AT>
+__device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, const AT *uv, int T,
+                              int r0, bool subtract) {
+    for (int e = threadIdx.x; e < FROWS * T; e += blockDim.x)
+        rows[e] = __ldcg(M + (long long)r0 * T + e);
     __syncthreads();
-    AT acc[4][4] = {};
-    tile_mma(X, Y, acc);
-    const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
-#pragma unroll
-    for (int u = 0; u < 4; ++u)
-#pragma unroll
-        for (int v = 0; v < 4; ++v)
-            D[(long long)(i * TILE + tr + u) * a.ld + a.p * TILE + tc + v] = -acc[u][v];
-}
-
-// ---------------------------------------------------------------------------
-// sparse-dense block products of the block Thomas recursion
-// ---------------------------------------------------------------------------
-
-// C_k[r][:] = sum_e lo_v[r][e] E_k[lo_q[r][e]][:]   (CTA per row r of block k+1)
-template <typename AT>
-__global__ void __launch_bounds__(256) k_lo_times(const int *__restrict__ lo_q,
-                                                   const AT *__restrict__ lo_v,
-                                                   const AT *__restrict__ E, AT *__restrict__ Cm,
-                                                   int T) {
-    const int r = blockIdx.x;
-    const int *q = lo_q + (long long)r * ELLW;
-    const AT *v = lo_v + (long long)r * ELLW;
     for (int c = threadIdx.x; c < T; c += blockDim.x) {
-        AT acc = 0;
-        for (int e = 0; e < ELLW; ++e) acc += v[e] * E[(long long)q[e] * T + c];
-        Cm[(long long)r * T + c] = acc;
+        AT acc[FROWS] = {};
+        const int *q = uq + (long long)c * ELLW;
+        const AT *v = uv + (long long)c * ELLW;
+        for (int e = 0; e < ELLW; ++e) {
+            const int qe = q[e];
+            const AT ve = v[e];
+#pragma unroll
+            for (int i = 0; i < FROWS; ++i) acc[i] += rows[i * T + qe] * ve;
+        }
+#pragma unroll
+        for (int i = 0; i < FROWS; ++i) {
+            AT *o = Out + (long long)(r0 + i) * T + c;
+            *o = subtract ? __ldcg(o) - acc[i] : acc[i];
+        }
     }
+    __syncthreads();
 }
 
-// Out[r][c] (=, or -=) sum_e M[r][up_q[c][e]] up_v[c][e]   (CTA per row r)
 template <typename AT>
-__global__ void __launch_bounds__(256) k_times_up(const int *__restrict__ up_q,
-                                                   const AT *__restrict__ up_v,
-                                                   const AT *__restrict__ M, AT *__restrict__ Out,
-                                                   int T, int subtract) {
+__global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    AT *row = reinterpret_cast<AT *>(smem_raw);
-    const int r = blockIdx.x;
-    for (int c = threadIdx.x; c < T; c += blockDim.x) row[c] = M[(long long)r * T + c];
-    __syncthreads();
-    for (int c = threadIdx.x; c < T; c += blockDim.x) {
-        const int *q = up_q + (long long)c * ELLW;
-        const AT *v = up_v + (long long)c * ELLW;
-        AT acc = 0;
-        for (int e = 0; e < ELLW; ++e) acc += row[q[e]] * v[e];
-        if (subtract) Out[(long long)r * T + c] -= acc;
-        else Out[(long long)r * T + c] = acc;
+    TileSmem<AT> &ts = *reinterpret_cast<TileSmem<AT> *>(smem_raw);
+    AT *rows = reinterpret_cast<AT *>(smem_raw);
+    const int T = a.T, nt = a.nt, G = gridDim.x, b = blockIdx.x;
+    const long long bsz = (long long)T * T;
+    for (int k = 0; k < a.nb; ++k) {
+        AT *Dk = a.D + k * bsz;
+        if (b == 0) tile_invert(ts, Dk, T, 0, a.err);
+        if (!grid_barrier(a.bar, a.err)) return;
+        for (int p = 0; p < nt; ++p) {
+            for (int it = b; it < nt - 1; it += G) {          // row panel: D_pj = P D_pj
+                const int j = it < p ? it : it + 1;
+                tile_product(ts, Dk, T, p, p, p, j, p, j, (AT)1, false);
+            }
+            if (!grid_barrier(a.bar, a.err)) return;
+            for (int it = b; it < (nt - 1) * (nt - 1); it += G) {   // D_ij -= D_ip D_pj
+                const int bi = it / (nt - 1), bj = it % (nt - 1);
+                const int i = bi < p ? bi : bi + 1, j = bj < p ? bj : bj + 1;
+                tile_product(ts, Dk, T, i, p, p, j, i, j, (AT)-1, true);
+            }
+            if (!grid_barrier(a.bar, a.err)) return;
+            for (int it = b; it < nt; it += G) {              // D_ip = -D_ip P ; next pivot tile
+                if (it == nt - 1) {
+                    if (p + 1 < nt) tile_invert(ts, Dk, T, p + 1, a.err);
+                } else {
+                    const int i = it < p ? it : it + 1;
+                    tile_product(ts, Dk, T, i, p, p, p, i, p, (AT)-1, false);
+                }
+            }
+            if (!grid_barrier(a.bar, a.err)) return;
+        }
+        if (k + 1 < a.nb) {
+            AT *Ck = a.C + k * bsz, *Fk = a.F + k * bsz;
+            const long long ell = (long long)T * ELLW;
+            const int *lq = a.lo_q + k * ell, *uq = a.up_q + k * ell;
+            const AT *lv = a.lo_v + k * ell, *uv = a.up_v + k * ell;
+            const int nchunk = T / FROWS;
+            for (int it = b; it < T + nchunk; it += G) {
+                if (it < T) {                                  // C_k row = Lo_k row * E_k
+                    const int r = it;
+                    for (int c = threadIdx.x; c < T; c += blockDim.x) {
+                        AT acc = 0;
+                        for (int e = 0; e < ELLW; ++e)
+                            acc += lv[(long long)r * ELLW + e] *
+                                   __ldcg(Dk + (long long)lq[(long long)r * ELLW + e] * T + c);
+                        Ck[(long long)r * T + c] = acc;
+                    }
+                } else {                                       // F_k = E_k Up_k
+                    rows_times_up(rows, Dk, Fk, uq, uv, T, (it - T) * FROWS, false);
+                }
+            }
+            if (!grid_barrier(a.bar, a.err)) return;
+            for (int it = b; it < nchunk; it += G)             // D_{k+1} -= C_k Up_k
+                rows_times_up(rows, Ck, Dk + bsz, uq, uv, T, it * FROWS, true);
+            if (!grid_barrier(a.bar, a.err)) return;
+        }
     }
 }
 
 // ---------------------------------------------------------------------------
-// solve kernels
+// cooperative solve: restriction, block forward / backward sweeps, prolongation
 // ---------------------------------------------------------------------------
 
-// y[b][r] = (subtract ? y[b][r] - : ) sum_c M[b][r][c] x[b][c]   (warp per row)
 template <typename AT>
-__global__ void __launch_bounds__(256) k_gemv(const AT *__restrict__ M, long long mstride,
-                                              const AT *__restrict__ x, long long xstride,
-                                              AT *__restrict__ y, long long ystride, int T,
-                                              int subtract) {
+struct SolArgs {
+    const double *t;
+    double *z;
+    int accumulate;
+    Interp P;
+    CGeom G;
+    const int *pos;
+    const AT *E, *C, *F;
+    AT *g, *x;
+    GridBar *bar;
+    int *err;
+};
+
+// y[r] (=, -=) sum_c M[r][c] xs[c] over rows distributed to warps of the grid
+template <typename AT>
+__device__ void grid_gemv(const AT *M, const AT *xsrc, AT *y, int T, AT *xs, bool subtract) {
+    for (int c = threadIdx.x; c < T; c += blockDim.x) xs[c] = __ldcg(xsrc + c);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int wpb = blockDim.x / 32;
+    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < T; r += gridDim.x * wpb) {
+        const AT *row = M + (long long)r * T;
+        AT acc = 0;
+        for (int c = lane; c < T; c += 32) acc += __ldcg(row + c) * xs[c];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) y[r] = subtract ? __ldcg(y + r) - acc : acc;
+    }
+}
+
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT *xs = reinterpret_cast<AT *>(smem_raw);
-    const int b = blockIdx.y;
-    M += b * mstride; x += b * xstride; y += b * ystride;
-    for (int c = threadIdx.x; c < T; c += blockDim.x) xs[c] = x[c];
-    __syncthreads();
-    const int lane = threadIdx.x & 31;
-    const int r = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (r >= T) return;
-    const AT *row = M + (long long)r * T;
-    AT acc = 0;
-    for (int c = lane; c < T; c += 32) acc += row[c] * xs[c];
+    const CGeom &G = a.G;
+    const Interp &P = a.P;
+    const int T = G.T;
+    const long long bsz = (long long)T * T;
+    const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
+    // g[pos(I)] = sum_a P(a, I) t[a]  (warp per coarse cell)
+    for (int I = blockIdx.x * wpb + (threadIdx.x >> 5); I < G.Nc; I += gridDim.x * wpb) {
+        const int Ix = I % G.cx, Iy = (I / G.cx) % G.cy, Iz = I / (G.cx * G.cy);
+        const int x0 = P.lo[0][Ix], x1 = P.hi[0][Ix];
+        const int y0 = P.lo[1][Iy], y1 = P.hi[1][Iy];
+        const int z0 = P.lo[2][Iz], z1 = P.hi[2][Iz];
+        const int wx = x1 - x0, wy = y1 - y0;
+        const int tot = wx * wy * (z1 - z0);
+        AT acc = 0;
+        for (int e = lane; e < tot; e += 32) {
+            const int ax = x0 + e % wx, ay = y0 + (e / wx) % wy, az = z0 + e / (wx * wy);
+            const AT w = (AT)w1(P, 0, ax, Ix) * (AT)w1(P, 1, ay, Iy) * (AT)w1(P, 2, az, Iz);
+            acc += w * (AT)a.t[ax + (long long)G.nx * (ay + (long long)G.ny * az)];
+        }
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) y[r] = subtract ? y[r] - acc : acc;
-}
-
-// g[pos(I)] = sum_a P(a, I) t[a]   (warp per coarse cell)
-template <typename AT>
-__global__ void __launch_bounds__(256) k_restrict(const double *__restrict__ t, Interp P, CGeom G,
-                                                  const int *__restrict__ pos, AT *__restrict__ g) {
-    const int lane = threadIdx.x & 31;
-    const int I = blockIdx.x * (blockDim.x / 32) + (threadIdx.x >> 5);
-    if (I >= G.Nc) return;
-    const int Ix = I % G.cx, Iy = (I / G.cx) % G.cy, Iz = I / (G.cx * G.cy);
-    const int x0 = P.lo[0][Ix], x1 = P.hi[0][Ix];
-    const int y0 = P.lo[1][Iy], y1 = P.hi[1][Iy];
-    const int z0 = P.lo[2][Iz], z1 = P.hi[2][Iz];
-    const int wx = x1 - x0, wy = y1 - y0;
-    const int tot = wx * wy * (z1 - z0);
-    AT acc = 0;
-    for (int e = lane; e < tot; e += 32) {
-        const int ax = x0 + e % wx, ay = y0 + (e / wx) % wy, az = z0 + e / (wx * wy);
-        const double w = w1(P, 0, ax, Ix) * w1(P, 1, ay, Iy) * w1(P, 2, az, Iz);
-        acc += (AT)w * (AT)t[ax + (long long)G.nx * (ay + (long long)G.ny * az)];
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) a.g[a.pos[I]] = acc;
     }
+    if (!grid_barrier(a.bar, a.err)) return;
+    for (int k = 1; k < G.nb; ++k) {               // g_k -= C_{k-1} g_{k-1}
+        grid_gemv(a.C + (k - 1) * bsz, a.g + (long long)(k - 1) * T, a.g + (long long)k * T, T, xs, true);
+        if (!grid_barrier(a.bar, a.err)) return;
+    }
+    // x_k = E_k g_k for every block
+    for (int rr = blockIdx.x * wpb + (threadIdx.x >> 5); rr < G.nb * T; rr += gridDim.x * wpb) {
+        const int k = rr / T;
+        const AT *row = a.E + k * bsz + (long long)(rr % T) * T;
+        const AT *gk = a.g + (long long)k * T;
+        AT acc = 0;
+        for (int c = lane; c < T; c += 32) acc += __ldcg(row + c) * __ldcg(gk + c);
 #pragma unroll
-    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-    if (lane == 0) g[pos[I]] = acc;
-}
-
-// z[a] (+)= sum over the 8 bracketing coarse cells P(a, I) x[pos(I)]
-template <typename AT>
-__global__ void __launch_bounds__(256) k_prolong(const AT *__restrict__ x, Interp P, CGeom G,
-                                                 const int *__restrict__ pos, double *__restrict__ z,
-                                                 int accumulate) {
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) a.x[rr] = acc;
+    }
+    if (!grid_barrier(a.bar, a.err)) return;
+    for (int k = G.nb - 2; k >= 0; --k) {          // x_k -= F_k x_{k+1}
+        grid_gemv(a.F + k * bsz, a.x + (long long)(k + 1) * T, a.x + (long long)k * T, T, xs, true);
+        if (!grid_barrier(a.bar, a.err)) return;
+    }
+    // z (+)= P x
     const long long N = (long long)G.nx * G.ny * G.nz;
-    for (long long a = blockIdx.x * (long long)blockDim.x + threadIdx.x; a < N;
-         a += (long long)gridDim.x * blockDim.x) {
-        const int ax = (int)(a % G.nx), ay = (int)((a / G.nx) % G.ny), az = (int)(a / ((long long)G.nx * G.ny));
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int ax = (int)(p % G.nx), ay = (int)((p / G.nx) % G.ny),
+                  az = (int)(p / ((long long)G.nx * G.ny));
         const int Ix[2] = {P.ia[0][ax], P.ib[0][ax]};
         const int Iy[2] = {P.ia[1][ay], P.ib[1][ay]};
         const int Iz[2] = {P.ia[2][az], P.ib[2][az]};
-        const double Wx[2] = {P.wa[0][ax], P.wb[0][ax]};
-        const double Wy[2] = {P.wa[1][ay], P.wb[1][ay]};
-        const double Wz[2] = {P.wa[2][az], P.wb[2][az]};
+        const AT Wx[2] = {(AT)P.wa[0][ax], (AT)P.wb[0][ax]};
+        const AT Wy[2] = {(AT)P.wa[1][ay], (AT)P.wb[1][ay]};
+        const AT Wz[2] = {(AT)P.wa[2][az], (AT)P.wb[2][az]};
         AT s = 0;
 #pragma unroll
         for (int u = 0; u < 2; ++u)
@@ -463,12 +588,12 @@ __global__ void __launch_bounds__(256) k_prolong(const AT *__restrict__ x, Inter
             for (int v = 0; v < 2; ++v)
 #pragma unroll
                 for (int w = 0; w < 2; ++w) {
-                    const double wt = Wx[w] * Wy[v] * Wz[u];
-                    if (wt == 0.0) continue;
+                    const AT wt = Wx[w] * Wy[v] * Wz[u];
+                    if (wt == (AT)0) continue;
                     const int I = Ix[w] + G.cx * (Iy[v] + G.cy * Iz[u]);
-                    s += (AT)wt * x[pos[I]];
+                    s += wt * __ldcg(a.x + a.pos[I]);
                 }
-        if (accumulate) z[a] += (double)s; else z[a] = (double)s;
+        if (a.accumulate) a.z[p] += (double)s; else a.z[p] = (double)s;
     }
 }
 
@@ -526,19 +651,27 @@ static CGeom geom_of(const Coarse *c) {
 }
 
 template <typename AT>
-static int set_smem_attrs_t() {
+static int configure_t(Coarse *c) {
     const int big = 227 * 1024;
-    RAS_CK(cudaFuncSetAttribute(k_times_up<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAS_CK(cudaFuncSetAttribute(k_gemv<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAS_CK(cudaFuncSetAttribute(k_gj_diag<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAS_CK(cudaFuncSetAttribute(k_gj_row<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAS_CK(cudaFuncSetAttribute(k_gj_update<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
-    RAS_CK(cudaFuncSetAttribute(k_gj_col<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_rap<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_coarse_factor<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_coarse_solve<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
+    const int WM = std::max(WX, std::max(WY, WZ));
+    c->rap_smem = sizeof(AT) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
+    c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
+    c->sol_smem = sizeof(AT) * (size_t)c->T;
+    if (c->rap_smem > (size_t)big || c->fac_smem > (size_t)big || c->sol_smem > (size_t)big)
+        return RAS_EINVAL;
+    int dev = 0, sms = 0, bf = 0, bs = 0;
+    RAS_CK(cudaGetDevice(&dev));
+    RAS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_coarse_factor<AT>, 256, c->fac_smem));
+    RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_coarse_solve<AT>, 256, c->sol_smem));
+    if (bf < 1 || bs < 1) return RAS_EINVAL;
+    c->fac_grid = sms * std::min(bf, 2);
+    c->sol_grid = sms * std::min(bs, 2);
     return RAS_OK;
-}
-
-static int set_smem_attrs(int prec) {
-    return prec == 64 ? set_smem_attrs_t<double>() : set_smem_attrs_t<float>();
 }
 
 int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
@@ -546,6 +679,10 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
     if (o.interp_order != 2) return RAS_EINVAL;
     if (o.coarse_prec != 64 && o.coarse_prec != 32) return RAS_EINVAL;
     for (int a = 0; a < 3; ++a) if (o.coarsen[a] < 1) return RAS_EINVAL;
+    int dev = 0, coop = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&coop, cudaDevAttrCooperativeLaunch, dev) != cudaSuccess || !coop)
+        return RAS_EINVAL;
     Coarse *c = new Coarse();
     auto fail = [&](int s) { coarse_free(c); return s; };
     c->prec = o.coarse_prec;
@@ -557,17 +694,20 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
         std::vector<int> ia, ib, lo, hi;
         std::vector<double> wa, wb;
         interp_axis(c->n[a], c->r[a], ia, ib, wa, wb, lo, hi, c->c[a]);
+        c->wmax[a] = 1;
+        for (size_t I = 0; I < lo.size(); ++I) c->wmax[a] = std::max(c->wmax[a], hi[I] - lo[I]);
         int rc = 0;
         if ((rc = dalloc(&c->d_ia[a], ia.size())) || (rc = dalloc(&c->d_ib[a], ib.size())) ||
             (rc = dalloc(&c->d_wa[a], wa.size())) || (rc = dalloc(&c->d_wb[a], wb.size())) ||
             (rc = dalloc(&c->d_lo[a], lo.size())) || (rc = dalloc(&c->d_hi[a], hi.size())))
             return fail(rc);
-        cudaMemcpy(c->d_ia[a], ia.data(), ia.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_ib[a], ib.data(), ib.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_wa[a], wa.data(), wa.size() * 8, cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_wb[a], wb.data(), wb.size() * 8, cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_lo[a], lo.data(), lo.size() * 4, cudaMemcpyHostToDevice);
-        cudaMemcpy(c->d_hi[a], hi.data(), hi.size() * 4, cudaMemcpyHostToDevice);
+        bool ok = cudaMemcpy(c->d_ia[a], ia.data(), ia.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_ib[a], ib.data(), ib.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_wa[a], wa.data(), wa.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_wb[a], wb.data(), wb.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_lo[a], lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
+                  cudaMemcpy(c->d_hi[a], hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
+        if (!ok) return fail(RAS_ECUDA);
     }
     c->Nc = c->c[0] * c->c[1] * c->c[2];
     // axes sorted by coarse size: fastest = smallest
@@ -595,7 +735,7 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
     const size_t bsz = (size_t)c->T * c->T;
     int rc = 0;
     if ((rc = dalloc(&c->d_pos, pos.size())) || (rc = dalloc(&c->d_cell, cell.size())) ||
-        (rc = dalloc(&c->d_err, 1)))
+        (rc = dalloc(&c->d_err, 1)) || (rc = dalloc(&c->d_bar, 1)))
         return fail(rc);
     unsigned char *p_ac, *p_d, *p_c, *p_f, *p_lv, *p_uv, *p_g, *p_x;
     const size_t nbm1 = (size_t)std::max(c->nb - 1, 1);
@@ -612,12 +752,14 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
     if (cudaMemcpy(c->d_pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemcpy(c->d_cell, cell.data(), cell.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
         cudaMemset(c->d_err, 0, 4) != cudaSuccess ||
+        cudaMemset(c->d_bar, 0, sizeof(GridBar)) != cudaSuccess ||
         cudaMemset(c->g, 0, (size_t)c->nb * c->T * c->esz) != cudaSuccess ||
-        cudaMemset(c->x, 0, (size_t)c->nb * c->T * c->esz) != cudaSuccess)
+        cudaMemset(c->x, 0, (size_t)c->nb * c->T * c->esz) != cudaSuccess ||
+        cudaMemset(c->lo_q, 0, nbm1 * c->T * ELLW * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->up_q, 0, nbm1 * c->T * ELLW * sizeof(int)) != cudaSuccess)
         return fail(RAS_ECUDA);
-    const int sm = (int)(c->T * c->esz);
-    if (sm > 227 * 1024) return fail(RAS_EINVAL);
-    if ((rc = set_smem_attrs(c->prec)) != RAS_OK) return fail(rc);
+    rc = c->prec == 64 ? configure_t<double>(c) : configure_t<float>(c);
+    if (rc) return fail(rc);
     *out = c;
     return RAS_OK;
 }
@@ -628,7 +770,7 @@ void coarse_free(Coarse *c) {
         dfree(c->d_ia[a]); dfree(c->d_ib[a]); dfree(c->d_wa[a]); dfree(c->d_wb[a]);
         dfree(c->d_lo[a]); dfree(c->d_hi[a]);
     }
-    dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err);
+    dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err); dfree(c->d_bar);
     dfree(c->lo_q); dfree(c->up_q);
     for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x})
         if (p) cudaFree(p);
@@ -636,33 +778,13 @@ void coarse_free(Coarse *c) {
 }
 
 template <typename AT>
-static int gj_invert(Coarse *c, AT *Dk, cudaStream_t st) {
-    const int nt = c->T / TILE;
-    GJArgs a{Dk, c->T, nt, 0, c->d_err};
-    const size_t sm = sizeof(GJSmem<AT>);
-    k_gj_diag<AT><<<1, 256, sm, st>>>(a);
-    RAS_LAUNCHED();
-    for (int p = 0; p < nt; ++p) {
-        a.p = p;
-        if (nt > 1) {
-            k_gj_row<AT><<<nt - 1, 256, sm, st>>>(a);
-            RAS_LAUNCHED();
-            k_gj_update<AT><<<(nt - 1) * (nt - 1), 256, sm, st>>>(a);
-            RAS_LAUNCHED();
-            k_gj_col<AT><<<nt, 256, sm, st>>>(a, p + 1 < nt ? 1 : 0);
-            RAS_LAUNCHED();
-        }
-    }
-    return RAS_OK;
-}
-
-template <typename AT>
 static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
     const CGeom G = geom_of(c);
     const Interp P = interp_of(c);
-    AT *Ac = (AT *)c->Ac, *D = (AT *)c->D, *Cm = (AT *)c->C, *Fm = (AT *)c->F;
+    AT *Ac = (AT *)c->Ac, *D = (AT *)c->D;
     const size_t bsz = (size_t)c->T * c->T;
-    k_rap<AT><<<c->Nc, 128, 0, st>>>(A, P, G, Ac);
+    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
+    k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, P, G, W, Ac);
     RAS_LAUNCHED();
     RAS_CK(cudaMemsetAsync(D, 0, c->nb * bsz * sizeof(AT), st));
     k_assemble<AT><<<grid_of((long long)c->nb * c->T), 256, 0, st>>>(Ac, c->d_pos, c->d_cell, G, D);
@@ -672,22 +794,13 @@ static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
             Ac, c->d_pos, c->d_cell, G, c->lo_q, (AT *)c->lo_v, c->up_q, (AT *)c->up_v, c->d_err);
         RAS_LAUNCHED();
     }
-    const size_t ell = (size_t)c->T * ELLW;
-    for (int k = 0; k < c->nb; ++k) {
-        AT *Dk = D + k * bsz;
-        RAS_TRY(gj_invert<AT>(c, Dk, st));           // E_k = D_k^{-1} in place
-        if (k + 1 < c->nb) {
-            AT *Ck = Cm + k * bsz, *Fk = Fm + k * bsz;
-            const int *lq = c->lo_q + k * ell, *uq = c->up_q + k * ell;
-            const AT *lv = (const AT *)c->lo_v + k * ell, *uv = (const AT *)c->up_v + k * ell;
-            k_lo_times<AT><<<c->T, 256, 0, st>>>(lq, lv, Dk, Ck, c->T);          // C_k = Lo_k E_k
-            RAS_LAUNCHED();
-            k_times_up<AT><<<c->T, 256, c->T * sizeof(AT), st>>>(uq, uv, Dk, Fk, c->T, 0);  // F_k
-            RAS_LAUNCHED();
-            k_times_up<AT><<<c->T, 256, c->T * sizeof(AT), st>>>(uq, uv, Ck, Dk + bsz, c->T, 1);
-            RAS_LAUNCHED();                                                   // D_{k+1} -= C_k Up_k
-        }
-    }
+    RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
+    FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, c->lo_q, c->up_q, (const AT *)c->lo_v,
+                   (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->d_bar, c->d_err};
+    void *args[] = {&fa};
+    RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor<AT>, dim3(c->fac_grid),
+                                       dim3(256), args, c->fac_smem, st));
+    RAS_LAUNCHED();
     return RAS_OK;
 }
 
@@ -701,37 +814,19 @@ int coarse_check(Coarse *c, cudaStream_t st) {
     RAS_CK(cudaStreamSynchronize(st));
     if (h) {
         RAS_CK(cudaMemsetAsync(c->d_err, 0, sizeof(int), st));
-        return h == 2 ? RAS_EINVAL : RAS_EZEROPIVOT;
+        return h == ERR_TIMEOUT ? RAS_ETIMEOUT : (h == ERR_ELL ? RAS_EINVAL : RAS_EZEROPIVOT);
     }
     return RAS_OK;
 }
 
 template <typename AT>
 static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st) {
-    const CGeom G = geom_of(c);
-    const Interp P = interp_of(c);
-    AT *g = (AT *)c->g, *x = (AT *)c->x;
-    const AT *E = (const AT *)c->D, *Cm = (const AT *)c->C, *Fm = (const AT *)c->F;
-    const long long bsz = (long long)c->T * c->T;
-    const int T = c->T;
-    k_restrict<AT><<<(c->Nc + 7) / 8, 256, 0, st>>>(t, P, G, c->d_pos, g);
-    RAS_LAUNCHED();
-    const dim3 rows((T + 7) / 8, 1);
-    const size_t sm = T * sizeof(AT);
-    for (int k = 1; k < c->nb; ++k) {            // g_k -= C_{k-1} g_{k-1}
-        k_gemv<AT><<<rows, 256, sm, st>>>(Cm + (k - 1) * bsz, 0, g + (long long)(k - 1) * T, 0,
-                                          g + (long long)k * T, 0, T, 1);
-        RAS_LAUNCHED();
-    }
-    // x_k = E_k g_k for every block at once
-    k_gemv<AT><<<dim3((T + 7) / 8, c->nb), 256, sm, st>>>(E, bsz, g, T, x, T, T, 0);
-    RAS_LAUNCHED();
-    for (int k = c->nb - 2; k >= 0; --k) {       // x_k -= F_k x_{k+1}
-        k_gemv<AT><<<rows, 256, sm, st>>>(Fm + k * bsz, 0, x + (long long)(k + 1) * T, 0,
-                                          x + (long long)k * T, 0, T, 1);
-        RAS_LAUNCHED();
-    }
-    k_prolong<AT><<<grid_of(c->N), 256, 0, st>>>(x, P, G, c->d_pos, z, accumulate);
+    RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
+    SolArgs<AT> sa{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
+                   (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, c->d_bar, c->d_err};
+    void *args[] = {&sa};
+    RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve<AT>, dim3(c->sol_grid),
+                                       dim3(256), args, c->sol_smem, st));
     RAS_LAUNCHED();
     return RAS_OK;
 }

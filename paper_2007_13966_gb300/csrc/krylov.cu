@@ -15,26 +15,27 @@ namespace ras {
 // Krylov kernels
 // ---------------------------------------------------------------------------
 
-constexpr int KV = MAX_MDOT + 1;   // vectors per multi-dot incl. the optional self product
 
-// partials[v][block] = sum_i V[v][i] w[i]  (v < k);  row k: sum_i w[i]^2 if self
+// partials[v][block] = sum_i V[v][i] w[i]  (v < k);  row k: sum_i w[i]^2 if self.
+// KM is the compile-time bound on k (the host picks the next power of two).
+template <int KM>
 __global__ void __launch_bounds__(RED_THREADS) k_mdot(const double *__restrict__ V, long long ldv,
                                                       int k, int self, const double *__restrict__ w,
                                                       int n, double *__restrict__ partials) {
-    double acc[KV];
+    double acc[KM + 1];
 #pragma unroll
-    for (int v = 0; v < KV; ++v) acc[v] = 0.0;
+    for (int v = 0; v <= KM; ++v) acc[v] = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const double wi = w[i];
 #pragma unroll
-        for (int v = 0; v < KV - 1; ++v)
+        for (int v = 0; v < KM; ++v)
             if (v < k) acc[v] = fma(V[v * ldv + i], wi, acc[v]);
-        if (self) acc[KV - 1] = fma(wi, wi, acc[KV - 1]);
+        if (self) acc[KM] = fma(wi, wi, acc[KM]);
     }
-    __shared__ double sh[RED_THREADS / 32][KV];
+    __shared__ double sh[RED_THREADS / 32][KM + 1];
     const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
 #pragma unroll
-    for (int v = 0; v < KV; ++v) {
+    for (int v = 0; v <= KM; ++v) {
         double s = acc[v];
 #pragma unroll
         for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
@@ -43,7 +44,7 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(const double *__restrict__
     __syncthreads();
     const int nv = k + (self ? 1 : 0);
     for (int t = threadIdx.x; t < nv; t += blockDim.x) {
-        const int v = t < k ? t : KV - 1;
+        const int v = t < k ? t : KM;
         double s = 0.0;
         for (int q = 0; q < RED_THREADS / 32; ++q) s += sh[q][v];
         partials[(long long)t * RED_BLOCKS + blockIdx.x] = s;
@@ -70,19 +71,19 @@ __global__ void k_finalize_rows(const double *__restrict__ partials, int nvec,
 }
 
 // w -= sum_v h[v] V[v]; optionally partial sums of the new w^2
-template <bool NORM>
+template <bool NORM, int KM>
 __global__ void __launch_bounds__(RED_THREADS) k_update(const double *__restrict__ V, long long ldv,
                                                         int k, const double *__restrict__ h,
                                                         double *__restrict__ w, int n,
                                                         double *__restrict__ partials) {
-    double hv[KV - 1];
+    double hv[KM];
 #pragma unroll
-    for (int v = 0; v < KV - 1; ++v) hv[v] = v < k ? h[v] : 0.0;
+    for (int v = 0; v < KM; ++v) hv[v] = v < k ? h[v] : 0.0;
     double acc = 0.0;
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         double s = w[i];
 #pragma unroll
-        for (int v = 0; v < KV - 1; ++v)
+        for (int v = 0; v < KM; ++v)
             if (v < k) s = fma(-hv[v], V[v * ldv + i], s);
         w[i] = s;
         if (NORM) acc = fma(s, s, acc);
@@ -99,6 +100,36 @@ __global__ void __launch_bounds__(RED_THREADS) k_update(const double *__restrict
             partials[blockIdx.x] = s;
         }
     }
+}
+
+// host dispatch on the next power of two >= k
+static int launch_mdot(const double *V, long long ld, int k, int self, const double *w, int n,
+                       double *partials, cudaStream_t st) {
+#define RAS_MDOT(KM) k_mdot<KM><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, self, w, n, partials)
+    if (k <= 1) RAS_MDOT(1);
+    else if (k <= 2) RAS_MDOT(2);
+    else if (k <= 4) RAS_MDOT(4);
+    else if (k <= 8) RAS_MDOT(8);
+    else if (k <= 16) RAS_MDOT(16);
+    else RAS_MDOT(32);
+#undef RAS_MDOT
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+template <bool NORM>
+static int launch_update(const double *V, long long ld, int k, const double *h, double *w, int n,
+                         double *partials, cudaStream_t st) {
+#define RAS_UPD(KM) k_update<NORM, KM><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, h, w, n, partials)
+    if (k <= 1) RAS_UPD(1);
+    else if (k <= 2) RAS_UPD(2);
+    else if (k <= 4) RAS_UPD(4);
+    else if (k <= 8) RAS_UPD(8);
+    else if (k <= 16) RAS_UPD(16);
+    else RAS_UPD(32);
+#undef RAS_UPD
+    RAS_LAUNCHED();
+    return RAS_OK;
 }
 
 struct Coefs {
@@ -171,20 +202,15 @@ int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, 
             RAS_TRY(precond_apply(pc, Vj, Zj, st));
             RAS_TRY(stencil_apply(A, P->nx, P->ny, P->nz, Zj, w, st));
             // CGS pass 1 (+ ||w||^2 before orthogonalisation)
-            k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, 1, w, N, red.partials);
-            RAS_LAUNCHED();
+            RAS_TRY(launch_mdot(V, ld, k, 1, w, N, red.partials, st));
             k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, k + 1, red.out, 0, 0);
             RAS_LAUNCHED();
-            k_update<false><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, red.out, w, N, nullptr);
-            RAS_LAUNCHED();
+            RAS_TRY(launch_update<false>(V, ld, k, red.out, w, N, nullptr, st));
             // CGS pass 2
-            k_mdot<<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, 0, w, N, red.partials);
-            RAS_LAUNCHED();
+            RAS_TRY(launch_mdot(V, ld, k, 0, w, N, red.partials, st));
             k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, k, red.out, k + 1, 0);
             RAS_LAUNCHED();
-            k_update<true><<<RED_BLOCKS, RED_THREADS, 0, st>>>(V, ld, k, red.out + k + 1, w, N,
-                                                               red.partials);
-            RAS_LAUNCHED();
+            RAS_TRY(launch_update<true>(V, ld, k, red.out + k + 1, w, N, red.partials, st));
             k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, 1, red.out, 2 * k + 1, 1);
             RAS_LAUNCHED();
             // v_{j+1} = w / h_{j+1,j} (unused if this step breaks down)
@@ -232,6 +258,7 @@ int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, 
         converged = beta <= tol || std::fabs(g[k]) <= tol;
         if (!converged && it < o.maxit) push(beta);
     }
+    RAS_TRY(precond_check(pc, st));
     if (stats) {
         stats->iters = it;
         stats->converged = converged ? 1 : 0;

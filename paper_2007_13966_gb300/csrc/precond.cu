@@ -42,6 +42,10 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
     return RAS_OK;
 }
 
+int precond_check(ras_precond *pc, cudaStream_t st) {
+    return pc->coarse ? coarse_check(pc->coarse, st) : RAS_OK;
+}
+
 // z = M^{-1} r for the configured preconditioner
 int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st) {
     const ras_problem *P = pc->prob;

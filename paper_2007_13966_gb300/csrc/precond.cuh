@@ -35,4 +35,6 @@ struct ras_precond {
 namespace ras {
 int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st);
 int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st);
+// reports (and clears) an error recorded by the asynchronous coarse solves
+int precond_check(ras_precond *pc, cudaStream_t st);
 }  // namespace ras
