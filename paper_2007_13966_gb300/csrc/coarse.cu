@@ -652,7 +652,9 @@ static CGeom geom_of(const Coarse *c) {
 
 template <typename AT>
 static int configure_t(Coarse *c) {
-    const int big = 227 * 1024;
+    // dynamic opt-in well above any need here and below the per-block limit
+    // minus the kernels' static shared memory
+    const int big = 200 * 1024;
     RAS_CK(cudaFuncSetAttribute(k_rap<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_factor<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_solve<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
