@@ -20,7 +20,9 @@
 #include "precond.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <numeric>
+#include <type_traits>
 
 namespace ras {
 
@@ -50,6 +52,7 @@ struct Coarse {
     void *Ac = nullptr;             // [125][Nc] Galerkin stencil (prec)
     void *D = nullptr, *C = nullptr, *F = nullptr;   // [nb][T][T]
     int *lo_q = nullptr, *up_q = nullptr;            // ELL column / row indices
+    int *lo_n = nullptr, *up_n = nullptr;            // ELL entries used per row / column
     void *lo_v = nullptr, *up_v = nullptr;           // ELL values
     void *g = nullptr, *x = nullptr;                 // [nb*T]
     int *d_err = nullptr;
@@ -211,7 +214,7 @@ template <typename AT>
 __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
                       const int *__restrict__ cell, CGeom G, int *__restrict__ lo_q,
                       AT *__restrict__ lo_v, int *__restrict__ up_q, AT *__restrict__ up_v,
-                      int *__restrict__ err) {
+                      int *__restrict__ lo_n, int *__restrict__ up_n, int *__restrict__ err) {
     const long long tot = (long long)(G.nb - 1) * G.T;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < tot;
          p += (long long)gridDim.x * blockDim.x) {
@@ -230,16 +233,23 @@ __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
                     lo_v[p * ELLW + nl] = Ac[(long long)o * G.Nc + I];
                 }
                 ++nl;
-                if (nu < ELLW) {   // Up_k[J][I] = A_c[J][I] (offset -d of row J)
-                    up_q[p * ELLW + nu] = pj % G.T;
-                    up_v[p * ELLW + nu] = Ac[(long long)(124 - o) * G.Nc + J];
+                if (nu < ELLW) {   // Up_k[J][I] = A_c[J][I] (offset -d of row J), [e][T] layout
+                    const long long u = (long long)k * ELLW * G.T + (long long)nu * G.T + (p % G.T);
+                    up_q[u] = pj % G.T;
+                    up_v[u] = Ac[(long long)(124 - o) * G.Nc + J];
                 }
                 ++nu;
             }
         }
         if (nl > ELLW || nu > ELLW) atomicExch(err, ERR_ELL);
+        lo_n[p] = min(nl, ELLW);
+        up_n[p] = min(nu, ELLW);
         for (int e = min(nl, ELLW); e < ELLW; ++e) { lo_q[p * ELLW + e] = 0; lo_v[p * ELLW + e] = 0; }
-        for (int e = min(nu, ELLW); e < ELLW; ++e) { up_q[p * ELLW + e] = 0; up_v[p * ELLW + e] = 0; }
+        for (int e = min(nu, ELLW); e < ELLW; ++e) {
+            const long long u = (long long)k * ELLW * G.T + (long long)e * G.T + (p % G.T);
+            up_q[u] = 0;
+            up_v[u] = 0;
+        }
     }
 }
 
@@ -291,39 +301,45 @@ template <typename AT>
 struct TileSmem {
     AT X[TILE][TILE + 1];
     AT Y[TILE][TILE + 1];
-    AT rowb[2][TILE];
-    AT colb[2][TILE];
+    AT rowb[2][4][TILE];   // four pivot rows (double buffered)
+    AT colb[2][TILE][4];   // four pivot columns (double buffered)
 };
 
+// correctly rounded reciprocal (IEEE round to nearest)
+__device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
+
+// in-place Gauss-Jordan inverse of a 4 x 4 block held in registers (no pivoting)
 template <typename AT>
-__device__ __forceinline__ void tile_to_smem(AT (*s)[TILE + 1], const AT *M, int ld, int ti, int tj) {
-    for (int e = threadIdx.x; e < TILE * TILE; e += blockDim.x) {
-        const int i = e / TILE, j = e % TILE;
-        s[i][j] = __ldcg(M + (long long)(ti * TILE + i) * ld + tj * TILE + j);
+__device__ __forceinline__ bool invert4(AT P[4][4]) {
+    bool ok = true;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+        const AT p = P[k][k];
+        ok = ok && (p != (AT)0) && isfinite(p);
+        const AT ip = recip_rn(p);
+        P[k][k] = (AT)1;
+#pragma unroll
+        for (int j = 0; j < 4; ++j) P[k][j] *= ip;
+#pragma unroll
+        for (int i = 0; i < 4; ++i) {
+            if (i == k) continue;
+            const AT f = P[i][k];
+            P[i][k] = (AT)0;
+#pragma unroll
+            for (int j = 0; j < 4; ++j) P[i][j] -= f * P[k][j];
+        }
     }
+    return ok;
 }
 
-// acc = X * Y (both in shared memory)
+// In-place Gauss-Jordan inverse of tile (ti, ti) of M without pivoting, four
+// pivots per step: the 4 x 4 pivot block is inverted (redundantly) by every
+// thread and applied as a rank-4 update. Thread t owns rows tr..tr+3 and
+// columns tc..tc+3, so pivot rows / columns are published by whole 4 x 4
+// register blocks (no runtime register indexing); one barrier per step.
 template <typename AT>
-__device__ __forceinline__ void tile_mma(AT (*X)[TILE + 1], AT (*Y)[TILE + 1], AT acc[4][4]) {
-    const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
-#pragma unroll 4
-    for (int k = 0; k < TILE; ++k) {
-        AT xa[4], yb[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) { xa[u] = X[tr + u][k]; yb[u] = Y[k][tc + u]; }
-#pragma unroll
-        for (int u = 0; u < 4; ++u)
-#pragma unroll
-            for (int v = 0; v < 4; ++v) acc[u][v] += xa[u] * yb[v];
-    }
-}
-
-// in-place Gauss-Jordan inverse of tile (ti, ti) of M, no pivoting; the tile
-// lives in registers, pivot row / column are exchanged through double-buffered
-// shared vectors (one barrier per pivot)
-template <typename AT>
-__device__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
+__device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
     AT a[4][4];
 #pragma unroll
@@ -331,30 +347,75 @@ __device__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
 #pragma unroll
         for (int v = 0; v < 4; ++v)
             a[u][v] = __ldcg(M + (long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v);
-    for (int kk = 0; kk < TILE; ++kk) {
-        const int par = kk & 1;
-        if (tr <= kk && kk < tr + 4) {
+    for (int kb = 0; kb < TILE; kb += 4) {
+        const int par = (kb >> 2) & 1;
+        if (tr == kb) {
 #pragma unroll
-            for (int v = 0; v < 4; ++v) sm.rowb[par][tc + v] = a[kk - tr][v];
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sm.rowb[par][u][tc + v] = a[u][v];
         }
-        if (tc <= kk && kk < tc + 4) {
+        if (tc == kb) {
 #pragma unroll
-            for (int u = 0; u < 4; ++u) sm.colb[par][tr + u] = a[u][kk - tc];
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) sm.colb[par][tr + u][v] = a[u][v];
         }
         __syncthreads();
-        const AT piv = sm.rowb[par][kk];
-        if (threadIdx.x == 0 && (!(piv != (AT)0) || !isfinite((double)piv))) atomicExch(err, ERR_PIVOT);
-        const AT ip = (AT)1 / piv;
+        AT Pi[4][4];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-            const int i = tr + u;
-            const AT ci = sm.colb[par][i] * ip;
+        for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) {
-                const int j = tc + v;
-                if (i == kk) a[u][v] = (j == kk) ? ip : a[u][v] * ip;
-                else if (j == kk) a[u][v] = -ci;
-                else a[u][v] -= ci * sm.rowb[par][j];
+            for (int v = 0; v < 4; ++v) Pi[u][v] = sm.rowb[par][u][kb + v];
+        if (!invert4(Pi) && threadIdx.x == 0) atomicExch(err, ERR_PIVOT);
+        if (tr == kb && tc == kb) {            // pivot block -> its inverse
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) a[u][v] = Pi[u][v];
+        } else if (tc == kb) {                 // pivot columns: -C Pi
+            AT c[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) c[u][m] = a[u][m];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    AT t = 0;
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) t += c[u][m] * Pi[m][v];
+                    a[u][v] = -t;
+                }
+        } else {
+            // W = Pi R for my columns (R: the four pivot rows)
+            AT W[4][4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    AT t = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) t += Pi[m][q] * sm.rowb[par][q][tc + v];
+                    W[m][v] = t;
+                }
+            if (tr == kb) {                    // pivot rows: Pi R
+#pragma unroll
+                for (int u = 0; u < 4; ++u)
+#pragma unroll
+                    for (int v = 0; v < 4; ++v) a[u][v] = W[u][v];
+            } else {                           // rank-4 update: a -= C W
+#pragma unroll
+                for (int u = 0; u < 4; ++u) {
+                    AT c[4];
+#pragma unroll
+                    for (int m = 0; m < 4; ++m) c[m] = sm.colb[par][tr + u][m];
+#pragma unroll
+                    for (int v = 0; v < 4; ++v)
+#pragma unroll
+                        for (int m = 0; m < 4; ++m) a[u][v] -= c[m] * W[m][v];
+                }
             }
         }
     }
@@ -365,22 +426,138 @@ __device__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
             M[(long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v] = a[u][v];
 }
 
-// out tile (oi, oj) = sign * tile(xi, xj) * tile(yi, yj)  (+ tile(oi,oj) if accumulate)
+// Scalar Gauss-Jordan (one pivot per barrier): fewest operations, used for
+// FP64 where the arithmetic pipe, not the barrier, bounds the tile inverse.
 template <typename AT>
-__device__ void tile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj, int yi, int yj,
-                             int oi, int oj, AT sign, bool accumulate) {
-    tile_to_smem(sm.X, M, ld, xi, xj);
-    tile_to_smem(sm.Y, M, ld, yi, yj);
-    __syncthreads();
-    AT acc[4][4] = {};
-    tile_mma(sm.X, sm.Y, acc);
-    __syncthreads();   // the output tile may alias an input tile
+__device__ void tile_invert_s(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
+    AT a[4][4];
 #pragma unroll
     for (int u = 0; u < 4; ++u)
 #pragma unroll
-        for (int v = 0; v < 4; ++v) {
-            AT *o = M + (long long)(oi * TILE + tr + u) * ld + oj * TILE + tc + v;
+        for (int v = 0; v < 4; ++v)
+            a[u][v] = __ldcg(M + (long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v);
+    for (int kk = 0; kk < TILE; ++kk) {
+        const int par = kk & 1;
+        if (tr <= kk && kk < tr + 4) {
+            const int u = kk - tr;
+#pragma unroll
+            for (int v = 0; v < 4; ++v)
+                sm.rowb[par][0][tc + v] = u == 0 ? a[0][v] : (u == 1 ? a[1][v] : (u == 2 ? a[2][v] : a[3][v]));
+        }
+        if (tc <= kk && kk < tc + 4) {
+            const int v = kk - tc;
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+                sm.colb[par][tr + u][0] = v == 0 ? a[u][0] : (v == 1 ? a[u][1] : (v == 2 ? a[u][2] : a[u][3]));
+        }
+        __syncthreads();
+        const AT piv = sm.rowb[par][0][kk];
+        if (threadIdx.x == 0 && (!(piv != (AT)0) || !isfinite(piv))) atomicExch(err, ERR_PIVOT);
+        const AT ip = recip_rn(piv);
+        AT rb[4];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) rb[v] = sm.rowb[par][0][tc + v] * ip;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+            const bool ri = (tr + u == kk);
+            const AT ci = sm.colb[par][tr + u][0];
+#pragma unroll
+            for (int v = 0; v < 4; ++v) {
+                const bool cj = (tc + v == kk);
+                AT nv = a[u][v] - ci * rb[v];
+                if (ri) nv = cj ? ip : rb[v];
+                else if (cj) nv = -ci * ip;
+                a[u][v] = nv;
+            }
+        }
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v)
+            M[(long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v] = a[u][v];
+}
+
+template <typename AT>
+__device__ __forceinline__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
+    if constexpr (sizeof(AT) == 8) tile_invert_s(sm, M, ld, ti, err);
+    else tile_invert_b4(sm, M, ld, ti, err);
+}
+
+// Sub-tile product: rows [r0, r0 + RR) and columns [c0, c0 + CC) of
+//     out(oi, oj) = sign * tile(xi, xj) * tile(yi, yj)  (+ out if accumulate),
+// 256 threads x BR x BC outputs. In-place use is safe when the output part
+// depends only on the staged part of the aliased input: a row panel
+// (out = P * out) is split by columns, a column panel (out = out * P) by rows.
+template <typename AT, int RR, int CC, int BR, int BC>
+__device__ void subtile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj, int yi, int yj,
+                                int oi, int oj, int r0, int c0, AT sign, bool accumulate) {
+    static_assert((RR / BR) * (CC / BC) == 256, "256 threads");
+    AT (*X)[TILE + 1] = sm.X;   // X[r][k], r < RR
+    AT (*Y)[TILE + 1] = sm.Y;   // Y[k][c], c < CC
+    // stage both parts with 16-byte loads, all issued before any is consumed
+    constexpr int VEC = 16 / sizeof(AT);
+    using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    constexpr int NX = RR * TILE / VEC / 256, NY = TILE * CC / VEC / 256;
+    static_assert(NX >= 1 && NY >= 1, "staging split");
+    V16 bx[NX], by[NY];
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+        const int e = threadIdx.x + 256 * m;            // vector index
+        const int r = e / (TILE / VEC), k = (e % (TILE / VEC)) * VEC;
+        bx[m] = __ldcg(reinterpret_cast<const V16 *>(M + (long long)(xi * TILE + r0 + r) * ld +
+                                                     xj * TILE + k));
+    }
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        const int k = e / (CC / VEC), c = (e % (CC / VEC)) * VEC;
+        by[m] = __ldcg(reinterpret_cast<const V16 *>(M + (long long)(yi * TILE + k) * ld + yj * TILE +
+                                                     c0 + c));
+    }
+#pragma unroll
+    for (int m = 0; m < NX; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        const int r = e / (TILE / VEC), k = (e % (TILE / VEC)) * VEC;
+        const AT *v = reinterpret_cast<const AT *>(&bx[m]);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) X[r][k + q] = v[q];
+    }
+#pragma unroll
+    for (int m = 0; m < NY; ++m) {
+        const int e = threadIdx.x + 256 * m;
+        const int k = e / (CC / VEC), c = (e % (CC / VEC)) * VEC;
+        const AT *v = reinterpret_cast<const AT *>(&by[m]);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) Y[k][c + q] = v[q];
+    }
+    __syncthreads();
+    constexpr int TPR = CC / BC;
+    const int rr = (threadIdx.x / TPR) * BR, cc = (threadIdx.x % TPR) * BC;
+    AT acc[BR][BC];
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+        for (int v = 0; v < BC; ++v) acc[u][v] = 0;
+#pragma unroll 4
+    for (int k = 0; k < TILE; ++k) {
+        AT xa[BR], yb[BC];
+#pragma unroll
+        for (int u = 0; u < BR; ++u) xa[u] = X[rr + u][k];
+#pragma unroll
+        for (int v = 0; v < BC; ++v) yb[v] = Y[k][cc + v];
+#pragma unroll
+        for (int u = 0; u < BR; ++u)
+#pragma unroll
+            for (int v = 0; v < BC; ++v) acc[u][v] += xa[u] * yb[v];
+    }
+    __syncthreads();   // the output may alias a staged input
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+        for (int v = 0; v < BC; ++v) {
+            AT *o = M + (long long)(oi * TILE + r0 + rr + u) * ld + oj * TILE + c0 + cc + v;
             *o = accumulate ? __ldcg(o) + sign * acc[u][v] : sign * acc[u][v];
         }
 }
@@ -392,7 +569,7 @@ __device__ void tile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj, in
 template <typename AT>
 struct FacArgs {
     AT *D, *C, *F;
-    const int *lo_q, *up_q;
+    const int *lo_q, *up_q, *lo_n, *up_n;
     const AT *lo_v, *up_v;
     int T, nt, nb;
     GridBar *bar;
@@ -401,20 +578,47 @@ struct FacArgs {
 
 // Out[r0+i][c] (=, -=) sum_e M[r0+i][uq[c][e]] uv[c][e] for a chunk of FROWS rows
 template <typename AT>
-__device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, const AT *uv, int T,
-                              int r0, bool subtract) {
-    for (int e = threadIdx.x; e < FROWS * T; e += blockDim.x)
-        rows[e] = __ldcg(M + (long long)r0 * T + e);
+__device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, const AT *uv,
+                              const int *un, int T, int r0, bool subtract) {
+    {
+        // FROWS x T contiguous values, 16-byte loads in batches of 8 per thread
+        constexpr int VEC = 16 / sizeof(AT);
+        using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+        const V16 *src = reinterpret_cast<const V16 *>(M + (long long)r0 * T);
+        V16 *dst = reinterpret_cast<V16 *>(rows);
+        const int nv = FROWS * T / VEC;
+        for (int base = 0; base < nv; base += 8 * 256) {
+            V16 buf[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int e = base + threadIdx.x + 256 * m;
+                if (e < nv) buf[m] = __ldcg(src + e);
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                const int e = base + threadIdx.x + 256 * m;
+                if (e < nv) dst[e] = buf[m];
+            }
+        }
+    }
     __syncthreads();
     for (int c = threadIdx.x; c < T; c += blockDim.x) {
         AT acc[FROWS] = {};
-        const int *q = uq + (long long)c * ELLW;
-        const AT *v = uv + (long long)c * ELLW;
-        for (int e = 0; e < ELLW; ++e) {
-            const int qe = q[e];
-            const AT ve = v[e];
+        const int ne = un[c];
+        // transposed ELL: entry e of column c at [e * T + c] (coalesced)
+        for (int e0 = 0; e0 < ne; e0 += 8) {
+            int qb[8];
+            AT vb[8];
 #pragma unroll
-            for (int i = 0; i < FROWS; ++i) acc[i] += rows[i * T + qe] * ve;
+            for (int m = 0; m < 8; ++m) {
+                const bool ok = e0 + m < ne;
+                qb[m] = ok ? uq[(long long)(e0 + m) * T + c] : 0;
+                vb[m] = ok ? uv[(long long)(e0 + m) * T + c] : (AT)0;
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+#pragma unroll
+                for (int i = 0; i < FROWS; ++i) acc[i] += rows[i * T + qb[m]] * vb[m];
         }
 #pragma unroll
         for (int i = 0; i < FROWS; ++i) {
@@ -434,26 +638,55 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
     const long long bsz = (long long)T * T;
     for (int k = 0; k < a.nb; ++k) {
         AT *Dk = a.D + k * bsz;
+        // prologue: pivot tile 0 and the row panel of step 0
         if (b == 0) tile_invert(ts, Dk, T, 0, a.err);
         if (!grid_barrier(a.bar, a.err)) return;
+        for (int it = b; it < 4 * (nt - 1); it += G) {
+            const int j = (it >> 2) + 1, q = it & 3;
+            subtile_product<AT, 64, 16, 2, 2>(ts, Dk, T, 0, 0, 0, j, 0, j, 0, 16 * q, (AT)1, false);
+        }
+        if (!grid_barrier(a.bar, a.err)) return;
         for (int p = 0; p < nt; ++p) {
-            for (int it = b; it < nt - 1; it += G) {          // row panel: D_pj = P D_pj
-                const int j = it < p ? it : it + 1;
-                tile_product(ts, Dk, T, p, p, p, j, p, j, (AT)1, false);
-            }
-            if (!grid_barrier(a.bar, a.err)) return;
-            for (int it = b; it < (nt - 1) * (nt - 1); it += G) {   // D_ij -= D_ip D_pj
-                const int bi = it / (nt - 1), bj = it % (nt - 1);
+            const bool nxt = p + 1 < nt;
+            // phase A: trailing update D_ij -= D_ip D_pj (i, j != p); the next
+            // pivot tile is updated and inverted by one CTA (item 0)
+            const int nu = (nt - 1) * (nt - 1);
+            for (int it = b; it < nu; it += G) {
+                const int t = nxt ? (it == 0 ? p * (nt - 1) + p : (it <= p * (nt - 1) + p ? it - 1 : it))
+                                  : it;
+                const int bi = t / (nt - 1), bj = t % (nt - 1);
                 const int i = bi < p ? bi : bi + 1, j = bj < p ? bj : bj + 1;
-                tile_product(ts, Dk, T, i, p, p, j, i, j, (AT)-1, true);
+                subtile_product<AT, 64, 64, 4, 4>(ts, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
+                if (nxt && it == 0) {
+                    __syncthreads();
+                    tile_invert(ts, Dk, T, p + 1, a.err);
+                }
             }
             if (!grid_barrier(a.bar, a.err)) return;
-            for (int it = b; it < nt; it += G) {              // D_ip = -D_ip P ; next pivot tile
-                if (it == nt - 1) {
-                    if (p + 1 < nt) tile_invert(ts, Dk, T, p + 1, a.err);
+            // phase B: column panel of step p (D_ip = -D_ip P_p, i != p, p+1),
+            // row panel of step p+1 (D_{p+1,j} = P_{p+1} D_{p+1,j}, j != p, p+1),
+            // and tile (p+1, p) = P_{p+1} (-D_{p+1,p} P_p)
+            const int ncol = nt - 1 - (nxt ? 1 : 0);
+            const int nrow = nxt ? nt - 2 : 0;
+            const int nB = 4 * ncol + 4 * nrow + (nxt ? 1 : 0);
+            for (int it = b; it < nB; it += G) {
+                if (it < 4 * ncol) {
+                    const int t = it >> 2, q = it & 3;
+                    const int i = t < p ? t : t + 2;      // skip p and p + 1
+                    subtile_product<AT, 16, 64, 2, 2>(ts, Dk, T, i, p, p, p, i, p, 16 * q, 0, (AT)-1,
+                                                      false);
+                } else if (it < 4 * ncol + 4 * nrow) {
+                    const int e = it - 4 * ncol;
+                    const int t = e >> 2, q = e & 3;
+                    const int j = t < p ? t : t + 2;      // skip p and p + 1
+                    subtile_product<AT, 64, 16, 2, 2>(ts, Dk, T, p + 1, p + 1, p + 1, j, p + 1, j, 0,
+                                                      16 * q, (AT)1, false);
                 } else {
-                    const int i = it < p ? it : it + 1;
-                    tile_product(ts, Dk, T, i, p, p, p, i, p, (AT)-1, false);
+                    subtile_product<AT, 64, 64, 4, 4>(ts, Dk, T, p + 1, p, p, p, p + 1, p, 0, 0, (AT)-1,
+                                                      false);
+                    __syncthreads();
+                    subtile_product<AT, 64, 64, 4, 4>(ts, Dk, T, p + 1, p + 1, p + 1, p, p + 1, p, 0, 0,
+                                                      (AT)1, false);
                 }
             }
             if (!grid_barrier(a.bar, a.err)) return;
@@ -462,25 +695,36 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
             AT *Ck = a.C + k * bsz, *Fk = a.F + k * bsz;
             const long long ell = (long long)T * ELLW;
             const int *lq = a.lo_q + k * ell, *uq = a.up_q + k * ell;
+            const int *ln = a.lo_n + (long long)k * T, *un = a.up_n + (long long)k * T;
             const AT *lv = a.lo_v + k * ell, *uv = a.up_v + k * ell;
             const int nchunk = T / FROWS;
             for (int it = b; it < T + nchunk; it += G) {
                 if (it < T) {                                  // C_k row = Lo_k row * E_k
                     const int r = it;
+                    const int ne = ln[r];
                     for (int c = threadIdx.x; c < T; c += blockDim.x) {
                         AT acc = 0;
-                        for (int e = 0; e < ELLW; ++e)
-                            acc += lv[(long long)r * ELLW + e] *
-                                   __ldcg(Dk + (long long)lq[(long long)r * ELLW + e] * T + c);
+                        for (int e0 = 0; e0 < ne; e0 += 8) {   // 8 row loads in flight
+                            AT eb[8], vb[8];
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) {
+                                const bool ok = e0 + m < ne;
+                                const long long le = (long long)r * ELLW + e0 + m;
+                                vb[m] = ok ? lv[le] : (AT)0;
+                                eb[m] = ok ? __ldcg(Dk + (long long)lq[le] * T + c) : (AT)0;
+                            }
+#pragma unroll
+                            for (int m = 0; m < 8; ++m) acc += vb[m] * eb[m];
+                        }
                         Ck[(long long)r * T + c] = acc;
                     }
                 } else {                                       // F_k = E_k Up_k
-                    rows_times_up(rows, Dk, Fk, uq, uv, T, (it - T) * FROWS, false);
+                    rows_times_up(rows, Dk, Fk, uq, uv, un, T, (it - T) * FROWS, false);
                 }
             }
             if (!grid_barrier(a.bar, a.err)) return;
             for (int it = b; it < nchunk; it += G)             // D_{k+1} -= C_k Up_k
-                rows_times_up(rows, Ck, Dk + bsz, uq, uv, T, it * FROWS, true);
+                rows_times_up(rows, Ck, Dk + bsz, uq, uv, un, T, it * FROWS, true);
             if (!grid_barrier(a.bar, a.err)) return;
         }
     }
@@ -504,19 +748,59 @@ struct SolArgs {
     int *err;
 };
 
+// dot of a matrix row with a shared-memory vector, 16-byte loads (T is a
+// multiple of 64 and rows start 16-byte aligned)
+// (GX: the vector is in global memory and read through L2 only)
+template <typename AT, bool GX = false>
+__device__ __forceinline__ AT row_dot(const AT *row, const AT *xs, int T, int lane) {
+    AT acc = 0;
+    auto X = [&](int c) { return GX ? __ldcg(xs + c) : xs[c]; };
+    constexpr int VEC = 16 / sizeof(AT);
+    using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    const V16 *rv = reinterpret_cast<const V16 *>(row);
+    const int nv = T / VEC;
+    for (int base = lane; base < nv; base += 32 * 8) {
+        V16 buf[8];
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (base + 32 * m < nv) buf[m] = __ldcg(rv + base + 32 * m);
+#pragma unroll
+        for (int m = 0; m < 8; ++m)
+            if (base + 32 * m < nv) {
+                const int c = (base + 32 * m) * VEC;
+                const AT *v = reinterpret_cast<const AT *>(&buf[m]);
+#pragma unroll
+                for (int q = 0; q < VEC; ++q) acc += v[q] * X(c + q);
+            }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    return acc;
+}
+
 // y[r] (=, -=) sum_c M[r][c] xs[c] over rows distributed to warps of the grid
 template <typename AT>
 __device__ void grid_gemv(const AT *M, const AT *xsrc, AT *y, int T, AT *xs, bool subtract) {
-    for (int c = threadIdx.x; c < T; c += blockDim.x) xs[c] = __ldcg(xsrc + c);
+    {
+        using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+        const int nv = T / (16 / (int)sizeof(AT));
+        const V16 *src = reinterpret_cast<const V16 *>(xsrc);
+        V16 *dst = reinterpret_cast<V16 *>(xs);
+        for (int base = threadIdx.x; base < nv; base += 4 * blockDim.x) {
+            V16 buf[4];
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (base + m * (int)blockDim.x < nv) buf[m] = __ldcg(src + base + m * blockDim.x);
+#pragma unroll
+            for (int m = 0; m < 4; ++m)
+                if (base + m * (int)blockDim.x < nv) dst[base + m * blockDim.x] = buf[m];
+        }
+    }
     __syncthreads();
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x / 32;
     for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < T; r += gridDim.x * wpb) {
-        const AT *row = M + (long long)r * T;
-        AT acc = 0;
-        for (int c = lane; c < T; c += 32) acc += __ldcg(row + c) * xs[c];
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const AT acc = row_dot(M + (long long)r * T, xs, T, lane);
         if (lane == 0) y[r] = subtract ? __ldcg(y + r) - acc : acc;
     }
 }
@@ -539,6 +823,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
         const int wx = x1 - x0, wy = y1 - y0;
         const int tot = wx * wy * (z1 - z0);
         AT acc = 0;
+#pragma unroll 4
         for (int e = lane; e < tot; e += 32) {
             const int ax = x0 + e % wx, ay = y0 + (e / wx) % wy, az = z0 + e / (wx * wy);
             const AT w = (AT)w1(P, 0, ax, Ix) * (AT)w1(P, 1, ay, Iy) * (AT)w1(P, 2, az, Iz);
@@ -557,11 +842,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     for (int rr = blockIdx.x * wpb + (threadIdx.x >> 5); rr < G.nb * T; rr += gridDim.x * wpb) {
         const int k = rr / T;
         const AT *row = a.E + k * bsz + (long long)(rr % T) * T;
-        const AT *gk = a.g + (long long)k * T;
-        AT acc = 0;
-        for (int c = lane; c < T; c += 32) acc += __ldcg(row + c) * __ldcg(gk + c);
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        const AT acc = row_dot<AT, true>(row, a.g + (long long)k * T, T, lane);
         if (lane == 0) a.x[rr] = acc;
     }
     if (!grid_barrier(a.bar, a.err)) return;
@@ -673,6 +954,16 @@ static int configure_t(Coarse *c) {
     if (bf < 1 || bs < 1) return RAS_EINVAL;
     c->fac_grid = sms * std::min(bf, 2);
     c->sol_grid = sms * std::min(bs, 2);
+    // tuning knobs: fewer CTAs make the grid barrier cheaper (clamped to the
+    // co-resident maximum, which the cooperative launch requires)
+    if (const char *e = getenv("RAS_COARSE_FACTOR_CTAS")) {
+        const int v = atoi(e);
+        if (v >= 1) c->fac_grid = std::min(v, sms * bf);
+    }
+    if (const char *e = getenv("RAS_COARSE_SOLVE_CTAS")) {
+        const int v = atoi(e);
+        if (v >= 1) c->sol_grid = std::min(v, sms * bs);
+    }
     return RAS_OK;
 }
 
@@ -744,6 +1035,7 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
     if ((rc = dalloc(&p_ac, (size_t)125 * c->Nc * c->esz)) || (rc = dalloc(&p_d, c->nb * bsz * c->esz)) ||
         (rc = dalloc(&p_c, nbm1 * bsz * c->esz)) || (rc = dalloc(&p_f, nbm1 * bsz * c->esz)) ||
         (rc = dalloc(&c->lo_q, nbm1 * c->T * ELLW)) || (rc = dalloc(&c->up_q, nbm1 * c->T * ELLW)) ||
+        (rc = dalloc(&c->lo_n, nbm1 * c->T)) || (rc = dalloc(&c->up_n, nbm1 * c->T)) ||
         (rc = dalloc(&p_lv, nbm1 * c->T * ELLW * c->esz)) ||
         (rc = dalloc(&p_uv, nbm1 * c->T * ELLW * c->esz)) ||
         (rc = dalloc(&p_g, (size_t)c->nb * c->T * c->esz)) ||
@@ -758,7 +1050,9 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
         cudaMemset(c->g, 0, (size_t)c->nb * c->T * c->esz) != cudaSuccess ||
         cudaMemset(c->x, 0, (size_t)c->nb * c->T * c->esz) != cudaSuccess ||
         cudaMemset(c->lo_q, 0, nbm1 * c->T * ELLW * sizeof(int)) != cudaSuccess ||
-        cudaMemset(c->up_q, 0, nbm1 * c->T * ELLW * sizeof(int)) != cudaSuccess)
+        cudaMemset(c->up_q, 0, nbm1 * c->T * ELLW * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->lo_n, 0, nbm1 * c->T * sizeof(int)) != cudaSuccess ||
+        cudaMemset(c->up_n, 0, nbm1 * c->T * sizeof(int)) != cudaSuccess)
         return fail(RAS_ECUDA);
     rc = c->prec == 64 ? configure_t<double>(c) : configure_t<float>(c);
     if (rc) return fail(rc);
@@ -773,7 +1067,7 @@ void coarse_free(Coarse *c) {
         dfree(c->d_lo[a]); dfree(c->d_hi[a]);
     }
     dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err); dfree(c->d_bar);
-    dfree(c->lo_q); dfree(c->up_q);
+    dfree(c->lo_q); dfree(c->up_q); dfree(c->lo_n); dfree(c->up_n);
     for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x})
         if (p) cudaFree(p);
     delete c;
@@ -793,11 +1087,12 @@ static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
     RAS_LAUNCHED();
     if (c->nb > 1) {
         k_ell<AT><<<grid_of((long long)(c->nb - 1) * c->T), 256, 0, st>>>(
-            Ac, c->d_pos, c->d_cell, G, c->lo_q, (AT *)c->lo_v, c->up_q, (AT *)c->up_v, c->d_err);
+            Ac, c->d_pos, c->d_cell, G, c->lo_q, (AT *)c->lo_v, c->up_q, (AT *)c->up_v, c->lo_n,
+            c->up_n, c->d_err);
         RAS_LAUNCHED();
     }
     RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
-    FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, c->lo_q, c->up_q, (const AT *)c->lo_v,
+    FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, c->lo_q, c->up_q, c->lo_n, c->up_n, (const AT *)c->lo_v,
                    (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->d_bar, c->d_err};
     void *args[] = {&fa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor<AT>, dim3(c->fac_grid),
