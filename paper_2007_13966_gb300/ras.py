@@ -22,7 +22,7 @@ RAS_EINVAL, RAS_ECUDA, RAS_ENOMEM, RAS_ENAN, RAS_EZEROPIVOT = -1, -2, -3, -4, -5
 EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_stencil_matvec",
             "ras_setup", "ras_precond_destroy", "ras_factor", "ras_apply", "gmres_solve",
             "newton_step", "ras_status_string", "ras_last_error", "ras_kernel_launches",
-            "ras_timing_enable", "ras_timing_read", "ras_apply_bytes"]
+            "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc"]
 
 
 class Grid(C.Structure):
@@ -107,6 +107,7 @@ def lib():
             "ras_timing_enable": (i, [vp, i]),
             "ras_timing_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong), i]),
             "ras_apply_bytes": (d, [vp]),
+            "ras_norm2_noalloc": (i, [vp, C.c_longlong, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -151,6 +152,13 @@ def stencil_struct(J):
     for s in range(7):
         st.c[s] = J[s].data_ptr()
     return st
+
+
+def norm2_noalloc(x, out, stream=None):
+    """||x||_2 into the one-element device tensor `out`; allocates nothing
+    (partial sums in the library's static device array)."""
+    check(lib().ras_norm2_noalloc(_ptr(x), x.numel(), _ptr(out), _stream(stream)),
+          "ras_norm2_noalloc")
 
 
 def kernel_launches() -> int:
