@@ -10,6 +10,7 @@
 #include "schwarz.cuh"
 
 #include <algorithm>
+#include <cstdlib>
 #include <map>
 #include <tuple>
 
@@ -151,9 +152,33 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
     const int bx = sh.bx, by = sh.by, bxy = sh.bx * sh.by;
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
-    for (int idx = threadIdx.x; idx < sh.ncell; idx += blockDim.x) {
-        const int i = idx % bx, j = (idx / bx) % by, k = idx / bxy;
-        Y[idx] = (Acc)P.r[g0 + i + (long long)nx * j + (long long)nxy * k];
+    // by x-rows of the box: lanes along x (coalesced), 4 rows in flight per warp
+    const int nrow = by * sh.bz;
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    for (int rbase = wid; rbase < nrow; rbase += 4 * nw) {
+        for (int i0 = 0; i0 < bx; i0 += 64) {
+            double v[4][2];
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int row = rbase + m * nw;
+                const int j = row % by, k = row / by;
+                const double *src = P.r + g0 + (long long)nx * j + (long long)nxy * k;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = i0 + lane + 32 * h;
+                    if (row < nrow && i < bx) v[m][h] = __ldg(src + i);
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < 4; ++m) {
+                const int row = rbase + m * nw;
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int i = i0 + lane + 32 * h;
+                    if (row < nrow && i < bx) Y[row * bx + i] = (Acc)v[m][h];
+                }
+            }
+        }
     }
 
     for (int t = 0; t < nstage; ++t) {
@@ -211,14 +236,16 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
     }
     cp_async_wait<0>();
 
-    // (R_i^0)^T: write the owned cells
-    for (int idx = threadIdx.x; idx < sh.ncell; idx += blockDim.x) {
-        const int i = idx % bx, j = (idx / bx) % by, k = idx / bxy;
-        if (i < si.ox0 || i >= si.ox1 || j < si.oy0 || j >= si.oy1 || k < si.oz0 || k >= si.oz1)
-            continue;
-        const long long g = g0 + i + (long long)nx * j + (long long)nxy * k;
-        const double v = (double)Y[idx];
-        if (P.accumulate) P.z[g] += v; else P.z[g] = v;
+    // (R_i^0)^T: write the owned cells, by x-rows (coalesced)
+    const int ox0 = si.ox0, ox1 = si.ox1;
+    for (int row = wid; row < nrow; row += nw) {
+        const int j = row % by, k = row / by;
+        if (j < si.oy0 || j >= si.oy1 || k < si.oz0 || k >= si.oz1) continue;
+        double *dst = P.z + g0 + (long long)nx * j + (long long)nxy * k;
+        for (int i = ox0 + lane; i < ox1; i += 32) {
+            const double v = (double)Y[row * bx + i];
+            if (P.accumulate) dst[i] += v; else dst[i] = v;
+        }
     }
 }
 
@@ -436,7 +463,10 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
         sh.nchunk = nch;
     }
     R.block = std::min(512, std::max(64, ((maxw_all + 31) / 32) * 32));
-    if (R.block > 256 && maxw_all < 384) R.block = 256;
+    if (const char *e = getenv("RAS_APPLY_THREADS")) {   // tuning knob
+        const int v = atoi(e);
+        if (v >= 32 && v <= 512 && v % 32 == 0) R.block = v;
+    }
     R.ycap = (ycap + 3) & ~3;
     R.lcap = (lcap + 3) & ~3;
     const size_t acc = prec == 64 ? 8 : 4;
@@ -520,10 +550,14 @@ int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t
     return RAS_OK;
 }
 
-// algorithmic bytes of one apply: both factor record sets once, r over the
-// overlapped boxes (FP64), z over the owned cells (FP64)
+// Algorithmic bytes of one apply: the ILU(0) factors once (7 values per
+// overlapped cell: 3 lower, 3 upper off-diagonals and the inverse pivot, at the
+// storage precision), r read once and z written once in FP64. (The kernel's
+// records carry the inverse pivot twice and r is re-read over the overlap;
+// those bytes are not counted.)
 double ras1_bytes(const Ras1 &R) {
-    return 2.0 * (double)R.ncell_total * R.rec_bytes + 8.0 * (double)R.ncell_total + 8.0 * (double)R.nown;
+    const double val = R.prec == 64 ? 8.0 : (R.prec == 32 ? 4.0 : 2.0);
+    return 7.0 * val * (double)R.ncell_total + 16.0 * (double)R.N;
 }
 
 }  // namespace ras
