@@ -55,6 +55,7 @@ struct Coarse {
     int *lo_n = nullptr, *up_n = nullptr;            // ELL entries used per row / column
     void *lo_v = nullptr, *up_v = nullptr;           // ELL values
     void *g = nullptr, *x = nullptr;                 // [nb*T]
+    void *Zs = nullptr;                              // scratch tile strip [TILE][T]
     int *d_err = nullptr;
     GridBar *d_bar = nullptr;
     size_t esz = 8;
@@ -263,27 +264,28 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-// returns false if this or another CTA has recorded an error (then callers
-// stop doing work but still return from the kernel promptly)
-__device__ bool grid_barrier(GridBar *bar, int *err) {
+// Grid barrier on a monotonically increasing arrival counter: barrier number e
+// (1, 2, ...) of a launch completes when the counter reaches e * gridDim.x, so
+// arrival is one non-returning atomic add and the wait a polled acquire load.
+// `epoch` is the caller's count of barriers passed (same in every thread); the
+// counter is reset to zero before every launch. Returns false if this or
+// another CTA has recorded an error (callers then stop working but return from
+// the kernel promptly); the wait is bounded (ERR_TIMEOUT).
+__device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch) {
     __shared__ int s_ok;
+    ++epoch;
     __syncthreads();
     if (threadIdx.x == 0) {
         int ok = (ld_acquire((const unsigned *)err) == 0);
         if (ok) {
-            const unsigned g = ld_acquire(&bar->gen);
+            const unsigned target = epoch * gridDim.x;
             __threadfence();
-            if (atomicAdd(&bar->count, 1u) == gridDim.x - 1) {
-                atomicExch(&bar->count, 0u);
-                __threadfence();
-                atomicAdd(&bar->gen, 1u);
-            } else {
-                long long it = 0;
-                while (ld_acquire(&bar->gen) == g) {
-                    if (++it > BAR_POLLS) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
-                    if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
-                    __nanosleep(32);
-                }
+            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+            long long it = 0;
+            while (ld_acquire(&bar->count) < target) {
+                if (++it > BAR_POLLS) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
+                if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
+                __nanosleep(20);
             }
             __threadfence();
         }
@@ -491,8 +493,9 @@ __device__ __forceinline__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int
 // depends only on the staged part of the aliased input: a row panel
 // (out = P * out) is split by columns, a column panel (out = out * P) by rows.
 template <typename AT, int RR, int CC, int BR, int BC>
-__device__ void subtile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj, int yi, int yj,
-                                int oi, int oj, int r0, int c0, AT sign, bool accumulate) {
+__device__ void subtile_product(TileSmem<AT> &sm, const AT *Xb, const AT *Yb, AT *Ob, int ld, int xi,
+                                int xj, int yi, int yj, int oi, int oj, int r0, int c0, AT sign,
+                                bool accumulate) {
     static_assert((RR / BR) * (CC / BC) == 256, "256 threads");
     AT (*X)[TILE + 1] = sm.X;   // X[r][k], r < RR
     AT (*Y)[TILE + 1] = sm.Y;   // Y[k][c], c < CC
@@ -506,14 +509,14 @@ __device__ void subtile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj,
     for (int m = 0; m < NX; ++m) {
         const int e = threadIdx.x + 256 * m;            // vector index
         const int r = e / (TILE / VEC), k = (e % (TILE / VEC)) * VEC;
-        bx[m] = __ldcg(reinterpret_cast<const V16 *>(M + (long long)(xi * TILE + r0 + r) * ld +
+        bx[m] = __ldcg(reinterpret_cast<const V16 *>(Xb + (long long)(xi * TILE + r0 + r) * ld +
                                                      xj * TILE + k));
     }
 #pragma unroll
     for (int m = 0; m < NY; ++m) {
         const int e = threadIdx.x + 256 * m;
         const int k = e / (CC / VEC), c = (e % (CC / VEC)) * VEC;
-        by[m] = __ldcg(reinterpret_cast<const V16 *>(M + (long long)(yi * TILE + k) * ld + yj * TILE +
+        by[m] = __ldcg(reinterpret_cast<const V16 *>(Yb + (long long)(yi * TILE + k) * ld + yj * TILE +
                                                      c0 + c));
     }
 #pragma unroll
@@ -557,7 +560,7 @@ __device__ void subtile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj,
     for (int u = 0; u < BR; ++u)
 #pragma unroll
         for (int v = 0; v < BC; ++v) {
-            AT *o = M + (long long)(oi * TILE + r0 + rr + u) * ld + oj * TILE + c0 + cc + v;
+            AT *o = Ob + (long long)(oi * TILE + r0 + rr + u) * ld + oj * TILE + c0 + cc + v;
             *o = accumulate ? __ldcg(o) + sign * acc[u][v] : sign * acc[u][v];
         }
 }
@@ -569,6 +572,7 @@ __device__ void subtile_product(TileSmem<AT> &sm, AT *M, int ld, int xi, int xj,
 template <typename AT>
 struct FacArgs {
     AT *D, *C, *F;
+    AT *Z;   // scratch: 64 rows x T (tile (0, 0) used) for -D_{p+1,p} P_p
     const int *lo_q, *up_q, *lo_n, *up_n;
     const AT *lo_v, *up_v;
     int T, nt, nb;
@@ -636,60 +640,66 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
     AT *rows = reinterpret_cast<AT *>(smem_raw);
     const int T = a.T, nt = a.nt, G = gridDim.x, b = blockIdx.x;
     const long long bsz = (long long)T * T;
+    unsigned epoch = 0;
     for (int k = 0; k < a.nb; ++k) {
         AT *Dk = a.D + k * bsz;
         // prologue: pivot tile 0 and the row panel of step 0
         if (b == 0) tile_invert(ts, Dk, T, 0, a.err);
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, epoch)) return;
         for (int it = b; it < 4 * (nt - 1); it += G) {
             const int j = (it >> 2) + 1, q = it & 3;
-            subtile_product<AT, 64, 16, 2, 2>(ts, Dk, T, 0, 0, 0, j, 0, j, 0, 16 * q, (AT)1, false);
+            subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, 0, 0, 0, j, 0, j, 0, 16 * q, (AT)1, false);
         }
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, epoch)) return;
         for (int p = 0; p < nt; ++p) {
             const bool nxt = p + 1 < nt;
             // phase A: trailing update D_ij -= D_ip D_pj (i, j != p); the next
             // pivot tile is updated and inverted by one CTA (item 0)
             const int nu = (nt - 1) * (nt - 1);
-            for (int it = b; it < nu; it += G) {
+            const int nz = nxt ? 4 : 0;   // Z = -D_{p+1,p} P_p into the scratch tile (row strips)
+            for (int it = b; it < nu + nz; it += G) {
+                if (it >= nu) {
+                    const int q = it - nu;
+                    subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, a.Z, T, p + 1, p, p, p, 0, 0, 16 * q, 0,
+                                                      (AT)-1, false);
+                    continue;
+                }
                 const int t = nxt ? (it == 0 ? p * (nt - 1) + p : (it <= p * (nt - 1) + p ? it - 1 : it))
                                   : it;
                 const int bi = t / (nt - 1), bj = t % (nt - 1);
                 const int i = bi < p ? bi : bi + 1, j = bj < p ? bj : bj + 1;
-                subtile_product<AT, 64, 64, 4, 4>(ts, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
+                subtile_product<AT, 64, 64, 4, 4>(ts, Dk, Dk, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
                 if (nxt && it == 0) {
                     __syncthreads();
                     tile_invert(ts, Dk, T, p + 1, a.err);
                 }
             }
-            if (!grid_barrier(a.bar, a.err)) return;
+            if (!grid_barrier(a.bar, a.err, epoch)) return;
             // phase B: column panel of step p (D_ip = -D_ip P_p, i != p, p+1),
             // row panel of step p+1 (D_{p+1,j} = P_{p+1} D_{p+1,j}, j != p, p+1),
             // and tile (p+1, p) = P_{p+1} (-D_{p+1,p} P_p)
             const int ncol = nt - 1 - (nxt ? 1 : 0);
             const int nrow = nxt ? nt - 2 : 0;
-            const int nB = 4 * ncol + 4 * nrow + (nxt ? 1 : 0);
+            const int nB = 4 * ncol + 4 * nrow + (nxt ? 4 : 0);
             for (int it = b; it < nB; it += G) {
                 if (it < 4 * ncol) {
                     const int t = it >> 2, q = it & 3;
                     const int i = t < p ? t : t + 2;      // skip p and p + 1
-                    subtile_product<AT, 16, 64, 2, 2>(ts, Dk, T, i, p, p, p, i, p, 16 * q, 0, (AT)-1,
-                                                      false);
+                    subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, Dk, T, i, p, p, p, i, p, 16 * q, 0,
+                                                      (AT)-1, false);
                 } else if (it < 4 * ncol + 4 * nrow) {
                     const int e = it - 4 * ncol;
                     const int t = e >> 2, q = e & 3;
                     const int j = t < p ? t : t + 2;      // skip p and p + 1
-                    subtile_product<AT, 64, 16, 2, 2>(ts, Dk, T, p + 1, p + 1, p + 1, j, p + 1, j, 0,
+                    subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, p + 1, p + 1, p + 1, j, p + 1, j,
+                                                      0, 16 * q, (AT)1, false);
+                } else {                                  // D_{p+1,p} = P_{p+1} Z (column strips)
+                    const int q = it - 4 * ncol - 4 * nrow;
+                    subtile_product<AT, 64, 16, 2, 2>(ts, Dk, a.Z, Dk, T, p + 1, p + 1, 0, 0, p + 1, p, 0,
                                                       16 * q, (AT)1, false);
-                } else {
-                    subtile_product<AT, 64, 64, 4, 4>(ts, Dk, T, p + 1, p, p, p, p + 1, p, 0, 0, (AT)-1,
-                                                      false);
-                    __syncthreads();
-                    subtile_product<AT, 64, 64, 4, 4>(ts, Dk, T, p + 1, p + 1, p + 1, p, p + 1, p, 0, 0,
-                                                      (AT)1, false);
                 }
             }
-            if (!grid_barrier(a.bar, a.err)) return;
+            if (!grid_barrier(a.bar, a.err, epoch)) return;
         }
         if (k + 1 < a.nb) {
             AT *Ck = a.C + k * bsz, *Fk = a.F + k * bsz;
@@ -722,10 +732,10 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
                     rows_times_up(rows, Dk, Fk, uq, uv, un, T, (it - T) * FROWS, false);
                 }
             }
-            if (!grid_barrier(a.bar, a.err)) return;
+            if (!grid_barrier(a.bar, a.err, epoch)) return;
             for (int it = b; it < nchunk; it += G)             // D_{k+1} -= C_k Up_k
                 rows_times_up(rows, Ck, Dk + bsz, uq, uv, un, T, it * FROWS, true);
-            if (!grid_barrier(a.bar, a.err)) return;
+            if (!grid_barrier(a.bar, a.err, epoch)) return;
         }
     }
 }
@@ -814,6 +824,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     const int T = G.T;
     const long long bsz = (long long)T * T;
     const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
+    unsigned epoch = 0;
     // g[pos(I)] = sum_a P(a, I) t[a]  (warp per coarse cell)
     for (int I = blockIdx.x * wpb + (threadIdx.x >> 5); I < G.Nc; I += gridDim.x * wpb) {
         const int Ix = I % G.cx, Iy = (I / G.cx) % G.cy, Iz = I / (G.cx * G.cy);
@@ -833,10 +844,10 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
         for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
         if (lane == 0) a.g[a.pos[I]] = acc;
     }
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, epoch)) return;
     for (int k = 1; k < G.nb; ++k) {               // g_k -= C_{k-1} g_{k-1}
         grid_gemv(a.C + (k - 1) * bsz, a.g + (long long)(k - 1) * T, a.g + (long long)k * T, T, xs, true);
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
     // x_k = E_k g_k for every block
     for (int rr = blockIdx.x * wpb + (threadIdx.x >> 5); rr < G.nb * T; rr += gridDim.x * wpb) {
@@ -845,10 +856,10 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
         const AT acc = row_dot<AT, true>(row, a.g + (long long)k * T, T, lane);
         if (lane == 0) a.x[rr] = acc;
     }
-    if (!grid_barrier(a.bar, a.err)) return;
+    if (!grid_barrier(a.bar, a.err, epoch)) return;
     for (int k = G.nb - 2; k >= 0; --k) {          // x_k -= F_k x_{k+1}
         grid_gemv(a.F + k * bsz, a.x + (long long)(k + 1) * T, a.x + (long long)k * T, T, xs, true);
-        if (!grid_barrier(a.bar, a.err)) return;
+        if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
     // z (+)= P x
     const long long N = (long long)G.nx * G.ny * G.nz;
@@ -1041,6 +1052,11 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
         (rc = dalloc(&p_g, (size_t)c->nb * c->T * c->esz)) ||
         (rc = dalloc(&p_x, (size_t)c->nb * c->T * c->esz)))
         return fail(rc);
+    {
+        unsigned char *p_z = nullptr;
+        if ((rc = dalloc(&p_z, (size_t)TILE * c->T * c->esz))) return fail(rc);
+        c->Zs = p_z;
+    }
     c->Ac = p_ac; c->D = p_d; c->C = p_c; c->F = p_f; c->lo_v = p_lv; c->up_v = p_uv;
     c->g = p_g; c->x = p_x;
     if (cudaMemcpy(c->d_pos, pos.data(), pos.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
@@ -1068,7 +1084,7 @@ void coarse_free(Coarse *c) {
     }
     dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err); dfree(c->d_bar);
     dfree(c->lo_q); dfree(c->up_q); dfree(c->lo_n); dfree(c->up_n);
-    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x})
+    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs})
         if (p) cudaFree(p);
     delete c;
 }
@@ -1092,7 +1108,7 @@ static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
         RAS_LAUNCHED();
     }
     RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
-    FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, c->lo_q, c->up_q, c->lo_n, c->up_n, (const AT *)c->lo_v,
+    FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n, (const AT *)c->lo_v,
                    (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->d_bar, c->d_err};
     void *args[] = {&fa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor<AT>, dim3(c->fac_grid),
