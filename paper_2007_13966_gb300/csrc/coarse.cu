@@ -56,6 +56,7 @@ struct Coarse {
     void *lo_v = nullptr, *up_v = nullptr;           // ELL values
     void *g = nullptr, *x = nullptr;                 // [nb*T]
     void *Zs = nullptr;                              // scratch tile strip [TILE][T]
+    void *rx = nullptr, *ry = nullptr;               // restriction passes [cx][ny][nz], [cx][cy][nz]
     int *d_err = nullptr;
     GridBar *d_bar = nullptr;
     size_t esz = 8;
@@ -754,6 +755,7 @@ struct SolArgs {
     const int *pos;
     const AT *E, *C, *F;
     AT *g, *x;
+    AT *rx, *ry;
     GridBar *bar;
     int *err;
 };
@@ -788,25 +790,29 @@ __device__ __forceinline__ AT row_dot(const AT *row, const AT *xs, int T, int la
     return acc;
 }
 
+// xs <- xsrc (T values, 16-byte loads, read through L2 only)
+template <typename AT>
+__device__ void stage_vector(const AT *xsrc, AT *xs, int T) {
+    using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    const int nv = T / (16 / (int)sizeof(AT));
+    const V16 *src = reinterpret_cast<const V16 *>(xsrc);
+    V16 *dst = reinterpret_cast<V16 *>(xs);
+    for (int base = threadIdx.x; base < nv; base += 4 * blockDim.x) {
+        V16 buf[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (base + m * (int)blockDim.x < nv) buf[m] = __ldcg(src + base + m * blockDim.x);
+#pragma unroll
+        for (int m = 0; m < 4; ++m)
+            if (base + m * (int)blockDim.x < nv) dst[base + m * blockDim.x] = buf[m];
+    }
+    __syncthreads();
+}
+
 // y[r] (=, -=) sum_c M[r][c] xs[c] over rows distributed to warps of the grid
 template <typename AT>
 __device__ void grid_gemv(const AT *M, const AT *xsrc, AT *y, int T, AT *xs, bool subtract) {
-    {
-        using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
-        const int nv = T / (16 / (int)sizeof(AT));
-        const V16 *src = reinterpret_cast<const V16 *>(xsrc);
-        V16 *dst = reinterpret_cast<V16 *>(xs);
-        for (int base = threadIdx.x; base < nv; base += 4 * blockDim.x) {
-            V16 buf[4];
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (base + m * (int)blockDim.x < nv) buf[m] = __ldcg(src + base + m * blockDim.x);
-#pragma unroll
-            for (int m = 0; m < 4; ++m)
-                if (base + m * (int)blockDim.x < nv) dst[base + m * blockDim.x] = buf[m];
-        }
-    }
-    __syncthreads();
+    stage_vector(xsrc, xs, T);
     const int lane = threadIdx.x & 31;
     const int wpb = blockDim.x / 32;
     for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < T; r += gridDim.x * wpb) {
@@ -825,67 +831,98 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     const long long bsz = (long long)T * T;
     const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
     unsigned epoch = 0;
-    // g[pos(I)] = sum_a P(a, I) t[a]  (warp per coarse cell)
-    for (int I = blockIdx.x * wpb + (threadIdx.x >> 5); I < G.Nc; I += gridDim.x * wpb) {
-        const int Ix = I % G.cx, Iy = (I / G.cx) % G.cy, Iz = I / (G.cx * G.cy);
-        const int x0 = P.lo[0][Ix], x1 = P.hi[0][Ix];
-        const int y0 = P.lo[1][Iy], y1 = P.hi[1][Iy];
-        const int z0 = P.lo[2][Iz], z1 = P.hi[2][Iz];
-        const int wx = x1 - x0, wy = y1 - y0;
-        const int tot = wx * wy * (z1 - z0);
+    // g = R t with R = P^T = Pz^T Py^T Px^T, one axis per pass
+    const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
+    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const long long n1 = (long long)G.cx * G.ny * G.nz;
+    for (long long e = gtid; e < n1; e += gstride) {          // x pass
+        const int Ix = (int)(e % G.cx);
+        const long long yz = e / G.cx;
+        const double *src = a.t + yz * G.nx;
         AT acc = 0;
-#pragma unroll 4
-        for (int e = lane; e < tot; e += 32) {
-            const int ax = x0 + e % wx, ay = y0 + (e / wx) % wy, az = z0 + e / (wx * wy);
-            const AT w = (AT)w1(P, 0, ax, Ix) * (AT)w1(P, 1, ay, Iy) * (AT)w1(P, 2, az, Iz);
-            acc += w * (AT)a.t[ax + (long long)G.nx * (ay + (long long)G.ny * az)];
-        }
-#pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if (lane == 0) a.g[a.pos[I]] = acc;
+        const int x0 = P.lo[0][Ix], x1 = P.hi[0][Ix];
+        for (int ax = x0; ax < x1; ++ax) acc += (AT)w1(P, 0, ax, Ix) * (AT)__ldg(src + ax);
+        a.rx[e] = acc;
     }
     if (!grid_barrier(a.bar, a.err, epoch)) return;
-    for (int k = 1; k < G.nb; ++k) {               // g_k -= C_{k-1} g_{k-1}
-        grid_gemv(a.C + (k - 1) * bsz, a.g + (long long)(k - 1) * T, a.g + (long long)k * T, T, xs, true);
+    const long long n2 = (long long)G.cx * G.cy * G.nz;
+    for (long long e = gtid; e < n2; e += gstride) {          // y pass
+        const int Ix = (int)(e % G.cx), Iy = (int)((e / G.cx) % G.cy);
+        const long long az = e / ((long long)G.cx * G.cy);
+        AT acc = 0;
+        const int y0 = P.lo[1][Iy], y1 = P.hi[1][Iy];
+        for (int ay = y0; ay < y1; ++ay)
+            acc += (AT)w1(P, 1, ay, Iy) * __ldcg(a.rx + Ix + (long long)G.cx * (ay + (long long)G.ny * az));
+        a.ry[e] = acc;
+    }
+    if (!grid_barrier(a.bar, a.err, epoch)) return;
+    for (long long I = gtid; I < G.Nc; I += gstride) {         // z pass
+        const int Ix = (int)(I % G.cx), Iy = (int)((I / G.cx) % G.cy), Iz = (int)(I / ((long long)G.cx * G.cy));
+        AT acc = 0;
+        const int z0 = P.lo[2][Iz], z1 = P.hi[2][Iz];
+        for (int az = z0; az < z1; ++az)
+            acc += (AT)w1(P, 2, az, Iz) * __ldcg(a.ry + Ix + (long long)G.cx * (Iy + (long long)G.cy * az));
+        a.g[a.pos[I]] = acc;
+    }
+    if (!grid_barrier(a.bar, a.err, epoch)) return;
+    // forward: g_k -= C_{k-1} g_{k-1}, and in the same phase x_{k-1} = E_{k-1} g_{k-1}
+    for (int k = 1; k <= G.nb; ++k) {
+        const AT *gp = a.g + (long long)(k - 1) * T;
+        stage_vector(gp, xs, T);
+        const int wpb2 = blockDim.x / 32;
+        const int rows = (k < G.nb) ? 2 * T : T;
+        for (int r = blockIdx.x * wpb2 + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb2) {
+            if (r < T) {   // x_{k-1} row
+                const AT acc = row_dot(a.E + (k - 1) * bsz + (long long)r * T, xs, T, lane);
+                if (lane == 0) a.x[(long long)(k - 1) * T + r] = acc;
+            } else {       // g_k row
+                const int rr = r - T;
+                const AT acc = row_dot(a.C + (k - 1) * bsz + (long long)rr * T, xs, T, lane);
+                AT *y = a.g + (long long)k * T + rr;
+                if (lane == 0) *y = __ldcg(y) - acc;
+            }
+        }
         if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
-    // x_k = E_k g_k for every block
-    for (int rr = blockIdx.x * wpb + (threadIdx.x >> 5); rr < G.nb * T; rr += gridDim.x * wpb) {
-        const int k = rr / T;
-        const AT *row = a.E + k * bsz + (long long)(rr % T) * T;
-        const AT acc = row_dot<AT, true>(row, a.g + (long long)k * T, T, lane);
-        if (lane == 0) a.x[rr] = acc;
-    }
-    if (!grid_barrier(a.bar, a.err, epoch)) return;
     for (int k = G.nb - 2; k >= 0; --k) {          // x_k -= F_k x_{k+1}
         grid_gemv(a.F + k * bsz, a.x + (long long)(k + 1) * T, a.x + (long long)k * T, T, xs, true);
         if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
-    // z (+)= P x
+    // z (+)= P x, four fine cells per thread with their loads in flight together
     const long long N = (long long)G.nx * G.ny * G.nz;
-    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
-         p += (long long)gridDim.x * blockDim.x) {
-        const int ax = (int)(p % G.nx), ay = (int)((p / G.nx) % G.ny),
-                  az = (int)(p / ((long long)G.nx * G.ny));
-        const int Ix[2] = {P.ia[0][ax], P.ib[0][ax]};
-        const int Iy[2] = {P.ia[1][ay], P.ib[1][ay]};
-        const int Iz[2] = {P.ia[2][az], P.ib[2][az]};
-        const AT Wx[2] = {(AT)P.wa[0][ax], (AT)P.wb[0][ax]};
-        const AT Wy[2] = {(AT)P.wa[1][ay], (AT)P.wb[1][ay]};
-        const AT Wz[2] = {(AT)P.wa[2][az], (AT)P.wb[2][az]};
-        AT s = 0;
+    for (long long p0 = gtid; p0 < N; p0 += 4 * gstride) {
+        AT sv[4];
 #pragma unroll
-        for (int u = 0; u < 2; ++u)
+        for (int m = 0; m < 4; ++m) {
+            const long long p = p0 + m * gstride;
+            sv[m] = 0;
+            if (p >= N) continue;
+            const int ax = (int)(p % G.nx), ay = (int)((p / G.nx) % G.ny),
+                      az = (int)(p / ((long long)G.nx * G.ny));
+            const int Ix[2] = {P.ia[0][ax], P.ib[0][ax]};
+            const int Iy[2] = {P.ia[1][ay], P.ib[1][ay]};
+            const int Iz[2] = {P.ia[2][az], P.ib[2][az]};
+            const AT Wx[2] = {(AT)P.wa[0][ax], (AT)P.wb[0][ax]};
+            const AT Wy[2] = {(AT)P.wa[1][ay], (AT)P.wb[1][ay]};
+            const AT Wz[2] = {(AT)P.wa[2][az], (AT)P.wb[2][az]};
+            AT s = 0;
 #pragma unroll
-            for (int v = 0; v < 2; ++v)
+            for (int u = 0; u < 2; ++u)
 #pragma unroll
-                for (int w = 0; w < 2; ++w) {
-                    const AT wt = Wx[w] * Wy[v] * Wz[u];
-                    if (wt == (AT)0) continue;
-                    const int I = Ix[w] + G.cx * (Iy[v] + G.cy * Iz[u]);
-                    s += wt * __ldcg(a.x + a.pos[I]);
-                }
-        if (a.accumulate) a.z[p] += (double)s; else a.z[p] = (double)s;
+                for (int v = 0; v < 2; ++v)
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const AT wt = Wx[w] * Wy[v] * Wz[u];
+                        const int I = Ix[w] + G.cx * (Iy[v] + G.cy * Iz[u]);
+                        if (wt != (AT)0) s += wt * __ldcg(a.x + a.pos[I]);
+                    }
+            sv[m] = s;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const long long p = p0 + m * gstride;
+            if (p < N) { if (a.accumulate) a.z[p] += (double)sv[m]; else a.z[p] = (double)sv[m]; }
+        }
     }
 }
 
@@ -1053,9 +1090,13 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
         (rc = dalloc(&p_x, (size_t)c->nb * c->T * c->esz)))
         return fail(rc);
     {
-        unsigned char *p_z = nullptr;
+        unsigned char *p_z = nullptr, *p_rx = nullptr, *p_ry = nullptr;
         if ((rc = dalloc(&p_z, (size_t)TILE * c->T * c->esz))) return fail(rc);
         c->Zs = p_z;
+        if ((rc = dalloc(&p_rx, (size_t)c->c[0] * c->n[1] * c->n[2] * c->esz))) return fail(rc);
+        c->rx = p_rx;
+        if ((rc = dalloc(&p_ry, (size_t)c->c[0] * c->c[1] * c->n[2] * c->esz))) return fail(rc);
+        c->ry = p_ry;
     }
     c->Ac = p_ac; c->D = p_d; c->C = p_c; c->F = p_f; c->lo_v = p_lv; c->up_v = p_uv;
     c->g = p_g; c->x = p_x;
@@ -1084,7 +1125,7 @@ void coarse_free(Coarse *c) {
     }
     dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err); dfree(c->d_bar);
     dfree(c->lo_q); dfree(c->up_q); dfree(c->lo_n); dfree(c->up_n);
-    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs})
+    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs, c->rx, c->ry})
         if (p) cudaFree(p);
     delete c;
 }
@@ -1136,7 +1177,8 @@ template <typename AT>
 static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st) {
     RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
     SolArgs<AT> sa{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
-                   (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, c->d_bar, c->d_err};
+                   (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
+                   (AT *)c->ry, c->d_bar, c->d_err};
     void *args[] = {&sa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve<AT>, dim3(c->sol_grid),
                                        dim3(256), args, c->sol_smem, st));
