@@ -43,7 +43,7 @@ WORKLOAD = ("3d 128x128x64 lognormal (1.05M cells), two-level V-cycle RAS 8x8x4 
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--factor-prec", type=int, default=32)
@@ -106,7 +106,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.gpu), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "50"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -210,21 +210,20 @@ def load_peaks():
 
 
 def load_traffic(key):
-    """Per-launch DRAM bytes of the kernel from the committed ncu summary, if it
-    was taken on the current kernel (the summary records the source hash)."""
-    path = os.path.join(ROOT, "profiles", "ncu_traffic.json")
-    try:
+    """Per-launch DRAM bytes (ncu dram__bytes_read.sum + dram__bytes_write.sum)
+    of the kernel from the committed profile summary, if the summary was taken
+    on the current source of that kernel (its line records the source hash)."""
+    import glob
+    import re
+    from paper_2007_13966_gb300 import build_lib
+    cur = build_lib.source_hash(build_lib.RAS_APPLY_FILES)
+    for path in sorted(glob.glob(os.path.join(ROOT, "profiles", "*.md"))):
         with open(path) as f:
-            d = json.load(f)
-        ent = d.get(key)
-        if not ent:
-            return None
-        from paper_2007_13966_gb300 import build_lib
-        if ent.get("source_hash") != build_lib.source_hash():
-            return None
-        return float(ent["bytes_per_launch"])
-    except Exception:
-        return None
+            for line in f:
+                m = re.match(r"bench-traffic: (\S+) bytes_per_launch=(\d+) source_hash=(\w+)", line.strip())
+                if m and m.group(1) == key and m.group(3) == cur:
+                    return float(m.group(2))
+    return None
 
 
 def gb300_arm(args):

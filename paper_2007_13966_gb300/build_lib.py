@@ -20,17 +20,23 @@ ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["problem.cu", "schwarz.cu", "precond.cu", "krylov.cu", "coarse.cu", "noalloc.cu"]
 
 
-def source_hash() -> str:
-    """Hash of the CUDA sources and the ABI header (identifies a kernel build)."""
+def source_hash(files=None) -> str:
+    """Hash of CUDA sources (all of csrc/ and the ABI header by default, or the
+    named csrc/ files): identifies the build a measurement was taken on."""
     import hashlib
     h = hashlib.sha256()
-    for fn in sorted(os.listdir(CSRC)) + ["../../include/ras.h"]:
+    names = sorted(os.listdir(CSRC)) + ["../../include/ras.h"] if files is None else list(files)
+    for fn in names:
         path = os.path.normpath(os.path.join(CSRC, fn))
         if path.endswith((".cu", ".cuh", ".h")) and os.path.isfile(path):
             h.update(os.path.basename(path).encode())
             with open(path, "rb") as f:
                 h.update(f.read())
     return h.hexdigest()[:16]
+
+
+# files that define the fine-level subdomain-solve kernel k_ras_apply
+RAS_APPLY_FILES = ("common.cuh", "schwarz.cuh", "schwarz.cu")
 
 
 def nvcc() -> str:
