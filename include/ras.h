@@ -83,13 +83,17 @@ typedef struct {
     int ilu_k;             /* 0 = ILU(0) subdomain solver (only value implemented)   */
     int factor_prec;       /* 64 = FP64 factors and solves; 32 = FP32 factors, FP32
                               solves; 16 = BF16-stored factors, FP32 solves          */
-    int nlevels;           /* 1 = one-level; 2 = two-level (Eq. equ:v-cycle)          */
-    int coarsen[3];        /* coarse:fine ratio per axis for nlevels = 2 (Table 7)    */
+    int nlevels;           /* 1 = one-level; 2 = two-level (Eq. equ:v-cycle);
+                              3 = three-level V-cycle (Algorithm 1, mu = nu = 1)     */
+    int coarsen[3];        /* coarse:fine ratio per axis of each coarsening (Table 7) */
     int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second (only value)  */
     int mlevel_type;       /* 0 = V-cycle, 1 = left-Kaskade, 2 = right-Kaskade,
                               3 = additive, 4 = coarse-only (Eqs. equ:v-cycle ..
                               equ:coarse-level)                                      */
     int coarse_prec;       /* 64 or 32: precision of the dense block coarse LU        */
+    int coarse_overlap;    /* nlevels = 3: overlap delta_c of the middle-level Schwarz
+                              smoother (px x py x pz subdomains, ILU(0) on the
+                              Galerkin operator's nonzero pattern, factor_prec)     */
 } ras_opts;
 
 typedef struct {
@@ -163,16 +167,22 @@ int ras_stencil_matvec(const ras_problem *prob, const ras_stencil *J, const doub
  * (Section 3.1, Fig. 1), per-subdomain boxes, the wavefront (level) schedule of
  * the natural-order ILU(0) triangular solves, factor storage, and for
  * nlevels = 2 the interpolation (Eq. equ:inter-second), the coarse grid and the
- * dense block-LU layout. Returns RAS_EINVAL for unsupported options. */
+ * dense block-LU layout; for nlevels = 3 also the middle grid (fine grid
+ * coarsened by coarsen[]) with its own partition (overlap coarse_overlap) and
+ * the coarsest grid (middle grid coarsened by coarsen[]) with its block-LU
+ * layout. Returns RAS_EINVAL for unsupported options (nlevels = 3 requires
+ * mlevel_type = 0). */
 int ras_setup(const ras_problem *prob, const ras_opts *opts, ras_precond **out);
 void ras_precond_destroy(ras_precond *pc);
 
 /* Numeric factorisation, once per Newton iteration: A_i = R_i^delta J
  * (R_i^delta)^T (Eq. equ:as-class), ILU(0) without pivoting in natural order
  * inside each overlapped subdomain, stored at factor_prec; for nlevels = 2 also
- * the Galerkin coarse operator R J P (R = P^T) and its dense block LU; the
- * two-level preconditioner also keeps a private copy of J for the fine-level
- * residuals of the multilevel combination, so J may be freed after the call.
+ * the Galerkin coarse operator R J P (R = P^T) and its dense block LU; for
+ * nlevels = 3 the middle operator A_1 = P_1^T J P_1 (FP64), the ILU(0) factors
+ * of its subdomains (on A_1's nonzero pattern) and the block LU of
+ * A_0 = P_0^T A_1 P_0. The multilevel preconditioners also keep a private copy
+ * of J for the fine-level residuals, so J may be freed after the call.
  * Synchronises the stream to check pivots: RAS_EZEROPIVOT on a zero or
  * non-finite pivot. */
 int ras_factor(ras_precond *pc, const ras_stencil *J, void *stream);
@@ -180,7 +190,10 @@ int ras_factor(ras_precond *pc, const ras_stencil *J, void *stream);
 /* z = M^{-1} r. One level: left-RAS, Eq. equ:as-left,
  *   z = sum_i (R_i^0)^T (L_i U_i)^{-1} R_i^delta r.
  * Two levels: the configured two-level combination (Eq. equ:v-cycle by
- * default). r, z: device [N], must not alias. Requires a prior ras_factor. */
+ * default). Three levels: Algorithm 1 with one RAS-Richardson pre- and
+ * post-smoothing step on the fine and middle levels and the exact block-LU
+ * solve on the coarsest. r, z: device [N], must not alias. Requires a prior
+ * ras_factor. */
 int ras_apply(ras_precond *pc, const double *r, double *z, void *stream);
 
 /* Right-preconditioned flexible GMRES(m) (Section 3, Eq. jacobian, Remark 2)

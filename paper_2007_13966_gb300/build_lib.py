@@ -17,7 +17,8 @@ CSRC = os.path.join(HERE, "csrc")
 OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libras.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
-SOURCES = ["problem.cu", "schwarz.cu", "precond.cu", "krylov.cu", "coarse.cu", "noalloc.cu"]
+SOURCES = ["problem.cu", "schwarz.cu", "precond.cu", "krylov.cu", "coarse.cu", "ras125.cu",
+           "noalloc.cu"]
 
 
 def source_hash(files=None) -> str:

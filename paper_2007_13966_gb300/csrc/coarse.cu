@@ -60,7 +60,7 @@ struct Coarse {
     int *d_err = nullptr;
     GridBar *d_bar = nullptr;
     size_t esz = 8;
-    size_t rap_smem = 0, fac_smem = 0, sol_smem = 0;
+    size_t rap_smem = 0, rap125_smem = 0, fac_smem = 0, sol_smem = 0;
     int fac_grid = 0, sol_grid = 0;
 };
 
@@ -171,6 +171,90 @@ __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapD
             const int e = threadIdx.x;
             const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
             const AT *wx_ = Wx + dx * 3 * WM;
+            AT acc = 0;
+            for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
+            out[e] += acc;
+        }
+        __syncthreads();
+    }
+    if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
+}
+
+// Galerkin product of a 125-point level operator A (the coarse operator of
+// the level above), same sum factorisation, one fine offset t at a time:
+//   A_c[I][I+d] = sum_t sum_a P(a,I) A_t(a) P(a + t, I + d).
+// Offsets whose values vanish on the whole support box are skipped.
+template <typename AT>
+__global__ void __launch_bounds__(256) k_rap125(const double *__restrict__ Af, Interp P, CGeom G,
+                                                RapDims W, AT *__restrict__ Ac) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AT *sm = reinterpret_cast<AT *>(smem_raw);
+    const int WX = W.wx, WY = W.wy, WZ = W.wz;
+    const int WM = max(WX, max(WY, WZ));
+    AT *Abox = sm;                              // [WZ][WY][WX]
+    AT *Wt = Abox + WX * WY * WZ;               // [3][5 d][5 t][WM]
+    AT *U = Wt + 75 * WM;                       // [5][WY][WX]
+    AT *V = U + 5 * WY * WX;                    // [25][WX]
+    AT *out = V + 25 * WX;                      // [125]
+
+    const int I = blockIdx.x;
+    const int Ic[3] = {I % G.cx, (I / G.cx) % G.cy, I / (G.cx * G.cy)};
+    const int cdim[3] = {G.cx, G.cy, G.cz};
+    const int ndim[3] = {G.nx, G.ny, G.nz};
+    const int lo[3] = {P.lo[0][Ic[0]], P.lo[1][Ic[1]], P.lo[2][Ic[2]]};
+    const int wx = P.hi[0][Ic[0]] - lo[0], wy = P.hi[1][Ic[1]] - lo[1], wz = P.hi[2][Ic[2]] - lo[2];
+    const int box = wx * wy * wz;
+    const long long nxy = (long long)G.nx * G.ny;
+    const long long Nf = nxy * G.nz;
+
+    // pair weights W[axis][d][t][a] = P(a, I) P(a + t - 2, I + d - 2)
+    for (int e = threadIdx.x; e < 75 * WM; e += blockDim.x) {
+        const int q = e % WM, ti = (e / WM) % 5, d = (e / (5 * WM)) % 5, axis = e / (25 * WM);
+        const int wa = axis == 0 ? wx : (axis == 1 ? wy : wz);
+        double w = 0.0;
+        if (q < wa) {
+            const int a = lo[axis] + q, as = a + ti - 2, J = Ic[axis] + d - 2;
+            if (J >= 0 && J < cdim[axis] && as >= 0 && as < ndim[axis])
+                w = w1(P, axis, a, Ic[axis]) * w1(P, axis, as, J);
+        }
+        Wt[e] = (AT)w;
+    }
+    if (threadIdx.x < 125) out[threadIdx.x] = 0;
+
+    for (int t = 0; t < 125; ++t) {
+        const int tx = t % 5 - 2, ty = (t / 5) % 5 - 2, tz = t / 25 - 2;
+        int nonzero = 0;
+        for (int e = threadIdx.x; e < box; e += blockDim.x) {
+            const int ax = e % wx, ay = (e / wx) % wy, az = e / (wx * wy);
+            const long long g = (lo[0] + ax) + (long long)G.nx * (lo[1] + ay) + nxy * (lo[2] + az);
+            const double v = Af[(long long)t * Nf + g];
+            nonzero |= (v != 0.0);
+            Abox[(az * WY + ay) * WX + ax] = (AT)v;
+        }
+        if (!__syncthreads_or(nonzero)) continue;
+        const AT *Wz = Wt + (2 * 25) * WM + (tz + 2) * WM;   // + dz * 5 * WM
+        const AT *Wy = Wt + (1 * 25) * WM + (ty + 2) * WM;
+        const AT *Wx = Wt + (0 * 25) * WM + (tx + 2) * WM;
+        for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
+            const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
+            const AT *wz_ = Wz + dz * 5 * WM;
+            AT acc = 0;
+            for (int az = 0; az < wz; ++az) acc += wz_[az] * Abox[(az * WY + ay) * WX + ax];
+            U[(dz * WY + ay) * WX + ax] = acc;
+        }
+        __syncthreads();
+        for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
+            const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
+            const AT *wy_ = Wy + dy * 5 * WM;
+            AT acc = 0;
+            for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * U[(dz * WY + ay) * WX + ax];
+            V[(dz * 5 + dy) * WX + ax] = acc;
+        }
+        __syncthreads();
+        if (threadIdx.x < 125) {
+            const int e = threadIdx.x;
+            const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
+            const AT *wx_ = Wx + dx * 5 * WM;
             AT acc = 0;
             for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
             out[e] += acc;
@@ -985,14 +1069,17 @@ static int configure_t(Coarse *c) {
     // minus the kernels' static shared memory
     const int big = 200 * 1024;
     RAS_CK(cudaFuncSetAttribute(k_rap<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_rap125<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_factor<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_solve<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
     const int WM = std::max(WX, std::max(WY, WZ));
     c->rap_smem = sizeof(AT) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
+    c->rap125_smem = sizeof(AT) * (size_t)(WX * WY * WZ + 75 * WM + 5 * WY * WX + 25 * WX + 125);
     c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
     c->sol_smem = sizeof(AT) * (size_t)c->T;
-    if (c->rap_smem > (size_t)big || c->fac_smem > (size_t)big || c->sol_smem > (size_t)big)
+    if (c->rap_smem > (size_t)big || c->rap125_smem > (size_t)big || c->fac_smem > (size_t)big ||
+        c->sol_smem > (size_t)big)
         return RAS_EINVAL;
     int dev = 0, sms = 0, bf = 0, bs = 0;
     RAS_CK(cudaGetDevice(&dev));
@@ -1015,7 +1102,34 @@ static int configure_t(Coarse *c) {
     return RAS_OK;
 }
 
+// interpolation tables of one axis on the device
+static int upload_axis(int n, int r, int *&d_ia, int *&d_ib, double *&d_wa, double *&d_wb, int *&d_lo,
+                       int *&d_hi, int &nc, int &wmax) {
+    std::vector<int> ia, ib, lo, hi;
+    std::vector<double> wa, wb;
+    interp_axis(n, r, ia, ib, wa, wb, lo, hi, nc);
+    wmax = 1;
+    for (size_t I = 0; I < lo.size(); ++I) wmax = std::max(wmax, hi[I] - lo[I]);
+    RAS_TRY(dalloc(&d_ia, ia.size()));
+    RAS_TRY(dalloc(&d_ib, ib.size()));
+    RAS_TRY(dalloc(&d_wa, wa.size()));
+    RAS_TRY(dalloc(&d_wb, wb.size()));
+    RAS_TRY(dalloc(&d_lo, lo.size()));
+    RAS_TRY(dalloc(&d_hi, hi.size()));
+    RAS_CK(cudaMemcpy(d_ia, ia.data(), ia.size() * 4, cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(d_ib, ib.data(), ib.size() * 4, cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(d_wa, wa.data(), wa.size() * 8, cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(d_wb, wb.data(), wb.size() * 8, cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(d_lo, lo.data(), lo.size() * 4, cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(d_hi, hi.data(), hi.size() * 4, cudaMemcpyHostToDevice));
+    return RAS_OK;
+}
+
 int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
+    return coarse_setup_grid(out, Pb->nx, Pb->ny, Pb->nz, o);
+}
+
+int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o) {
     *out = nullptr;
     if (o.interp_order != 2) return RAS_EINVAL;
     if (o.coarse_prec != 64 && o.coarse_prec != 32) return RAS_EINVAL;
@@ -1028,27 +1142,14 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
     auto fail = [&](int s) { coarse_free(c); return s; };
     c->prec = o.coarse_prec;
     c->esz = c->prec == 64 ? 8 : 4;
-    c->nx = Pb->nx; c->ny = Pb->ny; c->nz = Pb->nz; c->N = Pb->N;
-    c->n[0] = Pb->nx; c->n[1] = Pb->ny; c->n[2] = Pb->nz;
+    if (fnx < 1 || fny < 1 || fnz < 1) return fail(RAS_EINVAL);
+    c->nx = fnx; c->ny = fny; c->nz = fnz; c->N = fnx * fny * fnz;
+    c->n[0] = fnx; c->n[1] = fny; c->n[2] = fnz;
     for (int a = 0; a < 3; ++a) {
         c->r[a] = o.coarsen[a];
-        std::vector<int> ia, ib, lo, hi;
-        std::vector<double> wa, wb;
-        interp_axis(c->n[a], c->r[a], ia, ib, wa, wb, lo, hi, c->c[a]);
-        c->wmax[a] = 1;
-        for (size_t I = 0; I < lo.size(); ++I) c->wmax[a] = std::max(c->wmax[a], hi[I] - lo[I]);
-        int rc = 0;
-        if ((rc = dalloc(&c->d_ia[a], ia.size())) || (rc = dalloc(&c->d_ib[a], ib.size())) ||
-            (rc = dalloc(&c->d_wa[a], wa.size())) || (rc = dalloc(&c->d_wb[a], wb.size())) ||
-            (rc = dalloc(&c->d_lo[a], lo.size())) || (rc = dalloc(&c->d_hi[a], hi.size())))
-            return fail(rc);
-        bool ok = cudaMemcpy(c->d_ia[a], ia.data(), ia.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(c->d_ib[a], ib.data(), ib.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(c->d_wa[a], wa.data(), wa.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(c->d_wb[a], wb.data(), wb.size() * 8, cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(c->d_lo[a], lo.data(), lo.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess &&
-                  cudaMemcpy(c->d_hi[a], hi.data(), hi.size() * 4, cudaMemcpyHostToDevice) == cudaSuccess;
-        if (!ok) return fail(RAS_ECUDA);
+        const int rc = upload_axis(c->n[a], c->r[a], c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
+                                   c->d_lo[a], c->d_hi[a], c->c[a], c->wmax[a]);
+        if (rc) return fail(rc);
     }
     c->Nc = c->c[0] * c->c[1] * c->c[2];
     // axes sorted by coarse size: fastest = smallest
@@ -1130,15 +1231,12 @@ void coarse_free(Coarse *c) {
     delete c;
 }
 
+// dense block factorisation of the Galerkin operator already in c->Ac
 template <typename AT>
-static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
+static int factor_blocks_t(Coarse *c, cudaStream_t st) {
     const CGeom G = geom_of(c);
-    const Interp P = interp_of(c);
     AT *Ac = (AT *)c->Ac, *D = (AT *)c->D;
     const size_t bsz = (size_t)c->T * c->T;
-    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
-    k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, P, G, W, Ac);
-    RAS_LAUNCHED();
     RAS_CK(cudaMemsetAsync(D, 0, c->nb * bsz * sizeof(AT), st));
     k_assemble<AT><<<grid_of((long long)c->nb * c->T), 256, 0, st>>>(Ac, c->d_pos, c->d_cell, G, D);
     RAS_LAUNCHED();
@@ -1158,8 +1256,28 @@ static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
     return RAS_OK;
 }
 
+template <typename AT>
+static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
+    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
+    k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, (AT *)c->Ac);
+    RAS_LAUNCHED();
+    return factor_blocks_t<AT>(c, st);
+}
+
+template <typename AT>
+static int factor125_t(Coarse *c, const double *Af, cudaStream_t st) {
+    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
+    k_rap125<AT><<<c->Nc, 256, c->rap125_smem, st>>>(Af, interp_of(c), geom_of(c), W, (AT *)c->Ac);
+    RAS_LAUNCHED();
+    return factor_blocks_t<AT>(c, st);
+}
+
 int coarse_factor(Coarse *c, const Stencil7 &A, cudaStream_t st) {
     return c->prec == 64 ? factor_t<double>(c, A, st) : factor_t<float>(c, A, st);
+}
+
+int coarse_factor125(Coarse *c, const double *Af, cudaStream_t st) {
+    return c->prec == 64 ? factor125_t<double>(c, Af, st) : factor125_t<float>(c, Af, st);
 }
 
 int coarse_check(Coarse *c, cudaStream_t st) {
@@ -1194,6 +1312,128 @@ int coarse_correct(Coarse *c, const double *t, double *z, int accumulate, cudaSt
 double coarse_bytes(const Coarse *c) {
     // E, C, F read once per solve
     return (double)c->esz * c->T * c->T * (c->nb + 2.0 * (c->nb - 1));
+}
+
+
+// ---------------------------------------------------------------------------
+// transfer between a level and the next coarser one (Algorithm 1): the
+// Galerkin operator of a 7-point operator, restriction R = P^T, prolongation
+// ---------------------------------------------------------------------------
+
+struct Transfer {
+    Coarse geo;        // interpolation tables and grid sizes only (no factors)
+};
+
+// tc[I] = sum_a P(a, I) t[a] over the fine support box of I (FP64)
+__global__ void __launch_bounds__(256) k_restrict(Interp P, CGeom G, const double *__restrict__ t,
+                                                  double *__restrict__ tc) {
+    const long long nxy = (long long)G.nx * G.ny;
+    for (int I = blockIdx.x * blockDim.x + threadIdx.x; I < G.Nc; I += gridDim.x * blockDim.x) {
+        const int Ix = I % G.cx, Iy = (I / G.cx) % G.cy, Iz = I / (G.cx * G.cy);
+        double acc = 0.0;
+        for (int az = P.lo[2][Iz]; az < P.hi[2][Iz]; ++az) {
+            const double wz = w1(P, 2, az, Iz);
+            for (int ay = P.lo[1][Iy]; ay < P.hi[1][Iy]; ++ay) {
+                const double wyz = wz * w1(P, 1, ay, Iy);
+                const double *row = t + G.nx * (long long)ay + nxy * az;
+                for (int ax = P.lo[0][Ix]; ax < P.hi[0][Ix]; ++ax)
+                    acc += wyz * w1(P, 0, ax, Ix) * __ldg(row + ax);
+            }
+        }
+        tc[I] = acc;
+    }
+}
+
+// x[a] += sum_I P(a, I) xc[I] (eight coarse cells per fine cell, FP64)
+__global__ void __launch_bounds__(256) k_prolong(Interp P, CGeom G, const double *__restrict__ xc,
+                                                 double *__restrict__ x) {
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < N;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int ax = (int)(p % G.nx), ay = (int)((p / G.nx) % G.ny),
+                  az = (int)(p / ((long long)G.nx * G.ny));
+        const int Ix[2] = {P.ia[0][ax], P.ib[0][ax]};
+        const int Iy[2] = {P.ia[1][ay], P.ib[1][ay]};
+        const int Iz[2] = {P.ia[2][az], P.ib[2][az]};
+        const double Wx[2] = {P.wa[0][ax], P.wb[0][ax]};
+        const double Wy[2] = {P.wa[1][ay], P.wb[1][ay]};
+        const double Wz[2] = {P.wa[2][az], P.wb[2][az]};
+        double s = 0.0;
+#pragma unroll
+        for (int u = 0; u < 2; ++u)
+#pragma unroll
+            for (int v = 0; v < 2; ++v)
+#pragma unroll
+                for (int w = 0; w < 2; ++w) {
+                    const double wt = Wx[w] * Wy[v] * Wz[u];
+                    if (wt != 0.0) s += wt * __ldg(xc + Ix[w] + G.cx * (Iy[v] + G.cy * Iz[u]));
+                }
+        x[p] += s;
+    }
+}
+
+int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]) {
+    *out = nullptr;
+    if (nx < 1 || ny < 1 || nz < 1) return RAS_EINVAL;
+    for (int a = 0; a < 3; ++a) if (ratio[a] < 1) return RAS_EINVAL;
+    Transfer *t = new Transfer();
+    Coarse *c = &t->geo;
+    c->nx = nx; c->ny = ny; c->nz = nz; c->N = nx * ny * nz;
+    c->n[0] = nx; c->n[1] = ny; c->n[2] = nz;
+    for (int a = 0; a < 3; ++a) {
+        c->r[a] = ratio[a];
+        const int rc = upload_axis(c->n[a], c->r[a], c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
+                                   c->d_lo[a], c->d_hi[a], c->c[a], c->wmax[a]);
+        if (rc) { transfer_free(t); return rc; }
+    }
+    c->Nc = c->c[0] * c->c[1] * c->c[2];
+    const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
+    const int WM = std::max(WX, std::max(WY, WZ));
+    c->rap_smem = sizeof(double) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
+    if (c->rap_smem > (size_t)200 * 1024) { transfer_free(t); return RAS_EINVAL; }
+    if (cudaFuncSetAttribute(k_rap<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+        cudaSuccess) {
+        transfer_free(t);
+        return RAS_ECUDA;
+    }
+    *out = t;
+    return RAS_OK;
+}
+
+void transfer_free(Transfer *t) {
+    if (!t) return;
+    Coarse *c = &t->geo;
+    for (int a = 0; a < 3; ++a) {
+        dfree(c->d_ia[a]); dfree(c->d_ib[a]); dfree(c->d_wa[a]); dfree(c->d_wb[a]);
+        dfree(c->d_lo[a]); dfree(c->d_hi[a]);
+    }
+    delete t;
+}
+
+void transfer_dims(const Transfer *t, int c[3]) {
+    for (int a = 0; a < 3; ++a) c[a] = t->geo.c[a];
+}
+
+int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, cudaStream_t st) {
+    const Coarse *c = &t->geo;
+    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
+    k_rap<double><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, Ac);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+int transfer_restrict(Transfer *t, const double *x, double *xc, cudaStream_t st) {
+    const Coarse *c = &t->geo;
+    k_restrict<<<grid_of(c->Nc), 256, 0, st>>>(interp_of(c), geom_of(c), x, xc);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+int transfer_prolong(Transfer *t, const double *xc, double *x, cudaStream_t st) {
+    const Coarse *c = &t->geo;
+    k_prolong<<<grid_of(c->N), 256, 0, st>>>(interp_of(c), geom_of(c), xc, x);
+    RAS_LAUNCHED();
+    return RAS_OK;
 }
 
 }  // namespace ras

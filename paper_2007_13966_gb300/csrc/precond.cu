@@ -1,5 +1,6 @@
 // ras_setup / ras_factor / ras_apply: the one-level left-RAS preconditioner of
-// Eq. equ:as-left and the two-level combinations of Section 3.2.1.
+// Eq. equ:as-left, the two-level combinations of Section 3.2.1 and the
+// three-level V-cycle of Algorithm 1.
 #include "precond.cuh"
 
 namespace ras {
@@ -36,9 +37,43 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
         }
     }
     RAS_TRY(ras1_factor(pc->fine, A, st));
-    if (pc->coarse) RAS_TRY(coarse_factor(pc->coarse, A, st));
+    if (pc->xfer) {
+        // level 1: A_1 = P_1^T A P_1, its subdomain ILU(0) factors, and the
+        // coarsest operator A_0 = P_0^T A_1 P_0 with its dense block LU
+        RAS_TRY(transfer_galerkin7(pc->xfer, A, pc->A1, st));
+        RAS_TRY(ras125_factor(pc->mid, pc->A1, st));
+        RAS_TRY(coarse_factor125(pc->coarse, pc->A1, st));
+    } else if (pc->coarse) {
+        RAS_TRY(coarse_factor(pc->coarse, A, st));
+    }
     RAS_TRY(ras1_check(pc->fine, st));
+    if (pc->xfer) RAS_TRY(ras125_check(pc->mid, st));
     if (pc->coarse) RAS_TRY(coarse_check(pc->coarse, st));
+    return RAS_OK;
+}
+
+// Algorithm 1 with three levels, one pre- and one post-smoothing step of
+// Schwarz-preconditioned Richardson on the fine and middle levels, zero
+// initial guesses, exact solve on the coarsest level:
+//   z = M_2 r;  b_1 = P_1^T (r - A z);
+//   x_1 = M_1 b_1;  x_1 += P_0 A_0^{-1} P_0^T (b_1 - A_1 x_1);  x_1 += M_1 (b_1 - A_1 x_1);
+//   z += P_1 x_1;  z += M_2 (r - A z).
+static int three_level_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st) {
+    const ras_problem *P = pc->prob;
+    const int nx = P->nx, ny = P->ny, nz = P->nz;
+    const int *m = pc->n1;
+    double *t = pc->t1;
+    RAS_TRY(fine_apply(pc, r, z, 0, st));
+    RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));
+    RAS_TRY(transfer_restrict(pc->xfer, t, pc->b1, st));
+    RAS_TRY(ras125_apply(pc->mid, pc->b1, pc->x1, 0, st));
+    RAS_TRY(spmv125(pc->A1, m[0], m[1], m[2], pc->x1, pc->b1, pc->r1, st));
+    RAS_TRY(coarse_correct(pc->coarse, pc->r1, pc->x1, 1, st));
+    RAS_TRY(spmv125(pc->A1, m[0], m[1], m[2], pc->x1, pc->b1, pc->r1, st));
+    RAS_TRY(ras125_apply(pc->mid, pc->r1, pc->x1, 1, st));
+    RAS_TRY(transfer_prolong(pc->xfer, pc->x1, z, st));
+    RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));
+    RAS_TRY(fine_apply(pc, t, z, 1, st));
     return RAS_OK;
 }
 
@@ -50,6 +85,7 @@ int precond_check(ras_precond *pc, cudaStream_t st) {
 int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st) {
     const ras_problem *P = pc->prob;
     if (!pc->coarse) return fine_apply(pc, r, z, 0, st);
+    if (pc->xfer) return three_level_apply(pc, r, z, st);
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     double *t = pc->t1;
     switch (pc->opts.mlevel_type) {
@@ -89,16 +125,32 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
     if (!P || !o || !out) return RAS_EINVAL;
     *out = nullptr;
     if (o->ras_type != 1 || o->ilu_k != 0) return RAS_EINVAL;
-    if (o->nlevels != 1 && o->nlevels != 2) return RAS_EINVAL;
+    if (o->nlevels < 1 || o->nlevels > 3) return RAS_EINVAL;
     if (o->mlevel_type < 0 || o->mlevel_type > 4) return RAS_EINVAL;
+    if (o->nlevels == 3 && (o->mlevel_type != 0 || o->coarse_overlap < 0)) return RAS_EINVAL;
     ras_precond *pc = new ras_precond();
     pc->prob = P;
     pc->opts = *o;
     int rc = ras1_setup(pc->fine, P->nx, P->ny, P->nz, o->px, o->py, o->pz, o->overlap,
                         o->factor_prec);
     if (rc) { ras_precond_destroy(pc); return rc; }
-    if (o->nlevels == 2) {
-        rc = coarse_setup(&pc->coarse, P, *o);
+    if (o->nlevels == 3) {
+        rc = transfer_setup(&pc->xfer, P->nx, P->ny, P->nz, o->coarsen);
+        if (!rc) {
+            transfer_dims(pc->xfer, pc->n1);
+            pc->N1 = pc->n1[0] * pc->n1[1] * pc->n1[2];
+            rc = ras125_setup(pc->mid, pc->n1[0], pc->n1[1], pc->n1[2], o->px, o->py, o->pz,
+                              o->coarse_overlap, o->factor_prec);
+        }
+        if (!rc) rc = coarse_setup_grid(&pc->coarse, pc->n1[0], pc->n1[1], pc->n1[2], *o);
+        if (!rc) rc = dalloc(&pc->A1, (size_t)125 * pc->N1);
+        if (!rc) rc = dalloc(&pc->b1, pc->N1);
+        if (!rc) rc = dalloc(&pc->x1, pc->N1);
+        if (!rc) rc = dalloc(&pc->r1, pc->N1);
+        if (rc) { ras_precond_destroy(pc); return rc; }
+    }
+    if (o->nlevels >= 2) {
+        if (!pc->coarse) rc = coarse_setup(&pc->coarse, P, *o);
         if (!rc) rc = dalloc(&pc->t1, P->N);
         if (!rc) rc = dalloc(&pc->t2, P->N);
         if (!rc) rc = dalloc(&pc->t3, P->N);
@@ -113,6 +165,9 @@ extern "C" void ras_precond_destroy(ras_precond *pc) {
     if (!pc) return;
     ras1_free(pc->fine);
     if (pc->coarse) coarse_free(pc->coarse);
+    if (pc->xfer) transfer_free(pc->xfer);
+    ras125_free(pc->mid);
+    dfree(pc->A1); dfree(pc->b1); dfree(pc->x1); dfree(pc->r1);
     dfree(pc->t1); dfree(pc->t2); dfree(pc->t3);
     for (int s = 0; s < 7; ++s) dfree(pc->Acopy[s]);
     for (auto e : pc->ev) cudaEventDestroy(e);

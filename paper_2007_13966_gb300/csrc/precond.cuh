@@ -2,19 +2,34 @@
 // coarse-grid correction (Section 3.2).
 #pragma once
 
+#include "ras125.cuh"
 #include "schwarz.cuh"
 
 namespace ras {
 struct Coarse;
 int coarse_setup(Coarse **out, const ras_problem *P, const ras_opts &o);
+// the same on the grid of a coarser level (fine grid nx x ny x nz)
+int coarse_setup_grid(Coarse **out, int nx, int ny, int nz, const ras_opts &o);
 void coarse_free(Coarse *c);
 int coarse_factor(Coarse *c, const Stencil7 &A, cudaStream_t st);
+// the same from a 125-point level operator Af [125][nx*ny*nz] (FP64)
+int coarse_factor125(Coarse *c, const double *Af, cudaStream_t st);
 // reads and clears the coarse pivot / layout flag (synchronises)
 int coarse_check(Coarse *c, cudaStream_t st);
 // bytes of the dense block factors read by one coarse solve
 double coarse_bytes(const Coarse *c);
 // ec = A_c^{-1} R t, then z (+)= P ec  (accumulate selects += )
 int coarse_correct(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st);
+
+// grid transfer to the next coarser level (linear interpolation P, R = P^T)
+struct Transfer;
+int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]);
+void transfer_free(Transfer *t);
+void transfer_dims(const Transfer *t, int c[3]);
+// Ac [125][Nc] = P^T A P for a 7-point operator A (FP64)
+int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, cudaStream_t st);
+int transfer_restrict(Transfer *t, const double *x, double *xc, cudaStream_t st);   // xc = P^T x
+int transfer_prolong(Transfer *t, const double *xc, double *x, cudaStream_t st);    // x += P xc
 }  // namespace ras
 
 struct ras_precond {
@@ -25,6 +40,12 @@ struct ras_precond {
     ras::Stencil7 A{};          // copy of the operator of the last ras_factor (fine residuals)
     double *Acopy[7] = {};      // owned storage of that copy (two-level only)
     double *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;  // multilevel scratch [N]
+    // three levels (Algorithm 1): fine -> middle level 1 -> coarsest level 0
+    ras::Transfer *xfer = nullptr;       // fine grid -> level 1
+    int n1[3] = {0, 0, 0}, N1 = 0;       // level-1 grid
+    double *A1 = nullptr;                // [125][N1] Galerkin operator of level 1
+    ras::Ras125 mid;                     // RAS(ILU(0)) smoother of level 1
+    double *b1 = nullptr, *x1 = nullptr, *r1 = nullptr;  // level-1 vectors [N1]
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
