@@ -17,6 +17,10 @@ is resident in HBM. `e2e` repeats the steps through the same public API with
 the step's inputs copied from pinned host memory and the new state copied
 back, inside the timed region.
 
+`--workload c3` times the 60 x 220 x 85 channelised case with the three-level
+V-cycle of Algorithm 1 instead (middle level 30 x 110 x 43, coarsest 15 x 55 x
+22, ratio 2 per axis).
+
 Usage: python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
 N > 1 runs N independent replicas (one per GPU, launched by torchrun); the
 path has no data exchange between them.
@@ -38,6 +42,11 @@ METRIC = "sec per implicit step and ras_apply HBM GB/s, FP32-RAS vs FP64, at 1e-
 WORKLOAD = ("3d 128x128x64 lognormal (1.05M cells), two-level V-cycle RAS 8x8x4 overlap 2, "
             "ILU(0) FP32 factors, coarse 4x (32x32x16) FP32 dense block LU, FP64 FGMRES(30) "
             "rtol 1e-6, Newton rtol 1e-6, dt 0.1 day")
+WORKLOAD_C3 = ("3d 60x220x85 channelised (1.12M cells), three-level V-cycle RAS (Algorithm 1): "
+               "4x11x5 subdomains overlap 2 on the fine grid, middle level 30x110x43 with 4x11x5 "
+               "subdomains overlap 1 (ILU(0) on the Galerkin operator), coarsest 15x55x22 FP32 "
+               "dense block LU, ratio 2 per axis, FP64 FGMRES(30) rtol 1e-6, Newton rtol 1e-6, "
+               "dt 0.1 day")
 
 
 def parse():
@@ -52,6 +61,8 @@ def parse():
                     help="skip the all-FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="32x32x16 case (profiling / smoke)")
+    ap.add_argument("--workload", choices=["c2", "c3"], default="c2",
+                    help="c2: 128x128x64 two-level (default); c3: 60x220x85 three-level")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--kernel", choices=["ras_apply", "vcycle"], default=None,
                     help="kernel-only mode: factor once, then time REPS applications "
@@ -71,17 +82,30 @@ def dist_env():
 # workload
 # ---------------------------------------------------------------------------
 
-def make_reservoir(small=False):
+def make_reservoir(small=False, workload="c2"):
     from paper_2007_13966_gb300 import synthetic as syn
+    if workload == "c3":
+        return syn.channelised_reservoir()
     if small:
         return syn.lognormal_reservoir(32, 32, 16, 25.0, 25.0, 12.5, sigma=1.5, corr=8.0,
                                        seed_k=3, seed_phi=4, name="3d 32x32x16 lognormal")
     return syn.config_3d_1m()
 
 
-def precond_opts(small=False):
+def precond_opts(small=False, workload="c2"):
+    if workload == "c3":
+        return dict(parts=(4, 11, 5), overlap=2, nlevels=3, coarsen=(2, 2, 2), mlevel_type=0,
+                    coarse_overlap=1)
     parts = (2, 2, 1) if small else (8, 8, 4)
-    return dict(parts=parts, overlap=2, nlevels=2, coarsen=(4, 4, 4), mlevel_type=0)
+    return dict(parts=parts, overlap=2, nlevels=2, coarsen=(4, 4, 4), mlevel_type=0,
+                coarse_overlap=1)
+
+
+def make_precond(ras, gp, po, factor_prec, coarse_prec, nlevels=None):
+    return ras.Precond(gp, po["parts"], po["overlap"], factor_prec=factor_prec,
+                       nlevels=po["nlevels"] if nlevels is None else nlevels,
+                       coarsen=po["coarsen"], mlevel_type=po["mlevel_type"],
+                       coarse_prec=coarse_prec, coarse_overlap=po["coarse_overlap"])
 
 
 NEWTON = dict(rtol=1e-6, atol=1e-10, maxit=50, lin_rtol=1e-6, lin_atol=1e-8, restart=30,
@@ -238,13 +262,11 @@ def gb300_arm(args):
     torch.cuda.set_device(local)
     from paper_2007_13966_gb300 import ras
 
-    res = make_reservoir(args.small)
+    res = make_reservoir(args.small, args.workload)
     N = res.grid.n
     gp = ras.Problem(res)
-    po = precond_opts(args.small)
-    pc = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=args.factor_prec,
-                     nlevels=po["nlevels"], coarsen=po["coarsen"], mlevel_type=po["mlevel_type"],
-                     coarse_prec=args.coarse_prec)
+    po = precond_opts(args.small, args.workload)
+    pc = make_precond(ras, gp, po, args.factor_prec, args.coarse_prec)
     p0 = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
     state = {"p_l": p0.clone(), "p_lm1": p0.clone(), "step": 0}
 
@@ -275,17 +297,28 @@ def gb300_arm(args):
     # the all-FP64 form on the same step sequence, for the FP32-vs-FP64 comparison
     fp64 = None
     if not args.no_fp64_form and (args.factor_prec != 64 or args.coarse_prec != 64):
-        pc64 = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=64, nlevels=po["nlevels"],
-                           coarsen=po["coarsen"], mlevel_type=po["mlevel_type"], coarse_prec=64)
-        st64 = {"p_l": state["p_l"].clone(), "p_lm1": state["p_lm1"].clone(), "step": state["step"]}
+        pc64 = make_precond(ras, gp, po, 64, 64)
+        def clone(st):
+            return {"p_l": st["p_l"].clone(), "p_lm1": st["p_lm1"].clone(), "step": st["step"]}
+
+        st64 = clone(state)
         run_steps(gp, pc64, res, st64, 1, torch)
         k64 = max(1, min(args.steps, 2))
+        # one step of each form from the same FP64 state: max |p_lo - p_64| / max |p_64|
+        diffs = []
+        sa = clone(st64)
+        for _ in range(k64):
+            sb = clone(sa)
+            run_steps(gp, pc64, res, sa, 1, torch)
+            run_steps(gp, pc, res, sb, 1, torch)
+            diffs.append(float((sb["p_l"] - sa["p_l"]).abs().max() / sa["p_l"].abs().max()))
         t64, outs64 = timed(lambda: run_steps(gp, pc64, res, st64, k64, torch), torch, dist_on)
         t64 = max_over_ranks(t64, dist_on)
         fp64 = {"sec_per_step": t64 / k64, "steps": k64,
                 "newton_iters": [o["newton_iters"] for o in outs64],
                 "fgmres_iters": [o["lin_total"] for o in outs64],
-                "fp32_speedup": (t64 / k64) / sec_per_step}
+                "fp32_speedup": (t64 / k64) / sec_per_step,
+                "state_rel_diff_per_step": diffs}
         del pc64
 
     if rank != 0:
@@ -298,8 +331,9 @@ def gb300_arm(args):
     bytes_per_launch = pc.apply_bytes()
     avg_s = (apply_ms / 1e3) / max(apply_n, 1)
     achieved = bytes_per_launch / avg_s / 1e9 if apply_n else None
-    traffic = load_traffic("k_ras_apply_fp32_1m" if args.factor_prec == 32 else
-                           f"k_ras_apply_fp{args.factor_prec}_1m")
+    traffic = None
+    if args.workload == "c2" and not args.small:
+        traffic = load_traffic(f"k_ras_apply_fp{args.factor_prec}_1m")
     line = {
         "metric": METRIC,
         "value": sec_per_step,
@@ -314,9 +348,12 @@ def gb300_arm(args):
         "dtype": "f64+f32",
         "data": "synthetic",
         "config": {
-            "workload": WORKLOAD if not args.small else "3d 32x32x16 lognormal (profiling case)",
+            "workload": (WORKLOAD_C3 if args.workload == "c3" else
+                         WORKLOAD if not args.small else "3d 32x32x16 lognormal (profiling case)"),
             "cells": N, "subdomains": list(po["parts"]), "overlap": po["overlap"],
-            "coarse": [c for c in (32, 32, 16)] if not args.small else [8, 8, 4],
+            "levels": po["nlevels"],
+            "coarse": ([15, 55, 22] if args.workload == "c3" else
+                       [32, 32, 16] if not args.small else [8, 8, 4]),
             "factor_prec": args.factor_prec, "coarse_prec": args.coarse_prec,
             "parallelism": f"replicas x{ws}" if ws > 1 else "single GPU",
             "l2": "working set ~1 GB > 129 MB L2 (no flush needed)",
@@ -328,7 +365,8 @@ def gb300_arm(args):
                 "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
         "gpu_launches": int(launches),
         "roofline": {
-            "kernel": "k_ras_apply (fine-level subdomain ILU(0) solves, FP32 factors)",
+            "kernel": "k_ras_apply (fine-level subdomain ILU(0) solves, %s factors)"
+                      % {64: "FP64", 32: "FP32", 16: "BF16"}[args.factor_prec],
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic,
@@ -338,7 +376,7 @@ def gb300_arm(args):
         },
         "fp64_form": fp64,
     }
-    if ws == 1 and not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline and args.workload == "c2":
         line["cpu_baseline"] = cpu_baseline_subprocess(args)
     print(json.dumps(line), flush=True)
     if dist_on:
@@ -440,13 +478,12 @@ def kernel_mode(args):
     """Set up the workload, factor once, time `reps` preconditioner applications."""
     import torch
     from paper_2007_13966_gb300 import ras
-    res = make_reservoir(args.small)
+    res = make_reservoir(args.small, args.workload)
     N = res.grid.n
     gp = ras.Problem(res)
-    po = precond_opts(args.small)
-    nl = 1 if args.kernel == "ras_apply" else 2
-    pc = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=args.factor_prec, nlevels=nl,
-                     coarsen=po["coarsen"], mlevel_type=0, coarse_prec=args.coarse_prec)
+    po = precond_opts(args.small, args.workload)
+    nl = 1 if args.kernel == "ras_apply" else po["nlevels"]
+    pc = make_precond(ras, gp, po, args.factor_prec, args.coarse_prec, nlevels=nl)
     from paper_2007_13966_gb300 import synthetic as syn
     p = torch.tensor(syn.random_pressure(res, 3, 1.0, 3.0), device="cuda")
     p0 = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
