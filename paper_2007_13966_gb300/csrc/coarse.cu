@@ -7,12 +7,19 @@
 // Dense block LU: coarse cells are renumbered with the axes sorted by size
 // (fastest = smallest). A_c couples cells at most two cells apart, so two
 // consecutive planes of the slowest axis form one dense block of size T and
-// A_c is block tridiagonal: A = tridiag(Lo_{k-1}, D_k, Up_k). Block Thomas:
-//     D_0 = A_00,  E_k = D_k^{-1},  C_k = Lo_k E_k,  F_k = E_k Up_k,
-//     D_{k+1} = A_{k+1,k+1} - C_k Up_k.
-// Solve: g_k -= C_{k-1} g_{k-1} (forward), x_k = E_k g_k - F_k x_{k+1}.
-// Each E_k is computed in place by a blocked Gauss-Jordan inversion without
-// pivoting (64 x 64 tiles); Lo_k / Up_k are sparse and stored in ELL form.
+// A_c is block tridiagonal: A = tridiag(Lo_{k-1}, D_k, Up_k). Block
+// elimination from both ends towards a middle block m (a "twisted" block
+// Thomas: two independent chains of half the length). Edge e joins blocks e
+// and e+1; a top edge (e < m) eliminates its pivot block e into target block
+// e+1, a bottom edge (e >= m) its pivot block e+1 into target block e:
+//     Inv_pivot = S_pivot^{-1},  C_e = A(target, pivot) Inv,  F_e = Inv A(pivot, target),
+//     S_target = A(target, target) - C_e A(pivot, target),
+// with S = the block after the Schur updates it has received; the middle
+// block receives one update from each side. Solve: g_target -= C_e g_pivot
+// along both chains, x_m = S_m^{-1} g_m, then x_pivot = Inv g_pivot - F_e x_target
+// back along both chains. Each inverse is computed in place by a blocked
+// Gauss-Jordan inversion without pivoting (64 x 64 tiles); the off-diagonal
+// blocks are sparse and stored in ELL form.
 //
 // The factorisation and the solve each run as ONE cooperative persistent
 // kernel whose phases are separated by a grid barrier; the barrier gives up
@@ -47,6 +54,7 @@ struct Coarse {
     int *d_lo[3] = {}, *d_hi[3] = {};
     int af, am, as;                 // axis order: fastest, middle, slowest
     int T = 0, nb = 0;              // block size (multiple of TILE), number of blocks
+    int mid = 0;                    // middle block of the two-ended elimination
     int *d_pos = nullptr;           // natural coarse index -> block position
     int *d_cell = nullptr;          // block position -> natural coarse index or -1
     void *Ac = nullptr;             // [125][Nc] Galerkin stencil (prec)
@@ -55,12 +63,13 @@ struct Coarse {
     int *lo_n = nullptr, *up_n = nullptr;            // ELL entries used per row / column
     void *lo_v = nullptr, *up_v = nullptr;           // ELL values
     void *g = nullptr, *x = nullptr;                 // [nb*T]
-    void *Zs = nullptr;                              // scratch tile strip [TILE][T]
+    void *Zs = nullptr;                              // scratch tile strips [2][TILE][T]
     void *rx = nullptr, *ry = nullptr;               // restriction passes [cx][ny][nz], [cx][cy][nz]
     int *d_err = nullptr;
     GridBar *d_bar = nullptr;
     size_t esz = 8;
     size_t rap_smem = 0, rap125_smem = 0, fac_smem = 0, sol_smem = 0;
+    int rap125_ng = 25;             // offsets staged per round in k_rap125
     int fac_grid = 0, sol_grid = 0;
 };
 
@@ -85,7 +94,7 @@ __device__ __forceinline__ double w1(const Interp &P, int ax, int a, int I) {
 struct CGeom {
     int nx, ny, nz;       // fine
     int cx, cy, cz, Nc;   // coarse
-    int T, nb;
+    int T, nb, mid;
 };
 
 // ---------------------------------------------------------------------------
@@ -183,19 +192,22 @@ __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapD
 // Galerkin product of a 125-point level operator A (the coarse operator of
 // the level above), same sum factorisation, one fine offset t at a time:
 //   A_c[I][I+d] = sum_t sum_a P(a,I) A_t(a) P(a + t, I + d).
-// Offsets whose values vanish on the whole support box are skipped.
+// The support boxes of NG consecutive offsets are staged together (one round
+// of loads per group); offsets whose values vanish on the box are skipped.
 template <typename AT>
 __global__ void __launch_bounds__(256) k_rap125(const double *__restrict__ Af, Interp P, CGeom G,
-                                                RapDims W, AT *__restrict__ Ac) {
+                                                RapDims W, int NG, AT *__restrict__ Ac) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT *sm = reinterpret_cast<AT *>(smem_raw);
     const int WX = W.wx, WY = W.wy, WZ = W.wz;
     const int WM = max(WX, max(WY, WZ));
-    AT *Abox = sm;                              // [WZ][WY][WX]
-    AT *Wt = Abox + WX * WY * WZ;               // [3][5 d][5 t][WM]
+    const int BOX = WX * WY * WZ;
+    AT *Abox = sm;                              // [NG][WZ][WY][WX]
+    AT *Wt = Abox + (long long)NG * BOX;        // [3][5 d][5 t][WM]
     AT *U = Wt + 75 * WM;                       // [5][WY][WX]
     AT *V = U + 5 * WY * WX;                    // [25][WX]
     AT *out = V + 25 * WX;                      // [125]
+    int *nzf = reinterpret_cast<int *>(out + 128);   // [NG] offset has a nonzero in the box
 
     const int I = blockIdx.x;
     const int Ic[3] = {I % G.cx, (I / G.cx) % G.cy, I / (G.cx * G.cy)};
@@ -221,47 +233,62 @@ __global__ void __launch_bounds__(256) k_rap125(const double *__restrict__ Af, I
     }
     if (threadIdx.x < 125) out[threadIdx.x] = 0;
 
-    for (int t = 0; t < 125; ++t) {
-        const int tx = t % 5 - 2, ty = (t / 5) % 5 - 2, tz = t / 25 - 2;
-        int nonzero = 0;
-        for (int e = threadIdx.x; e < box; e += blockDim.x) {
-            const int ax = e % wx, ay = (e / wx) % wy, az = e / (wx * wy);
-            const long long g = (lo[0] + ax) + (long long)G.nx * (lo[1] + ay) + nxy * (lo[2] + az);
-            const double v = Af[(long long)t * Nf + g];
-            nonzero |= (v != 0.0);
-            Abox[(az * WY + ay) * WX + ax] = (AT)v;
-        }
-        if (!__syncthreads_or(nonzero)) continue;
-        const AT *Wz = Wt + (2 * 25) * WM + (tz + 2) * WM;   // + dz * 5 * WM
-        const AT *Wy = Wt + (1 * 25) * WM + (ty + 2) * WM;
-        const AT *Wx = Wt + (0 * 25) * WM + (tx + 2) * WM;
-        for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
-            const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
-            const AT *wz_ = Wz + dz * 5 * WM;
-            AT acc = 0;
-            for (int az = 0; az < wz; ++az) acc += wz_[az] * Abox[(az * WY + ay) * WX + ax];
-            U[(dz * WY + ay) * WX + ax] = acc;
+    for (int t0 = 0; t0 < 125; t0 += NG) {
+        const int ng = min(NG, 125 - t0);
+        for (int g = threadIdx.x; g < ng; g += blockDim.x) nzf[g] = 0;
+        __syncthreads();
+        for (int e = threadIdx.x; e < ng * box; e += blockDim.x) {
+            const int g = e / box, q = e % box;
+            const int ax = q % wx, ay = (q / wx) % wy, az = q / (wx * wy);
+            const long long gi = (lo[0] + ax) + (long long)G.nx * (lo[1] + ay) + nxy * (lo[2] + az);
+            const double v = Af[(long long)(t0 + g) * Nf + gi];
+            if (v != 0.0) nzf[g] = 1;
+            Abox[(long long)g * BOX + (az * WY + ay) * WX + ax] = (AT)v;
         }
         __syncthreads();
-        for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
-            const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
-            const AT *wy_ = Wy + dy * 5 * WM;
-            AT acc = 0;
-            for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * U[(dz * WY + ay) * WX + ax];
-            V[(dz * 5 + dy) * WX + ax] = acc;
+        for (int g = 0; g < ng; ++g) {
+            if (!nzf[g]) continue;
+            const int t = t0 + g;
+            const int tx = t % 5 - 2, ty = (t / 5) % 5 - 2, tz = t / 25 - 2;
+            const AT *Ab = Abox + (long long)g * BOX;
+            const AT *Wz = Wt + (2 * 25) * WM + (tz + 2) * WM;   // + dz * 5 * WM
+            const AT *Wy = Wt + (1 * 25) * WM + (ty + 2) * WM;
+            const AT *Wx = Wt + (0 * 25) * WM + (tx + 2) * WM;
+            for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
+                const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
+                const AT *wz_ = Wz + dz * 5 * WM;
+                AT acc = 0;
+                for (int az = 0; az < wz; ++az) acc += wz_[az] * Ab[(az * WY + ay) * WX + ax];
+                U[(dz * WY + ay) * WX + ax] = acc;
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
+                const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
+                const AT *wy_ = Wy + dy * 5 * WM;
+                AT acc = 0;
+                for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * U[(dz * WY + ay) * WX + ax];
+                V[(dz * 5 + dy) * WX + ax] = acc;
+            }
+            __syncthreads();
+            if (threadIdx.x < 125) {
+                const int e = threadIdx.x;
+                const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
+                const AT *wx_ = Wx + dx * 5 * WM;
+                AT acc = 0;
+                for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
+                out[e] += acc;
+            }
+            __syncthreads();
         }
-        __syncthreads();
-        if (threadIdx.x < 125) {
-            const int e = threadIdx.x;
-            const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
-            const AT *wx_ = Wx + dx * 5 * WM;
-            AT acc = 0;
-            for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
-            out[e] += acc;
-        }
-        __syncthreads();
     }
     if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
+}
+
+// FP32 Galerkin values into the FP64 level-operator storage
+__global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst, long long n) {
+    for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < n;
+         i += (long long)gridDim.x * blockDim.x)
+        dst[i] = (double)src[i];
 }
 
 // natural coarse index -> neighbour at offset o (or -1)
@@ -293,9 +320,13 @@ __global__ void k_assemble(const AT *__restrict__ Ac, const int *__restrict__ po
     }
 }
 
-// ELL forms of the couplings between block k and k+1:
-//   lo: rows of block k+1 -> (column in block k, A_c value)   [Lo_k]
-//   up: columns of block k+1 -> (row in block k, A_c value)   [Up_k, by column]
+// pivot / target block of edge e (see the header)
+__host__ __device__ __forceinline__ int edge_pivot(int e, int mid) { return e < mid ? e : e + 1; }
+__host__ __device__ __forceinline__ int edge_target(int e, int mid) { return e < mid ? e + 1 : e; }
+
+// ELL forms of the couplings across edge e:
+//   row ELL: rows of the target block -> (column in the pivot block, A_c value)  [A(target, pivot)]
+//   col ELL: columns of the target block -> (row in the pivot block, A_c value)  [A(pivot, target), by column]
 template <typename AT>
 __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
                       const int *__restrict__ cell, CGeom G, int *__restrict__ lo_q,
@@ -304,23 +335,23 @@ __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
     const long long tot = (long long)(G.nb - 1) * G.T;
     for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < tot;
          p += (long long)gridDim.x * blockDim.x) {
-        const int k = (int)(p / G.T);
-        const long long row = p + G.T;   // position in block k+1
-        const int I = cell[row];
+        const int e = (int)(p / G.T);
+        const int pv = edge_pivot(e, G.mid), tg = edge_target(e, G.mid);
+        const int I = cell[(long long)tg * G.T + p % G.T];   // row of the target block
         int nl = 0, nu = 0;
         if (I >= 0) {
             for (int o = 0; o < 125; ++o) {
                 const int J = nbr_index(G, I, o);
                 if (J < 0) continue;
                 const int pj = pos[J];
-                if (pj / G.T != k) continue;
-                if (nl < ELLW) {   // Lo_k[I][J] = A_c[I][J] (offset o of row I)
+                if (pj / G.T != pv) continue;
+                if (nl < ELLW) {   // A(target, pivot)[I][J] (offset o of row I)
                     lo_q[p * ELLW + nl] = pj % G.T;
                     lo_v[p * ELLW + nl] = Ac[(long long)o * G.Nc + I];
                 }
                 ++nl;
-                if (nu < ELLW) {   // Up_k[J][I] = A_c[J][I] (offset -d of row J), [e][T] layout
-                    const long long u = (long long)k * ELLW * G.T + (long long)nu * G.T + (p % G.T);
+                if (nu < ELLW) {   // A(pivot, target)[J][I] (offset -o of row J), [e][T] layout
+                    const long long u = (long long)e * ELLW * G.T + (long long)nu * G.T + (p % G.T);
                     up_q[u] = pj % G.T;
                     up_v[u] = Ac[(long long)(124 - o) * G.Nc + J];
                 }
@@ -330,9 +361,9 @@ __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
         if (nl > ELLW || nu > ELLW) atomicExch(err, ERR_ELL);
         lo_n[p] = min(nl, ELLW);
         up_n[p] = min(nu, ELLW);
-        for (int e = min(nl, ELLW); e < ELLW; ++e) { lo_q[p * ELLW + e] = 0; lo_v[p * ELLW + e] = 0; }
-        for (int e = min(nu, ELLW); e < ELLW; ++e) {
-            const long long u = (long long)k * ELLW * G.T + (long long)e * G.T + (p % G.T);
+        for (int q = min(nl, ELLW); q < ELLW; ++q) { lo_q[p * ELLW + q] = 0; lo_v[p * ELLW + q] = 0; }
+        for (int q = min(nu, ELLW); q < ELLW; ++q) {
+            const long long u = (long long)e * ELLW * G.T + (long long)q * G.T + (p % G.T);
             up_q[u] = 0;
             up_v[u] = 0;
         }
@@ -390,13 +421,17 @@ struct TileSmem {
     AT Y[TILE][TILE + 1];
     AT rowb[2][4][TILE];   // four pivot rows (double buffered)
     AT colb[2][TILE][4];   // four pivot columns (double buffered)
+    AT piv[2][4][4];       // inverse of the current / next 4 x 4 pivot block
 };
 
 // correctly rounded reciprocal (IEEE round to nearest)
 __device__ __forceinline__ float recip_rn(float x) { return __frcp_rn(x); }
 __device__ __forceinline__ double recip_rn(double x) { return __drcp_rn(x); }
 
-// in-place Gauss-Jordan inverse of a 4 x 4 block held in registers (no pivoting)
+// in-place Gauss-Jordan inverse of a 4 x 4 block held in registers (no pivoting);
+// FP32 takes the hardware reciprocal (a few ulp), FP64 the correctly rounded one
+__device__ __forceinline__ float recip_fast(float x) { return __fdividef(1.0f, x); }
+__device__ __forceinline__ double recip_fast(double x) { return recip_rn(x); }
 template <typename AT>
 __device__ __forceinline__ bool invert4(AT P[4][4]) {
     bool ok = true;
@@ -404,7 +439,7 @@ __device__ __forceinline__ bool invert4(AT P[4][4]) {
     for (int k = 0; k < 4; ++k) {
         const AT p = P[k][k];
         ok = ok && (p != (AT)0) && isfinite(p);
-        const AT ip = recip_rn(p);
+        const AT ip = recip_fast(p);
         P[k][k] = (AT)1;
 #pragma unroll
         for (int j = 0; j < 4; ++j) P[k][j] *= ip;
@@ -421,10 +456,14 @@ __device__ __forceinline__ bool invert4(AT P[4][4]) {
 }
 
 // In-place Gauss-Jordan inverse of tile (ti, ti) of M without pivoting, four
-// pivots per step: the 4 x 4 pivot block is inverted (redundantly) by every
-// thread and applied as a rank-4 update. Thread t owns rows tr..tr+3 and
-// columns tc..tc+3, so pivot rows / columns are published by whole 4 x 4
-// register blocks (no runtime register indexing); one barrier per step.
+// pivots per step (block column K = kb..kb+3, Pi = A_KK^{-1}):
+//     A_Kj <- Pi A_Kj,  A_ij <- A_ij - A_iK (Pi A_Kj),  A_iK <- -A_iK Pi,  A_KK <- Pi.
+// Thread t owns rows tr..tr+3 and columns tc..tc+3 (no runtime register
+// indexing). Per step: the pivot-row owners form Pi A_Kj and publish it, the
+// pivot-column owners publish A_iK (barrier), every other thread applies the
+// rank-4 update; the owner of the next pivot block inverts it as soon as its
+// own update is done and publishes Pi for the next step (barrier). The 4 x 4
+// inverse takes approximate reciprocals (FP32 preconditioner factors).
 template <typename AT>
 __device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
@@ -434,38 +473,59 @@ __device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err
 #pragma unroll
         for (int v = 0; v < 4; ++v)
             a[u][v] = __ldcg(M + (long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v);
+    auto invert_publish = [&](int par) {
+        AT P[4][4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) P[u][v] = a[u][v];
+        if (!invert4(P)) atomicExch(err, ERR_PIVOT);
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) sm.piv[par][u][v] = P[u][v];
+    };
+    if (tr == 0 && tc == 0) invert_publish(0);
+    __syncthreads();
     for (int kb = 0; kb < TILE; kb += 4) {
         const int par = (kb >> 2) & 1;
-        if (tr == kb) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) sm.rowb[par][u][tc + v] = a[u][v];
-        }
-        if (tc == kb) {
-#pragma unroll
-            for (int u = 0; u < 4; ++u)
-#pragma unroll
-                for (int v = 0; v < 4; ++v) sm.colb[par][tr + u][v] = a[u][v];
-        }
-        __syncthreads();
         AT Pi[4][4];
 #pragma unroll
         for (int u = 0; u < 4; ++u)
 #pragma unroll
-            for (int v = 0; v < 4; ++v) Pi[u][v] = sm.rowb[par][u][kb + v];
-        if (!invert4(Pi) && threadIdx.x == 0) atomicExch(err, ERR_PIVOT);
-        if (tr == kb && tc == kb) {            // pivot block -> its inverse
+            for (int v = 0; v < 4; ++v) Pi[u][v] = sm.piv[par][u][v];
+        if (tr == kb && tc == kb) {                  // pivot block -> its inverse
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
                 for (int v = 0; v < 4; ++v) a[u][v] = Pi[u][v];
-        } else if (tc == kb) {                 // pivot columns: -C Pi
+        } else if (tr == kb) {                       // pivot rows: Pi A_Kj, published
+            AT W[4][4];
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    AT t = 0;
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) t += Pi[u][q] * a[q][v];
+                    W[u][v] = t;
+                }
+#pragma unroll
+            for (int u = 0; u < 4; ++u)
+#pragma unroll
+                for (int v = 0; v < 4; ++v) {
+                    a[u][v] = W[u][v];
+                    sm.rowb[par][u][tc + v] = W[u][v];
+                }
+        } else if (tc == kb) {                       // pivot columns: publish A_iK, then -A_iK Pi
             AT c[4][4];
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
-                for (int m = 0; m < 4; ++m) c[u][m] = a[u][m];
+                for (int v = 0; v < 4; ++v) {
+                    c[u][v] = a[u][v];
+                    sm.colb[par][tr + u][v] = a[u][v];
+                }
 #pragma unroll
             for (int u = 0; u < 4; ++u)
 #pragma unroll
@@ -475,36 +535,27 @@ __device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err
                     for (int m = 0; m < 4; ++m) t += c[u][m] * Pi[m][v];
                     a[u][v] = -t;
                 }
-        } else {
-            // W = Pi R for my columns (R: the four pivot rows)
+        }
+        __syncthreads();
+        if (tr != kb && tc != kb) {                  // rank-4 update a -= A_iK (Pi A_Kj)
             AT W[4][4];
 #pragma unroll
             for (int m = 0; m < 4; ++m)
 #pragma unroll
-                for (int v = 0; v < 4; ++v) {
-                    AT t = 0;
+                for (int v = 0; v < 4; ++v) W[m][v] = sm.rowb[par][m][tc + v];
 #pragma unroll
-                    for (int q = 0; q < 4; ++q) t += Pi[m][q] * sm.rowb[par][q][tc + v];
-                    W[m][v] = t;
-                }
-            if (tr == kb) {                    // pivot rows: Pi R
+            for (int u = 0; u < 4; ++u) {
+                AT c[4];
 #pragma unroll
-                for (int u = 0; u < 4; ++u)
+                for (int m = 0; m < 4; ++m) c[m] = sm.colb[par][tr + u][m];
 #pragma unroll
-                    for (int v = 0; v < 4; ++v) a[u][v] = W[u][v];
-            } else {                           // rank-4 update: a -= C W
+                for (int v = 0; v < 4; ++v)
 #pragma unroll
-                for (int u = 0; u < 4; ++u) {
-                    AT c[4];
-#pragma unroll
-                    for (int m = 0; m < 4; ++m) c[m] = sm.colb[par][tr + u][m];
-#pragma unroll
-                    for (int v = 0; v < 4; ++v)
-#pragma unroll
-                        for (int m = 0; m < 4; ++m) a[u][v] -= c[m] * W[m][v];
-                }
+                    for (int m = 0; m < 4; ++m) a[u][v] -= c[m] * W[m][v];
             }
+            if (tr == kb + 4 && tc == kb + 4) invert_publish(par ^ 1);   // next pivot block
         }
+        __syncthreads();
     }
 #pragma unroll
     for (int u = 0; u < 4; ++u)
@@ -657,10 +708,10 @@ __device__ void subtile_product(TileSmem<AT> &sm, const AT *Xb, const AT *Yb, AT
 template <typename AT>
 struct FacArgs {
     AT *D, *C, *F;
-    AT *Z;   // scratch: 64 rows x T (tile (0, 0) used) for -D_{p+1,p} P_p
+    AT *Z;   // scratch: per chain 64 rows x T (tile (0, 0) used) for -D_{p+1,p} P_p
     const int *lo_q, *up_q, *lo_n, *up_n;
     const AT *lo_v, *up_v;
-    int T, nt, nb;
+    int T, nt, nb, mid;
     GridBar *bar;
     int *err;
 };
@@ -718,110 +769,164 @@ __device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, con
     __syncthreads();
 }
 
+// In-place inverses of the blocks blk[0..nblk) (one chain each), panel by
+// panel; the pivot tile of the next panel of each block is updated and
+// inverted by a CTA of its own (when the grid has more CTAs than chains).
+template <typename AT>
+__device__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT> &ts, const int *blk, int nblk,
+                              unsigned &epoch) {
+    const int T = a.T, nt = a.nt, G = gridDim.x, b = blockIdx.x;
+    const long long bsz = (long long)T * T;
+    // prologue: pivot tile 0 and the row panel of step 0
+    for (int c = b; c < nblk; c += G) tile_invert(ts, a.D + blk[c] * bsz, T, 0, a.err);
+    if (!grid_barrier(a.bar, a.err, epoch)) return false;
+    {
+        const int n0 = 4 * (nt - 1);
+        for (int it = b; it < nblk * n0; it += G) {
+            AT *Dk = a.D + blk[it / n0] * bsz;
+            const int j = ((it % n0) >> 2) + 1, q = it & 3;
+            subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, 0, 0, 0, j, 0, j, 0, 16 * q, (AT)1, false);
+        }
+    }
+    if (!grid_barrier(a.bar, a.err, epoch)) return false;
+    const bool own = G > nblk;              // CTAs 0..nblk-1 do only the pivot tiles
+    for (int p = 0; p < nt; ++p) {
+        const bool nxt = p + 1 < nt;
+        // phase A: trailing update D_ij -= D_ip D_pj (i, j != p); the next
+        // pivot tile is updated and inverted by one CTA per chain
+        const int nu = (nt - 1) * (nt - 1);
+        const int nz = nxt ? 4 : 0;           // Z = -D_{p+1,p} P_p into the chain's scratch strip
+        const int dpiv = p * (nt - 1) + p;    // update item of tile (p+1, p+1)
+        const int nreg = nu - (nxt ? 1 : 0) + nz;
+        auto update = [&](int c, int t) {     // update item t (in 0..nu) of chain c
+            AT *Dk = a.D + blk[c] * bsz;
+            const int bi = t / (nt - 1), bj = t % (nt - 1);
+            const int i = bi < p ? bi : bi + 1, j = bj < p ? bj : bj + 1;
+            subtile_product<AT, 64, 64, 4, 4>(ts, Dk, Dk, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
+        };
+        auto regular = [&](int q) {            // q in 0..nblk*nreg
+            const int c = q / nreg, r = q % nreg;
+            if (r >= nreg - nz) {
+                AT *Dk = a.D + blk[c] * bsz;
+                const int z = r - (nreg - nz);
+                subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, a.Z + (long long)c * TILE * T, T, p + 1, p,
+                                                  p, p, 0, 0, 16 * z, 0, (AT)-1, false);
+                return;
+            }
+            update(c, nxt && r >= dpiv ? r + 1 : r);
+        };
+        auto special = [&](int c) {
+            update(c, dpiv);
+            __syncthreads();
+            tile_invert(ts, a.D + blk[c] * bsz, T, p + 1, a.err);
+        };
+        if (nxt && own) {
+            if (b < nblk) special(b);
+            else
+                for (int q = b - nblk; q < nblk * nreg; q += G - nblk) regular(q);
+        } else {
+            const int ns = nxt ? nblk : 0;
+            for (int it = b; it < ns + nblk * nreg; it += G) {
+                if (it < ns) special(it);
+                else regular(it - ns);
+            }
+        }
+        if (!grid_barrier(a.bar, a.err, epoch)) return false;
+        // phase B: column panel of step p (D_ip = -D_ip P_p, i != p, p+1),
+        // row panel of step p+1 (D_{p+1,j} = P_{p+1} D_{p+1,j}, j != p, p+1),
+        // and tile (p+1, p) = P_{p+1} (-D_{p+1,p} P_p)
+        const int ncol = nt - 1 - (nxt ? 1 : 0);
+        const int nrow = nxt ? nt - 2 : 0;
+        const int nB = 4 * ncol + 4 * nrow + (nxt ? 4 : 0);
+        for (int it2 = b; it2 < nblk * nB; it2 += G) {
+            const int c = it2 / nB, it = it2 % nB;
+            AT *Dk = a.D + blk[c] * bsz;
+            if (it < 4 * ncol) {
+                const int t = it >> 2, q = it & 3;
+                const int i = t < p ? t : t + 2;      // skip p and p + 1
+                subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, Dk, T, i, p, p, p, i, p, 16 * q, 0,
+                                                  (AT)-1, false);
+            } else if (it < 4 * ncol + 4 * nrow) {
+                const int e = it - 4 * ncol;
+                const int t = e >> 2, q = e & 3;
+                const int j = t < p ? t : t + 2;      // skip p and p + 1
+                subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, p + 1, p + 1, p + 1, j, p + 1, j,
+                                                  0, 16 * q, (AT)1, false);
+            } else {                                  // D_{p+1,p} = P_{p+1} Z (column strips)
+                const int q = it - 4 * ncol - 4 * nrow;
+                subtile_product<AT, 64, 16, 2, 2>(ts, Dk, a.Z + (long long)c * TILE * T, Dk, T, p + 1,
+                                                  p + 1, 0, 0, p + 1, p, 0, 16 * q, (AT)1, false);
+            }
+        }
+        if (!grid_barrier(a.bar, a.err, epoch)) return false;
+    }
+    return true;
+}
+
+// Two-ended block elimination (see the header): at step s the top chain
+// inverts block s and the bottom chain block nb-1-s, then both form C_e, F_e
+// of their edge and update their target block; the middle block is inverted
+// last.
 template <typename AT>
 __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<AT> &ts = *reinterpret_cast<TileSmem<AT> *>(smem_raw);
     AT *rows = reinterpret_cast<AT *>(smem_raw);
-    const int T = a.T, nt = a.nt, G = gridDim.x, b = blockIdx.x;
+    const int T = a.T, G = gridDim.x, b = blockIdx.x, nb = a.nb, mid = a.mid;
     const long long bsz = (long long)T * T;
+    const int ntop = mid, nbot = nb - 1 - mid;
+    const int nsteps = max(ntop, nbot);
     unsigned epoch = 0;
-    for (int k = 0; k < a.nb; ++k) {
-        AT *Dk = a.D + k * bsz;
-        // prologue: pivot tile 0 and the row panel of step 0
-        if (b == 0) tile_invert(ts, Dk, T, 0, a.err);
-        if (!grid_barrier(a.bar, a.err, epoch)) return;
-        for (int it = b; it < 4 * (nt - 1); it += G) {
-            const int j = (it >> 2) + 1, q = it & 3;
-            subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, 0, 0, 0, j, 0, j, 0, 16 * q, (AT)1, false);
+    for (int s = 0; s <= nsteps; ++s) {
+        int blk[2], edg[2], nblk = 0, ne = 0;
+        if (s < nsteps) {
+            if (s < ntop) { blk[nblk++] = s; edg[ne++] = s; }
+            if (s < nbot) { blk[nblk++] = nb - 1 - s; edg[ne++] = nb - 2 - s; }
+        } else {
+            blk[nblk++] = mid;
         }
-        if (!grid_barrier(a.bar, a.err, epoch)) return;
-        for (int p = 0; p < nt; ++p) {
-            const bool nxt = p + 1 < nt;
-            // phase A: trailing update D_ij -= D_ip D_pj (i, j != p); the next
-            // pivot tile is updated and inverted by one CTA (item 0)
-            const int nu = (nt - 1) * (nt - 1);
-            const int nz = nxt ? 4 : 0;   // Z = -D_{p+1,p} P_p into the scratch tile (row strips)
-            for (int it = b; it < nu + nz; it += G) {
-                if (it >= nu) {
-                    const int q = it - nu;
-                    subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, a.Z, T, p + 1, p, p, p, 0, 0, 16 * q, 0,
-                                                      (AT)-1, false);
-                    continue;
-                }
-                const int t = nxt ? (it == 0 ? p * (nt - 1) + p : (it <= p * (nt - 1) + p ? it - 1 : it))
-                                  : it;
-                const int bi = t / (nt - 1), bj = t % (nt - 1);
-                const int i = bi < p ? bi : bi + 1, j = bj < p ? bj : bj + 1;
-                subtile_product<AT, 64, 64, 4, 4>(ts, Dk, Dk, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
-                if (nxt && it == 0) {
-                    __syncthreads();
-                    tile_invert(ts, Dk, T, p + 1, a.err);
-                }
-            }
-            if (!grid_barrier(a.bar, a.err, epoch)) return;
-            // phase B: column panel of step p (D_ip = -D_ip P_p, i != p, p+1),
-            // row panel of step p+1 (D_{p+1,j} = P_{p+1} D_{p+1,j}, j != p, p+1),
-            // and tile (p+1, p) = P_{p+1} (-D_{p+1,p} P_p)
-            const int ncol = nt - 1 - (nxt ? 1 : 0);
-            const int nrow = nxt ? nt - 2 : 0;
-            const int nB = 4 * ncol + 4 * nrow + (nxt ? 4 : 0);
-            for (int it = b; it < nB; it += G) {
-                if (it < 4 * ncol) {
-                    const int t = it >> 2, q = it & 3;
-                    const int i = t < p ? t : t + 2;      // skip p and p + 1
-                    subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, Dk, T, i, p, p, p, i, p, 16 * q, 0,
-                                                      (AT)-1, false);
-                } else if (it < 4 * ncol + 4 * nrow) {
-                    const int e = it - 4 * ncol;
-                    const int t = e >> 2, q = e & 3;
-                    const int j = t < p ? t : t + 2;      // skip p and p + 1
-                    subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, p + 1, p + 1, p + 1, j, p + 1, j,
-                                                      0, 16 * q, (AT)1, false);
-                } else {                                  // D_{p+1,p} = P_{p+1} Z (column strips)
-                    const int q = it - 4 * ncol - 4 * nrow;
-                    subtile_product<AT, 64, 16, 2, 2>(ts, Dk, a.Z, Dk, T, p + 1, p + 1, 0, 0, p + 1, p, 0,
-                                                      16 * q, (AT)1, false);
-                }
-            }
-            if (!grid_barrier(a.bar, a.err, epoch)) return;
-        }
-        if (k + 1 < a.nb) {
-            AT *Ck = a.C + k * bsz, *Fk = a.F + k * bsz;
-            const long long ell = (long long)T * ELLW;
-            const int *lq = a.lo_q + k * ell, *uq = a.up_q + k * ell;
-            const int *ln = a.lo_n + (long long)k * T, *un = a.up_n + (long long)k * T;
-            const AT *lv = a.lo_v + k * ell, *uv = a.up_v + k * ell;
-            const int nchunk = T / FROWS;
-            for (int it = b; it < T + nchunk; it += G) {
-                if (it < T) {                                  // C_k row = Lo_k row * E_k
-                    const int r = it;
-                    const int ne = ln[r];
-                    for (int c = threadIdx.x; c < T; c += blockDim.x) {
-                        AT acc = 0;
-                        for (int e0 = 0; e0 < ne; e0 += 8) {   // 8 row loads in flight
-                            AT eb[8], vb[8];
+        if (!invert_blocks(a, ts, blk, nblk, epoch)) return;
+        if (s == nsteps) break;
+        const long long ell = (long long)T * ELLW;
+        const int nchunk = T / FROWS;
+        const int nE = T + nchunk;
+        for (int it2 = b; it2 < ne * nE; it2 += G) {
+            const int e = edg[it2 / nE], it = it2 % nE;
+            const AT *Inv = a.D + edge_pivot(e, mid) * bsz;
+            if (it < T) {                                   // C_e row = A(target, pivot) row * Inv
+                const int *lq = a.lo_q + e * ell;
+                const AT *lv = a.lo_v + e * ell;
+                const int r = it;
+                const int nel = a.lo_n[(long long)e * T + r];
+                AT *Ce = a.C + e * bsz;
+                for (int c = threadIdx.x; c < T; c += blockDim.x) {
+                    AT acc = 0;
+                    for (int e0 = 0; e0 < nel; e0 += 8) {   // 8 row loads in flight
+                        AT eb[8], vb[8];
 #pragma unroll
-                            for (int m = 0; m < 8; ++m) {
-                                const bool ok = e0 + m < ne;
-                                const long long le = (long long)r * ELLW + e0 + m;
-                                vb[m] = ok ? lv[le] : (AT)0;
-                                eb[m] = ok ? __ldcg(Dk + (long long)lq[le] * T + c) : (AT)0;
-                            }
-#pragma unroll
-                            for (int m = 0; m < 8; ++m) acc += vb[m] * eb[m];
+                        for (int m = 0; m < 8; ++m) {
+                            const bool ok = e0 + m < nel;
+                            const long long le = (long long)r * ELLW + e0 + m;
+                            vb[m] = ok ? lv[le] : (AT)0;
+                            eb[m] = ok ? __ldcg(Inv + (long long)lq[le] * T + c) : (AT)0;
                         }
-                        Ck[(long long)r * T + c] = acc;
+#pragma unroll
+                        for (int m = 0; m < 8; ++m) acc += vb[m] * eb[m];
                     }
-                } else {                                       // F_k = E_k Up_k
-                    rows_times_up(rows, Dk, Fk, uq, uv, un, T, (it - T) * FROWS, false);
+                    Ce[(long long)r * T + c] = acc;
                 }
+            } else {                                        // F_e = Inv A(pivot, target)
+                rows_times_up(rows, Inv, a.F + e * bsz, a.up_q + e * ell, a.up_v + e * ell,
+                              a.up_n + (long long)e * T, T, (it - T) * FROWS, false);
             }
-            if (!grid_barrier(a.bar, a.err, epoch)) return;
-            for (int it = b; it < nchunk; it += G)             // D_{k+1} -= C_k Up_k
-                rows_times_up(rows, Ck, Dk + bsz, uq, uv, un, T, it * FROWS, true);
-            if (!grid_barrier(a.bar, a.err, epoch)) return;
         }
+        if (!grid_barrier(a.bar, a.err, epoch)) return;
+        for (int it2 = b; it2 < ne * nchunk; it2 += G) {    // S_target -= C_e A(pivot, target)
+            const int e = edg[it2 / nchunk], it = it2 % nchunk;
+            rows_times_up(rows, a.C + e * bsz, a.D + edge_target(e, mid) * bsz, a.up_q + e * ell,
+                          a.up_v + e * ell, a.up_n + (long long)e * T, T, it * FROWS, true);
+        }
+        if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
 }
 
@@ -949,27 +1054,47 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
         a.g[a.pos[I]] = acc;
     }
     if (!grid_barrier(a.bar, a.err, epoch)) return;
-    // forward: g_k -= C_{k-1} g_{k-1}, and in the same phase x_{k-1} = E_{k-1} g_{k-1}
-    for (int k = 1; k <= G.nb; ++k) {
-        const AT *gp = a.g + (long long)(k - 1) * T;
-        stage_vector(gp, xs, T);
-        const int wpb2 = blockDim.x / 32;
-        const int rows = (k < G.nb) ? 2 * T : T;
-        for (int r = blockIdx.x * wpb2 + (threadIdx.x >> 5); r < rows; r += gridDim.x * wpb2) {
-            if (r < T) {   // x_{k-1} row
-                const AT acc = row_dot(a.E + (k - 1) * bsz + (long long)r * T, xs, T, lane);
-                if (lane == 0) a.x[(long long)(k - 1) * T + r] = acc;
-            } else {       // g_k row
-                const int rr = r - T;
-                const AT acc = row_dot(a.C + (k - 1) * bsz + (long long)rr * T, xs, T, lane);
-                AT *y = a.g + (long long)k * T + rr;
+    // forward along both chains: g_target -= C_e g_pivot, and in the same
+    // phase x_pivot = Inv_pivot g_pivot (the back-substitution adds -F_e x_target)
+    const int nb = G.nb, mid = G.mid, ntop = mid, nbot = nb - 1 - mid;
+    const int nsteps = max(ntop, nbot);
+    for (int s = 0; s < nsteps; ++s) {
+        int edg[2], ne = 0;
+        if (s < ntop) edg[ne++] = s;
+        if (s < nbot) edg[ne++] = nb - 2 - s;
+        for (int c = 0; c < ne; ++c)
+            stage_vector(a.g + (long long)edge_pivot(edg[c], mid) * T, xs + (long long)c * T, T);
+        for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < ne * 2 * T; r += gridDim.x * wpb) {
+            const int c = r / (2 * T), rr = r % (2 * T), e = edg[c];
+            const AT *xv = xs + (long long)c * T;
+            if (rr < T) {   // x_pivot row
+                const int pv = edge_pivot(e, mid);
+                const AT acc = row_dot(a.E + pv * bsz + (long long)rr * T, xv, T, lane);
+                if (lane == 0) a.x[(long long)pv * T + rr] = acc;
+            } else {        // g_target row
+                const AT acc = row_dot(a.C + e * bsz + (long long)(rr - T) * T, xv, T, lane);
+                AT *y = a.g + (long long)edge_target(e, mid) * T + (rr - T);
                 if (lane == 0) *y = __ldcg(y) - acc;
             }
         }
         if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
-    for (int k = G.nb - 2; k >= 0; --k) {          // x_k -= F_k x_{k+1}
-        grid_gemv(a.F + k * bsz, a.x + (long long)(k + 1) * T, a.x + (long long)k * T, T, xs, true);
+    // middle block
+    grid_gemv(a.E + mid * bsz, a.g + (long long)mid * T, a.x + (long long)mid * T, T, xs, false);
+    if (!grid_barrier(a.bar, a.err, epoch)) return;
+    // back along both chains: x_pivot -= F_e x_target
+    for (int s = 0; s < nsteps; ++s) {
+        int edg[2], ne = 0;
+        if (s < ntop) edg[ne++] = ntop - 1 - s;
+        if (s < nbot) edg[ne++] = mid + s;
+        for (int c = 0; c < ne; ++c)
+            stage_vector(a.x + (long long)edge_target(edg[c], mid) * T, xs + (long long)c * T, T);
+        for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < ne * T; r += gridDim.x * wpb) {
+            const int c = r / T, rr = r % T, e = edg[c];
+            const AT acc = row_dot(a.F + e * bsz + (long long)rr * T, xs + (long long)c * T, T, lane);
+            AT *y = a.x + (long long)edge_pivot(e, mid) * T + rr;
+            if (lane == 0) *y = __ldcg(y) - acc;
+        }
         if (!grid_barrier(a.bar, a.err, epoch)) return;
     }
     // z (+)= P x, four fine cells per thread with their loads in flight together
@@ -1059,7 +1184,7 @@ static CGeom geom_of(const Coarse *c) {
     CGeom G;
     G.nx = c->nx; G.ny = c->ny; G.nz = c->nz;
     G.cx = c->c[0]; G.cy = c->c[1]; G.cz = c->c[2]; G.Nc = c->Nc;
-    G.T = c->T; G.nb = c->nb;
+    G.T = c->T; G.nb = c->nb; G.mid = c->mid;
     return G;
 }
 
@@ -1075,9 +1200,14 @@ static int configure_t(Coarse *c) {
     const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
     const int WM = std::max(WX, std::max(WY, WZ));
     c->rap_smem = sizeof(AT) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
-    c->rap125_smem = sizeof(AT) * (size_t)(WX * WY * WZ + 75 * WM + 5 * WY * WX + 25 * WX + 125);
+    // offsets staged per round: 25 (one plane of offsets) when it fits, else fewer
+    for (c->rap125_ng = 25;; c->rap125_ng = c->rap125_ng > 5 ? 5 : 1) {
+        c->rap125_smem = sizeof(AT) * (size_t)(c->rap125_ng * WX * WY * WZ + 75 * WM + 5 * WY * WX +
+                                               25 * WX + 128) + 25 * sizeof(int);
+        if (c->rap125_smem <= (size_t)big || c->rap125_ng == 1) break;
+    }
     c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
-    c->sol_smem = sizeof(AT) * (size_t)c->T;
+    c->sol_smem = sizeof(AT) * (size_t)2 * c->T;
     if (c->rap_smem > (size_t)big || c->rap125_smem > (size_t)big || c->fac_smem > (size_t)big ||
         c->sol_smem > (size_t)big)
         return RAS_EINVAL;
@@ -1161,6 +1291,7 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
     const int Treal = planes * nf * nm;
     c->T = ((Treal + TILE - 1) / TILE) * TILE;
     c->nb = (ns + planes - 1) / planes;
+    c->mid = c->nb == 1 ? 0 : (c->nb + 1) / 2;   // the two chains differ in length
     if ((long long)c->T * c->T * c->nb * c->esz > (8LL << 30)) return fail(RAS_EINVAL);
     std::vector<int> pos(c->Nc), cell((size_t)c->nb * c->T, -1);
     for (int z = 0; z < c->c[2]; ++z)
@@ -1192,7 +1323,7 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
         return fail(rc);
     {
         unsigned char *p_z = nullptr, *p_rx = nullptr, *p_ry = nullptr;
-        if ((rc = dalloc(&p_z, (size_t)TILE * c->T * c->esz))) return fail(rc);
+        if ((rc = dalloc(&p_z, (size_t)2 * TILE * c->T * c->esz))) return fail(rc);
         c->Zs = p_z;
         if ((rc = dalloc(&p_rx, (size_t)c->c[0] * c->n[1] * c->n[2] * c->esz))) return fail(rc);
         c->rx = p_rx;
@@ -1248,7 +1379,7 @@ static int factor_blocks_t(Coarse *c, cudaStream_t st) {
     }
     RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
     FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n, (const AT *)c->lo_v,
-                   (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->d_bar, c->d_err};
+                   (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, c->d_bar, c->d_err};
     void *args[] = {&fa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor<AT>, dim3(c->fac_grid),
                                        dim3(256), args, c->fac_smem, st));
@@ -1267,7 +1398,8 @@ static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
 template <typename AT>
 static int factor125_t(Coarse *c, const double *Af, cudaStream_t st) {
     RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
-    k_rap125<AT><<<c->Nc, 256, c->rap125_smem, st>>>(Af, interp_of(c), geom_of(c), W, (AT *)c->Ac);
+    k_rap125<AT><<<c->Nc, 256, c->rap125_smem, st>>>(Af, interp_of(c), geom_of(c), W, c->rap125_ng,
+                                                      (AT *)c->Ac);
     RAS_LAUNCHED();
     return factor_blocks_t<AT>(c, st);
 }
@@ -1392,7 +1524,9 @@ int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]) {
     c->rap_smem = sizeof(double) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
     if (c->rap_smem > (size_t)200 * 1024) { transfer_free(t); return RAS_EINVAL; }
     if (cudaFuncSetAttribute(k_rap<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
-        cudaSuccess) {
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_rap<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess) {
         transfer_free(t);
         return RAS_ECUDA;
     }
@@ -1414,10 +1548,18 @@ void transfer_dims(const Transfer *t, int c[3]) {
     for (int a = 0; a < 3; ++a) c[a] = t->geo.c[a];
 }
 
-int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, cudaStream_t st) {
+int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, float *scratch, cudaStream_t st) {
     const Coarse *c = &t->geo;
     RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
-    k_rap<double><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, Ac);
+    if (!scratch) {
+        k_rap<double><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, Ac);
+        RAS_LAUNCHED();
+        return RAS_OK;
+    }
+    const size_t smem32 = c->rap_smem / 2;
+    k_rap<float><<<c->Nc, 256, smem32, st>>>(A, interp_of(c), geom_of(c), W, scratch);
+    RAS_LAUNCHED();
+    k_widen<<<grid_of(125LL * c->Nc), 256, 0, st>>>(scratch, Ac, 125LL * c->Nc);
     RAS_LAUNCHED();
     return RAS_OK;
 }

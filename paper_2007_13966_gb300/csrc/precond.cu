@@ -40,7 +40,7 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
     if (pc->xfer) {
         // level 1: A_1 = P_1^T A P_1, its subdomain ILU(0) factors, and the
         // coarsest operator A_0 = P_0^T A_1 P_0 with its dense block LU
-        RAS_TRY(transfer_galerkin7(pc->xfer, A, pc->A1, st));
+        RAS_TRY(transfer_galerkin7(pc->xfer, A, pc->A1, pc->A1f, st));
         RAS_TRY(ras125_factor(pc->mid, pc->A1, st));
         RAS_TRY(coarse_factor125(pc->coarse, pc->A1, st));
     } else if (pc->coarse) {
@@ -144,6 +144,9 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
         }
         if (!rc) rc = coarse_setup_grid(&pc->coarse, pc->n1[0], pc->n1[1], pc->n1[2], *o);
         if (!rc) rc = dalloc(&pc->A1, (size_t)125 * pc->N1);
+        // reduced-precision factors: the middle operator is formed in FP32, as
+        // the coarse operator of the two-level method is for coarse_prec 32
+        if (!rc && o->factor_prec != 64) rc = dalloc(&pc->A1f, (size_t)125 * pc->N1);
         if (!rc) rc = dalloc(&pc->b1, pc->N1);
         if (!rc) rc = dalloc(&pc->x1, pc->N1);
         if (!rc) rc = dalloc(&pc->r1, pc->N1);
@@ -167,7 +170,7 @@ extern "C" void ras_precond_destroy(ras_precond *pc) {
     if (pc->coarse) coarse_free(pc->coarse);
     if (pc->xfer) transfer_free(pc->xfer);
     ras125_free(pc->mid);
-    dfree(pc->A1); dfree(pc->b1); dfree(pc->x1); dfree(pc->r1);
+    dfree(pc->A1); dfree(pc->A1f); dfree(pc->b1); dfree(pc->x1); dfree(pc->r1);
     dfree(pc->t1); dfree(pc->t2); dfree(pc->t3);
     for (int s = 0; s < 7; ++s) dfree(pc->Acopy[s]);
     for (auto e : pc->ev) cudaEventDestroy(e);

@@ -26,8 +26,9 @@ struct Transfer;
 int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]);
 void transfer_free(Transfer *t);
 void transfer_dims(const Transfer *t, int c[3]);
-// Ac [125][Nc] = P^T A P for a 7-point operator A (FP64)
-int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, cudaStream_t st);
+// Ac [125][Nc] = P^T A P for a 7-point operator A, stored in FP64; formed in
+// FP64, or in FP32 (then widened) when an FP32 scratch [125][Nc] is given
+int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, float *scratch, cudaStream_t st);
 int transfer_restrict(Transfer *t, const double *x, double *xc, cudaStream_t st);   // xc = P^T x
 int transfer_prolong(Transfer *t, const double *xc, double *x, cudaStream_t st);    // x += P xc
 }  // namespace ras
@@ -44,6 +45,7 @@ struct ras_precond {
     ras::Transfer *xfer = nullptr;       // fine grid -> level 1
     int n1[3] = {0, 0, 0}, N1 = 0;       // level-1 grid
     double *A1 = nullptr;                // [125][N1] Galerkin operator of level 1
+    float *A1f = nullptr;                // FP32 scratch of A1 (reduced-precision factors)
     ras::Ras125 mid;                     // RAS(ILU(0)) smoother of level 1
     double *b1 = nullptr, *x1 = nullptr, *r1 = nullptr;  // level-1 vectors [N1]
     bool timing = false;

@@ -104,6 +104,9 @@ __device__ __forceinline__ void copy_shape(Shape125 &dst, const Shape125 &src) {
     for (int t = threadIdx.x; t < (int)(sizeof(Shape125) / 4); t += blockDim.x) d[t] = s[t];
 }
 
+constexpr int PD = 3;        // pivots in flight in the factorisation
+constexpr int AD = 4;        // levels of solve records in flight
+
 __device__ __forceinline__ double sel4(const double (&w)[4], int r) {
     return r == 0 ? w[0] : (r == 1 ? w[1] : (r == 2 ? w[2] : w[3]));
 }
@@ -119,7 +122,7 @@ struct Fac125 {
     const unsigned *cells;
     const double *A;          // [125][N]
     int nx, ny, nz;
-    double *work;             // [nrow][64]: upper row of U (upper slots) and u_nn (slot 63)
+    double *work;             // [nrow][64]: upper row of U (upper slots) and 1/u_nn (slot 63)
     void *fwd, *bwd;          // records: L (lower slots); U (upper slots) and 1/u_nn (slot 63)
     int *err;
 };
@@ -127,11 +130,13 @@ struct Fac125 {
 // IKJ incomplete LU of one overlapped box in natural order, no pivoting: for
 // every lower column m of row n's pattern, in ascending order,
 //     w_m <- w_m / u_mm,   w_c <- w_c - w_m u_mc   (pattern columns c > m),
+// (the division taken as a product with 1/u_mm, formed once per row: FP64
+// instructions are scarce on this GPU and every lane would repeat it),
 // where the pattern is the nonzeros of A_i plus the diagonal; the row's final
 // w holds L (c < n) and U (c >= n). One warp per row: lane t holds the values
 // at offsets t, t + 32, t + 64, t + 96. The U row of each pivot m is read from
-// the FP64 work rows written at earlier levels (the next pivot's values are
-// fetched while the current one is applied).
+// the FP64 work rows written at earlier levels (the U values of the next PD
+// pivots are in flight while the current one is applied).
 template <int PREC>
 __global__ void __launch_bounds__(512) k_ras125_factor(Fac125 P) {
     extern __shared__ int posq[];                 // natural local index -> level-order row
@@ -200,7 +205,7 @@ __global__ void __launch_bounds__(512) k_ras125_factor(Fac125 P) {
                 if (m1) { const int s = 31 + __ffs(m1); m1 &= m1 - 1; return s; }
                 return -1;
             };
-            struct Pivot { int om; unsigned need; double piv; double u[4]; };
+            struct Pivot { int om; unsigned need; double pinv; double u[4]; };
             auto fetch = [&](int s, Pivot &f) {
                 const int om = sh.lowo[s];
                 const int mx = off_dx(om), my = off_dy(om), mz = off_dz(om);
@@ -208,7 +213,7 @@ __global__ void __launch_bounds__(512) k_ras125_factor(Fac125 P) {
                 const double *wr = work + (long long)posq[n + dm] * RREC;
                 f.om = om;
                 f.need = 0;
-                f.piv = wr[RREC - 1];
+                f.pinv = wr[RREC - 1];
 #pragma unroll
                 for (int r = 0; r < 4; ++r) {
                     const int cx = ox[r] - mx, cy = oy[r] - my, cz = oz[r] - mz;
@@ -218,26 +223,35 @@ __global__ void __launch_bounds__(512) k_ras125_factor(Fac125 P) {
                     if (need) f.need |= 1u << r;
                 }
             };
-            Pivot cur, nxt;
-            int s = take();
-            if (s >= 0) fetch(s, nxt);
-            while (s >= 0) {
-                cur = nxt;
-                const int s2 = take();
-                if (s2 >= 0) fetch(s2, nxt);
-                const int rm = cur.om >> 5, lm_lane = cur.om & 31;
-                const double wm = __shfl_sync(0xffffffffu, sel4(w, rm), lm_lane);
-                const double lm = wm / cur.piv;
-                if (lane == lm_lane) {
-                    if (rm == 0) w[0] = lm;
-                    else if (rm == 1) w[1] = lm;
-                    else if (rm == 2) w[2] = lm;
-                    else w[3] = lm;
-                }
+            // pivots in order, their U rows fetched PD pivots ahead (register ring)
+            Pivot pb[PD];
+            int ps[PD];
 #pragma unroll
-                for (int r = 0; r < 4; ++r)
-                    if (cur.need & (1u << r)) w[r] -= lm * cur.u[r];
-                s = s2;
+            for (int u = 0; u < PD; ++u) {
+                ps[u] = take();
+                if (ps[u] >= 0) fetch(ps[u], pb[u]);
+            }
+            bool more = ps[0] >= 0;
+            while (more) {
+#pragma unroll
+                for (int u = 0; u < PD; ++u) {
+                    if (ps[u] < 0) { more = false; break; }
+                    const Pivot cur = pb[u];
+                    ps[u] = take();
+                    if (ps[u] >= 0) fetch(ps[u], pb[u]);
+                    const int rm = cur.om >> 5, lm_lane = cur.om & 31;
+                    const double wm = __shfl_sync(0xffffffffu, sel4(w, rm), lm_lane);
+                    const double lm = wm * cur.pinv;
+                    if (lane == lm_lane) {
+                        if (rm == 0) w[0] = lm;
+                        else if (rm == 1) w[1] = lm;
+                        else if (rm == 2) w[2] = lm;
+                        else w[3] = lm;
+                    }
+#pragma unroll
+                    for (int r = 0; r < 4; ++r)
+                        if (cur.need & (1u << r)) w[r] -= lm * cur.u[r];
+                }
             }
             const double piv = __shfl_sync(0xffffffffu, w[1], CENTRE125 - 32);
             if (lane == 0 && (!(piv != 0.0) || !isfinite(piv))) atomicExch(P.err, 1);
@@ -255,8 +269,9 @@ __global__ void __launch_bounds__(512) k_ras125_factor(Fac125 P) {
                     const int ls = nL - 1 - sh.uslot[OP125 - 1 - o];
                     store_val<PREC>(P.fwd, row * RREC + ls, w[r]);
                 } else if (o == CENTRE125) {
-                    wrow[RREC - 1] = piv;
-                    store_val<PREC>(P.bwd, row * RREC + RREC - 1, 1.0 / piv);
+                    const double pinv = 1.0 / piv;
+                    wrow[RREC - 1] = pinv;
+                    store_val<PREC>(P.bwd, row * RREC + RREC - 1, pinv);
                 }
             }
         }
@@ -278,18 +293,21 @@ struct App125 {
     double *z;
     int nx, ny, nz;
     int accumulate;
+    int ycap;
 };
 
 // z = sum_i (R_i^0)^T U_i^{-1} L_i^{-1} R_i^delta r with, per row (one warp),
 //     forward   y_n = r_n - sum_{m<n} l_nm y_m,
 //     backward  z_n = (y_n - sum_{m>n} u_nm z_m) / u_nn,
 // lane t taking the couplings of slots t and t + 32 (slot 63 of the backward
-// record holds 1/u_nn). Accumulation in FP64 (64) or FP32 (32, 16).
+// record holds 1/u_nn). Accumulation in FP64 (64) or FP32 (32, 16). Each
+// warp's first row of a level is loaded AD levels ahead (register ring).
 template <int PREC>
 __global__ void __launch_bounds__(512) k_ras125_apply(App125 P) {
     using Acc = typename Val125<PREC>::Acc;
     extern __shared__ __align__(16) unsigned char smem[];
     Acc *Y = reinterpret_cast<Acc *>(smem);
+    int *lvl_s = reinterpret_cast<int *>(smem + (size_t)P.ycap * sizeof(Acc));
     __shared__ Shape125 sh;
     const Sub125 si = P.subs[blockIdx.x];
     copy_shape(sh, P.shapes[si.shape]);
@@ -322,44 +340,90 @@ __global__ void __launch_bounds__(512) k_ras125_apply(App125 P) {
         return (unsigned)i < (unsigned)bx && (unsigned)j < (unsigned)by && (unsigned)k < (unsigned)bz;
     };
     const long long fbase = si.foff * RREC;
+    for (int t = threadIdx.x; t <= sh.nlev; t += blockDim.x) lvl_s[t] = lvl[t];
     __syncthreads();
 
-    for (int l = 0; l < sh.nlev; ++l) {
-        const int q1 = lvl[l + 1];
-        for (int q = lvl[l] + wid; q < q1; q += nw) {
-            const unsigned e = cells[q];
-            const int i = e & 255u, j = (e >> 8) & 255u, k = (e >> 16) & 255u;
-            const int n = i + bx * j + bxy * k;
-            const long long rb = fbase + (long long)q * RREC;
-            Acc acc = 0;
-#pragma unroll
-            for (int h = 0; h < 2; ++h)
-                if (lv[h] && inbox(i + lx[h], j + ly[h], k + lz[h]))
-                    acc += load_val<PREC>(P.fwd, rb + lane + 32 * h) * Y[n + ld[h]];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) Y[n] -= acc;
+    // the first row of each level for this warp, fetched AD levels ahead
+    struct Row { int q; unsigned e; Acc v0, v1; };
+    auto fetch = [&](int l, const void *rec) {
+        Row rw;
+        rw.q = -1;
+        rw.e = 0;
+        rw.v0 = rw.v1 = 0;
+        if (l >= 0 && l < sh.nlev) {
+            const int q = lvl_s[l] + wid;
+            if (q < lvl_s[l + 1]) {
+                const long long rb = fbase + (long long)q * RREC;
+                rw.q = q;
+                rw.e = __ldg(cells + q);
+                rw.v0 = load_val<PREC>(rec, rb + lane);
+                rw.v1 = load_val<PREC>(rec, rb + lane + 32);
+            }
         }
-        __syncthreads();
+        return rw;
+    };
+    // forward row: y_n = r_n - sum_{m<n} l_nm y_m
+    auto fwd_row = [&](unsigned e, Acc a0, Acc a1) {
+        const int i = e & 255u, j = (e >> 8) & 255u, k = (e >> 16) & 255u;
+        const int n = i + bx * j + bxy * k;
+        Acc acc = 0;
+        if (lv[0] && inbox(i + lx[0], j + ly[0], k + lz[0])) acc += a0 * Y[n + ld[0]];
+        if (lv[1] && inbox(i + lx[1], j + ly[1], k + lz[1])) acc += a1 * Y[n + ld[1]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        if (lane == 0) Y[n] -= acc;
+    };
+    // backward row: z_n = (y_n - sum_{m>n} u_nm z_m) / u_nn (slot 63 = 1/u_nn)
+    auto bwd_row = [&](unsigned e, Acc b0, Acc b1) {
+        const int i = e & 255u, j = (e >> 8) & 255u, k = (e >> 16) & 255u;
+        const int n = i + bx * j + bxy * k;
+        Acc acc = 0;
+        if (lv[0] && inbox(i + ux[0], j + uy[0], k + uz[0])) acc += b0 * Y[n + ud[0]];
+        if (lv[1] && inbox(i + ux[1], j + uy[1], k + uz[1])) acc += b1 * Y[n + ud[1]];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+        const Acc dinv = __shfl_sync(0xffffffffu, b1, 31);
+        if (lane == 0) Y[n] = (Y[n] - acc) * dinv;
+    };
+
+    Row ring[AD];
+#pragma unroll
+    for (int u = 0; u < AD; ++u) ring[u] = fetch(u, P.fwd);
+    for (int lb = 0; lb < sh.nlev; lb += AD) {
+#pragma unroll
+        for (int u = 0; u < AD; ++u) {
+            const int l = lb + u;
+            if (l < sh.nlev) {
+                const Row cur = ring[u];
+                ring[u] = fetch(l + AD, P.fwd);
+                if (cur.q >= 0) fwd_row(cur.e, cur.v0, cur.v1);
+                for (int q = lvl_s[l] + wid + nw; q < lvl_s[l + 1]; q += nw) {
+                    const long long rb = fbase + (long long)q * RREC;
+                    fwd_row(__ldg(cells + q), load_val<PREC>(P.fwd, rb + lane),
+                            load_val<PREC>(P.fwd, rb + lane + 32));
+                }
+                __syncthreads();
+            }
+        }
     }
-    for (int l = sh.nlev - 1; l >= 0; --l) {
-        const int q1 = lvl[l + 1];
-        for (int q = lvl[l] + wid; q < q1; q += nw) {
-            const unsigned e = cells[q];
-            const int i = e & 255u, j = (e >> 8) & 255u, k = (e >> 16) & 255u;
-            const int n = i + bx * j + bxy * k;
-            const long long rb = fbase + (long long)q * RREC;
-            const Acc b1 = load_val<PREC>(P.bwd, rb + lane + 32);
-            Acc acc = 0;
-            if (lv[0] && inbox(i + ux[0], j + uy[0], k + uz[0]))
-                acc += load_val<PREC>(P.bwd, rb + lane) * Y[n + ud[0]];
-            if (lv[1] && inbox(i + ux[1], j + uy[1], k + uz[1])) acc += b1 * Y[n + ud[1]];
 #pragma unroll
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            const Acc dinv = __shfl_sync(0xffffffffu, b1, 31);
-            if (lane == 0) Y[n] = (Y[n] - acc) * dinv;
+    for (int u = 0; u < AD; ++u) ring[u] = fetch(sh.nlev - 1 - u, P.bwd);
+    for (int lb = 0; lb < sh.nlev; lb += AD) {
+#pragma unroll
+        for (int u = 0; u < AD; ++u) {
+            const int l = sh.nlev - 1 - (lb + u);
+            if (l >= 0) {
+                const Row cur = ring[u];
+                ring[u] = fetch(l - AD, P.bwd);
+                if (cur.q >= 0) bwd_row(cur.e, cur.v0, cur.v1);
+                for (int q = lvl_s[l] + wid + nw; q < lvl_s[l + 1]; q += nw) {
+                    const long long rb = fbase + (long long)q * RREC;
+                    bwd_row(__ldg(cells + q), load_val<PREC>(P.bwd, rb + lane),
+                            load_val<PREC>(P.bwd, rb + lane + 32));
+                }
+                __syncthreads();
+            }
         }
-        __syncthreads();
     }
     for (int t = threadIdx.x; t < sh.ncell; t += blockDim.x) {
         const int i = t % bx, j = (t / bx) % by, k = t / bxy;
@@ -505,7 +569,8 @@ int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int 
     R.lcap = lcap;
     R.nwarps = std::min(16, std::max(4, maxw));
     const size_t acc = prec == 64 ? 8 : 4;
-    R.smem_apply = (size_t)ycap * acc;
+    R.ycap = (ycap + 3) & ~3;
+    R.smem_apply = (size_t)R.ycap * acc + (size_t)lcap * sizeof(int);
     R.smem_factor = (size_t)ycap * sizeof(int);
     if (R.smem_apply > (size_t)SMEM125_MAX || R.smem_factor > (size_t)SMEM125_MAX) return RAS_EINVAL;
     const size_t esz = prec == 64 ? 8 : (prec == 32 ? 4 : 2);
@@ -583,6 +648,7 @@ int ras125_apply(Ras125 &R, const double *r, double *z, int accumulate, cudaStre
     P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.cells = R.d_cells;
     P.fwd = R.d_fwd; P.bwd = R.d_bwd; P.r = r; P.z = z;
     P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.accumulate = accumulate;
+    P.ycap = R.ycap;
     const int threads = 32 * R.nwarps;
     if (R.prec == 64) k_ras125_apply<64><<<R.nsub, threads, R.smem_apply, st>>>(P);
     else if (R.prec == 32) k_ras125_apply<32><<<R.nsub, threads, R.smem_apply, st>>>(P);

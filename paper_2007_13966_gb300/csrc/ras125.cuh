@@ -46,7 +46,7 @@ struct Ras125 {
     Shape125 *d_shapes = nullptr;
     int *d_lvl = nullptr;
     unsigned *d_cells = nullptr;
-    double *d_work = nullptr;            // [nrow][64] FP64 upper rows + pivot (factor only)
+    double *d_work = nullptr;            // [nrow][64] FP64 upper rows + 1/pivot (factor only)
     void *d_fwd = nullptr, *d_bwd = nullptr;   // [nrow][64] records at prec
     int *d_err = nullptr;
 };
