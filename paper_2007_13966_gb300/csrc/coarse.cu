@@ -692,13 +692,21 @@ __device__ void subtile_product(TileSmem<AT> &sm, const AT *Xb, const AT *Yb, AT
             for (int v = 0; v < BC; ++v) acc[u][v] += xa[u] * yb[v];
     }
     __syncthreads();   // the output may alias a staged input
+    // all reads of the old output before any store (one round of loads)
+    AT prev[BR][BC];
 #pragma unroll
     for (int u = 0; u < BR; ++u)
 #pragma unroll
-        for (int v = 0; v < BC; ++v) {
-            AT *o = Ob + (long long)(oi * TILE + r0 + rr + u) * ld + oj * TILE + c0 + cc + v;
-            *o = accumulate ? __ldcg(o) + sign * acc[u][v] : sign * acc[u][v];
-        }
+        for (int v = 0; v < BC; ++v)
+            prev[u][v] = accumulate
+                ? __ldcg(Ob + (long long)(oi * TILE + r0 + rr + u) * ld + oj * TILE + c0 + cc + v)
+                : (AT)0;
+#pragma unroll
+    for (int u = 0; u < BR; ++u)
+#pragma unroll
+        for (int v = 0; v < BC; ++v)
+            Ob[(long long)(oi * TILE + r0 + rr + u) * ld + oj * TILE + c0 + cc + v] =
+                prev[u][v] + sign * acc[u][v];
 }
 
 // ---------------------------------------------------------------------------
@@ -760,11 +768,12 @@ __device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, con
 #pragma unroll
                 for (int i = 0; i < FROWS; ++i) acc[i] += rows[i * T + qb[m]] * vb[m];
         }
+        AT prev[FROWS];
 #pragma unroll
-        for (int i = 0; i < FROWS; ++i) {
-            AT *o = Out + (long long)(r0 + i) * T + c;
-            *o = subtract ? __ldcg(o) - acc[i] : acc[i];
-        }
+        for (int i = 0; i < FROWS; ++i) prev[i] = subtract ? __ldcg(Out + (long long)(r0 + i) * T + c) : (AT)0;
+#pragma unroll
+        for (int i = 0; i < FROWS; ++i)
+            Out[(long long)(r0 + i) * T + c] = subtract ? prev[i] - acc[i] : acc[i];
     }
     __syncthreads();
 }
@@ -773,7 +782,7 @@ __device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, con
 // panel; the pivot tile of the next panel of each block is updated and
 // inverted by a CTA of its own (when the grid has more CTAs than chains).
 template <typename AT>
-__device__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT> &ts, const int *blk, int nblk,
+__device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT> &ts, const int *blk, int nblk,
                               unsigned &epoch) {
     const int T = a.T, nt = a.nt, G = gridDim.x, b = blockIdx.x;
     const long long bsz = (long long)T * T;
