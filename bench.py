@@ -274,6 +274,10 @@ def gb300_arm(args):
     run_steps(gp, pc, res, state, args.warmup, torch)
     torch.cuda.synchronize()
 
+    def clone(st):
+        return {"p_l": st["p_l"].clone(), "p_lm1": st["p_lm1"].clone(), "step": st["step"]}
+
+    s0 = clone(state)   # the state the timed steps start from
     # timed region: K implicit steps on resident state
     sampler = ClockSampler(local)
     sampler.start()
@@ -298,26 +302,27 @@ def gb300_arm(args):
     fp64 = None
     if not args.no_fp64_form and (args.factor_prec != 64 or args.coarse_prec != 64):
         pc64 = make_precond(ras, gp, po, 64, 64)
-        def clone(st):
-            return {"p_l": st["p_l"].clone(), "p_lm1": st["p_lm1"].clone(), "step": st["step"]}
-
-        st64 = clone(state)
-        run_steps(gp, pc64, res, st64, 1, torch)
-        k64 = max(1, min(args.steps, 2))
+        run_steps(gp, pc64, res, clone(s0), 1, torch)   # warm-up of the FP64 handle
+        k64 = max(1, min(args.steps, 3))
+        # both forms timed on the same first k64 steps of the timed region
+        sa, sb = clone(s0), clone(s0)
+        t64, outs64 = timed(lambda: run_steps(gp, pc64, res, sa, k64, torch), torch, dist_on)
+        tlo, _ = timed(lambda: run_steps(gp, pc, res, sb, k64, torch), torch, dist_on)
+        t64 = max_over_ranks(t64, dist_on)
+        tlo = max_over_ranks(tlo, dist_on)
         # one step of each form from the same FP64 state: max |p_lo - p_64| / max |p_64|
         diffs = []
-        sa = clone(st64)
+        sx = clone(s0)
         for _ in range(k64):
-            sb = clone(sa)
-            run_steps(gp, pc64, res, sa, 1, torch)
-            run_steps(gp, pc, res, sb, 1, torch)
-            diffs.append(float((sb["p_l"] - sa["p_l"]).abs().max() / sa["p_l"].abs().max()))
-        t64, outs64 = timed(lambda: run_steps(gp, pc64, res, st64, k64, torch), torch, dist_on)
-        t64 = max_over_ranks(t64, dist_on)
+            sy = clone(sx)
+            run_steps(gp, pc64, res, sx, 1, torch)
+            run_steps(gp, pc, res, sy, 1, torch)
+            diffs.append(float((sy["p_l"] - sx["p_l"]).abs().max() / sx["p_l"].abs().max()))
         fp64 = {"sec_per_step": t64 / k64, "steps": k64,
                 "newton_iters": [o["newton_iters"] for o in outs64],
                 "fgmres_iters": [o["lin_total"] for o in outs64],
-                "fp32_speedup": (t64 / k64) / sec_per_step,
+                "reduced_sec_per_step_same_steps": tlo / k64,
+                "fp32_speedup": t64 / tlo,
                 "state_rel_diff_per_step": diffs}
         del pc64
 
