@@ -107,6 +107,60 @@ struct RapDims {
     int wx, wy, wz;   // maximum support widths (shared-memory capacity)
 };
 
+// The three sum-factorised contractions of one fine-operator term for one
+// coarse row (z, then y, then x):
+//   U[dz][ay][ax] = sum_az Wz[dz][az] A[az][ay][ax],
+//   V[dz][dy][ax] = sum_ay Wy[dy][ay] U[dz][ay][ax],
+//   out[dz][dy][dx] += sum_ax Wx[dx][ax] V[dz][dy][ax].
+// uix / vix hold the index decomposition of the first two passes (computed once
+// per coarse row: dz << 16 | ay * WX + ax, and dz << 16 | dy << 8 | ax).
+template <typename AT>
+__device__ __forceinline__ void rap_term(const AT *Ab, const AT *Wz, const AT *Wy, const AT *Wx,
+                                         int dstride, AT *U, AT *V, AT *out, const int *uix,
+                                         const int *vix, int wx, int wy, int wz, int WX, int WY) {
+    const int nU = 5 * wy * wx, nV = 25 * wx, plane = WY * WX;
+    for (int e = threadIdx.x; e < nU; e += blockDim.x) {
+        const int code = uix[e];
+        const int dz = code >> 16, ab = code & 0xffff;
+        const AT *wz_ = Wz + dz * dstride;
+        AT acc = 0;
+        for (int az = 0; az < wz; ++az) acc += wz_[az] * Ab[az * plane + ab];
+        U[dz * plane + ab] = acc;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < nV; e += blockDim.x) {
+        const int code = vix[e];
+        const int dz = code >> 16, dy = (code >> 8) & 0xff, ax = code & 0xff;
+        const AT *wy_ = Wy + dy * dstride;
+        const AT *u = U + dz * plane + ax;
+        AT acc = 0;
+        for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * u[ay * WX];
+        V[(dz * 5 + dy) * WX + ax] = acc;
+    }
+    __syncthreads();
+    if (threadIdx.x < 125) {
+        const int e = threadIdx.x;
+        const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
+        const AT *wx_ = Wx + dx * dstride;
+        AT acc = 0;
+        for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
+        out[e] += acc;
+    }
+    __syncthreads();
+}
+
+// the index tables of rap_term for a coarse row with supports wx, wy
+__device__ __forceinline__ void rap_tables(int *uix, int *vix, int wx, int wy, int WX) {
+    for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
+        const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
+        uix[e] = (dz << 16) | (ay * WX + ax);
+    }
+    for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
+        const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
+        vix[e] = (dz << 16) | (dy << 8) | ax;
+    }
+}
+
 template <typename AT>
 __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapDims W,
                                              AT *__restrict__ Ac) {
@@ -119,6 +173,8 @@ __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapD
     AT *U = Wt + 45 * WM;                       // [5][WY][WX]
     AT *V = U + 5 * WY * WX;                    // [25][WX]
     AT *out = V + 25 * WX;                      // [125]
+    int *uix = reinterpret_cast<int *>(out + 128);   // [5][WY][WX]
+    int *vix = uix + 5 * WY * WX;                    // [25][WX]
 
     const int I = blockIdx.x;
     const int Ic[3] = {I % G.cx, (I / G.cx) % G.cy, I / (G.cx * G.cy)};
@@ -128,12 +184,15 @@ __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapD
     const int wx = P.hi[0][Ic[0]] - lo[0], wy = P.hi[1][Ic[1]] - lo[1], wz = P.hi[2][Ic[2]] - lo[2];
     const int box = wx * wy * wz;
     const long long nxy = (long long)G.nx * G.ny;
+    rap_tables(uix, vix, wx, wy, WX);
 
     for (int e = threadIdx.x; e < 7 * box; e += blockDim.x) {
         const int s = e / box, q = e % box;
         const int ax = q % wx, ay = (q / wx) % wy, az = q / (wx * wy);
         const long long g = (lo[0] + ax) + (long long)G.nx * (lo[1] + ay) + nxy * (lo[2] + az);
-        Abox[((s * WZ + az) * WY + ay) * WX + ax] = (AT)A.c[s][g];
+        const double *src = s == 0 ? A.c[0] : s == 1 ? A.c[1] : s == 2 ? A.c[2] : s == 3 ? A.c[3]
+                          : s == 4 ? A.c[4] : s == 5 ? A.c[5] : A.c[6];   // no indexed parameter copy
+        Abox[((s * WZ + az) * WY + ay) * WX + ax] = (AT)src[g];
     }
     // pair weights W[axis][d][s][a] = P(a, I) P(a + s, I + d)
     for (int e = threadIdx.x; e < 45 * WM; e += blockDim.x) {
@@ -160,31 +219,7 @@ __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapD
         const AT *Wz = Wt + (2 * 15) * WM + (sz + 1) * WM;   // + dz * 3 * WM
         const AT *Wy = Wt + (1 * 15) * WM + (sy + 1) * WM;
         const AT *Wx = Wt + (0 * 15) * WM + (sx + 1) * WM;
-        for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
-            const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
-            const AT *wz_ = Wz + dz * 3 * WM;
-            AT acc = 0;
-            for (int az = 0; az < wz; ++az) acc += wz_[az] * As[(az * WY + ay) * WX + ax];
-            U[(dz * WY + ay) * WX + ax] = acc;
-        }
-        __syncthreads();
-        for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
-            const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
-            const AT *wy_ = Wy + dy * 3 * WM;
-            AT acc = 0;
-            for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * U[(dz * WY + ay) * WX + ax];
-            V[(dz * 5 + dy) * WX + ax] = acc;
-        }
-        __syncthreads();
-        if (threadIdx.x < 125) {
-            const int e = threadIdx.x;
-            const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
-            const AT *wx_ = Wx + dx * 3 * WM;
-            AT acc = 0;
-            for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
-            out[e] += acc;
-        }
-        __syncthreads();
+        rap_term(As, Wz, Wy, Wx, 3 * WM, U, V, out, uix, vix, wx, wy, wz, WX, WY);
     }
     if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
 }
@@ -208,6 +243,8 @@ __global__ void __launch_bounds__(256) k_rap125(const double *__restrict__ Af, I
     AT *V = U + 5 * WY * WX;                    // [25][WX]
     AT *out = V + 25 * WX;                      // [125]
     int *nzf = reinterpret_cast<int *>(out + 128);   // [NG] offset has a nonzero in the box
+    int *uix = nzf + 32;                             // [5][WY][WX]
+    int *vix = uix + 5 * WY * WX;                    // [25][WX]
 
     const int I = blockIdx.x;
     const int Ic[3] = {I % G.cx, (I / G.cx) % G.cy, I / (G.cx * G.cy)};
@@ -218,6 +255,7 @@ __global__ void __launch_bounds__(256) k_rap125(const double *__restrict__ Af, I
     const int box = wx * wy * wz;
     const long long nxy = (long long)G.nx * G.ny;
     const long long Nf = nxy * G.nz;
+    rap_tables(uix, vix, wx, wy, WX);
 
     // pair weights W[axis][d][t][a] = P(a, I) P(a + t - 2, I + d - 2)
     for (int e = threadIdx.x; e < 75 * WM; e += blockDim.x) {
@@ -254,31 +292,7 @@ __global__ void __launch_bounds__(256) k_rap125(const double *__restrict__ Af, I
             const AT *Wz = Wt + (2 * 25) * WM + (tz + 2) * WM;   // + dz * 5 * WM
             const AT *Wy = Wt + (1 * 25) * WM + (ty + 2) * WM;
             const AT *Wx = Wt + (0 * 25) * WM + (tx + 2) * WM;
-            for (int e = threadIdx.x; e < 5 * wy * wx; e += blockDim.x) {
-                const int dz = e / (wy * wx), ay = (e / wx) % wy, ax = e % wx;
-                const AT *wz_ = Wz + dz * 5 * WM;
-                AT acc = 0;
-                for (int az = 0; az < wz; ++az) acc += wz_[az] * Ab[(az * WY + ay) * WX + ax];
-                U[(dz * WY + ay) * WX + ax] = acc;
-            }
-            __syncthreads();
-            for (int e = threadIdx.x; e < 25 * wx; e += blockDim.x) {
-                const int dz = e / (5 * wx), dy = (e / wx) % 5, ax = e % wx;
-                const AT *wy_ = Wy + dy * 5 * WM;
-                AT acc = 0;
-                for (int ay = 0; ay < wy; ++ay) acc += wy_[ay] * U[(dz * WY + ay) * WX + ax];
-                V[(dz * 5 + dy) * WX + ax] = acc;
-            }
-            __syncthreads();
-            if (threadIdx.x < 125) {
-                const int e = threadIdx.x;
-                const int dx = e % 5, dy = (e / 5) % 5, dz = e / 25;
-                const AT *wx_ = Wx + dx * 5 * WM;
-                AT acc = 0;
-                for (int ax = 0; ax < wx; ++ax) acc += wx_[ax] * V[(dz * 5 + dy) * WX + ax];
-                out[e] += acc;
-            }
-            __syncthreads();
+            rap_term(Ab, Wz, Wy, Wx, 5 * WM, U, V, out, uix, vix, wx, wy, wz, WX, WY);
         }
     }
     if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
@@ -1208,11 +1222,12 @@ static int configure_t(Coarse *c) {
     RAS_CK(cudaFuncSetAttribute(k_coarse_solve<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
     const int WM = std::max(WX, std::max(WY, WZ));
-    c->rap_smem = sizeof(AT) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
+    const size_t tables = sizeof(int) * (size_t)(5 * WY * WX + 25 * WX);
+    c->rap_smem = sizeof(AT) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 128) + tables;
     // offsets staged per round: 25 (one plane of offsets) when it fits, else fewer
     for (c->rap125_ng = 25;; c->rap125_ng = c->rap125_ng > 5 ? 5 : 1) {
         c->rap125_smem = sizeof(AT) * (size_t)(c->rap125_ng * WX * WY * WZ + 75 * WM + 5 * WY * WX +
-                                               25 * WX + 128) + 25 * sizeof(int);
+                                               25 * WX + 128) + 32 * sizeof(int) + tables;
         if (c->rap125_smem <= (size_t)big || c->rap125_ng == 1) break;
     }
     c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
@@ -1530,7 +1545,8 @@ int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]) {
     c->Nc = c->c[0] * c->c[1] * c->c[2];
     const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
     const int WM = std::max(WX, std::max(WY, WZ));
-    c->rap_smem = sizeof(double) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 125);
+    c->rap_smem = sizeof(double) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 128) +
+                  sizeof(int) * (size_t)(5 * WY * WX + 25 * WX);
     if (c->rap_smem > (size_t)200 * 1024) { transfer_free(t); return RAS_EINVAL; }
     if (cudaFuncSetAttribute(k_rap<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
             cudaSuccess ||
@@ -1565,7 +1581,10 @@ int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, float *scratc
         RAS_LAUNCHED();
         return RAS_OK;
     }
-    const size_t smem32 = c->rap_smem / 2;
+    const size_t smem32 = sizeof(float) * (size_t)(7 * c->wmax[0] * c->wmax[1] * c->wmax[2] +
+                                                   45 * std::max(c->wmax[0], std::max(c->wmax[1], c->wmax[2])) +
+                                                   5 * c->wmax[1] * c->wmax[0] + 25 * c->wmax[0] + 128) +
+                          sizeof(int) * (size_t)(5 * c->wmax[1] * c->wmax[0] + 25 * c->wmax[0]);
     k_rap<float><<<c->Nc, 256, smem32, st>>>(A, interp_of(c), geom_of(c), W, scratch);
     RAS_LAUNCHED();
     k_widen<<<grid_of(125LL * c->Nc), 256, 0, st>>>(scratch, Ac, 125LL * c->Nc);
