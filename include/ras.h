@@ -79,7 +79,12 @@ typedef struct {
 typedef struct {
     int px, py, pz;        /* subdomain counts per axis (Omega_i, Fig. 1)             */
     int overlap;           /* delta >= 0 (cells per side, cut at the boundary)       */
-    int ras_type;          /* 1 = left-RAS, Eq. equ:as-left (only value implemented) */
+    int ras_type;          /* fine-level combination of the subdomain solves:
+                              0 = AS, Eq. equ:as-class (sum over overlapped boxes),
+                              1 = left-RAS, Eq. equ:as-left (owned cells, default),
+                              2 = right-RAS, Eq. equ:as-right (owned-cell input,
+                              sum over overlapped boxes); 0 and 2 sum the boxes
+                              covering a cell in ascending box order            */
     int ilu_k;             /* 0 = ILU(0) subdomain solver (only value implemented)   */
     int factor_prec;       /* 64 = FP64 factors and solves; 32 = FP32 factors, FP32
                               solves; 16 = BF16-stored factors, FP32 solves          */
@@ -188,7 +193,9 @@ void ras_precond_destroy(ras_precond *pc);
 int ras_factor(ras_precond *pc, const ras_stencil *J, void *stream);
 
 /* z = M^{-1} r. One level: left-RAS, Eq. equ:as-left,
- *   z = sum_i (R_i^0)^T (L_i U_i)^{-1} R_i^delta r.
+ *   z = sum_i (R_i^0)^T (L_i U_i)^{-1} R_i^delta r
+ * (or AS / right-RAS by ras_type, which then also serves as M in the
+ * multilevel combinations).
  * Two levels: the configured two-level combination (Eq. equ:v-cycle by
  * default). Three levels: Algorithm 1 with one RAS-Richardson pre- and
  * post-smoothing step on the fine and middle levels and the exact block-LU

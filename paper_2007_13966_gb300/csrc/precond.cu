@@ -124,7 +124,7 @@ using namespace ras;
 extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **out) {
     if (!P || !o || !out) return RAS_EINVAL;
     *out = nullptr;
-    if (o->ras_type != 1 || o->ilu_k != 0) return RAS_EINVAL;
+    if (o->ras_type < 0 || o->ras_type > 2 || o->ilu_k != 0) return RAS_EINVAL;
     if (o->nlevels < 1 || o->nlevels > 3) return RAS_EINVAL;
     if (o->mlevel_type < 0 || o->mlevel_type > 4) return RAS_EINVAL;
     if (o->nlevels == 3 && (o->mlevel_type != 0 || o->coarse_overlap < 0)) return RAS_EINVAL;
@@ -132,7 +132,7 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
     pc->prob = P;
     pc->opts = *o;
     int rc = ras1_setup(pc->fine, P->nx, P->ny, P->nz, o->px, o->py, o->pz, o->overlap,
-                        o->factor_prec);
+                        o->factor_prec, o->ras_type);
     if (rc) { ras_precond_destroy(pc); return rc; }
     if (o->nlevels == 3) {
         rc = transfer_setup(&pc->xfer, P->nx, P->ny, P->nz, o->coarsen);

@@ -108,6 +108,8 @@ struct ApplyParams {
     int nx, ny, nz;
     int accumulate;
     int ycap, lcap, nbuf, chunk_cells;
+    int kind;        // 1 left-RAS; 0 AS, 2 right-RAS (box solutions to zbuf)
+    double *zbuf;
 };
 
 template <int PREC, int NBUF>
@@ -172,10 +174,14 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
 #pragma unroll
             for (int m = 0; m < 4; ++m) {
                 const int row = rbase + m * nw;
+                // right-RAS: R_i^0 on the input (cells owned by other boxes read as 0)
+                const int j = row % by, k = row / by;
+                const bool orow = P.kind != 2 || (j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1);
 #pragma unroll
                 for (int h = 0; h < 2; ++h) {
                     const int i = i0 + lane + 32 * h;
-                    if (row < nrow && i < bx) Y[row * bx + i] = (Acc)v[m][h];
+                    const bool own = orow && (P.kind != 2 || (i >= si.ox0 && i < si.ox1));
+                    if (row < nrow && i < bx) Y[row * bx + i] = own ? (Acc)v[m][h] : (Acc)0;
                 }
             }
         }
@@ -236,6 +242,11 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
     }
     cp_async_wait<0>();
 
+    if (P.kind != 1) {   // AS / right-RAS: the whole box solution, summed per cell later
+        double *dst = P.zbuf + si.foff;
+        for (int q = threadIdx.x; q < sh.ncell; q += blockDim.x) dst[q] = (double)Y[q];
+        return;
+    }
     // (R_i^0)^T: write the owned cells, by x-rows (coalesced)
     const int ox0 = si.ox0, ox1 = si.ox1;
     for (int row = wid; row < nrow; row += nw) {
@@ -246,6 +257,39 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
             const double v = (double)Y[row * bx + i];
             if (P.accumulate) dst[i] += v; else dst[i] = v;
         }
+    }
+}
+
+// z (+)= sum over the overlapped boxes covering each cell of their solution
+// ((R_i^delta)^T), boxes in ascending index order (deterministic)
+struct SumParams {
+    const SubInfo *subs;
+    const ShapeInfo *shapes;
+    const int *clo[3], *chi[3];   // per axis and coordinate: parts whose boxes cover it
+    int parts[3];
+    int nx, ny, nz;
+    const double *zbuf;
+    double *z;
+    int accumulate;
+};
+
+__global__ void __launch_bounds__(256) k_ras_sum(SumParams P) {
+    const long long N = (long long)P.nx * P.ny * P.nz;
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+        const int c[3] = {(int)(n % P.nx), (int)((n / P.nx) % P.ny), (int)(n / ((long long)P.nx * P.ny))};
+        double acc = 0.0;
+        for (int pz = P.clo[2][c[2]]; pz <= P.chi[2][c[2]]; ++pz) {
+            for (int py = P.clo[1][c[1]]; py <= P.chi[1][c[1]]; ++py) {
+                for (int px = P.clo[0][c[0]]; px <= P.chi[0][c[0]]; ++px) {
+                    const SubInfo si = P.subs[px + P.parts[0] * (py + P.parts[1] * pz)];
+                    const ShapeInfo &sh = P.shapes[si.shape];
+                    const int q = (c[0] - si.e0x) + sh.bx * ((c[1] - si.e0y) + sh.by * (c[2] - si.e0z));
+                    acc += P.zbuf[si.foff + q];
+                }
+            }
+        }
+        P.z[n] = P.accumulate ? P.z[n] + acc : acc;
     }
 }
 
@@ -333,8 +377,11 @@ static int set_factor_attr(size_t) {
     return RAS_OK;
 }
 
-int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec) {
+int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec,
+               int kind) {
     if (px < 1 || py < 1 || pz < 1 || overlap < 0) return RAS_EINVAL;
+    if (kind < 0 || kind > 2) return RAS_EINVAL;
+    R.kind = kind;
     if (px > nx || py > ny || pz > nz) return RAS_EINVAL;
     if (prec != 64 && prec != 32 && prec != 16) return RAS_EINVAL;
     R.nx = nx; R.ny = ny; R.nz = nz; R.N = nx * ny * nz;
@@ -501,6 +548,25 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     if (prec == 64) { RAS_TRY(set_apply_attr<64, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<64>(R.smem_factor)); }
     if (prec == 32) { RAS_TRY(set_apply_attr<32, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<32>(R.smem_factor)); }
     if (prec == 16) { RAS_TRY(set_apply_attr<16, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<16>(R.smem_factor)); }
+    if (kind != 1) {
+        // per axis and coordinate, the (contiguous) range of parts whose overlapped
+        // boxes cover it; box solutions are kept per record offset
+        R.parts[0] = px; R.parts[1] = py; R.parts[2] = pz;
+        for (int a = 0; a < 3; ++a) {
+            std::vector<int> lo(dims[a], parts[a]), hi(dims[a], -1);
+            for (int q = 0; q < parts[a]; ++q) {
+                const int e0 = std::max(cuts[a][q] - overlap, 0);
+                const int e1 = std::min(cuts[a][q + 1] + overlap, dims[a]);
+                for (int i = e0; i < e1; ++i) { lo[i] = std::min(lo[i], q); hi[i] = std::max(hi[i], q); }
+            }
+            RAS_TRY(dalloc(&R.d_clo[a], lo.size()));
+            RAS_TRY(dalloc(&R.d_chi[a], hi.size()));
+            RAS_CK(cudaMemcpy(R.d_clo[a], lo.data(), lo.size() * sizeof(int), cudaMemcpyHostToDevice));
+            RAS_CK(cudaMemcpy(R.d_chi[a], hi.data(), hi.size() * sizeof(int), cudaMemcpyHostToDevice));
+        }
+        RAS_TRY(dalloc(&R.zbuf, (size_t)R.nrec));
+        RAS_CK(cudaMemset(R.zbuf, 0, (size_t)R.nrec * sizeof(double)));
+    }
     return RAS_OK;
 }
 
@@ -510,6 +576,8 @@ void ras1_free(Ras1 &R) {
     if (R.d_fwd) cudaFree(R.d_fwd);
     if (R.d_bwd) cudaFree(R.d_bwd);
     R.d_fwd = R.d_bwd = nullptr;
+    dfree(R.zbuf);
+    for (int a = 0; a < 3; ++a) { dfree(R.d_clo[a]); dfree(R.d_chi[a]); }
 }
 
 int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st) {
@@ -543,10 +611,21 @@ int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t
     P.fwd = (const unsigned char *)R.d_fwd; P.bwd = (const unsigned char *)R.d_bwd;
     P.r = r; P.z = z; P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.accumulate = accumulate;
     P.ycap = R.ycap; P.lcap = R.lcap; P.nbuf = R.nbuf; P.chunk_cells = R.chunk_cells;
+    P.kind = R.kind; P.zbuf = R.zbuf;
     if (R.prec == 64) k_ras_apply<64, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
     else if (R.prec == 32) k_ras_apply<32, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
     else k_ras_apply<16, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
     RAS_LAUNCHED();
+    if (R.kind != 1) {
+        SumParams Q;
+        Q.subs = R.d_subs; Q.shapes = R.d_shapes;
+        for (int a = 0; a < 3; ++a) { Q.clo[a] = R.d_clo[a]; Q.chi[a] = R.d_chi[a]; Q.parts[a] = R.parts[a]; }
+        Q.nx = R.nx; Q.ny = R.ny; Q.nz = R.nz;
+        Q.zbuf = R.zbuf; Q.z = z; Q.accumulate = accumulate;
+        const int grid = (int)std::min<long long>(((long long)R.N + 255) / 256, 152LL * 16);
+        k_ras_sum<<<grid, 256, 0, st>>>(Q);
+        RAS_LAUNCHED();
+    }
     return RAS_OK;
 }
 

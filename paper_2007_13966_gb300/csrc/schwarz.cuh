@@ -49,17 +49,27 @@ struct Ras1 {
     unsigned *d_cells = nullptr;
     void *d_fwd = nullptr, *d_bwd = nullptr;
     int *d_err = nullptr;
+    // AS (kind 0) and right-RAS (kind 2): each box's whole solution goes to zbuf
+    // (at the box's record offset), then every cell sums the boxes covering it
+    int kind = 1;
+    double *zbuf = nullptr;
+    int *d_clo[3] = {}, *d_chi[3] = {}; // per axis and coordinate: first / last part covering it
+    int parts[3] = {1, 1, 1};
     std::vector<SubInfo> subs;
     std::vector<ShapeInfo> shapes;
 };
 
-int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec);
+int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec,
+               int kind = 1);
 void ras1_free(Ras1 &R);
 // numeric ILU(0) of every A_i = R_i^delta A (R_i^delta)^T; no synchronisation
 int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st);
 // reads and clears the pivot flag (synchronises)
 int ras1_check(Ras1 &R, cudaStream_t st);
-// z = M^{-1} r (accumulate = 0) or z += M^{-1} r (accumulate = 1)
+// z = M^{-1} r (accumulate = 0) or z += M^{-1} r (accumulate = 1), with
+// M^{-1} = sum_i (R_i^0)^T A_i^{-1} R_i^delta (left-RAS, kind 1),
+// sum_i (R_i^delta)^T A_i^{-1} R_i^delta (AS, kind 0) or
+// sum_i (R_i^delta)^T A_i^{-1} R_i^0 (right-RAS, kind 2)
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st);
 double ras1_bytes(const Ras1 &R);
 
