@@ -241,6 +241,40 @@ const char *ras_status_string(int status);
  * overwrites all of it before reading it. */
 int ras_norm2_noalloc(const double *x, long long n, double *result, void *stream);
 
+/* ----------------------------------------------------------------------------
+ * Discrete adjoint of the time loop. The paper computes no sensitivities;
+ * these calls give the pieces of the adjoint of the residual of Section 2
+ * (Eq. gover_sys with Eqs. implicit-method-bdf1 / -bdf2) with respect to
+ * per-cell log-permeability multipliers theta (k_{a,i} = k0_{a,i} exp(theta_i)
+ * on every axis; the transmissibility of a cell's fixed-pressure connections
+ * scales with its permeability). For a time loop with objective Phi(p^1..p^L):
+ *   J_l^T lambda^l = -dPhi/dp^l + (2/dt) s(p^{l+1}) lambda^{l+1}
+ *                    - (1/(2 dt)) s(p^{l+2}) lambda^{l+2},
+ *   dPhi/dtheta = sum_l (dF^l/dtheta)^T lambda^l,
+ * with s(p) = V phi c(p) and the history terms of the BDF2 steps.
+ * All arrays are device [N] FP64 unless stated; asynchronous on `stream`.
+ * ------------------------------------------------------------------------- */
+
+/* JT = J^T as a 7-point operator: JT->c[s][n] = J->c[opp(s)][neighbour s of n]
+ * (e.g. JT -x of cell n = J +x of cell n - 1), zero where the neighbour is
+ * absent. J and JT must not share arrays (RAS_EINVAL). */
+int ras_stencil_transpose(const ras_problem *prob, const ras_stencil *J, ras_stencil *JT,
+                          void *stream);
+
+/* rhs = -dphi + c1 s(p1) lam1 + c2 s(p2) lam2, s(p) = V phi c(p) per cell; a
+ * term whose state (p1 or p2) is NULL is absent, dphi NULL reads as 0. */
+int ras_adjoint_rhs(const ras_problem *prob, const double *dphi, const double *p1,
+                    const double *lam1, double c1, const double *p2, const double *lam2,
+                    double c2, double *rhs, void *stream);
+
+/* grad += (dF/dtheta)^T lam at the state p: per face (lam_i - lam_j) T mbar
+ * (p_i - p_j) k_j / (k_i + k_j) to cell i (and symmetrically to j), per
+ * connection lam_i T_c mbar (p_i - p_c). Uses the problem's per-cell mobility
+ * scratch (do not overlap with residual_eval of the same problem on another
+ * stream). */
+int ras_grad_logk(ras_problem *prob, const double *p, const double *lam, double *grad,
+                  void *stream);
+
 /* Text of the last CUDA runtime failure seen by the library (static storage,
  * empty if none); diagnostic only. */
 const char *ras_last_error(void);

@@ -110,6 +110,7 @@ struct ras_problem {
     double hx, hy, hz, V;
     double a, b, R, T, mu, inv_mu;
     double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *phi = nullptr;
+    double *kx = nullptr, *ky = nullptr, *kz = nullptr;   // permeabilities (sensitivities)
     int nconn = 0;
     int *conn_ptr = nullptr;       // [N+1] CSR of connections per cell
     double *conn_p = nullptr, *conn_T = nullptr, *conn_m = nullptr;

@@ -380,6 +380,84 @@ __global__ void k_conn_mobility(int nconn, EosConst E, const double *__restrict_
         cm[q] = eos_cell(cp[q], E).m;
 }
 
+// ---------------------------------------------------------------------------
+// discrete adjoint of the time loop (no counterpart in the paper): J^T as a
+// 7-point operator, the adjoint right-hand side with the BDF2 history terms,
+// and (dF/dtheta)^T lambda for per-cell log-permeability multipliers theta
+// ---------------------------------------------------------------------------
+
+// JT[s][n] = J[opp(s)][neighbour s of n]: (J^T)_{n, n-1} = dF_{n-1}/dp_n = J[+x][n-1], ...
+__global__ void __launch_bounds__(256) k_stencil_transpose(int nx, int ny, int nz, JacOut J,
+                                                           JacOut JT) {
+    const int N = nx * ny * nz, nxy = nx * ny;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const int i = n % nx, j = (n / nx) % ny, k = n / nxy;
+        JT.c[0][n] = J.c[0][n];
+        JT.c[1][n] = i > 0 ? J.c[2][n - 1] : 0.0;
+        JT.c[2][n] = i < nx - 1 ? J.c[1][n + 1] : 0.0;
+        JT.c[3][n] = j > 0 ? J.c[4][n - nx] : 0.0;
+        JT.c[4][n] = j < ny - 1 ? J.c[3][n + nx] : 0.0;
+        JT.c[5][n] = k > 0 ? J.c[6][n - nxy] : 0.0;
+        JT.c[6][n] = k < nz - 1 ? J.c[5][n + nxy] : 0.0;
+    }
+}
+
+// rhs = -dphi + c1 s(p1) lam1 + c2 s(p2) lam2 with s(p) = V phi c(p); a term
+// whose state is null is absent
+__global__ void __launch_bounds__(256) k_adjoint_rhs(int N, EosConst E, double Vol,
+                                                     const double *__restrict__ phi,
+                                                     const double *__restrict__ dphi,
+                                                     const double *__restrict__ p1,
+                                                     const double *__restrict__ l1, double c1,
+                                                     const double *__restrict__ p2,
+                                                     const double *__restrict__ l2, double c2,
+                                                     double *__restrict__ rhs) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        double r = dphi ? -dphi[n] : 0.0;
+        if (p1) r += c1 * Vol * phi[n] * eos_cell(p1[n], E).c * l1[n];
+        if (p2) r += c2 * Vol * phi[n] * eos_cell(p2[n], E).c * l2[n];
+        rhs[n] = r;
+    }
+}
+
+__global__ void __launch_bounds__(256) k_mobility(int N, EosConst E, const double *__restrict__ p,
+                                                  double *__restrict__ m) {
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x)
+        m[n] = eos_cell(p[n], E).m;
+}
+
+// grad_n += sum over the faces of n of (lam_n - lam_q) T mbar (p_n - p_q) k_q / (k_n + k_q)
+//           + sum over the connections of n of lam_n T_c mbar (p_n - p_c)
+// (dT_f / dtheta_n = T_f k_q / (k_n + k_q) for the harmonic face transmissibility,
+// k along the face's axis; connection transmissibilities scale with k_n)
+__global__ void __launch_bounds__(256) k_grad_logk(
+    int nx, int ny, int nz, const double *__restrict__ p, const double *__restrict__ m,
+    const double *__restrict__ lam, const double *__restrict__ kx, const double *__restrict__ ky,
+    const double *__restrict__ kz, const double *__restrict__ Tx, const double *__restrict__ Ty,
+    const double *__restrict__ Tz, const int *__restrict__ conn_ptr,
+    const double *__restrict__ conn_p, const double *__restrict__ conn_T,
+    const double *__restrict__ conn_m, double *__restrict__ grad) {
+    const int N = nx * ny * nz, nxy = nx * ny;
+    for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
+        const int i = n % nx, j = (n / nx) % ny, k = n / nxy;
+        const double pn = p[n], mn = m[n], ln = lam[n];
+        double g = 0.0;
+        auto face = [&](double T, int q, const double *ka) {
+            const double flux = T * 0.5 * (mn + m[q]) * (pn - p[q]);
+            g += (ln - lam[q]) * flux * ka[q] / (ka[n] + ka[q]);
+        };
+        if (i < nx - 1) face(Tx[n], n + 1, kx);
+        if (i > 0) face(Tx[n - 1], n - 1, kx);
+        if (j < ny - 1) face(Ty[n], n + nx, ky);
+        if (j > 0) face(Ty[n - nx], n - nx, ky);
+        if (k < nz - 1) face(Tz[n], n + nxy, kz);
+        if (k > 0) face(Tz[n - nxy], n - nxy, kz);
+        for (int q = conn_ptr[n]; q < conn_ptr[n + 1]; ++q)
+            g += ln * conn_T[q] * 0.5 * (mn + conn_m[q]) * (pn - conn_p[q]);
+        grad[n] += g;
+    }
+}
+
 static EosConst eos_const(const ras_problem *P) {
     EosConst E;
     E.alpha = P->a / (P->R * P->R * P->T * P->T);
@@ -436,7 +514,8 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     if ((rc = dalloc(&P->Tx, N)) || (rc = dalloc(&P->Ty, N)) || (rc = dalloc(&P->Tz, N)) ||
         (rc = dalloc(&P->phi, N)) || (rc = dalloc(&P->eos_m, N)) || (rc = dalloc(&P->eos_dm, N)) ||
         (rc = dalloc(&P->conn_ptr, N + 1)) || (rc = dalloc(&P->conn_p, rock->nconn)) ||
-        (rc = dalloc(&P->conn_T, rock->nconn)) || (rc = dalloc(&P->conn_m, rock->nconn)))
+        (rc = dalloc(&P->conn_T, rock->nconn)) || (rc = dalloc(&P->conn_m, rock->nconn)) ||
+        (rc = dalloc(&P->kx, N)) || (rc = dalloc(&P->ky, N)) || (rc = dalloc(&P->kz, N)))
         return fail(rc);
     if ((rc = reduce_ws_init(P->red))) return fail(rc);
     P->nconn = rock->nconn;
@@ -447,6 +526,9 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
         return e == cudaSuccess;
     };
     bool ok = ck(cudaMemcpyAsync(P->phi, rock->phi, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ok = ok && ck(cudaMemcpyAsync(P->kx, rock->kx, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ok = ok && ck(cudaMemcpyAsync(P->ky, rock->ky, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    ok = ok && ck(cudaMemcpyAsync(P->kz, rock->kz, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (rock->nconn > 0) {
         ok = ok && ck(cudaMemcpyAsync(cell, rock->conn_cell, rock->nconn * sizeof(int),
                                       cudaMemcpyDeviceToDevice, st));
@@ -477,6 +559,7 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
 extern "C" void ras_problem_destroy(ras_problem *P) {
     if (!P) return;
     dfree(P->Tx); dfree(P->Ty); dfree(P->Tz); dfree(P->phi);
+    dfree(P->kx); dfree(P->ky); dfree(P->kz);
     dfree(P->eos_m); dfree(P->eos_dm);
     dfree(P->conn_ptr); dfree(P->conn_p); dfree(P->conn_T); dfree(P->conn_m);
     reduce_ws_free(P->red);
@@ -561,4 +644,41 @@ extern "C" long long ras_kernel_launches(void) { return g_launches.load(); }
 extern "C" const char *ras_last_error(void) {
     std::lock_guard<std::mutex> lk(ras::g_err_mu);
     return ras::g_last_error.c_str();
+}
+
+extern "C" int ras_stencil_transpose(const ras_problem *P, const ras_stencil *J, ras_stencil *JT,
+                                     void *stream) {
+    if (!P || !J || !JT) return RAS_EINVAL;
+    for (int s = 0; s < 7; ++s) {
+        if (!J->c[s] || !JT->c[s]) return RAS_EINVAL;
+        for (int t = 0; t < 7; ++t) if (J->c[s] == JT->c[t]) return RAS_EINVAL;   // no aliasing
+    }
+    JacOut a, b;
+    for (int s = 0; s < 7; ++s) { a.c[s] = J->c[s]; b.c[s] = JT->c[s]; }
+    k_stencil_transpose<<<grid_for(P->N), 256, 0, S(stream)>>>(P->nx, P->ny, P->nz, a, b);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+extern "C" int ras_adjoint_rhs(const ras_problem *P, const double *dphi, const double *p1,
+                               const double *lam1, double c1, const double *p2,
+                               const double *lam2, double c2, double *rhs, void *stream) {
+    if (!P || !rhs || (p1 && !lam1) || (p2 && !lam2)) return RAS_EINVAL;
+    k_adjoint_rhs<<<grid_for(P->N), 256, 0, S(stream)>>>(P->N, eos_const(P), P->V, P->phi, dphi,
+                                                          p1, lam1, c1, p2, lam2, c2, rhs);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+extern "C" int ras_grad_logk(ras_problem *P, const double *p, const double *lam, double *grad,
+                             void *stream) {
+    if (!P || !p || !lam || !grad) return RAS_EINVAL;
+    cudaStream_t st = S(stream);
+    k_mobility<<<grid_for(P->N), 256, 0, st>>>(P->N, eos_const(P), p, P->eos_m);
+    RAS_LAUNCHED();
+    k_grad_logk<<<grid_for(P->N), 256, 0, st>>>(P->nx, P->ny, P->nz, p, P->eos_m, lam, P->kx, P->ky,
+                                                 P->kz, P->Tx, P->Ty, P->Tz, P->conn_ptr, P->conn_p,
+                                                 P->conn_T, P->conn_m, grad);
+    RAS_LAUNCHED();
+    return RAS_OK;
 }

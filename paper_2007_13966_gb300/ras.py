@@ -22,7 +22,8 @@ RAS_EINVAL, RAS_ECUDA, RAS_ENOMEM, RAS_ENAN, RAS_EZEROPIVOT = -1, -2, -3, -4, -5
 EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_stencil_matvec",
             "ras_setup", "ras_precond_destroy", "ras_factor", "ras_apply", "gmres_solve",
             "newton_step", "ras_status_string", "ras_last_error", "ras_kernel_launches",
-            "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc"]
+            "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc",
+            "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk"]
 
 
 class Grid(C.Structure):
@@ -108,6 +109,9 @@ def lib():
             "ras_timing_read": (i, [vp, C.POINTER(d), C.POINTER(C.c_longlong), i]),
             "ras_apply_bytes": (d, [vp]),
             "ras_norm2_noalloc": (i, [vp, C.c_longlong, vp, vp]),
+            "ras_stencil_transpose": (i, [vp, C.POINTER(Stencil), C.POINTER(Stencil), vp]),
+            "ras_adjoint_rhs": (i, [vp, vp, vp, vp, d, vp, vp, d, vp, vp]),
+            "ras_grad_logk": (i, [vp, vp, vp, vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -209,6 +213,20 @@ class Problem:
                                   C.byref(nrm) if want_norm else None, _stream()),
               "residual_eval")
         return nrm.value if want_norm else None
+
+    def stencil_transpose(self, J, JT):
+        Js, JTs = stencil_struct(J), stencil_struct(JT)
+        check(lib().ras_stencil_transpose(self.h, C.byref(Js), C.byref(JTs), _stream()),
+              "ras_stencil_transpose")
+
+    def adjoint_rhs(self, dphi, p1, lam1, c1, p2, lam2, c2, rhs):
+        opt = lambda t: _ptr(t) if t is not None else None
+        check(lib().ras_adjoint_rhs(self.h, opt(dphi), opt(p1), opt(lam1), float(c1), opt(p2),
+                                    opt(lam2), float(c2), _ptr(rhs), _stream()), "ras_adjoint_rhs")
+
+    def grad_logk(self, p, lam, grad):
+        check(lib().ras_grad_logk(self.h, _ptr(p), _ptr(lam), _ptr(grad), _stream()),
+              "ras_grad_logk")
 
     def matvec(self, J, x, y):
         Js = stencil_struct(J)
