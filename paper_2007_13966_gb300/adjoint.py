@@ -36,6 +36,8 @@ class AdjointOpts:
     adj_rtol: float = 1e-12
     restart: int = 30
     maxit: int = 4000
+    nlevels: int = 1                 # 2: two-level V-cycle (forward and adjoint solves)
+    coarsen: tuple = (4, 4, 4)
 
 
 def scaled_reservoir(res, theta):
@@ -55,7 +57,8 @@ def run_forward(res, theta, nsteps, opts: AdjointOpts):
     """(problem handle, states p^0..p^L on the device, objective, producer cells)."""
     r = scaled_reservoir(res, theta)
     gp = ras.Problem(r)
-    pc = ras.Precond(gp, opts.parts, opts.overlap, factor_prec=64)
+    pc = ras.Precond(gp, opts.parts, opts.overlap, factor_prec=64, nlevels=opts.nlevels,
+                     coarsen=opts.coarsen, coarse_prec=64)
     N = r.grid.n
     p0 = torch.full((N,), r.p0, dtype=torch.float64, device="cuda")
     states = [p0.clone()]
@@ -88,7 +91,8 @@ def adjoint_gradient(gp, dt, states, cells, opts: AdjointOpts):
     rhs = torch.zeros(N, **f64)
     dphi = torch.zeros(N, **f64)
     grad = torch.zeros(N, **f64)
-    pcT = ras.Precond(gp, opts.parts, opts.overlap, factor_prec=64, ras_type=2)
+    pcT = ras.Precond(gp, opts.parts, opts.overlap, factor_prec=64, ras_type=2,
+                      nlevels=opts.nlevels, coarsen=opts.coarsen, coarse_prec=64)
     lam = [None] * (L + 3)
     for l in range(L, 0, -1):
         order = 1 if l == 1 else 2

@@ -104,3 +104,16 @@ def test_gradient_matches_finite_differences(ras):
     err = np.abs(g[idx] - np.array(fd)).max() / np.abs(g).max()
     print("fd max relative error", err)
     assert err <= 1e-4
+
+
+def test_gradient_with_two_level_solves(ras):
+    """The gradient does not depend on the preconditioner: two-level V-cycle
+    (right-RAS smoother on J^T) for the forward and adjoint solves."""
+    from paper_2007_13966_gb300 import adjoint as gadj
+    res = reservoir((16, 12, 8), seed=5)
+    cells = oadj.producer_cells(res)
+    _, grad_ref, _ = oadj.adjoint_gradient(res, 3, cells)
+    opts = gadj.AdjointOpts(parts=(2, 2, 2), overlap=1, nlevels=2, coarsen=(2, 2, 2))
+    theta = torch.zeros(res.grid.n, dtype=torch.float64, device="cuda", requires_grad=True)
+    gadj.objective(theta, res, 3, opts).backward()
+    assert rel_err(host(theta.grad), grad_ref) < 1e-7
