@@ -85,7 +85,11 @@ typedef struct {
                               2 = right-RAS, Eq. equ:as-right (owned-cell input,
                               sum over overlapped boxes); 0 and 2 sum the boxes
                               covering a cell in ascending box order            */
-    int ilu_k;             /* 0 = ILU(0) subdomain solver (only value implemented)   */
+    int ilu_k;             /* level of fill k of the ILU(k) subdomain solver (natural
+                              order in each box, no pivoting; Section 4's ILU(k)
+                              variants): 0 = ILU(0); 1, 2 = ILU(1), ILU(2) (the fill
+                              of larger k leaves the 5x5x5 neighbourhood:
+                              RAS_EINVAL); k > 0 requires ras_type = 1           */
     int factor_prec;       /* 64 = FP64 factors and solves; 32 = FP32 factors, FP32
                               solves; 16 = BF16-stored factors, FP32 solves          */
     int nlevels;           /* 1 = one-level; 2 = two-level (Eq. equ:v-cycle);

@@ -19,7 +19,8 @@ static int fine_apply(ras_precond *pc, const double *r, double *z, int accumulat
         e1 = pc->ev[pc->ev_used++];
         RAS_CK(cudaEventRecord(e0, st));
     }
-    RAS_TRY(ras1_apply(pc->fine, r, z, accumulate, st));
+    if (pc->use125) RAS_TRY(ras125_apply(pc->fine125, r, z, accumulate, st));
+    else RAS_TRY(ras1_apply(pc->fine, r, z, accumulate, st));
     if (pc->timing) RAS_CK(cudaEventRecord(e1, st));
     return RAS_OK;
 }
@@ -36,7 +37,13 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
             pc->A.c[s] = pc->Acopy[s];
         }
     }
-    RAS_TRY(ras1_factor(pc->fine, A, st));
+    if (pc->use125) {
+        const ras_problem *P = pc->prob;
+        RAS_TRY(embed7(A, P->nx, P->ny, P->nz, pc->A125, st));
+        RAS_TRY(ras125_factor(pc->fine125, pc->A125, st));
+    } else {
+        RAS_TRY(ras1_factor(pc->fine, A, st));
+    }
     if (pc->xfer) {
         // level 1: A_1 = P_1^T A P_1, its subdomain ILU(0) factors, and the
         // coarsest operator A_0 = P_0^T A_1 P_0 with its dense block LU
@@ -46,7 +53,8 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
     } else if (pc->coarse) {
         RAS_TRY(coarse_factor(pc->coarse, A, st));
     }
-    RAS_TRY(ras1_check(pc->fine, st));
+    if (pc->use125) RAS_TRY(ras125_check(pc->fine125, st));
+    else RAS_TRY(ras1_check(pc->fine, st));
     if (pc->xfer) RAS_TRY(ras125_check(pc->mid, st));
     if (pc->coarse) RAS_TRY(coarse_check(pc->coarse, st));
     return RAS_OK;
@@ -124,15 +132,26 @@ using namespace ras;
 extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **out) {
     if (!P || !o || !out) return RAS_EINVAL;
     *out = nullptr;
-    if (o->ras_type < 0 || o->ras_type > 2 || o->ilu_k != 0) return RAS_EINVAL;
+    if (o->ras_type < 0 || o->ras_type > 2 || o->ilu_k < 0) return RAS_EINVAL;
+    if (o->ilu_k > 0 && o->ras_type != 1) return RAS_EINVAL;
     if (o->nlevels < 1 || o->nlevels > 3) return RAS_EINVAL;
     if (o->mlevel_type < 0 || o->mlevel_type > 4) return RAS_EINVAL;
     if (o->nlevels == 3 && (o->mlevel_type != 0 || o->coarse_overlap < 0)) return RAS_EINVAL;
     ras_precond *pc = new ras_precond();
     pc->prob = P;
     pc->opts = *o;
-    int rc = ras1_setup(pc->fine, P->nx, P->ny, P->nz, o->px, o->py, o->pz, o->overlap,
+    int rc;
+    if (o->ilu_k > 0) {
+        pc->use125 = true;
+        rc = ras125_setup(pc->fine125, P->nx, P->ny, P->nz, o->px, o->py, o->pz, o->overlap,
+                          o->factor_prec, o->ilu_k);
+        if (!rc) rc = dalloc(&pc->A125, (size_t)125 * P->N);
+        if (!rc && cudaMemset(pc->A125, 0, (size_t)125 * P->N * sizeof(double)) != cudaSuccess)
+            rc = RAS_ECUDA;
+    } else {
+        rc = ras1_setup(pc->fine, P->nx, P->ny, P->nz, o->px, o->py, o->pz, o->overlap,
                         o->factor_prec, o->ras_type);
+    }
     if (rc) { ras_precond_destroy(pc); return rc; }
     if (o->nlevels == 3) {
         rc = transfer_setup(&pc->xfer, P->nx, P->ny, P->nz, o->coarsen);
@@ -167,6 +186,8 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
 extern "C" void ras_precond_destroy(ras_precond *pc) {
     if (!pc) return;
     ras1_free(pc->fine);
+    ras125_free(pc->fine125);
+    dfree(pc->A125);
     if (pc->coarse) coarse_free(pc->coarse);
     if (pc->xfer) transfer_free(pc->xfer);
     ras125_free(pc->mid);
@@ -211,5 +232,6 @@ extern "C" int ras_timing_read(ras_precond *pc, double *total_ms, long long *lau
 }
 
 extern "C" double ras_apply_bytes(const ras_precond *pc) {
-    return pc ? ras1_bytes(pc->fine) : 0.0;
+    if (!pc) return 0.0;
+    return pc->use125 ? ras125_bytes(pc->fine125) : ras1_bytes(pc->fine);
 }

@@ -37,6 +37,11 @@ struct ras_precond {
     const ras_problem *prob = nullptr;
     ras_opts opts{};
     ras::Ras1 fine;
+    // ILU(k > 0): the fine level runs on the 125-offset machinery (7-point
+    // operator embedded, level-of-fill pattern per box shape)
+    bool use125 = false;
+    ras::Ras125 fine125;
+    double *A125 = nullptr;             // [125][N] embedded fine operator
     ras::Coarse *coarse = nullptr;
     ras::Stencil7 A{};          // copy of the operator of the last ras_factor (fine residuals)
     double *Acopy[7] = {};      // owned storage of that copy (two-level only)

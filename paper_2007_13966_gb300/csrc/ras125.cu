@@ -125,6 +125,7 @@ struct Fac125 {
     double *work;             // [nrow][64]: upper row of U (upper slots) and 1/u_nn (slot 63)
     void *fwd, *bwd;          // records: L (lower slots); U (upper slots) and 1/u_nn (slot 63)
     int *err;
+    const unsigned *mask;     // ILU(k) patterns (null: the nonzeros of A plus the diagonal)
 };
 
 // IKJ incomplete LU of one overlapped box in natural order, no pivoting: for
@@ -180,24 +181,28 @@ __global__ void __launch_bounds__(512) k_ras125_factor(Fac125 P) {
             const long long g = g0 + i + P.nx * (long long)j + nxy * k;
             double w[4];
             bool pat[4];
+            const unsigned *msk = P.mask ? P.mask + sh.mask_off + 4LL * n : nullptr;
+            auto in_pattern = [&](int o, double v) {   // o in the box
+                return msk ? ((msk[o >> 5] >> (o & 31)) & 1u) != 0u : (v != 0.0 || o == CENTRE125);
+            };
 #pragma unroll
             for (int r = 0; r < 4; ++r) {
                 const bool inb = live[r] && inbox(i + ox[r], j + oy[r], k + oz[r]);
                 const double v = inb ? P.A[(long long)(lane + 32 * r) * N + g] : 0.0;
                 w[r] = v;
-                pat[r] = inb && (v != 0.0 || lane + 32 * r == CENTRE125);
+                pat[r] = inb && in_pattern(lane + 32 * r, v);
             }
             // lower pattern columns in ascending natural order (slot order)
             bool p0 = false, p1 = false;
             if (lane < nL) {
                 const int o = sh.lowo[lane];
                 p0 = inbox(i + off_dx(o), j + off_dy(o), k + off_dz(o)) &&
-                     P.A[(long long)o * N + g] != 0.0;
+                     in_pattern(o, P.A[(long long)o * N + g]);
             }
             if (lane + 32 < nL) {
                 const int o = sh.lowo[lane + 32];
                 p1 = inbox(i + off_dx(o), j + off_dy(o), k + off_dz(o)) &&
-                     P.A[(long long)o * N + g] != 0.0;
+                     in_pattern(o, P.A[(long long)o * N + g]);
             }
             unsigned m0 = __ballot_sync(0xffffffffu, p0), m1 = __ballot_sync(0xffffffffu, p1);
             auto take = [&]() -> int {
@@ -499,10 +504,85 @@ static void build_shape(Shape125 &sh, std::vector<int> &lvl_tab, std::vector<uns
     cell_tab.insert(cell_tab.end(), ordered.begin(), ordered.end());
 }
 
+// Level-of-fill ILU(k) pattern of one box shape on the 7-point structure:
+// lev(n, c) = 0 for the couplings of the 7-point stencil inside the box and
+// the diagonal; for every lower entry m of row n with lev(n, m) <= k, taken in
+// ascending natural order, and every upper entry c of row m with
+// lev(m, c) <= k: lev(n, c) = min(lev(n, c), lev(n, m) + lev(m, c) + 1) when
+// that is <= k. Returns RAS_EINVAL if a kept entry lies outside the 5x5x5
+// neighbourhood.
+static int build_iluk_mask(Shape125 &sh, int k, std::vector<unsigned> &mask_tab) {
+    const int bx = sh.bx, by = sh.by, bz = sh.bz, bxy = bx * by, nc = sh.ncell;
+    const int ax7[6] = {off_enc(-1, 0, 0), off_enc(1, 0, 0), off_enc(0, -1, 0),
+                        off_enc(0, 1, 0), off_enc(0, 0, -1), off_enc(0, 0, 1)};
+    std::vector<signed char> lev((size_t)nc * OP125, 127);
+    sh.mask_off = (int)mask_tab.size();
+    for (int n = 0; n < nc; ++n) {
+        const int i = n % bx, j = (n / bx) % by, kk = n / bxy;
+        signed char *L = &lev[(size_t)n * OP125];
+        L[CENTRE125] = 0;
+        for (int o : ax7) {
+            const int a = i + off_dx(o), b = j + off_dy(o), c = kk + off_dz(o);
+            if (a >= 0 && a < bx && b >= 0 && b < by && c >= 0 && c < bz) L[o] = 0;
+        }
+        for (int s = 0; s < sh.nL; ++s) {
+            const int om = sh.lowo[s];
+            if (L[om] > k) continue;
+            const int mx = off_dx(om), my = off_dy(om), mz = off_dz(om);
+            const signed char *Lm = &lev[(size_t)(n + mx + bx * my + bxy * mz) * OP125];
+            for (int u = 0; u < sh.nL; ++u) {
+                const int ou = sh.upo[u];
+                if (Lm[ou] > k) continue;
+                const int nl = L[om] + Lm[ou] + 1;
+                if (nl > k) continue;
+                const int cx = mx + off_dx(ou), cy = my + off_dy(ou), cz = mz + off_dz(ou);
+                if (cx < -2 || cx > 2 || cy < -2 || cy > 2 || cz < -2 || cz > 2) return RAS_EINVAL;
+                const int oc = off_enc(cx, cy, cz);
+                if (nl < L[oc]) L[oc] = (signed char)nl;
+            }
+        }
+        unsigned wds[4] = {0u, 0u, 0u, 0u};
+        for (int o = 0; o < OP125; ++o)
+            if (L[o] <= k) wds[o >> 5] |= 1u << (o & 31);
+        mask_tab.insert(mask_tab.end(), wds, wds + 4);
+    }
+    return RAS_OK;
+}
+
+__global__ void __launch_bounds__(256) k_embed7(Stencil7 A, int nx, int ny, int nz,
+                                                double *__restrict__ A125) {
+    const long long N = (long long)nx * ny * nz;
+    const int slot[7] = {CENTRE125, off_enc(-1, 0, 0), off_enc(1, 0, 0), off_enc(0, -1, 0),
+                         off_enc(0, 1, 0), off_enc(0, 0, -1), off_enc(0, 0, 1)};
+    for (long long n = blockIdx.x * (long long)blockDim.x + threadIdx.x; n < N;
+         n += (long long)gridDim.x * blockDim.x) {
+#pragma unroll
+        for (int s = 0; s < 7; ++s) A125[(long long)slot[s] * N + n] = A.c[s][n];
+    }
+}
+
+int embed7(const Stencil7 &A, int nx, int ny, int nz, double *A125, cudaStream_t st) {
+    const long long N = (long long)nx * ny * nz;
+    const int grid = (int)std::min<long long>((N + 255) / 256, 152LL * 16);
+    k_embed7<<<grid, 256, 0, st>>>(A, nx, ny, nz, A125);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+// bytes one apply reads and writes: both 64-value records per row at the
+// stored precision, r read and z written once
+double ras125_bytes(const Ras125 &R) {
+    const double esz = R.prec == 64 ? 8.0 : (R.prec == 32 ? 4.0 : 2.0);
+    return 2.0 * RREC * esz * (double)R.nrow + 16.0 * (double)R.N;
+}
+
 constexpr int SMEM125_MAX = 200 * 1024;
 
-int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec) {
+int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec,
+                 int ilu_k) {
     if (nx < 1 || ny < 1 || nz < 1) return RAS_EINVAL;
+    if (ilu_k < 0) return RAS_EINVAL;
+    R.ilu_k = ilu_k;
     if (px < 1 || py < 1 || pz < 1 || overlap < 0) return RAS_EINVAL;
     if (px > nx || py > ny || pz > nz) return RAS_EINVAL;
     if (prec != 64 && prec != 32 && prec != 16) return RAS_EINVAL;
@@ -515,6 +595,7 @@ int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int 
     std::map<std::tuple<int, int, int>, int> shape_id;
     std::vector<int> lvl_tab;
     std::vector<unsigned> cell_tab;
+    std::vector<unsigned> mask_tab;
     R.subs.clear();
     R.shapes.clear();
     long long foff = 0;
@@ -541,6 +622,8 @@ int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int 
                     Shape125 sh{};
                     sh.bx = bx; sh.by = by; sh.bz = bz; sh.ncell = ncell;
                     build_shape(sh, lvl_tab, cell_tab);
+                    sh.mask_off = 0;
+                    if (ilu_k > 0) RAS_TRY(build_iluk_mask(sh, ilu_k, mask_tab));
                     sid = (int)R.shapes.size();
                     shape_id[key] = sid;
                     R.shapes.push_back(sh);
@@ -581,6 +664,11 @@ int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int 
     RAS_TRY(dalloc(&R.d_lvl, lvl_tab.size()));
     RAS_TRY(dalloc(&R.d_cells, cell_tab.size()));
     RAS_TRY(dalloc(&R.d_err, 1));
+    if (ilu_k > 0) {
+        RAS_TRY(dalloc(&R.d_mask, mask_tab.size()));
+        RAS_CK(cudaMemcpy(R.d_mask, mask_tab.data(), mask_tab.size() * sizeof(unsigned),
+                          cudaMemcpyHostToDevice));
+    }
     RAS_TRY(dalloc(&R.d_work, nval));
     RAS_TRY(dalloc(&fw, nval * esz));
     R.d_fwd = fw;
@@ -614,6 +702,7 @@ int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int 
 void ras125_free(Ras125 &R) {
     dfree(R.d_subs); dfree(R.d_shapes); dfree(R.d_lvl); dfree(R.d_cells); dfree(R.d_err);
     dfree(R.d_work);
+    dfree(R.d_mask);
     if (R.d_fwd) cudaFree(R.d_fwd);
     if (R.d_bwd) cudaFree(R.d_bwd);
     R.d_fwd = R.d_bwd = nullptr;
@@ -624,6 +713,7 @@ int ras125_factor(Ras125 &R, const double *A, cudaStream_t st) {
     P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.cells = R.d_cells;
     P.A = A; P.nx = R.nx; P.ny = R.ny; P.nz = R.nz;
     P.work = R.d_work; P.fwd = R.d_fwd; P.bwd = R.d_bwd; P.err = R.d_err;
+    P.mask = R.d_mask;
     const int threads = 32 * R.nwarps;
     if (R.prec == 64) k_ras125_factor<64><<<R.nsub, threads, R.smem_factor, st>>>(P);
     else if (R.prec == 32) k_ras125_factor<32><<<R.nsub, threads, R.smem_factor, st>>>(P);

@@ -24,6 +24,7 @@ struct Shape125 {
     unsigned char lowo[64];     // lower offsets, ascending natural distance
     unsigned char upo[64];      // upper offsets, ascending natural distance
     signed char uslot[128];     // offset -> position in upo, or -1
+    int mask_off;               // ILU(k) pattern: 4 words of offset bits per cell (natural order)
 };
 
 struct Sub125 {
@@ -49,9 +50,17 @@ struct Ras125 {
     double *d_work = nullptr;            // [nrow][64] FP64 upper rows + 1/pivot (factor only)
     void *d_fwd = nullptr, *d_bwd = nullptr;   // [nrow][64] records at prec
     int *d_err = nullptr;
+    int ilu_k = 0;                       // 0: pattern = nonzeros of A; k > 0: level-of-fill k
+    unsigned *d_mask = nullptr;          // ILU(k) patterns per box shape
 };
 
-int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec);
+// ilu_k > 0: ILU(k) on the 7-point structure of each box (fill must stay within
+// two cells along each axis: k <= 2 for natural order; RAS_EINVAL otherwise)
+int ras125_setup(Ras125 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec,
+                 int ilu_k = 0);
+// A125 [125][N] <- the 7-point operator A (the other slots must already be zero)
+int embed7(const Stencil7 &A, int nx, int ny, int nz, double *A125, cudaStream_t st);
+double ras125_bytes(const Ras125 &R);
 void ras125_free(Ras125 &R);
 // ILU(0) of every A_i = R_i^delta A (R_i^delta)^T; A: [125][N] FP64; no synchronisation
 int ras125_factor(Ras125 &R, const double *A, cudaStream_t st);

@@ -270,8 +270,8 @@ class Precond:
 
     def __init__(self, prob: Problem, parts, overlap, factor_prec=64, nlevels=1,
                  coarsen=(2, 2, 2), mlevel_type=0, coarse_prec=64, interp_order=2,
-                 coarse_overlap=1, ras_type=1):
-        o = Opts(parts[0], parts[1], parts[2], overlap, ras_type, 0, factor_prec, nlevels,
+                 coarse_overlap=1, ras_type=1, ilu_k=0):
+        o = Opts(parts[0], parts[1], parts[2], overlap, ras_type, ilu_k, factor_prec, nlevels,
                  (C.c_int * 3)(*coarsen), interp_order, mlevel_type, coarse_prec,
                  coarse_overlap)
         h = C.c_void_p()
