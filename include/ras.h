@@ -102,7 +102,16 @@ typedef struct {
     int coarse_prec;       /* 64 or 32: precision of the dense block coarse LU        */
     int coarse_overlap;    /* nlevels = 3: overlap delta_c of the middle-level Schwarz
                               smoother (px x py x pz subdomains, ILU(0) on the
-                              Galerkin operator's nonzero pattern, factor_prec)     */
+                              Galerkin operator's nonzero pattern, factor_prec);
+                              coarse_solver = 1: overlap of the coarse-grid
+                              Schwarz preconditioner                                */
+    int coarse_solver;     /* nlevels = 2: 0 = exact dense block LU; 1 = FGMRES(30)
+                              on the Galerkin coarse operator preconditioned by
+                              left-RAS(ILU(0)) on the coarse grid (min(p, coarse
+                              cells) subdomains per axis, overlap coarse_overlap,
+                              coarse_prec factors), stopped at coarse_rtol
+                              (Remark 2, Section 4: 0.2)                          */
+    double coarse_rtol;    /* relative tolerance of the coarse FGMRES (> 0)           */
 } ras_opts;
 
 typedef struct {

@@ -163,14 +163,16 @@ static inline int gridn(int n) {
     return std::max(1, std::min(g, 152 * 8));
 }
 
-int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, double *x,
-           const ras_krylov_opts &o, ras_krylov_stats *stats, cudaStream_t st) {
-    const int N = P->N;
+// Flexible GMRES(m) on any operator: apply_M(v, z) (z = M^{-1} v), apply_A(z, w)
+// (w = A z), resid(b, x, r) (r = b - A x), finish() after the last iteration.
+// V [(m+1) N], Z [m N], w, r [N] are the caller's workspace.
+template <class ApplyM, class ApplyA, class Resid, class Finish>
+static int fgmres_core(int N, double *V, double *Z, double *w, double *r, ReduceWs &red,
+                       ApplyM apply_M, ApplyA apply_A, Resid resid, Finish finish,
+                       const double *b, double *x, const ras_krylov_opts &o,
+                       ras_krylov_stats *stats, cudaStream_t st) {
     const int m = o.restart;
     if (m < 1 || m > MAX_MDOT - 1 || o.maxit < 1) return RAS_EINVAL;
-    RAS_TRY(ensure_krylov(P, m));
-    ReduceWs &red = P->red;
-    double *V = P->kV, *Z = P->kZ, *w = P->kw, *r = P->kr;
     const long long ld = N;
     auto push = [&](double v) {
         if (stats && stats->history && stats->history_len < stats->history_cap)
@@ -199,8 +201,8 @@ int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, 
         for (int j = 0; j < m; ++j) {
             const int k = j + 1;
             double *Vj = V + (size_t)j * N, *Zj = Z + (size_t)j * N;
-            RAS_TRY(precond_apply(pc, Vj, Zj, st));
-            RAS_TRY(stencil_apply(A, P->nx, P->ny, P->nz, Zj, w, st));
+            RAS_TRY(apply_M(Vj, Zj));
+            RAS_TRY(apply_A(Zj, w));
             // CGS pass 1 (+ ||w||^2 before orthogonalisation)
             RAS_TRY(launch_mdot(V, ld, k, 1, w, N, red.partials, st));
             k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, k + 1, red.out, 0, 0);
@@ -252,13 +254,13 @@ int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, 
         }
         k_combine<<<gridn(N), 256, 0, st>>>(x, Z, ld, k, c, N);
         RAS_LAUNCHED();
-        RAS_TRY(stencil_residual(A, P->nx, P->ny, P->nz, b, x, r, st));
+        RAS_TRY(resid(b, x, r));
         RAS_TRY(norm2_sync(red, r, N, &beta, st));
         if (!std::isfinite(beta)) return RAS_ENAN;
         converged = beta <= tol || std::fabs(g[k]) <= tol;
         if (!converged && it < o.maxit) push(beta);
     }
-    RAS_TRY(precond_check(pc, st));
+    RAS_TRY(finish());
     if (stats) {
         stats->iters = it;
         stats->converged = converged ? 1 : 0;
@@ -266,6 +268,96 @@ int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, 
         stats->rfinal = beta;
     }
     return converged ? RAS_OK : RAS_GMRES_MAXIT;
+}
+
+int fgmres(ras_problem *P, const Stencil7 &A, ras_precond *pc, const double *b, double *x,
+           const ras_krylov_opts &o, ras_krylov_stats *stats, cudaStream_t st) {
+    if (o.restart < 1 || o.restart > MAX_MDOT - 1 || o.maxit < 1) return RAS_EINVAL;
+    RAS_TRY(ensure_krylov(P, o.restart));
+    const int nx = P->nx, ny = P->ny, nz = P->nz;
+    return fgmres_core(
+        P->N, P->kV, P->kZ, P->kw, P->kr, P->red,
+        [&](const double *v, double *z) { return precond_apply(pc, v, z, st); },
+        [&](const double *z, double *y) { return stencil_apply(A, nx, ny, nz, z, y, st); },
+        [&](const double *bb, const double *xx, double *rr) {
+            return stencil_residual(A, nx, ny, nz, bb, xx, rr, st);
+        },
+        [&]() { return precond_check(pc, st); }, b, x, o, stats, st);
+}
+
+// ---------------------------------------------------------------------------
+// inexact coarse solve (Remark 2): FGMRES on the Galerkin coarse operator,
+// preconditioned by left-RAS with ILU(0) on the coarse grid
+// ---------------------------------------------------------------------------
+
+struct IterCoarse {
+    Transfer *xfer = nullptr;
+    int c[3] = {1, 1, 1}, Nc = 0, Nf = 0;     // coarse grid, fine cells
+    double *Ac = nullptr;                     // [125][Nc] FP64
+    Ras125 M;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr;
+    double *tc = nullptr, *xc = nullptr;
+    ReduceWs red;
+    ras_krylov_opts ko{};
+};
+
+int itcoarse_setup(IterCoarse **out, int nx, int ny, int nz, const ras_opts &o) {
+    *out = nullptr;
+    IterCoarse *c = new IterCoarse();
+    auto fail = [&](int s) { itcoarse_free(c); return s; };
+    int rc = transfer_setup(&c->xfer, nx, ny, nz, o.coarsen);
+    if (rc) return fail(rc);
+    transfer_dims(c->xfer, c->c);
+    c->Nc = c->c[0] * c->c[1] * c->c[2];
+    c->Nf = nx * ny * nz;
+    const int parts[3] = {std::min(o.px, c->c[0]), std::min(o.py, c->c[1]), std::min(o.pz, c->c[2])};
+    if ((rc = ras125_setup(c->M, c->c[0], c->c[1], c->c[2], parts[0], parts[1], parts[2],
+                           o.coarse_overlap, o.coarse_prec == 32 ? 32 : 64)))
+        return fail(rc);
+    c->ko.restart = 30;
+    c->ko.maxit = 200;
+    c->ko.rtol = o.coarse_rtol;
+    c->ko.atol = 0.0;
+    const size_t Nc = c->Nc;
+    if ((rc = dalloc(&c->Ac, 125 * Nc)) || (rc = dalloc(&c->V, (c->ko.restart + 1) * Nc)) ||
+        (rc = dalloc(&c->Z, c->ko.restart * Nc)) || (rc = dalloc(&c->w, Nc)) ||
+        (rc = dalloc(&c->r, Nc)) || (rc = dalloc(&c->tc, Nc)) || (rc = dalloc(&c->xc, Nc)) ||
+        (rc = reduce_ws_init(c->red)))
+        return fail(rc);
+    *out = c;
+    return RAS_OK;
+}
+
+void itcoarse_free(IterCoarse *c) {
+    if (!c) return;
+    if (c->xfer) transfer_free(c->xfer);
+    ras125_free(c->M);
+    dfree(c->Ac); dfree(c->V); dfree(c->Z); dfree(c->w); dfree(c->r); dfree(c->tc); dfree(c->xc);
+    reduce_ws_free(c->red);
+    delete c;
+}
+
+int itcoarse_factor(IterCoarse *c, const Stencil7 &A, cudaStream_t st) {
+    RAS_TRY(transfer_galerkin7(c->xfer, A, c->Ac, nullptr, st));
+    return ras125_factor(c->M, c->Ac, st);
+}
+
+int itcoarse_check(IterCoarse *c, cudaStream_t st) { return ras125_check(c->M, st); }
+
+int itcoarse_correct(IterCoarse *c, const double *t, double *z, int accumulate, cudaStream_t st) {
+    RAS_TRY(transfer_restrict(c->xfer, t, c->tc, st));
+    const int *d = c->c;
+    const int s = fgmres_core(
+        c->Nc, c->V, c->Z, c->w, c->r, c->red,
+        [&](const double *v, double *y) { return ras125_apply(c->M, v, y, 0, st); },
+        [&](const double *y, double *q) { return spmv125(c->Ac, d[0], d[1], d[2], y, nullptr, q, st); },
+        [&](const double *bb, const double *xx, double *rr) {
+            return spmv125(c->Ac, d[0], d[1], d[2], xx, bb, rr, st);
+        },
+        [&]() { return RAS_OK; }, c->tc, c->xc, c->ko, nullptr, st);
+    if (s < 0) return s;   // an inexact coarse solve that ran out of iterations is still used
+    if (!accumulate) RAS_TRY(vec_set(z, 0.0, c->Nf, st));
+    return transfer_prolong(c->xfer, c->xc, z, st);
 }
 
 int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const double *plm1,

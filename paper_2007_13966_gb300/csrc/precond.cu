@@ -28,7 +28,7 @@ static int fine_apply(ras_precond *pc, const double *r, double *z, int accumulat
 int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
     Stencil7 A;
     for (int s = 0; s < 7; ++s) A.c[s] = J->c[s];
-    if (pc->coarse) {
+    if (pc->coarse || pc->icoarse) {
         // the multilevel combinations apply J again inside ras_apply: keep a copy
         const int N = pc->prob->N;
         for (int s = 0; s < 7; ++s) {
@@ -52,12 +52,21 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
         RAS_TRY(coarse_factor125(pc->coarse, pc->A1, st));
     } else if (pc->coarse) {
         RAS_TRY(coarse_factor(pc->coarse, A, st));
+    } else if (pc->icoarse) {
+        RAS_TRY(itcoarse_factor(pc->icoarse, A, st));
     }
     if (pc->use125) RAS_TRY(ras125_check(pc->fine125, st));
     else RAS_TRY(ras1_check(pc->fine, st));
     if (pc->xfer) RAS_TRY(ras125_check(pc->mid, st));
     if (pc->coarse) RAS_TRY(coarse_check(pc->coarse, st));
+    if (pc->icoarse) RAS_TRY(itcoarse_check(pc->icoarse, st));
     return RAS_OK;
+}
+
+// two-level coarse correction z (+)= P A_c^{-1} R t, exact or inexact
+static int coarse_corr(ras_precond *pc, const double *t, double *z, int accumulate, cudaStream_t st) {
+    if (pc->icoarse) return itcoarse_correct(pc->icoarse, t, z, accumulate, st);
+    return coarse_correct(pc->coarse, t, z, accumulate, st);
 }
 
 // Algorithm 1 with three levels, one pre- and one post-smoothing step of
@@ -86,13 +95,13 @@ static int three_level_apply(ras_precond *pc, const double *r, double *z, cudaSt
 }
 
 int precond_check(ras_precond *pc, cudaStream_t st) {
-    return pc->coarse ? coarse_check(pc->coarse, st) : RAS_OK;
+    return pc->coarse ? coarse_check(pc->coarse, st) : RAS_OK;   // the inexact coarse solve has no deferred error
 }
 
 // z = M^{-1} r for the configured preconditioner
 int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st) {
     const ras_problem *P = pc->prob;
-    if (!pc->coarse) return fine_apply(pc, r, z, 0, st);
+    if (!pc->coarse && !pc->icoarse) return fine_apply(pc, r, z, 0, st);
     if (pc->xfer) return three_level_apply(pc, r, z, st);
     const int nx = P->nx, ny = P->ny, nz = P->nz;
     double *t = pc->t1;
@@ -100,26 +109,26 @@ int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st) 
         case 0:  // V-cycle, Eq. equ:v-cycle
             RAS_TRY(fine_apply(pc, r, z, 0, st));                       // e1 = M r
             RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));   // t = r - A e1
-            RAS_TRY(coarse_correct(pc->coarse, t, z, 1, st));            // e2 = e1 + P Ac^-1 R t
+            RAS_TRY(coarse_corr(pc, t, z, 1, st));                       // e2 = e1 + P Ac^-1 R t
             RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));   // t = r - A e2
             RAS_TRY(fine_apply(pc, t, z, 1, st));                        // e = e2 + M t
             return RAS_OK;
         case 1:  // left-Kaskade, Eq. equ:left-Kas: c + M (r - A c)
-            RAS_TRY(coarse_correct(pc->coarse, r, z, 0, st));
+            RAS_TRY(coarse_corr(pc, r, z, 0, st));
             RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));
             RAS_TRY(fine_apply(pc, t, z, 1, st));
             return RAS_OK;
         case 2:  // right-Kaskade, Eq. equ:right-Kas: e + C (r - A e)
             RAS_TRY(fine_apply(pc, r, z, 0, st));
             RAS_TRY(stencil_residual(pc->A, nx, ny, nz, r, z, t, st));
-            RAS_TRY(coarse_correct(pc->coarse, t, z, 1, st));
+            RAS_TRY(coarse_corr(pc, t, z, 1, st));
             return RAS_OK;
         case 3:  // additive, Eq. equ:two-additive
             RAS_TRY(fine_apply(pc, r, z, 0, st));
-            RAS_TRY(coarse_correct(pc->coarse, r, z, 1, st));
+            RAS_TRY(coarse_corr(pc, r, z, 1, st));
             return RAS_OK;
         case 4:  // coarse only, Eq. equ:coarse-level
-            return coarse_correct(pc->coarse, r, z, 0, st);
+            return coarse_corr(pc, r, z, 0, st);
         default:
             return RAS_EINVAL;
     }
@@ -137,6 +146,9 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
     if (o->nlevels < 1 || o->nlevels > 3) return RAS_EINVAL;
     if (o->mlevel_type < 0 || o->mlevel_type > 4) return RAS_EINVAL;
     if (o->nlevels == 3 && (o->mlevel_type != 0 || o->coarse_overlap < 0)) return RAS_EINVAL;
+    if (o->coarse_solver < 0 || o->coarse_solver > 1) return RAS_EINVAL;
+    if (o->coarse_solver == 1 && (o->nlevels != 2 || !(o->coarse_rtol > 0.0) || o->coarse_overlap < 0))
+        return RAS_EINVAL;
     ras_precond *pc = new ras_precond();
     pc->prob = P;
     pc->opts = *o;
@@ -172,7 +184,8 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
         if (rc) { ras_precond_destroy(pc); return rc; }
     }
     if (o->nlevels >= 2) {
-        if (!pc->coarse) rc = coarse_setup(&pc->coarse, P, *o);
+        if (o->coarse_solver == 1) rc = itcoarse_setup(&pc->icoarse, P->nx, P->ny, P->nz, *o);
+        else if (!pc->coarse) rc = coarse_setup(&pc->coarse, P, *o);
         if (!rc) rc = dalloc(&pc->t1, P->N);
         if (!rc) rc = dalloc(&pc->t2, P->N);
         if (!rc) rc = dalloc(&pc->t3, P->N);
@@ -189,6 +202,7 @@ extern "C" void ras_precond_destroy(ras_precond *pc) {
     ras125_free(pc->fine125);
     dfree(pc->A125);
     if (pc->coarse) coarse_free(pc->coarse);
+    if (pc->icoarse) itcoarse_free(pc->icoarse);
     if (pc->xfer) transfer_free(pc->xfer);
     ras125_free(pc->mid);
     dfree(pc->A1); dfree(pc->A1f); dfree(pc->b1); dfree(pc->x1); dfree(pc->r1);

@@ -31,6 +31,16 @@ void transfer_dims(const Transfer *t, int c[3]);
 int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, float *scratch, cudaStream_t st);
 int transfer_restrict(Transfer *t, const double *x, double *xc, cudaStream_t st);   // xc = P^T x
 int transfer_prolong(Transfer *t, const double *xc, double *x, cudaStream_t st);    // x += P xc
+
+// inexact coarse solve: FGMRES on A_c = P^T A P preconditioned by left-RAS(ILU(0))
+// on the coarse grid, to a relative tolerance
+struct IterCoarse;
+int itcoarse_setup(IterCoarse **out, int nx, int ny, int nz, const ras_opts &o);
+void itcoarse_free(IterCoarse *c);
+int itcoarse_factor(IterCoarse *c, const Stencil7 &A, cudaStream_t st);
+int itcoarse_check(IterCoarse *c, cudaStream_t st);
+// xc ~= A_c^{-1} R t, then z (+)= P xc
+int itcoarse_correct(IterCoarse *c, const double *t, double *z, int accumulate, cudaStream_t st);
 }  // namespace ras
 
 struct ras_precond {
@@ -43,6 +53,7 @@ struct ras_precond {
     ras::Ras125 fine125;
     double *A125 = nullptr;             // [125][N] embedded fine operator
     ras::Coarse *coarse = nullptr;
+    ras::IterCoarse *icoarse = nullptr;   // coarse_solver = 1 (two levels)
     ras::Stencil7 A{};          // copy of the operator of the last ras_factor (fine residuals)
     double *Acopy[7] = {};      // owned storage of that copy (two-level only)
     double *t1 = nullptr, *t2 = nullptr, *t3 = nullptr;  // multilevel scratch [N]

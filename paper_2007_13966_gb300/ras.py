@@ -51,7 +51,8 @@ class Opts(C.Structure):
     _fields_ = [("px", C.c_int), ("py", C.c_int), ("pz", C.c_int), ("overlap", C.c_int),
                 ("ras_type", C.c_int), ("ilu_k", C.c_int), ("factor_prec", C.c_int),
                 ("nlevels", C.c_int), ("coarsen", C.c_int * 3), ("interp_order", C.c_int),
-                ("mlevel_type", C.c_int), ("coarse_prec", C.c_int), ("coarse_overlap", C.c_int)]
+                ("mlevel_type", C.c_int), ("coarse_prec", C.c_int), ("coarse_overlap", C.c_int),
+                ("coarse_solver", C.c_int), ("coarse_rtol", C.c_double)]
 
 
 class KrylovOpts(C.Structure):
@@ -270,10 +271,10 @@ class Precond:
 
     def __init__(self, prob: Problem, parts, overlap, factor_prec=64, nlevels=1,
                  coarsen=(2, 2, 2), mlevel_type=0, coarse_prec=64, interp_order=2,
-                 coarse_overlap=1, ras_type=1, ilu_k=0):
+                 coarse_overlap=1, ras_type=1, ilu_k=0, coarse_solver=0, coarse_rtol=0.2):
         o = Opts(parts[0], parts[1], parts[2], overlap, ras_type, ilu_k, factor_prec, nlevels,
                  (C.c_int * 3)(*coarsen), interp_order, mlevel_type, coarse_prec,
-                 coarse_overlap)
+                 coarse_overlap, coarse_solver, coarse_rtol)
         h = C.c_void_p()
         check(lib().ras_setup(prob.h, C.byref(o), C.byref(h)), "ras_setup")
         self.h = h
