@@ -95,7 +95,9 @@ typedef struct {
     int nlevels;           /* 1 = one-level; 2 = two-level (Eq. equ:v-cycle);
                               3 = three-level V-cycle (Algorithm 1, mu = nu = 1)     */
     int coarsen[3];        /* coarse:fine ratio per axis of each coarsening (Table 7) */
-    int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second (only value)  */
+    int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second; 1 = nearest
+                              coarse centre, Eq. equ:inter-frist (order 3 couples
+                              coarse cells three apart: not supported)            */
     int mlevel_type;       /* 0 = V-cycle, 1 = left-Kaskade, 2 = right-Kaskade,
                               3 = additive, 4 = coarse-only (Eqs. equ:v-cycle ..
                               equ:coarse-level)                                      */

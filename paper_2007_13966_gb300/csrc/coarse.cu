@@ -1167,9 +1167,12 @@ static int grid_of(long long n, int threads = 256) {
     return (int)std::max(1LL, std::min(g, 152LL * 16));
 }
 
+// One axis of I_{j-1}^j: order 2, tensor-product linear between the bracketing
+// coarse centres (Eq. equ:inter-second), constant beyond the outermost ones;
+// order 1, the nearest coarse centre (Eq. equ:inter-frist), the lower on ties.
 static void interp_axis(int n, int r, std::vector<int> &ia, std::vector<int> &ib,
                         std::vector<double> &wa, std::vector<double> &wb, std::vector<int> &lo,
-                        std::vector<int> &hi, int &nc) {
+                        std::vector<int> &hi, int &nc, int order) {
     nc = n > 1 ? (n + r - 1) / r : 1;
     ia.assign(n, 0); ib.assign(n, 0); wa.assign(n, 1.0); wb.assign(n, 0.0);
     std::vector<double> xc(nc);
@@ -1177,6 +1180,13 @@ static void interp_axis(int n, int r, std::vector<int> &ia, std::vector<int> &ib
     if (n > 1) {
         for (int i = 0; i < n; ++i) {
             const double x = i + 0.5;
+            if (order == 1) {
+                int best = 0;
+                for (int I = 1; I < nc; ++I)
+                    if (std::fabs(xc[I] - x) < std::fabs(xc[best] - x)) best = I;
+                ia[i] = ib[i] = best; wa[i] = 1.0; wb[i] = 0.0;
+                continue;
+            }
             int I0 = (int)(std::upper_bound(xc.begin(), xc.end(), x) - xc.begin()) - 1;
             if (I0 < 0) { ia[i] = ib[i] = 0; wa[i] = 1.0; wb[i] = 0.0; }
             else if (I0 >= nc - 1) { ia[i] = ib[i] = nc - 1; wa[i] = 1.0; wb[i] = 0.0; }
@@ -1257,11 +1267,11 @@ static int configure_t(Coarse *c) {
 }
 
 // interpolation tables of one axis on the device
-static int upload_axis(int n, int r, int *&d_ia, int *&d_ib, double *&d_wa, double *&d_wb, int *&d_lo,
+static int upload_axis(int n, int r, int order, int *&d_ia, int *&d_ib, double *&d_wa, double *&d_wb, int *&d_lo,
                        int *&d_hi, int &nc, int &wmax) {
     std::vector<int> ia, ib, lo, hi;
     std::vector<double> wa, wb;
-    interp_axis(n, r, ia, ib, wa, wb, lo, hi, nc);
+    interp_axis(n, r, ia, ib, wa, wb, lo, hi, nc, order);
     wmax = 1;
     for (size_t I = 0; I < lo.size(); ++I) wmax = std::max(wmax, hi[I] - lo[I]);
     RAS_TRY(dalloc(&d_ia, ia.size()));
@@ -1285,7 +1295,7 @@ int coarse_setup(Coarse **out, const ras_problem *Pb, const ras_opts &o) {
 
 int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o) {
     *out = nullptr;
-    if (o.interp_order != 2) return RAS_EINVAL;
+    if (o.interp_order != 1 && o.interp_order != 2) return RAS_EINVAL;
     if (o.coarse_prec != 64 && o.coarse_prec != 32) return RAS_EINVAL;
     for (int a = 0; a < 3; ++a) if (o.coarsen[a] < 1) return RAS_EINVAL;
     int dev = 0, coop = 0;
@@ -1301,7 +1311,7 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
     c->n[0] = fnx; c->n[1] = fny; c->n[2] = fnz;
     for (int a = 0; a < 3; ++a) {
         c->r[a] = o.coarsen[a];
-        const int rc = upload_axis(c->n[a], c->r[a], c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
+        const int rc = upload_axis(c->n[a], c->r[a], o.interp_order, c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
                                    c->d_lo[a], c->d_hi[a], c->c[a], c->wmax[a]);
         if (rc) return fail(rc);
     }
@@ -1528,7 +1538,7 @@ __global__ void __launch_bounds__(256) k_prolong(Interp P, CGeom G, const double
     }
 }
 
-int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]) {
+int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3], int order) {
     *out = nullptr;
     if (nx < 1 || ny < 1 || nz < 1) return RAS_EINVAL;
     for (int a = 0; a < 3; ++a) if (ratio[a] < 1) return RAS_EINVAL;
@@ -1538,7 +1548,7 @@ int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]) {
     c->n[0] = nx; c->n[1] = ny; c->n[2] = nz;
     for (int a = 0; a < 3; ++a) {
         c->r[a] = ratio[a];
-        const int rc = upload_axis(c->n[a], c->r[a], c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
+        const int rc = upload_axis(c->n[a], c->r[a], order, c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
                                    c->d_lo[a], c->d_hi[a], c->c[a], c->wmax[a]);
         if (rc) { transfer_free(t); return rc; }
     }

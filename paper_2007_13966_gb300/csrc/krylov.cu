@@ -305,7 +305,7 @@ int itcoarse_setup(IterCoarse **out, int nx, int ny, int nz, const ras_opts &o) 
     *out = nullptr;
     IterCoarse *c = new IterCoarse();
     auto fail = [&](int s) { itcoarse_free(c); return s; };
-    int rc = transfer_setup(&c->xfer, nx, ny, nz, o.coarsen);
+    int rc = transfer_setup(&c->xfer, nx, ny, nz, o.coarsen, o.interp_order);
     if (rc) return fail(rc);
     transfer_dims(c->xfer, c->c);
     c->Nc = c->c[0] * c->c[1] * c->c[2];

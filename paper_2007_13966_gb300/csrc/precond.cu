@@ -147,6 +147,7 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
     if (o->mlevel_type < 0 || o->mlevel_type > 4) return RAS_EINVAL;
     if (o->nlevels == 3 && (o->mlevel_type != 0 || o->coarse_overlap < 0)) return RAS_EINVAL;
     if (o->coarse_solver < 0 || o->coarse_solver > 1) return RAS_EINVAL;
+    if (o->nlevels > 1 && o->interp_order != 1 && o->interp_order != 2) return RAS_EINVAL;
     if (o->coarse_solver == 1 && (o->nlevels != 2 || !(o->coarse_rtol > 0.0) || o->coarse_overlap < 0))
         return RAS_EINVAL;
     ras_precond *pc = new ras_precond();
@@ -166,7 +167,7 @@ extern "C" int ras_setup(const ras_problem *P, const ras_opts *o, ras_precond **
     }
     if (rc) { ras_precond_destroy(pc); return rc; }
     if (o->nlevels == 3) {
-        rc = transfer_setup(&pc->xfer, P->nx, P->ny, P->nz, o->coarsen);
+        rc = transfer_setup(&pc->xfer, P->nx, P->ny, P->nz, o->coarsen, o->interp_order);
         if (!rc) {
             transfer_dims(pc->xfer, pc->n1);
             pc->N1 = pc->n1[0] * pc->n1[1] * pc->n1[2];

@@ -23,7 +23,7 @@ int coarse_correct(Coarse *c, const double *t, double *z, int accumulate, cudaSt
 
 // grid transfer to the next coarser level (linear interpolation P, R = P^T)
 struct Transfer;
-int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3]);
+int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3], int order = 2);
 void transfer_free(Transfer *t);
 void transfer_dims(const Transfer *t, int c[3]);
 // Ac [125][Nc] = P^T A P for a 7-point operator A, stored in FP64; formed in
