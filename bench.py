@@ -61,8 +61,9 @@ def parse():
                     help="skip the all-FP64 comparison run")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--small", action="store_true", help="32x32x16 case (profiling / smoke)")
-    ap.add_argument("--workload", choices=["c2", "c3"], default="c2",
-                    help="c2: 128x128x64 two-level (default); c3: 60x220x85 three-level")
+    ap.add_argument("--workload", choices=["c2", "c3", "c4"], default="c2",
+                    help="c2: 128x128x64 two-level (default); c3: 60x220x85 three-level; "
+                         "c4: 64 independent reservoirs of 32^3..96^3 solved concurrently")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
     ap.add_argument("--kernel", choices=["ras_apply", "vcycle"], default=None,
                     help="kernel-only mode: factor once, then time REPS applications "
@@ -509,8 +510,67 @@ def kernel_mode(args):
                       "GBps": B / (ms / max(n, 1) / 1e3) / 1e9 if n else None}))
 
 
+WORKLOAD_C4 = ("64 independent 3d lognormal reservoirs, edges uniform in 32..96 (seed 7), "
+               "per-instance seeds, one-level left-RAS ILU(0) with ~16^3 subdomains, overlap 1, "
+               "FP32 factors inside FP64 FGMRES(30), each on its own CUDA stream, 16 host threads")
+
+
+def c4_arm(args):
+    """One batch step = every reservoir of the batch advances one implicit step."""
+    import torch
+    ws, rank, local = dist_env()
+    dist_on = ws > 1
+    if dist_on:
+        import torch.distributed as dist
+        dist.init_process_group("gloo")
+    torch.cuda.set_device(local)
+    from paper_2007_13966_gb300 import batch
+    from paper_2007_13966_gb300 import synthetic as syn
+
+    def make(n, i):
+        h = 100.0 / 128
+        return syn.lognormal_reservoir(n, n, n, n * h, n * h, n * h, sigma=1.5, corr=8.0,
+                                       seed_k=100 + i, seed_phi=200 + i)
+
+    res = batch.random_batch(64, 32, 96, 7, make)
+    b = batch.Batch(res, batch.BatchOpts(box=16, overlap=1, factor_prec=args.factor_prec,
+                                         threads=16))
+    b.advance(max(args.warmup, 1))
+    sampler = ClockSampler(local)
+    sampler.start()
+    n0 = None
+    from paper_2007_13966_gb300 import ras
+    n0 = ras.kernel_launches()
+    t, _ = timed(lambda: b.advance(args.steps), torch, dist_on)
+    launches = ras.kernel_launches() - n0
+    clocks = sampler.stop()
+    t = max_over_ranks(t, dist_on)
+    # the same batch advanced one instance after another, for context
+    b.opts.threads = 1
+    t1, _ = timed(lambda: b.advance(1), torch, dist_on)
+    if rank != 0:
+        return
+    cells = b.cells
+    line = {
+        "metric": METRIC, "value": t / args.steps, "unit": "s/step", "n_gpus": ws,
+        "steps": args.steps, "warmup": max(args.warmup, 1), "ms_per_step": t / args.steps * 1e3,
+        "higher_is_better": False, "scaling": "weak", "vs_baseline": None, "dtype": "f64+f32",
+        "data": "synthetic",
+        "config": {"workload": WORKLOAD_C4, "instances": len(res), "cells": cells,
+                   "parallelism": "concurrent streams on one GPU"},
+        "cell_steps_per_s": cells * args.steps / t,
+        "sequential_sec_per_step": t1,
+        "concurrency_speedup": t1 / (t / args.steps),
+        "clocks": clocks, "gpu_launches": int(launches), "e2e": None,
+    }
+    print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
+    if args.workload == "c4" and args.impl != "reference" and not args.kernel:
+        c4_arm(args)
+        return
     if args.kernel:
         kernel_mode(args)
         return
