@@ -42,6 +42,7 @@ constexpr long long BAR_POLLS = 1LL << 22;   // ~1-2 s of polling before a barri
 struct GridBar {
     unsigned count;
     unsigned gen;
+    long long polls;   // poll limit of this launch (<= 0: BAR_POLLS)
 };
 
 struct Coarse {
@@ -67,6 +68,7 @@ struct Coarse {
     void *rx = nullptr, *ry = nullptr;               // restriction passes [cx][ny][nz], [cx][cy][nz]
     int *d_err = nullptr;
     GridBar *d_bar = nullptr;
+    long long bar_polls = 0;        // poll limit currently held by d_bar
     size_t esz = 8;
     size_t rap_smem = 0, rap125_smem = 0, fac_smem = 0, sol_smem = 0;
     int rap125_ng = 25;             // offsets staged per round in k_rap125
@@ -409,11 +411,12 @@ __device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch) {
         int ok = (ld_acquire((const unsigned *)err) == 0);
         if (ok) {
             const unsigned target = epoch * gridDim.x;
+            const long long lim = bar->polls > 0 ? bar->polls : BAR_POLLS;
             __threadfence();
             asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
             long long it = 0;
             while (ld_acquire(&bar->count) < target) {
-                if (++it > BAR_POLLS) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
+                if (++it > lim) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
                 if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
                 __nanosleep(20);
             }
@@ -1203,6 +1206,22 @@ static void interp_axis(int n, int r, std::vector<int> &ia, std::vector<int> &ib
     }
 }
 
+// Zero the grid barrier of a cooperative launch and set its poll limit:
+// RAS_BARRIER_POLLS (environment, read at every launch) shortens the bounded
+// wait, so that a test can make it run out and check the RAS_ETIMEOUT path.
+static int reset_bar(Coarse *c, cudaStream_t st) {
+    long long polls = 0;
+    if (const char *e = getenv("RAS_BARRIER_POLLS")) polls = atoll(e);
+    if (polls != c->bar_polls) {        // the limit stays on the device between launches
+        GridBar b{0u, 0u, polls};
+        RAS_CK(cudaMemcpyAsync(c->d_bar, &b, sizeof(GridBar), cudaMemcpyHostToDevice, st));
+        c->bar_polls = polls;
+    } else {
+        RAS_CK(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), st));
+    }
+    return RAS_OK;
+}
+
 static Interp interp_of(const Coarse *c) {
     Interp P;
     for (int a = 0; a < 3; ++a) {
@@ -1411,7 +1430,7 @@ static int factor_blocks_t(Coarse *c, cudaStream_t st) {
             c->up_n, c->d_err);
         RAS_LAUNCHED();
     }
-    RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
+    RAS_TRY(reset_bar(c, st));
     FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n, (const AT *)c->lo_v,
                    (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, c->d_bar, c->d_err};
     void *args[] = {&fa};
@@ -1459,7 +1478,7 @@ int coarse_check(Coarse *c, cudaStream_t st) {
 
 template <typename AT>
 static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st) {
-    RAS_CK(cudaMemsetAsync(c->d_bar, 0, sizeof(GridBar), st));
+    RAS_TRY(reset_bar(c, st));
     SolArgs<AT> sa{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
                    (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
                    (AT *)c->ry, c->d_bar, c->d_err};
