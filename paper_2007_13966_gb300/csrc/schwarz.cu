@@ -97,30 +97,42 @@ __device__ __forceinline__ void stage_bytes(unsigned char *dst, const unsigned c
 // kernels
 // ---------------------------------------------------------------------------
 
+// q / d for 0 <= q < 2^16 and 1 <= d <= 256 as a multiply-high by ceil(2^32 / d)
+// (exact in that range: q (ceil(2^32/d) d - 2^32) < 2^32 since the excess is < d)
+__host__ __device__ __forceinline__ unsigned magic_div(int d) {
+    return d == 1 ? 0u : (unsigned)((0x100000000ull + (unsigned)d - 1) / (unsigned)d);
+}
+__device__ __forceinline__ int fast_div(int q, int d, unsigned m) {
+    return d == 1 ? q : (int)__umulhi((unsigned)q, m);
+}
+
+
 struct ApplyParams {
     const SubInfo *subs;
     const ShapeInfo *shapes;
     const int *lvl, *chunk;
-    const unsigned *cells;
+    const int *cidx;          // per shape, level order: local natural index of each cell
     const unsigned char *fwd, *bwd;
     const double *r;
     double *z;
     int nx, ny, nz;
     int accumulate;
-    int ycap, lcap, nbuf, chunk_cells;
+    int ycap, gcap, lcap, nbuf, chunk_cells;
     int kind;        // 1 left-RAS; 0 AS, 2 right-RAS (box solutions to zbuf)
     double *zbuf;
 };
 
 template <int PREC, int NBUF>
-__global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
+__global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
     using R = typename RecT<PREC>::T;
     using Acc = typename RecT<PREC>::Acc;
     constexpr int RB = (int)sizeof(R);
     extern __shared__ __align__(16) unsigned char smem[];
-    Acc *Y = reinterpret_cast<Acc *>(smem);
-    int *lvl_s = reinterpret_cast<int *>(smem + ((size_t)P.ycap * sizeof(Acc)));
-    unsigned char *ring = smem + ((size_t)P.ycap * sizeof(Acc)) + (size_t)P.lcap * sizeof(int);
+    // [zero guard: gcap][Y: ycap][zero guard: gcap][level starts][ring]
+    Acc *Y = reinterpret_cast<Acc *>(smem) + P.gcap;
+    const size_t ybytes = ((size_t)P.ycap + 2 * (size_t)P.gcap) * sizeof(Acc);
+    int *lvl_s = reinterpret_cast<int *>(smem + ybytes);
+    unsigned char *ring = smem + ybytes + (size_t)P.lcap * sizeof(int);
     const int rcap = ((P.chunk_cells * RB + 32) + 15) & ~15;
     const int ccap = ((P.chunk_cells * 4 + 32) + 15) & ~15;
     unsigned char *ring_rec = ring;
@@ -130,6 +142,10 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
     const ShapeInfo sh = P.shapes[si.shape];
     const int *chunk_lev = P.chunk + sh.chunk_off;
     for (int t = threadIdx.x; t <= sh.nlev; t += blockDim.x) lvl_s[t] = P.lvl[sh.lvl_off + t];
+    for (int t = threadIdx.x; t < sh.bx * sh.by; t += blockDim.x) {
+        Y[-1 - t] = (Acc)0;
+        Y[sh.ncell + t] = (Acc)0;
+    }
     __syncthreads();
 
     const int nstage = 2 * sh.nchunk;
@@ -142,7 +158,7 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
             stage_bytes(ring_rec + (size_t)slot * rcap, fw ? P.fwd : P.bwd,
                         (si.foff + qa) * (long long)RB, (si.foff + qb) * (long long)RB);
             stage_bytes(ring_cell + (size_t)slot * ccap,
-                        reinterpret_cast<const unsigned char *>(P.cells),
+                        reinterpret_cast<const unsigned char *>(P.cidx),
                         (sh.cell_off + (long long)qa) * 4, (sh.cell_off + (long long)qb) * 4);
         }
         cp_async_commit();
@@ -150,43 +166,44 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
 #pragma unroll
     for (int t = 0; t < NBUF - 1; ++t) issue(t);
 
-    // gather R_i^delta r into shared memory
+    // gather R_i^delta r into shared memory, flat over the box's cells with GB
+    // loads in flight per thread before any is consumed (the gather is bound by
+    // the bytes in flight per SM, not by bandwidth)
+    constexpr int GB = 12;   // the largest batch without spills at 64 registers
     const int bx = sh.bx, by = sh.by, bxy = sh.bx * sh.by;
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
-    // by x-rows of the box: lanes along x (coalesced), 4 rows in flight per warp
-    const int nrow = by * sh.bz;
-    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, nw = blockDim.x >> 5;
-    for (int rbase = wid; rbase < nrow; rbase += 4 * nw) {
-        for (int i0 = 0; i0 < bx; i0 += 64) {
-            double v[4][2];
+    const double *rg = P.r + g0;
+    const unsigned mbx = magic_div(bx), mby = magic_div(by);
+    for (int q0 = threadIdx.x; q0 < sh.ncell; q0 += GB * blockDim.x) {
+        double v[GB];
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int row = rbase + m * nw;
-                const int j = row % by, k = row / by;
-                const double *src = P.r + g0 + (long long)nx * j + (long long)nxy * k;
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = i0 + lane + 32 * h;
-                    if (row < nrow && i < bx) v[m][h] = __ldg(src + i);
-                }
+        for (int m = 0; m < GB; ++m) {
+            const int q = q0 + m * (int)blockDim.x;
+            if (q < sh.ncell) {
+                const int row = fast_div(q, bx, mbx), k = fast_div(row, by, mby);
+                v[m] = __ldg(rg + (q - row * bx) + nx * (row - k * by) + nxy * k);
             }
+        }
 #pragma unroll
-            for (int m = 0; m < 4; ++m) {
-                const int row = rbase + m * nw;
-                // right-RAS: R_i^0 on the input (cells owned by other boxes read as 0)
-                const int j = row % by, k = row / by;
-                const bool orow = P.kind != 2 || (j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1);
-#pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int i = i0 + lane + 32 * h;
-                    const bool own = orow && (P.kind != 2 || (i >= si.ox0 && i < si.ox1));
-                    if (row < nrow && i < bx) Y[row * bx + i] = own ? (Acc)v[m][h] : (Acc)0;
+        for (int m = 0; m < GB; ++m) {
+            const int q = q0 + m * (int)blockDim.x;
+            if (q < sh.ncell) {
+                bool own = true;
+                if (P.kind == 2) {   // right-RAS: R_i^0 on the input (cells of other boxes read as 0)
+                    const int row = fast_div(q, bx, mbx), k = fast_div(row, by, mby);
+                    const int i = q - row * bx, j = row - k * by;
+                    own = i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 &&
+                          k < si.oz1;
                 }
+                Y[q] = own ? (Acc)v[m] : (Acc)0;
             }
         }
     }
 
+    // Sweeps, level by level. A neighbour outside the box has a zero factor value and
+    // reads a finite value (a cell of the box or the zero guard band on either side
+    // of Y), so no cell needs a flag test.
     for (int t = 0; t < nstage; ++t) {
         cp_async_wait<NBUF - 2>();
         __syncthreads();
@@ -198,23 +215,20 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
         const int slot = t % NBUF;
         const unsigned char *rec = ring_rec + (size_t)slot * rcap +
                                    (int)(((si.foff + qa) * (long long)RB) & 15);
-        const unsigned char *cel = ring_cell + (size_t)slot * ccap +
-                                   (int)(((sh.cell_off + (long long)qa) * 4) & 15);
+        const int *cel = reinterpret_cast<const int *>(
+            ring_cell + (size_t)slot * ccap + (int)(((sh.cell_off + (long long)qa) * 4) & 15));
         if (fw) {
             // forward: w_n = (r_n - sum_{m<n} a_nm w_m) / d_n, w = D^{-1} L^{-1} r
             for (int l = l0; l < l1; ++l) {
                 const int q1 = lvl_s[l + 1];
                 for (int q = lvl_s[l] + threadIdx.x; q < q1; q += blockDim.x) {
-                    const unsigned e = *reinterpret_cast<const unsigned *>(cel + 4 * (q - qa));
+                    const int n = cel[q - qa];
                     Acc ax, ay, az, dinv;
                     load_rec<Acc, R>(rec + (size_t)RB * (q - qa), ax, ay, az, dinv);
-                    const int n = (int)(e & 255u) + bx * (int)((e >> 8) & 255u) +
-                                  bxy * (int)((e >> 16) & 255u);
-                    const unsigned fl = e >> 24;
                     Acc s = Y[n];
-                    if (fl & F_MZ) s -= az * Y[n - bxy];
-                    if (fl & F_MY) s -= ay * Y[n - bx];
-                    if (fl & F_MX) s -= ax * Y[n - 1];
+                    s -= az * Y[n - bxy];
+                    s -= ay * Y[n - bx];
+                    s -= ax * Y[n - 1];
                     Y[n] = s * dinv;
                 }
                 __syncthreads();
@@ -224,16 +238,12 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
             for (int l = l1 - 1; l >= l0; --l) {
                 const int q1 = lvl_s[l + 1];
                 for (int q = lvl_s[l] + threadIdx.x; q < q1; q += blockDim.x) {
-                    const unsigned e = *reinterpret_cast<const unsigned *>(cel + 4 * (q - qa));
+                    const int n = cel[q - qa];
                     Acc ax, ay, az, dinv;
                     load_rec<Acc, R>(rec + (size_t)RB * (q - qa), ax, ay, az, dinv);
-                    const int n = (int)(e & 255u) + bx * (int)((e >> 8) & 255u) +
-                                  bxy * (int)((e >> 16) & 255u);
-                    const unsigned fl = e >> 24;
-                    Acc s = 0;
-                    if (fl & F_PX) s += ax * Y[n + 1];
-                    if (fl & F_PY) s += ay * Y[n + bx];
-                    if (fl & F_PZ) s += az * Y[n + bxy];
+                    Acc s = ax * Y[n + 1];
+                    s += ay * Y[n + bx];
+                    s += az * Y[n + bxy];
                     Y[n] = Y[n] - dinv * s;
                 }
                 __syncthreads();
@@ -247,16 +257,32 @@ __global__ void __launch_bounds__(512) k_ras_apply(ApplyParams P) {
         for (int q = threadIdx.x; q < sh.ncell; q += blockDim.x) dst[q] = (double)Y[q];
         return;
     }
-    // (R_i^0)^T: write the owned cells, by x-rows (coalesced)
-    const int ox0 = si.ox0, ox1 = si.ox1;
-    for (int row = wid; row < nrow; row += nw) {
-        const int j = row % by, k = row / by;
-        if (j < si.oy0 || j >= si.oy1 || k < si.oz0 || k >= si.oz1) continue;
-        double *dst = P.z + g0 + (long long)nx * j + (long long)nxy * k;
-        for (int i = ox0 + lane; i < ox1; i += 32) {
-            const double v = (double)Y[row * bx + i];
-            if (P.accumulate) dst[i] += v; else dst[i] = v;
+    // (R_i^0)^T: write the owned cells, flat over the owned box (GW old values in
+    // flight per thread when accumulating)
+    constexpr int GW = 8;
+    const int owx = si.ox1 - si.ox0, owy = si.oy1 - si.oy0;
+    const int nown = owx * owy * (si.oz1 - si.oz0);
+    const unsigned mox = magic_div(owx), moy = magic_div(owy);
+    double *zg = P.z + g0;
+    for (int q0 = threadIdx.x; q0 < nown; q0 += GW * blockDim.x) {
+        int yq[GW], go[GW];
+        double prev[GW];
+#pragma unroll
+        for (int m = 0; m < GW; ++m) {
+            const int q = q0 + m * (int)blockDim.x;
+            yq[m] = -1;
+            prev[m] = 0.0;
+            if (q < nown) {
+                const int row = fast_div(q, owx, mox), k = fast_div(row, owy, moy);
+                const int i = si.ox0 + q - row * owx, j = si.oy0 + row - k * owy, kk = si.oz0 + k;
+                yq[m] = i + bx * j + bxy * kk;
+                go[m] = i + nx * j + nxy * kk;
+                if (P.accumulate) prev[m] = zg[go[m]];
+            }
         }
+#pragma unroll
+        for (int m = 0; m < GW; ++m)
+            if (yq[m] >= 0) zg[go[m]] = prev[m] + (double)Y[yq[m]];
     }
 }
 
@@ -395,10 +421,11 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     std::map<std::tuple<int, int, int>, int> shape_id;
     std::vector<int> lvl_tab, chunk_tab;
     std::vector<unsigned> cell_tab;
+    std::vector<int> cidx_tab;        // same positions as cell_tab: i + bx (j + by k)
     R.subs.clear();
     R.shapes.clear();
     long long foff = 0;
-    int maxw_all = 0, ycap = 0, lcap = 0;
+    int maxw_all = 0, ycap = 0, lcap = 0, gcap = 0;
     for (int kz = 0; kz < pz; ++kz)
         for (int jy = 0; jy < py; ++jy)
             for (int ix = 0; ix < px; ++ix) {
@@ -447,13 +474,17 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
                             };
                             return nat(a) < nat(b);
                         });
-                    while (cell_tab.size() % 4) cell_tab.push_back(0);
+                    while (cell_tab.size() % 4) { cell_tab.push_back(0); cidx_tab.push_back(0); }
                     sh.cell_off = (int)cell_tab.size();
                     sh.lvl_off = (int)lvl_tab.size();
                     int pos = 0, maxw = 0;
                     for (auto &L : levels) {
                         lvl_tab.push_back(pos);
-                        for (unsigned e : L) cell_tab.push_back(e);
+                        for (unsigned e : L) {
+                            cell_tab.push_back(e);
+                            cidx_tab.push_back((int)(e & 255u) + bx * ((int)((e >> 8) & 255u) +
+                                                                       by * (int)((e >> 16) & 255u)));
+                        }
                         pos += (int)L.size();
                         maxw = std::max(maxw, (int)L.size());
                     }
@@ -461,6 +492,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
                     sh.maxw = maxw;
                     maxw_all = std::max(maxw_all, maxw);
                     ycap = std::max(ycap, ncell);
+                    gcap = std::max(gcap, bx * by);
                     lcap = std::max(lcap, sh.nlev + 1);
                     R.shapes.push_back(sh);
                     sid = (int)R.shapes.size() - 1;
@@ -515,11 +547,12 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
         if (v >= 32 && v <= 512 && v % 32 == 0) R.block = v;
     }
     R.ycap = (ycap + 3) & ~3;
+    R.gcap = (gcap + 3) & ~3;
     R.lcap = (lcap + 3) & ~3;
     const size_t acc = prec == 64 ? 8 : 4;
     const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
     const size_t ccap = ((R.chunk_cells * 4 + 32) + 15) & ~15;
-    R.smem_apply = R.ycap * acc + R.lcap * sizeof(int) + R.nbuf * (rcap + ccap);
+    R.smem_apply = (R.ycap + 2 * (size_t)R.gcap) * acc + R.lcap * sizeof(int) + R.nbuf * (rcap + ccap);
     R.smem_factor = (size_t)R.ycap * sizeof(double);
     if (R.smem_apply > 227 * 1024 || R.smem_factor > 227 * 1024) return RAS_EINVAL;
 
@@ -528,6 +561,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     RAS_TRY(dalloc(&R.d_lvl, lvl_tab.size()));
     RAS_TRY(dalloc(&R.d_chunk, chunk_tab.size()));
     RAS_TRY(dalloc(&R.d_cells, cell_tab.size() + 16));
+    RAS_TRY(dalloc(&R.d_cidx, cidx_tab.size() + 16));
     RAS_TRY(dalloc(&R.d_err, 1));
     unsigned char *fw = nullptr, *bw = nullptr;
     RAS_TRY(dalloc(&fw, (size_t)R.nrec * R.rec_bytes + 64));
@@ -540,6 +574,8 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     RAS_CK(cudaMemcpy(R.d_chunk, chunk_tab.data(), chunk_tab.size() * sizeof(int),
                       cudaMemcpyHostToDevice));
     RAS_CK(cudaMemset(R.d_cells, 0, (cell_tab.size() + 16) * sizeof(unsigned)));
+    RAS_CK(cudaMemset(R.d_cidx, 0, (cidx_tab.size() + 16) * sizeof(int)));
+    RAS_CK(cudaMemcpy(R.d_cidx, cidx_tab.data(), cidx_tab.size() * sizeof(int), cudaMemcpyHostToDevice));
     RAS_CK(cudaMemcpy(R.d_cells, cell_tab.data(), cell_tab.size() * sizeof(unsigned),
                       cudaMemcpyHostToDevice));
     RAS_CK(cudaMemset(R.d_err, 0, sizeof(int)));
@@ -572,7 +608,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
 
 void ras1_free(Ras1 &R) {
     dfree(R.d_subs); dfree(R.d_shapes); dfree(R.d_lvl); dfree(R.d_chunk); dfree(R.d_cells);
-    dfree(R.d_err);
+    dfree(R.d_cidx); dfree(R.d_err);
     if (R.d_fwd) cudaFree(R.d_fwd);
     if (R.d_bwd) cudaFree(R.d_bwd);
     R.d_fwd = R.d_bwd = nullptr;
@@ -607,10 +643,10 @@ int ras1_check(Ras1 &R, cudaStream_t st) {
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st) {
     ApplyParams P;
     P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.chunk = R.d_chunk;
-    P.cells = R.d_cells;
+    P.cidx = R.d_cidx;
     P.fwd = (const unsigned char *)R.d_fwd; P.bwd = (const unsigned char *)R.d_bwd;
     P.r = r; P.z = z; P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.accumulate = accumulate;
-    P.ycap = R.ycap; P.lcap = R.lcap; P.nbuf = R.nbuf; P.chunk_cells = R.chunk_cells;
+    P.ycap = R.ycap; P.gcap = R.gcap; P.lcap = R.lcap; P.nbuf = R.nbuf; P.chunk_cells = R.chunk_cells;
     P.kind = R.kind; P.zbuf = R.zbuf;
     if (R.prec == 64) k_ras_apply<64, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);
     else if (R.prec == 32) k_ras_apply<32, 3><<<R.nsub, R.block, R.smem_apply, st>>>(P);

@@ -39,6 +39,7 @@ struct Ras1 {
     int chunk_cells = 1024; // max cells per staged chunk
     int nbuf = 3;           // staged chunks in flight
     int ycap = 0, lcap = 0; // smem capacities (cells, levels + 1)
+    int gcap = 0;           // zero guard band on each side of the apply's vector (cells)
     size_t smem_apply = 0, smem_factor = 0;
     long long nrec = 0;     // factor records (incl. padding)
     long long ncell_total = 0;  // sum of overlapped cells
@@ -47,6 +48,7 @@ struct Ras1 {
     ShapeInfo *d_shapes = nullptr;
     int *d_lvl = nullptr, *d_chunk = nullptr;
     unsigned *d_cells = nullptr;
+    int *d_cidx = nullptr;  // level-ordered local natural index of each cell (apply)
     void *d_fwd = nullptr, *d_bwd = nullptr;
     int *d_err = nullptr;
     // AS (kind 0) and right-RAS (kind 2): each box's whole solution goes to zbuf
