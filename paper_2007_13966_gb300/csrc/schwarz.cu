@@ -149,6 +149,7 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
     __syncthreads();
 
     const int nstage = 2 * sh.nchunk;
+    const bool one = (int)blockDim.x >= sh.maxw;   // one cell per thread per level
     auto issue = [&](int t) {
         if (t < nstage) {
             const bool fw = t < sh.nchunk;
@@ -217,6 +218,48 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
                                    (int)(((si.foff + qa) * (long long)RB) & 15);
         const int *cel = reinterpret_cast<const int *>(
             ring_cell + (size_t)slot * ccap + (int)(((sh.cell_off + (long long)qa) * 4) & 15));
+        // When the block covers the widest level, a level is one guarded pass (no loop
+        // back-edge before the barrier) with addresses from per-chunk bases.
+        const int tid = threadIdx.x;
+        const int *cel_t = cel - qa + tid;                       // cel_t[lo]: cell lo + tid
+        const unsigned char *rec_t = rec + (long long)RB * (tid - qa);
+        if (one) {
+            if (fw) {
+#pragma unroll 2
+                for (int l = l0; l < l1; ++l) {
+                    const int lo = lvl_s[l];
+                    if (lo + tid < lvl_s[l + 1]) {
+                        const int n = cel_t[lo];
+                        Acc ax, ay, az, dinv;
+                        load_rec<Acc, R>(rec_t + (size_t)RB * lo, ax, ay, az, dinv);
+                        Acc *yn = Y + n;
+                        Acc s = yn[0];
+                        s -= az * yn[-bxy];
+                        s -= ay * yn[-bx];
+                        s -= ax * yn[-1];
+                        yn[0] = s * dinv;
+                    }
+                    __syncthreads();
+                }
+            } else {
+#pragma unroll 2
+                for (int l = l1 - 1; l >= l0; --l) {
+                    const int lo = lvl_s[l];
+                    if (lo + tid < lvl_s[l + 1]) {
+                        const int n = cel_t[lo];
+                        Acc ax, ay, az, dinv;
+                        load_rec<Acc, R>(rec_t + (size_t)RB * lo, ax, ay, az, dinv);
+                        Acc *yn = Y + n;
+                        Acc s = ax * yn[1];
+                        s += ay * yn[bx];
+                        s += az * yn[bxy];
+                        yn[0] = yn[0] - dinv * s;
+                    }
+                    __syncthreads();
+                }
+            }
+            continue;
+        }
         if (fw) {
             // forward: w_n = (r_n - sum_{m<n} a_nm w_m) / d_n, w = D^{-1} L^{-1} r
             for (int l = l0; l < l1; ++l) {
@@ -523,7 +566,11 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     }
     R.nrec = foff;
     // chunks of consecutive levels with at most chunk_cells cells
-    const int base_chunk = prec == 64 ? 384 : 1024;
+    int base_chunk = prec == 64 ? 384 : 1024;
+    if (const char *e = getenv("RAS_APPLY_CHUNK")) {     // tuning knob
+        const int v = atoi(e);
+        if (v >= 64 && v <= 8192) base_chunk = v;
+    }
     R.chunk_cells = std::max(base_chunk, maxw_all);
     R.nbuf = 3;
     for (auto &sh : R.shapes) {
