@@ -741,7 +741,9 @@ struct FacArgs {
     int *err;
 };
 
-// Out[r0+i][c] (=, -=) sum_e M[r0+i][uq[c][e]] uv[c][e] for a chunk of FROWS rows
+// Out[r0+i][c] (=, -=) sum_e M[r0+i][uq[c][e]] uv[c][e] for a chunk of FROWS rows.
+// A thread takes CPT columns at once, so the coupling loads of all of them are in
+// flight together (each column's terms are still summed in entry order).
 template <typename AT>
 __device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, const AT *uv,
                               const int *un, int T, int r0, bool subtract) {
@@ -767,32 +769,97 @@ __device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, con
         }
     }
     __syncthreads();
-    for (int c = threadIdx.x; c < T; c += blockDim.x) {
-        AT acc[FROWS] = {};
-        const int ne = un[c];
-        // transposed ELL: entry e of column c at [e * T + c] (coalesced)
-        for (int e0 = 0; e0 < ne; e0 += 8) {
-            int qb[8];
-            AT vb[8];
+    constexpr int CPT = sizeof(AT) == 4 ? 4 : 2;   // register budget
+    const int nb = blockDim.x;
+    for (int c0 = threadIdx.x; c0 < T; c0 += CPT * nb) {
+        AT acc[CPT][FROWS];
+        int ne[CPT], nmax = 0;
 #pragma unroll
-            for (int m = 0; m < 8; ++m) {
-                const bool ok = e0 + m < ne;
-                qb[m] = ok ? uq[(long long)(e0 + m) * T + c] : 0;
-                vb[m] = ok ? uv[(long long)(e0 + m) * T + c] : (AT)0;
+        for (int j = 0; j < CPT; ++j) {
+            const int c = c0 + j * nb;
+            ne[j] = c < T ? un[c] : 0;
+            nmax = max(nmax, ne[j]);
+#pragma unroll
+            for (int i = 0; i < FROWS; ++i) acc[j][i] = (AT)0;
+        }
+        // transposed ELL: entry e of column c at [e * T + c] (coalesced)
+        for (int e0 = 0; e0 < nmax; e0 += 4) {
+            int qb[CPT][4];
+            AT vb[CPT][4];
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+#pragma unroll
+                for (int m = 0; m < 4; ++m) {
+                    const bool ok = e0 + m < ne[j];
+                    const long long at = (long long)(e0 + m) * T + c0 + j * nb;
+                    qb[j][m] = ok ? uq[at] : 0;
+                    vb[j][m] = ok ? uv[at] : (AT)0;
+                }
+#pragma unroll
+            for (int j = 0; j < CPT; ++j)
+#pragma unroll
+                for (int m = 0; m < 4; ++m)
+#pragma unroll
+                    for (int i = 0; i < FROWS; ++i) acc[j][i] += rows[i * T + qb[j][m]] * vb[j][m];
+        }
+        AT prev[CPT][FROWS];
+#pragma unroll
+        for (int j = 0; j < CPT; ++j)
+#pragma unroll
+            for (int i = 0; i < FROWS; ++i) {
+                const int c = c0 + j * nb;
+                prev[j][i] = subtract && c < T ? __ldcg(Out + (long long)(r0 + i) * T + c) : (AT)0;
             }
 #pragma unroll
-            for (int m = 0; m < 8; ++m)
+        for (int j = 0; j < CPT; ++j)
 #pragma unroll
-                for (int i = 0; i < FROWS; ++i) acc[i] += rows[i * T + qb[m]] * vb[m];
-        }
-        AT prev[FROWS];
-#pragma unroll
-        for (int i = 0; i < FROWS; ++i) prev[i] = subtract ? __ldcg(Out + (long long)(r0 + i) * T + c) : (AT)0;
-#pragma unroll
-        for (int i = 0; i < FROWS; ++i)
-            Out[(long long)(r0 + i) * T + c] = subtract ? prev[i] - acc[i] : acc[i];
+            for (int i = 0; i < FROWS; ++i) {
+                const int c = c0 + j * nb;
+                if (c < T) Out[(long long)(r0 + i) * T + c] = subtract ? prev[j][i] - acc[j][i] : acc[j][i];
+            }
     }
     __syncthreads();
+}
+
+// out[c] = sum_e lv[e] Inv[lq[e]][c] for one row (c < T): the row's couplings are
+// staged in shared memory, then every thread keeps NB 16-byte loads of Inv rows in
+// flight (terms summed in entry order).
+template <typename AT>
+__device__ void sparse_row_times(const AT *Inv, const int *lq, const AT *lv, int nel, AT *out, int T,
+                                 unsigned char *smem) {
+    int *sq = reinterpret_cast<int *>(smem);
+    AT *sv = reinterpret_cast<AT *>(smem + ELLW * sizeof(int));
+    __syncthreads();                      // the shared memory of the previous item is free
+    for (int m = threadIdx.x; m < nel; m += blockDim.x) { sq[m] = lq[m]; sv[m] = lv[m]; }
+    __syncthreads();
+    constexpr int VEC = 16 / sizeof(AT), NB = 16;
+    using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    const int ng = T / VEC;
+    for (int g = threadIdx.x; g < ng; g += blockDim.x) {
+        AT acc[VEC];
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc[q] = (AT)0;
+        for (int e0 = 0; e0 < nel; e0 += NB) {
+            V16 buf[NB];
+#pragma unroll
+            for (int m = 0; m < NB; ++m)
+                if (e0 + m < nel) buf[m] = __ldcg(reinterpret_cast<const V16 *>(Inv + (long long)sq[e0 + m] * T) + g);
+#pragma unroll
+            for (int m = 0; m < NB; ++m)
+                if (e0 + m < nel) {
+                    const AT w = sv[e0 + m];
+                    const AT *v = reinterpret_cast<const AT *>(&buf[m]);
+#pragma unroll
+                    for (int q = 0; q < VEC; ++q) acc[q] += w * v[q];
+                }
+        }
+        V16 o;
+        AT *ov = reinterpret_cast<AT *>(&o);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) ov[q] = acc[q];
+        reinterpret_cast<V16 *>(out)[g] = o;
+    }
+    __syncthreads();                      // the next item may overwrite the staged couplings
 }
 
 // In-place inverses of the blocks blk[0..nblk) (one chain each), panel by
@@ -920,27 +987,10 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
             const int e = edg[it2 / nE], it = it2 % nE;
             const AT *Inv = a.D + edge_pivot(e, mid) * bsz;
             if (it < T) {                                   // C_e row = A(target, pivot) row * Inv
-                const int *lq = a.lo_q + e * ell;
-                const AT *lv = a.lo_v + e * ell;
                 const int r = it;
-                const int nel = a.lo_n[(long long)e * T + r];
-                AT *Ce = a.C + e * bsz;
-                for (int c = threadIdx.x; c < T; c += blockDim.x) {
-                    AT acc = 0;
-                    for (int e0 = 0; e0 < nel; e0 += 8) {   // 8 row loads in flight
-                        AT eb[8], vb[8];
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) {
-                            const bool ok = e0 + m < nel;
-                            const long long le = (long long)r * ELLW + e0 + m;
-                            vb[m] = ok ? lv[le] : (AT)0;
-                            eb[m] = ok ? __ldcg(Inv + (long long)lq[le] * T + c) : (AT)0;
-                        }
-#pragma unroll
-                        for (int m = 0; m < 8; ++m) acc += vb[m] * eb[m];
-                    }
-                    Ce[(long long)r * T + c] = acc;
-                }
+                const long long at = e * ell + (long long)r * ELLW;
+                sparse_row_times(Inv, a.lo_q + at, a.lo_v + at, a.lo_n[(long long)e * T + r],
+                                 a.C + e * bsz + (long long)r * T, T, smem_raw);
             } else {                                        // F_e = Inv A(pivot, target)
                 rows_times_up(rows, Inv, a.F + e * bsz, a.up_q + e * ell, a.up_v + e * ell,
                               a.up_n + (long long)e * T, T, (it - T) * FROWS, false);
