@@ -27,6 +27,7 @@
 #include "precond.cuh"
 
 #include <algorithm>
+#include <cstddef>
 #include <cstdlib>
 #include <numeric>
 #include <type_traits>
@@ -39,9 +40,13 @@ constexpr int FROWS = 8;    // rows of a dense block staged per CTA in the spars
 constexpr int ERR_PIVOT = 1, ERR_ELL = 2, ERR_TIMEOUT = 7;
 constexpr long long BAR_POLLS = 1LL << 22;   // ~1-2 s of polling before a barrier gives up
 
+// arrival counter and release word on separate 128-byte lines (the waiting CTAs
+// poll `gen`, not the line the arrivals add to)
 struct GridBar {
     unsigned count;
+    unsigned pad0[31];
     unsigned gen;
+    unsigned pad1[31];
     long long polls;   // poll limit of this launch (<= 0: BAR_POLLS)
 };
 
@@ -73,6 +78,7 @@ struct Coarse {
     size_t rap_smem = 0, rap125_smem = 0, fac_smem = 0, sol_smem = 0;
     int rap125_ng = 25;             // offsets staged per round in k_rap125
     int fac_grid = 0, sol_grid = 0;
+    int sol_npf = 0;                // rows per warp prefetched by the solve
 };
 
 // ---------------------------------------------------------------------------
@@ -396,32 +402,46 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
+__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
+    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
+    unsigned old;
+    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
+    return old;
+}
+
 // Grid barrier on a monotonically increasing arrival counter: barrier number e
-// (1, 2, ...) of a launch completes when the counter reaches e * gridDim.x, so
-// arrival is one non-returning atomic add and the wait a polled acquire load.
-// `epoch` is the caller's count of barriers passed (same in every thread); the
-// counter is reset to zero before every launch. Returns false if this or
-// another CTA has recorded an error (callers then stop working but return from
-// the kernel promptly); the wait is bounded (ERR_TIMEOUT).
+// (1, 2, ...) of a launch is complete when the counter reaches e * gridDim.x. Each
+// CTA arrives with one atomic add (acquire-release: the CTA whose add completes the
+// count has then acquired every arrival) and that CTA publishes e in `gen`
+// (release); the others poll `gen` (acquire), at most the launch's poll
+// limit. `epoch` is the caller's count of barriers passed (same in every thread);
+// counter and gen are reset to zero before every launch. The error word is read at
+// entry without waiting for it (its value is consulted after the barrier) and every
+// 1024 polls. Returns false if this or any CTA has flagged an error or the wait ran
+// out (ERR_TIMEOUT is then set).
 __device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch) {
     __shared__ int s_ok;
     ++epoch;
     __syncthreads();
     if (threadIdx.x == 0) {
-        int ok = (ld_acquire((const unsigned *)err) == 0);
-        if (ok) {
-            const unsigned target = epoch * gridDim.x;
-            const long long lim = bar->polls > 0 ? bar->polls : BAR_POLLS;
-            __threadfence();
-            asm volatile("red.release.gpu.global.add.u32 [%0], 1;" ::"l"(&bar->count) : "memory");
+        const unsigned e0 = *reinterpret_cast<volatile const unsigned *>(err);
+        int ok = 1;
+        const long long lim = bar->polls > 0 ? bar->polls : BAR_POLLS;
+        __threadfence();
+        const unsigned target = epoch * gridDim.x;
+        if (atom_add_acq_rel(&bar->count, 1u) == target - 1) {
+            st_release(&bar->gen, epoch);
+        } else {
             long long it = 0;
-            while (ld_acquire(&bar->count) < target) {
+            while (ld_acquire(&bar->gen) < epoch) {
                 if (++it > lim) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
                 if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
-                __nanosleep(20);
             }
-            __threadfence();
         }
+        if (e0 != 0) ok = 0;
+        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -1023,7 +1043,34 @@ struct SolArgs {
     AT *rx, *ry;
     GridBar *bar;
     int *err;
+    int npf;   // matrix rows per warp prefetched into shared memory per stage (0..2)
 };
+
+__device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
+    const unsigned sa = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(gmem) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit_all() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
+// dot of a shared-memory matrix row with a shared-memory vector; lane l reads the
+// 16-byte pieces l, l + 32, ... (the pieces it copied itself)
+template <typename AT>
+__device__ __forceinline__ AT row_dot_s(const AT *row, const AT *xs, int T, int lane) {
+    constexpr int VEC = 16 / sizeof(AT);
+    using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    const V16 *rv = reinterpret_cast<const V16 *>(row);
+    AT acc = 0;
+    for (int v = lane; v < T / VEC; v += 32) {
+        const V16 b = rv[v];
+        const AT *w = reinterpret_cast<const AT *>(&b);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) acc += w[q] * xs[v * VEC + q];
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    return acc;
+}
 
 // dot of a matrix row with a shared-memory vector, 16-byte loads (T is a
 // multiple of 64 and rows start 16-byte aligned)
@@ -1074,18 +1121,6 @@ __device__ void stage_vector(const AT *xsrc, AT *xs, int T) {
     __syncthreads();
 }
 
-// y[r] (=, -=) sum_c M[r][c] xs[c] over rows distributed to warps of the grid
-template <typename AT>
-__device__ void grid_gemv(const AT *M, const AT *xsrc, AT *y, int T, AT *xs, bool subtract) {
-    stage_vector(xsrc, xs, T);
-    const int lane = threadIdx.x & 31;
-    const int wpb = blockDim.x / 32;
-    for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < T; r += gridDim.x * wpb) {
-        const AT acc = row_dot(M + (long long)r * T, xs, T, lane);
-        if (lane == 0) y[r] = subtract ? __ldcg(y + r) - acc : acc;
-    }
-}
-
 template <typename AT>
 __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1096,6 +1131,54 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     const long long bsz = (long long)T * T;
     const int lane = threadIdx.x & 31, wpb = blockDim.x / 32;
     unsigned epoch = 0;
+    // Block sweeps as 2 nsteps + 1 stages separated by grid barriers: forward along
+    // both chains (g_target -= C_e g_pivot, and x_pivot = Inv_pivot g_pivot), the
+    // middle block (x_mid = Inv_mid g_mid), back along both chains
+    // (x_pivot -= F_e x_target). The matrix rows of a stage do not depend on the
+    // vectors, so each warp copies its first npf rows of the next stage into shared
+    // memory before the barrier (the copies overlap the barrier and the next
+    // vector staging); further rows are read directly.
+    const int nb = G.nb, mid = G.mid, ntop = mid, nbot = nb - 1 - mid;
+    const int nsteps = max(ntop, nbot), nstage = 2 * nsteps + 1;
+    const int wg = blockIdx.x * wpb + (threadIdx.x >> 5), nwt = gridDim.x * wpb;
+    AT *rbuf = xs + 2 * (long long)T + (long long)(threadIdx.x >> 5) * a.npf * T;
+    constexpr int VEC = 16 / sizeof(AT);
+    auto edges_of = [&](int st, int *edg) {
+        int ne = 0;
+        if (st < nsteps) {
+            if (st < ntop) edg[ne++] = st;
+            if (st < nbot) edg[ne++] = nb - 2 - st;
+        } else if (st > nsteps) {
+            const int q = st - nsteps - 1;
+            if (q < ntop) edg[ne++] = ntop - 1 - q;
+            if (q < nbot) edg[ne++] = mid + q;
+        }
+        return ne;
+    };
+    auto nrows_of = [&](int st, int ne) { return st < nsteps ? ne * 2 * T : (st == nsteps ? T : ne * T); };
+    auto row_ptr = [&](int st, const int *edg, int r) -> const AT * {
+        if (st < nsteps) {
+            const int c = r / (2 * T), rr = r % (2 * T), e = edg[c];
+            return rr < T ? a.E + edge_pivot(e, mid) * bsz + (long long)rr * T
+                          : a.C + e * bsz + (long long)(rr - T) * T;
+        }
+        if (st == nsteps) return a.E + mid * bsz + (long long)r * T;
+        return a.F + edg[r / T] * bsz + (long long)(r % T) * T;
+    };
+    auto prefetch = [&](int st) {
+        if (st < nstage) {
+            int edg[2];
+            const int nr = nrows_of(st, edges_of(st, edg));
+            for (int k = 0; k < a.npf; ++k) {
+                const int r = wg + k * nwt;
+                if (r >= nr) break;
+                const AT *src = row_ptr(st, edg, r);
+                for (int v = lane; v < T / VEC; v += 32) cp_async16_cg(rbuf + (long long)k * T + v * VEC, src + v * VEC);
+            }
+        }
+        cp_async_commit_all();
+    };
+    prefetch(0);   // lands during the restriction
     // g = R t with R = P^T = Pz^T Py^T Px^T, one axis per pass
     const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
     const long long gstride = (long long)gridDim.x * blockDim.x;
@@ -1109,7 +1192,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
         for (int ax = x0; ax < x1; ++ax) acc += (AT)w1(P, 0, ax, Ix) * (AT)__ldg(src + ax);
         a.rx[e] = acc;
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) return;
+    if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
     const long long n2 = (long long)G.cx * G.cy * G.nz;
     for (long long e = gtid; e < n2; e += gstride) {          // y pass
         const int Ix = (int)(e % G.cx), Iy = (int)((e / G.cx) % G.cy);
@@ -1120,7 +1203,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
             acc += (AT)w1(P, 1, ay, Iy) * __ldcg(a.rx + Ix + (long long)G.cx * (ay + (long long)G.ny * az));
         a.ry[e] = acc;
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) return;
+    if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
     for (long long I = gtid; I < G.Nc; I += gstride) {         // z pass
         const int Ix = (int)(I % G.cx), Iy = (int)((I / G.cx) % G.cy), Iz = (int)(I / ((long long)G.cx * G.cy));
         AT acc = 0;
@@ -1129,49 +1212,46 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
             acc += (AT)w1(P, 2, az, Iz) * __ldcg(a.ry + Ix + (long long)G.cx * (Iy + (long long)G.cy * az));
         a.g[a.pos[I]] = acc;
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) return;
-    // forward along both chains: g_target -= C_e g_pivot, and in the same
-    // phase x_pivot = Inv_pivot g_pivot (the back-substitution adds -F_e x_target)
-    const int nb = G.nb, mid = G.mid, ntop = mid, nbot = nb - 1 - mid;
-    const int nsteps = max(ntop, nbot);
-    for (int s = 0; s < nsteps; ++s) {
-        int edg[2], ne = 0;
-        if (s < ntop) edg[ne++] = s;
-        if (s < nbot) edg[ne++] = nb - 2 - s;
-        for (int c = 0; c < ne; ++c)
-            stage_vector(a.g + (long long)edge_pivot(edg[c], mid) * T, xs + (long long)c * T, T);
-        for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < ne * 2 * T; r += gridDim.x * wpb) {
-            const int c = r / (2 * T), rr = r % (2 * T), e = edg[c];
-            const AT *xv = xs + (long long)c * T;
-            if (rr < T) {   // x_pivot row
-                const int pv = edge_pivot(e, mid);
-                const AT acc = row_dot(a.E + pv * bsz + (long long)rr * T, xv, T, lane);
-                if (lane == 0) a.x[(long long)pv * T + rr] = acc;
-            } else {        // g_target row
-                const AT acc = row_dot(a.C + e * bsz + (long long)(rr - T) * T, xv, T, lane);
-                AT *y = a.g + (long long)edge_target(e, mid) * T + (rr - T);
-                if (lane == 0) *y = __ldcg(y) - acc;
+    if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
+    for (int st = 0; st < nstage; ++st) {
+        int edg[2];
+        const int ne = edges_of(st, edg);
+        if (st < nsteps)
+            for (int c = 0; c < ne; ++c)
+                stage_vector(a.g + (long long)edge_pivot(edg[c], mid) * T, xs + (long long)c * T, T);
+        else if (st == nsteps)
+            stage_vector(a.g + (long long)mid * T, xs, T);
+        else
+            for (int c = 0; c < ne; ++c)
+                stage_vector(a.x + (long long)edge_target(edg[c], mid) * T, xs + (long long)c * T, T);
+        cp_async_wait_all();
+        __syncwarp();
+        const int nr = nrows_of(st, ne);
+        int k = 0;
+        for (int r = wg; r < nr; r += nwt, ++k) {
+            const AT *xv = xs + (long long)(st < nsteps ? r / (2 * T) : (st == nsteps ? 0 : r / T)) * T;
+            const AT acc = k < a.npf ? row_dot_s(rbuf + (long long)k * T, xv, T, lane)
+                                     : row_dot(row_ptr(st, edg, r), xv, T, lane);
+            if (lane == 0) {
+                if (st < nsteps) {
+                    const int c = r / (2 * T), rr = r % (2 * T), e = edg[c];
+                    if (rr < T) {
+                        a.x[(long long)edge_pivot(e, mid) * T + rr] = acc;
+                    } else {
+                        AT *y = a.g + (long long)edge_target(e, mid) * T + (rr - T);
+                        *y = __ldcg(y) - acc;
+                    }
+                } else if (st == nsteps) {
+                    a.x[(long long)mid * T + r] = acc;
+                } else {
+                    AT *y = a.x + (long long)edge_pivot(edg[r / T], mid) * T + (r % T);
+                    *y = __ldcg(y) - acc;
+                }
             }
         }
-        if (!grid_barrier(a.bar, a.err, epoch)) return;
-    }
-    // middle block
-    grid_gemv(a.E + mid * bsz, a.g + (long long)mid * T, a.x + (long long)mid * T, T, xs, false);
-    if (!grid_barrier(a.bar, a.err, epoch)) return;
-    // back along both chains: x_pivot -= F_e x_target
-    for (int s = 0; s < nsteps; ++s) {
-        int edg[2], ne = 0;
-        if (s < ntop) edg[ne++] = ntop - 1 - s;
-        if (s < nbot) edg[ne++] = mid + s;
-        for (int c = 0; c < ne; ++c)
-            stage_vector(a.x + (long long)edge_target(edg[c], mid) * T, xs + (long long)c * T, T);
-        for (int r = blockIdx.x * wpb + (threadIdx.x >> 5); r < ne * T; r += gridDim.x * wpb) {
-            const int c = r / T, rr = r % T, e = edg[c];
-            const AT acc = row_dot(a.F + e * bsz + (long long)rr * T, xs + (long long)c * T, T, lane);
-            AT *y = a.x + (long long)edge_pivot(e, mid) * T + rr;
-            if (lane == 0) *y = __ldcg(y) - acc;
-        }
-        if (!grid_barrier(a.bar, a.err, epoch)) return;
+        __syncwarp();                      // this warp's reads of its row buffer are done
+        prefetch(st + 1);
+        if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
     }
     // z (+)= P x, four fine cells per thread with their loads in flight together
     const long long N = (long long)G.nx * G.ny * G.nz;
@@ -1263,11 +1343,12 @@ static int reset_bar(Coarse *c, cudaStream_t st) {
     long long polls = 0;
     if (const char *e = getenv("RAS_BARRIER_POLLS")) polls = atoll(e);
     if (polls != c->bar_polls) {        // the limit stays on the device between launches
-        GridBar b{0u, 0u, polls};
+        GridBar b{};
+        b.polls = polls;
         RAS_CK(cudaMemcpyAsync(c->d_bar, &b, sizeof(GridBar), cudaMemcpyHostToDevice, st));
         c->bar_polls = polls;
     } else {
-        RAS_CK(cudaMemsetAsync(c->d_bar, 0, 2 * sizeof(unsigned), st));
+        RAS_CK(cudaMemsetAsync(c->d_bar, 0, offsetof(GridBar, polls), st));
     }
     return RAS_OK;
 }
@@ -1310,7 +1391,10 @@ static int configure_t(Coarse *c) {
         if (c->rap125_smem <= (size_t)big || c->rap125_ng == 1) break;
     }
     c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
-    c->sol_smem = sizeof(AT) * (size_t)2 * c->T;
+    // the solve prefetches up to two (FP32) or one (FP64) matrix rows per warp
+    c->sol_npf = sizeof(AT) == 4 ? 2 : 1;
+    while (c->sol_npf > 0 && sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T > (size_t)big) --c->sol_npf;
+    c->sol_smem = sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T;
     if (c->rap_smem > (size_t)big || c->rap125_smem > (size_t)big || c->fac_smem > (size_t)big ||
         c->sol_smem > (size_t)big)
         return RAS_EINVAL;
@@ -1531,7 +1615,7 @@ static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cuda
     RAS_TRY(reset_bar(c, st));
     SolArgs<AT> sa{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
                    (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
-                   (AT *)c->ry, c->d_bar, c->d_err};
+                   (AT *)c->ry, c->d_bar, c->d_err, c->sol_npf};
     void *args[] = {&sa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve<AT>, dim3(c->sol_grid),
                                        dim3(256), args, c->sol_smem, st));
