@@ -236,6 +236,54 @@ int newton_step(ras_problem *prob, ras_precond *pc, double *p, const double *p_l
                 const double *p_lm1, double dt, int bdf_order, const ras_newton_opts *opts,
                 ras_newton_stats *stats, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batches of independent reservoirs (the paper treats one reservoir; several
+ * unrelated reservoirs solved together on one GPU are this library's
+ * extension). A batch references n existing problem handles and their
+ * preconditioners -- one-level left-RAS (nlevels 1, ras_type 1, ilu_k 0), all
+ * with the same factor_prec, each problem in the batch once -- and owns one set
+ * of Krylov vectors for all of them (the reservoirs' vectors concatenated,
+ * (2 restart + 1) x sum of N doubles plus five more vectors). Every FGMRES
+ * operation runs for all reservoirs in one launch: the subdomain solves of all
+ * reservoirs' boxes, their 7-point operators, the Arnoldi dot products and
+ * updates; each reservoir keeps its own Krylov scalars, stop test and Newton
+ * line search, evaluated on the host after one synchronisation per Arnoldi step
+ * for the whole batch. A reservoir whose solve has finished does no further
+ * work. Results equal the single-reservoir routines' up to the order of the
+ * floating-point sums (each reduction is still deterministic). The handles must
+ * outlive the batch; a batch must not be used concurrently from several host
+ * threads. All pointer arrays below are HOST arrays of n entries (the vectors
+ * they point to are device vectors of each reservoir's N). */
+typedef struct ras_batch ras_batch;
+
+/* Returns RAS_EINVAL if n < 1, a pointer is NULL, a preconditioner is not of the
+ * kind above or does not belong to its problem, a problem appears twice, or the
+ * total padded length exceeds 2^31 - 1; RAS_ENOMEM if device memory runs out. */
+int ras_batch_create(int n, ras_problem *const *problems, ras_precond *const *preconds,
+                     ras_batch **out);
+void ras_batch_destroy(ras_batch *batch);
+
+/* FGMRES on every reservoir: J[i] x[i] = rhs[i] right-preconditioned by the
+ * reservoir's current factors (ras_factor first), the single-reservoir
+ * gmres_solve's iteration per reservoir. J: host array of n stencils (device
+ * coefficient arrays); rhs, x: host arrays of n device pointers; stats: host
+ * array of n (or NULL). Returns RAS_OK, or RAS_GMRES_MAXIT if some reservoir
+ * stopped at maxit (its stats say which). */
+int ras_batch_gmres(ras_batch *batch, const ras_stencil *J, const double *const *rhs,
+                    double *const *x, const ras_krylov_opts *opts, ras_krylov_stats *stats,
+                    void *stream);
+
+/* One implicit time step of every reservoir: newton_step's iteration per
+ * reservoir (factor, batched FGMRES, cubic backtracking), the reservoirs'
+ * residual evaluations launched together before each synchronisation.
+ * p[i]: device [N_i], in: initial guess, out: p^{l+1}; p_l, p_lm1 (bdf_order 2):
+ * host arrays of device pointers; dt: host array of n step sizes; stats: host
+ * array of n (or NULL). Returns RAS_OK, or the status of the first reservoir (in
+ * batch order) that did not meet its Newton test. */
+int ras_batch_newton_step(ras_batch *batch, double *const *p, const double *const *p_l,
+                          const double *const *p_lm1, const double *dt, int bdf_order,
+                          const ras_newton_opts *opts, ras_newton_stats *stats, void *stream);
+
 /* Human-readable description of a status code (static storage). */
 const char *ras_status_string(int status);
 

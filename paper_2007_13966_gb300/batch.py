@@ -1,12 +1,16 @@
-"""Many independent reservoirs solved concurrently on one GPU.
+"""Many independent reservoirs solved together on one GPU.
 
-Each reservoir has its own problem and preconditioner handles and its own CUDA
-stream; a pool of host threads drives the time loops (the library's calls
-release the interpreter lock while they run, and their host synchronisations
-wait on their own stream only), so the small per-reservoir kernels of
-different instances overlap on the device. The Newton / FGMRES scalar logic
-stays on the host, one Arnoldi step at a time, so the loops are not captured
-into CUDA graphs.
+Every reservoir has its own problem and preconditioner handles. Two drivers:
+
+* fused (default): one library batch handle (ras_batch_*) advances all
+  reservoirs in lock step; every FGMRES operation of all reservoirs (their
+  subdomain solves, operators, Arnoldi dot products and updates) is one kernel
+  launch, and one host synchronisation per Arnoldi step serves the batch.
+* streams: each reservoir on its own CUDA stream, driven by a pool of host
+  threads (the library's calls release the interpreter lock; their host
+  synchronisations wait on their own stream only).
+
+The Newton / FGMRES scalar logic stays on the host, one Arnoldi step at a time.
 """
 from __future__ import annotations
 
@@ -27,6 +31,9 @@ class BatchOpts:
     threads: int = 8
     rtol: float = 1e-6
     lin_rtol: float = 1e-6
+    fused: bool = True            # one batch handle; False: one stream per reservoir
+    nlevels: int = 1              # 2: two-level V-cycle with the exact coarse solve
+    coarsen: tuple = (4, 4, 4)
 
 
 def parts_for(res, box):
@@ -35,13 +42,14 @@ def parts_for(res, box):
 
 
 class _Instance:
-    def __init__(self, res, opts: BatchOpts):
+    def __init__(self, res, opts: BatchOpts, own_stream=True):
         self.res, self.opts = res, opts
-        self.stream = torch.cuda.Stream()
+        self.stream = torch.cuda.Stream() if own_stream else torch.cuda.current_stream()
         with torch.cuda.stream(self.stream):
             self.gp = ras.Problem(res)
             self.pc = ras.Precond(self.gp, parts_for(res, opts.box), opts.overlap,
-                                  factor_prec=opts.factor_prec)
+                                  factor_prec=opts.factor_prec, nlevels=opts.nlevels,
+                                  coarsen=opts.coarsen, coarse_prec=opts.factor_prec)
             N = res.grid.n
             self.p_l = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
             self.p_lm1 = self.p_l.clone()
@@ -69,7 +77,12 @@ class Batch:
 
     def __init__(self, reservoirs, opts: BatchOpts | None = None):
         self.opts = opts or BatchOpts()
-        self.inst = self._map(lambda r: _Instance(r, self.opts), reservoirs)
+        self.solver = None
+        if self.opts.fused:
+            self.inst = [_Instance(r, self.opts, own_stream=False) for r in reservoirs]
+            self.solver = ras.BatchSolver([i.gp for i in self.inst], [i.pc for i in self.inst])
+        else:
+            self.inst = self._map(lambda r: _Instance(r, self.opts), reservoirs)
 
     def _map(self, fn, items):
         if self.opts.threads <= 1:
@@ -78,7 +91,23 @@ class Batch:
             return list(ex.map(fn, items))
 
     def advance(self, nsteps):
-        self._map(lambda i: i.advance(nsteps), self.inst)
+        if self.solver is None:
+            self._map(lambda i: i.advance(nsteps), self.inst)
+            return
+        o = self.opts
+        for _ in range(nsteps):
+            step = self.inst[0].step
+            order = 1 if step == 0 else 2
+            ps = [i.p_l.clone() for i in self.inst]
+            st, outs = self.solver.newton_step(
+                ps, [i.p_l for i in self.inst], [i.p_lm1 for i in self.inst] if order == 2 else None,
+                [i.res.dt for i in self.inst], order, rtol=o.rtol, lin_rtol=o.lin_rtol)
+            if st != 0:
+                raise RuntimeError(f"ras_batch_newton_step status {st}")
+            for i, p, out in zip(self.inst, ps, outs):
+                i.iters.append((out["newton_iters"], out["lin_total"]))
+                i.p_lm1, i.p_l = i.p_l, p
+                i.step += 1
 
     @property
     def cells(self):

@@ -1,0 +1,768 @@
+// Many independent reservoirs advanced together on one GPU: a batched inexact
+// Newton step (Section 2) whose FGMRES iterations run each operation for every
+// reservoir in one launch -- the left-RAS subdomain solves of all reservoirs'
+// boxes (Eq. equ:as-left), their 7-point operators, the Arnoldi dot products and
+// updates -- while the scalar logic of each reservoir (Givens rotations, stop
+// tests, cubic backtracking) stays on the host. One host synchronisation per
+// Arnoldi step serves the whole batch. With two-level V-cycle preconditioners
+// (Eq. equ:v-cycle) the fine-level solves and residuals are batched the same way
+// and each reservoir's exact coarse correction is one cooperative launch of its
+// own.
+//
+// Vectors of the batch are the reservoirs' vectors concatenated (each starting
+// at a multiple of 32 cells). The vector kernels run on chunks of BCH cells of
+// one reservoir each, so every reduction is a fixed per-chunk partial followed
+// by a fixed-order sum over that reservoir's chunks (deterministic). A reservoir
+// whose solve has finished is switched off in a device mask; its chunks and
+// boxes return at once.
+#include "precond.cuh"
+
+#include <algorithm>
+#include <cstring>
+
+namespace ras {
+
+constexpr int BCH = 2048;               // cells per CTA of the batched vector kernels
+constexpr int OST = 2 * MAX_MDOT + 8;   // device results per reservoir
+
+struct BOp {                    // one reservoir's 7-point operator
+    const double *c[7];
+    int nx, ny, nz;
+    unsigned long long mx, my;  // ceil(2^64 / nx), ceil(2^64 / ny) (0 for 1)
+};
+
+struct BChunk {
+    int inst, start, count;
+};
+
+// q / d as a 64-bit multiply-high by ceil(2^64 / d): exact for 0 <= q < 2^32 and
+// 1 <= d < 2^31 (q times the multiplier's excess over 2^64 / d stays below 2^64)
+__device__ __forceinline__ int bdiv(int q, int d, unsigned long long m) {
+    return d == 1 ? q : (int)__umul64hi((unsigned long long)q, m);
+}
+static unsigned long long bmagic(int d) { return d == 1 ? 0ull : (~0ull / (unsigned long long)d) + 1ull; }
+
+// y = A x, or y = b - A x, per reservoir (the arithmetic of the single-reservoir
+// operator)
+template <bool RESID>
+__global__ void __launch_bounds__(256) k_bstencil(const BOp *__restrict__ ops, const BChunk *__restrict__ ch,
+                                                  const long long *__restrict__ off,
+                                                  const unsigned char *__restrict__ active,
+                                                  const double *__restrict__ b, const double *__restrict__ x,
+                                                  double *__restrict__ y) {
+    const BChunk c = ch[blockIdx.x];
+    if (!active[c.inst]) return;
+    const BOp A = ops[c.inst];
+    const int nx = A.nx, ny = A.ny, nz = A.nz, nxy = nx * ny;
+    const long long o = off[c.inst];
+    const double *xi = x + o;
+    double *yi = y + o;
+    for (int q = threadIdx.x; q < c.count; q += blockDim.x) {
+        const int n = c.start + q;
+        const int row = bdiv(n, nx, A.mx), k = bdiv(row, ny, A.my);
+        const int i = n - row * nx, j = row - k * ny;
+        double s = A.c[0][n] * xi[n];
+        if (i > 0) s = fma(A.c[1][n], xi[n - 1], s);
+        if (i < nx - 1) s = fma(A.c[2][n], xi[n + 1], s);
+        if (j > 0) s = fma(A.c[3][n], xi[n - nx], s);
+        if (j < ny - 1) s = fma(A.c[4][n], xi[n + nx], s);
+        if (k > 0) s = fma(A.c[5][n], xi[n - nxy], s);
+        if (k < nz - 1) s = fma(A.c[6][n], xi[n + nxy], s);
+        yi[n] = RESID ? b[o + n] - s : s;
+    }
+}
+
+// block sum of `acc` -> partials[slot * nch + blockIdx.x] (RED_THREADS threads)
+__device__ __forceinline__ void block_partial(double acc, double *sh, double *partials, long long at) {
+    const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    __syncthreads();
+    if (lane == 0) sh[wid] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < RED_THREADS / 32; ++q) s += sh[q];
+        partials[at] = s;
+    }
+}
+
+// partials[v][chunk] = sum over the chunk of V[v] w (v < k); row KM: w . w if self
+template <int KM>
+__global__ void __launch_bounds__(RED_THREADS) k_bmdot(const double *__restrict__ V, long long ldv, int k,
+                                                       int self, const double *__restrict__ w,
+                                                       const BChunk *__restrict__ ch,
+                                                       const long long *__restrict__ off,
+                                                       const unsigned char *__restrict__ active,
+                                                       double *__restrict__ partials, int nch) {
+    const BChunk c = ch[blockIdx.x];
+    if (!active[c.inst]) return;
+    const long long base = off[c.inst] + c.start;
+    double acc[KM + 1];
+#pragma unroll
+    for (int v = 0; v <= KM; ++v) acc[v] = 0.0;
+    for (int q = threadIdx.x; q < c.count; q += blockDim.x) {
+        const double wi = w[base + q];
+#pragma unroll
+        for (int v = 0; v < KM; ++v)
+            if (v < k) acc[v] = fma(V[v * ldv + base + q], wi, acc[v]);
+        if (self) acc[KM] = fma(wi, wi, acc[KM]);
+    }
+    __shared__ double sh[RED_THREADS / 32];
+    for (int v = 0; v < k; ++v) block_partial(acc[v], sh, partials, (long long)v * nch + blockIdx.x);
+    if (self) block_partial(acc[KM], sh, partials, (long long)k * nch + blockIdx.x);
+}
+
+// out[inst][slot0 + v] = sum of the reservoir's chunk partials of row v, in chunk
+// order (one warp per reservoir); the last row's square root if sqrt_last
+__global__ void k_bfinalize(const double *__restrict__ partials, int nch, int nvec,
+                            const int *__restrict__ ch0, const int *__restrict__ chn,
+                            const unsigned char *__restrict__ active, double *__restrict__ out, int slot0,
+                            int sqrt_last, int ninst) {
+    const int inst = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    if (inst >= ninst || !active[inst]) return;
+    const int lane = threadIdx.x & 31, a = ch0[inst], cnt = chn[inst];
+    for (int v = 0; v < nvec; ++v) {
+        double acc = 0.0;
+        for (int q = lane; q < cnt; q += 32) acc += partials[(long long)v * nch + a + q];
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+        if (lane == 0) out[(long long)inst * OST + slot0 + v] = (sqrt_last && v == nvec - 1) ? sqrt(acc) : acc;
+    }
+}
+
+// w -= sum_v h[v] V[v] with the reservoir's coefficients h = out[inst][hslot ..];
+// partial sums of the new w . w if NORM
+template <bool NORM, int KM>
+__global__ void __launch_bounds__(RED_THREADS) k_bupdate(const double *__restrict__ V, long long ldv, int k,
+                                                         const double *__restrict__ out, int hslot,
+                                                         double *__restrict__ w, const BChunk *__restrict__ ch,
+                                                         const long long *__restrict__ off,
+                                                         const unsigned char *__restrict__ active,
+                                                         double *__restrict__ partials) {
+    const BChunk c = ch[blockIdx.x];
+    if (!active[c.inst]) return;
+    const long long base = off[c.inst] + c.start;
+    const double *h = out + (long long)c.inst * OST + hslot;
+    double hv[KM];
+#pragma unroll
+    for (int v = 0; v < KM; ++v) hv[v] = v < k ? h[v] : 0.0;
+    double acc = 0.0;
+    for (int q = threadIdx.x; q < c.count; q += blockDim.x) {
+        double s = w[base + q];
+#pragma unroll
+        for (int v = 0; v < KM; ++v)
+            if (v < k) s = fma(-hv[v], V[v * ldv + base + q], s);
+        w[base + q] = s;
+        if (NORM) acc = fma(s, s, acc);
+    }
+    if (NORM) {
+        __shared__ double sh[RED_THREADS / 32];
+        block_partial(acc, sh, partials, blockIdx.x);
+    }
+}
+
+// y = x / s[inst * stride] per reservoir
+__global__ void __launch_bounds__(256) k_bscale(double *__restrict__ y, const double *__restrict__ x,
+                                                const double *__restrict__ s, int stride,
+                                                const BChunk *__restrict__ ch, const long long *__restrict__ off,
+                                                const unsigned char *__restrict__ active) {
+    const BChunk c = ch[blockIdx.x];
+    if (!active[c.inst]) return;
+    const long long base = off[c.inst] + c.start;
+    const double d = s[(long long)c.inst * stride];
+    for (int q = threadIdx.x; q < c.count; q += blockDim.x) y[base + q] = x[base + q] / d;
+}
+
+// x += sum_{v < kk[inst]} y[inst][v] Z[v] per reservoir
+__global__ void __launch_bounds__(256) k_bcombine(double *__restrict__ x, const double *__restrict__ Z,
+                                                  long long ldz, const double *__restrict__ y,
+                                                  const int *__restrict__ kk, const BChunk *__restrict__ ch,
+                                                  const long long *__restrict__ off,
+                                                  const unsigned char *__restrict__ active) {
+    const BChunk c = ch[blockIdx.x];
+    if (!active[c.inst]) return;
+    const long long base = off[c.inst] + c.start;
+    const int k = kk[c.inst];
+    const double *yc = y + (long long)c.inst * MAX_MDOT;
+    for (int q = threadIdx.x; q < c.count; q += blockDim.x) {
+        double s = x[base + q];
+        for (int v = 0; v < k; ++v) s = fma(yc[v], Z[v * ldz + base + q], s);
+        x[base + q] = s;
+    }
+}
+
+}  // namespace ras
+
+using namespace ras;
+
+struct ras_batch {
+    int n = 0;
+    std::vector<ras_problem *> P;
+    std::vector<ras_precond *> pc;
+    std::vector<long long> off;              // cell offset of each reservoir
+    long long Ntot = 0;
+    int nch = 0, nbox = 0;
+    std::vector<int> ch0, chn;               // per reservoir: first chunk, chunks
+    int prec = 32, block = 0;
+    size_t smem = 0;
+    bool twolevel = false;                   // two-level V-cycle preconditioners
+    std::vector<BOp> ops, opsM;              // host copies: FGMRES operators, V-cycle operators
+    std::vector<unsigned char> act;          // host copy of the mask
+    // device tables
+    BOp *d_ops = nullptr, *d_opsM = nullptr;
+    BChunk *d_ch = nullptr;
+    long long *d_off = nullptr;
+    int *d_ch0 = nullptr, *d_chn = nullptr, *d_kk = nullptr;
+    unsigned char *d_act = nullptr;
+    ApplyParams *d_ap = nullptr;
+    int *d_box_inst = nullptr, *d_box_local = nullptr;
+    double *partials = nullptr, *out = nullptr, *h_out = nullptr, *d_y = nullptr, *d_beta = nullptr;
+    // Krylov and batch vectors
+    int m = 0;
+    double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *b = nullptr, *x = nullptr,
+           *tmp = nullptr, *t = nullptr;
+};
+
+namespace ras {
+
+static void batch_free(ras_batch *B) {
+    if (!B) return;
+    dfree(B->d_ops); dfree(B->d_opsM); dfree(B->t); dfree(B->d_ch); dfree(B->d_off); dfree(B->d_ch0); dfree(B->d_chn); dfree(B->d_kk);
+    dfree(B->d_act); dfree(B->d_ap); dfree(B->d_box_inst); dfree(B->d_box_local);
+    dfree(B->partials); dfree(B->out); dfree(B->d_y); dfree(B->d_beta);
+    if (B->h_out) cudaFreeHost(B->h_out);
+    dfree(B->V); dfree(B->Z); dfree(B->w); dfree(B->r); dfree(B->b); dfree(B->x); dfree(B->tmp);
+    delete B;
+}
+
+static int upload_mask(ras_batch *B, cudaStream_t st) {
+    RAS_CK(cudaMemcpyAsync(B->d_act, B->act.data(), B->n, cudaMemcpyHostToDevice, st));
+    return RAS_OK;
+}
+
+static int ensure_krylov_b(ras_batch *B, int m) {
+    if (B->m >= m) return RAS_OK;
+    dfree(B->V); dfree(B->Z);
+    B->m = 0;
+    RAS_TRY(dalloc(&B->V, (size_t)(m + 1) * B->Ntot));
+    RAS_TRY(dalloc(&B->Z, (size_t)m * B->Ntot));
+    B->m = m;
+    return RAS_OK;
+}
+
+// launches over the batch's chunks
+static int b_mdot(ras_batch *B, const double *V, int k, int self, const double *w, cudaStream_t st) {
+#define RAS_BMDOT(KM) k_bmdot<KM><<<B->nch, RED_THREADS, 0, st>>>(V, B->Ntot, k, self, w, B->d_ch, B->d_off, \
+                                                                   B->d_act, B->partials, B->nch)
+    if (k <= 1) RAS_BMDOT(1);
+    else if (k <= 2) RAS_BMDOT(2);
+    else if (k <= 4) RAS_BMDOT(4);
+    else if (k <= 8) RAS_BMDOT(8);
+    else if (k <= 16) RAS_BMDOT(16);
+    else RAS_BMDOT(32);
+#undef RAS_BMDOT
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+static int b_finalize(ras_batch *B, int nvec, int slot0, int sqrt_last, cudaStream_t st) {
+    const int wpb = 4;
+    k_bfinalize<<<(B->n + wpb - 1) / wpb, 32 * wpb, 0, st>>>(B->partials, B->nch, nvec, B->d_ch0, B->d_chn,
+                                                             B->d_act, B->out, slot0, sqrt_last, B->n);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+template <bool NORM>
+static int b_update(ras_batch *B, int k, int hslot, double *w, cudaStream_t st) {
+#define RAS_BUPD(KM) k_bupdate<NORM, KM><<<B->nch, RED_THREADS, 0, st>>>(B->V, B->Ntot, k, B->out, hslot, w, \
+                                                                         B->d_ch, B->d_off, B->d_act, B->partials)
+    if (k <= 1) RAS_BUPD(1);
+    else if (k <= 2) RAS_BUPD(2);
+    else if (k <= 4) RAS_BUPD(4);
+    else if (k <= 8) RAS_BUPD(8);
+    else if (k <= 16) RAS_BUPD(16);
+    else RAS_BUPD(32);
+#undef RAS_BUPD
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+template <bool RESID>
+static int b_stencil(ras_batch *B, const double *b, const double *x, double *y, cudaStream_t st,
+                     const BOp *ops = nullptr) {
+    k_bstencil<RESID><<<B->nch, 256, 0, st>>>(ops ? ops : B->d_ops, B->d_ch, B->d_off, B->d_act, b, x, y);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+static int b_scale(ras_batch *B, double *y, const double *x, const double *s, int stride, cudaStream_t st) {
+    k_bscale<<<B->nch, 256, 0, st>>>(y, x, s, stride, B->d_ch, B->d_off, B->d_act);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+// z = M^{-1} v for the reservoirs in the mask: left-RAS, or the two-level V-cycle
+//   z = M v;  t = v - A z;  z += P A_c^{-1} R t;  t = v - A z;  z += M t
+// (A: the operator of each reservoir's last factorisation)
+static int b_precond(ras_batch *B, const double *v, double *z, cudaStream_t st) {
+    BatchApply A{B->d_ap, B->d_box_inst, B->d_box_local, B->d_off, B->d_act, v, z, 0};
+    RAS_TRY(ras1_apply_batch(A, B->nbox, B->prec, B->block, B->smem, st));
+    if (!B->twolevel) return RAS_OK;
+    RAS_TRY(b_stencil<true>(B, v, z, B->t, st, B->d_opsM));
+    for (int i = 0; i < B->n; ++i)
+        if (B->act[i]) RAS_TRY(coarse_correct(B->pc[i]->coarse, B->t + B->off[i], z + B->off[i], 1, st));
+    RAS_TRY(b_stencil<true>(B, v, z, B->t, st, B->d_opsM));
+    A.r = B->t;
+    A.accumulate = 1;
+    return ras1_apply_batch(A, B->nbox, B->prec, B->block, B->smem, st);
+}
+
+// the V-cycle operators of the reservoirs factored since the last upload
+static int refresh_opsM(ras_batch *B, cudaStream_t st) {
+    if (!B->twolevel) return RAS_OK;
+    for (int i = 0; i < B->n; ++i)
+        for (int s = 0; s < 7; ++s) B->opsM[i].c[s] = B->pc[i]->A.c[s];
+    RAS_CK(cudaMemcpyAsync(B->d_opsM, B->opsM.data(), B->n * sizeof(BOp), cudaMemcpyHostToDevice, st));
+    return RAS_OK;
+}
+
+// out[inst][0] = ||vec of inst|| for the reservoirs in the mask (synchronises)
+static int b_norms(ras_batch *B, const double *v, std::vector<double> &res, cudaStream_t st) {
+    RAS_TRY(b_mdot(B, nullptr, 0, 1, v, st));
+    RAS_TRY(b_finalize(B, 1, 0, 1, st));
+    RAS_CK(cudaMemcpyAsync(B->h_out, B->out, (size_t)B->n * OST * sizeof(double), cudaMemcpyDeviceToHost, st));
+    RAS_CK(cudaStreamSynchronize(st));
+    for (int i = 0; i < B->n; ++i) res[i] = B->h_out[(size_t)i * OST];
+    return RAS_OK;
+}
+
+// Batched right-preconditioned FGMRES(m) (the steps of the single-reservoir
+// routine, per reservoir) on B->b -> B->x for the reservoirs with want[i];
+// operators in B->ops (uploaded by the caller).
+static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const ras_krylov_opts &o,
+                   ras_krylov_stats *stats, cudaStream_t st) {
+    const int n = B->n, m = o.restart;
+    if (m < 1 || m > MAX_MDOT - 1 || o.maxit < 1) return RAS_EINVAL;
+    RAS_TRY(ensure_krylov_b(B, m));
+    const long long Nt = B->Ntot;
+    auto push = [&](int i, double v) {
+        if (!stats) return;
+        ras_krylov_stats &S = stats[i];
+        if (S.history && S.history_len < S.history_cap) S.history[S.history_len++] = v;
+    };
+    if (stats)
+        for (int i = 0; i < n; ++i)
+            if (want[i]) { stats[i].history_len = 0; stats[i].iters = 0; stats[i].converged = 0; }
+    B->act = want;
+    RAS_TRY(upload_mask(B, st));
+    std::vector<double> bnorm(n, 0.0), beta(n, 0.0), tol(n, 0.0);
+    RAS_TRY(b_norms(B, B->b, bnorm, st));
+    for (int i = 0; i < n; ++i) {
+        if (!want[i]) continue;
+        if (!std::isfinite(bnorm[i])) return RAS_ENAN;
+        tol[i] = std::max(o.rtol * bnorm[i], o.atol);
+        beta[i] = bnorm[i];
+        push(i, beta[i]);
+    }
+    RAS_TRY(vec_set(B->x, 0.0, (int)Nt, st));
+    RAS_TRY(vec_copy(B->r, B->b, (int)Nt, st));
+    std::vector<int> it(n, 0), jend(n, 0);
+    std::vector<unsigned char> conv(n, 0), cyc(n, 0);
+    for (int i = 0; i < n; ++i) conv[i] = want[i] && beta[i] <= tol[i];
+    std::vector<double> H((size_t)n * (m + 1) * m), cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
+    std::vector<double> y((size_t)n * MAX_MDOT, 0.0);
+    std::vector<int> kk(n, 0);
+    std::vector<double> lastg(n, 0.0);
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            cyc[i] = want[i] && !conv[i] && it[i] < o.maxit;
+            any = any || cyc[i];
+        }
+        if (!any) break;
+        // V_0 = r / beta
+        RAS_CK(cudaMemcpyAsync(B->d_beta, beta.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+        B->act = cyc;
+        RAS_TRY(upload_mask(B, st));
+        RAS_TRY(b_scale(B, B->V, B->r, B->d_beta, 1, st));
+        std::fill(H.begin(), H.end(), 0.0);
+        std::fill(g.begin(), g.end(), 0.0);
+        for (int i = 0; i < n; ++i) { g[(size_t)i * (m + 1)] = beta[i]; jend[i] = 0; }
+        std::vector<unsigned char> live = cyc;
+        for (int j = 0; j < m; ++j) {
+            bool anyl = false;
+            for (int i = 0; i < n; ++i) anyl = anyl || live[i];
+            if (!anyl) break;
+            const int k = j + 1;
+            double *Vj = B->V + (size_t)j * Nt, *Zj = B->Z + (size_t)j * Nt;
+            RAS_TRY(b_precond(B, Vj, Zj, st));
+            RAS_TRY(b_stencil<false>(B, nullptr, Zj, B->w, st));
+            RAS_TRY(b_mdot(B, B->V, k, 1, B->w, st));
+            RAS_TRY(b_finalize(B, k + 1, 0, 0, st));
+            RAS_TRY(b_update<false>(B, k, 0, B->w, st));
+            RAS_TRY(b_mdot(B, B->V, k, 0, B->w, st));
+            RAS_TRY(b_finalize(B, k, k + 1, 0, st));
+            RAS_TRY(b_update<true>(B, k, k + 1, B->w, st));
+            RAS_TRY(b_finalize(B, 1, 2 * k + 1, 1, st));
+            RAS_TRY(b_scale(B, B->V + (size_t)(j + 1) * Nt, B->w, B->out + 2 * k + 1, OST, st));
+            RAS_CK(cudaMemcpyAsync(B->h_out, B->out, (size_t)n * OST * sizeof(double), cudaMemcpyDeviceToHost, st));
+            RAS_CK(cudaStreamSynchronize(st));
+            bool changed = false;
+            for (int i = 0; i < n; ++i) {
+                if (!live[i]) continue;
+                const double *hh = B->h_out + (size_t)i * OST;
+                double *Hi = &H[(size_t)i * (m + 1) * m];
+                auto Hc = [&](int a, int c) -> double & { return Hi[(size_t)a * m + c]; };
+                double *csi = &cs[(size_t)i * m], *sni = &sn[(size_t)i * m], *gi = &g[(size_t)i * (m + 1)];
+                for (int a = 0; a < k; ++a) Hc(a, j) = hh[a] + hh[k + 1 + a];
+                const double wnorm0 = std::sqrt(hh[k]);
+                const double hn = hh[2 * k + 1];
+                Hc(j + 1, j) = hn;
+                if (!std::isfinite(hn) || !std::isfinite(wnorm0)) return RAS_ENAN;
+                const bool breakdown = hn <= 1e-14 * wnorm0;
+                for (int a = 0; a < j; ++a) {
+                    const double t = csi[a] * Hc(a, j) + sni[a] * Hc(a + 1, j);
+                    Hc(a + 1, j) = -sni[a] * Hc(a, j) + csi[a] * Hc(a + 1, j);
+                    Hc(a, j) = t;
+                }
+                const double den = std::hypot(Hc(j, j), Hc(j + 1, j));
+                csi[j] = Hc(j, j) / den;
+                sni[j] = Hc(j + 1, j) / den;
+                Hc(j, j) = den;
+                Hc(j + 1, j) = 0.0;
+                gi[j + 1] = -sni[j] * gi[j];
+                gi[j] = csi[j] * gi[j];
+                ++it[i];
+                const double res = std::fabs(gi[j + 1]);
+                push(i, res);
+                jend[i] = j + 1;
+                if (res <= tol[i] || breakdown || it[i] >= o.maxit) { live[i] = 0; changed = true; }
+            }
+            if (changed) {
+                B->act = live;
+                RAS_TRY(upload_mask(B, st));
+            }
+        }
+        // x += Z y per reservoir (its own Krylov dimension)
+        for (int i = 0; i < n; ++i) {
+            kk[i] = 0;
+            if (!cyc[i]) continue;
+            const int kq = jend[i];
+            const double *Hi = &H[(size_t)i * (m + 1) * m];
+            const double *gi = &g[(size_t)i * (m + 1)];
+            double *yi = &y[(size_t)i * MAX_MDOT];
+            for (int a = kq - 1; a >= 0; --a) {
+                double s = gi[a];
+                for (int l = a + 1; l < kq; ++l) s -= Hi[(size_t)a * m + l] * yi[l];
+                yi[a] = s / Hi[(size_t)a * m + a];
+            }
+            kk[i] = kq;
+            lastg[i] = gi[kq];
+        }
+        RAS_CK(cudaMemcpyAsync(B->d_y, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
+        RAS_CK(cudaMemcpyAsync(B->d_kk, kk.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        B->act = cyc;
+        RAS_TRY(upload_mask(B, st));
+        k_bcombine<<<B->nch, 256, 0, st>>>(B->x, B->Z, Nt, B->d_y, B->d_kk, B->d_ch, B->d_off, B->d_act);
+        RAS_LAUNCHED();
+        RAS_TRY(b_stencil<true>(B, B->b, B->x, B->r, st));
+        std::vector<double> nb(n, 0.0);
+        RAS_TRY(b_norms(B, B->r, nb, st));
+        for (int i = 0; i < n; ++i) {
+            if (!cyc[i]) continue;
+            beta[i] = nb[i];
+            if (!std::isfinite(beta[i])) return RAS_ENAN;
+            conv[i] = beta[i] <= tol[i] || std::fabs(lastg[i]) <= tol[i];
+            if (!conv[i] && it[i] < o.maxit) push(i, beta[i]);
+        }
+    }
+    for (int i = 0; i < n; ++i)
+        if (want[i]) RAS_TRY(precond_check(B->pc[i], st));
+    int status = RAS_OK;
+    for (int i = 0; i < n; ++i) {
+        if (!want[i]) continue;
+        if (stats) {
+            stats[i].iters = it[i];
+            stats[i].converged = conv[i] ? 1 : 0;
+            stats[i].r0 = bnorm[i];
+            stats[i].rfinal = beta[i];
+        }
+        if (!conv[i]) status = RAS_GMRES_MAXIT;
+    }
+    return status;
+}
+
+static void set_ops(ras_batch *B, int i, double *const *J) {
+    for (int s = 0; s < 7; ++s) B->ops[i].c[s] = J[s];
+}
+
+static int upload_ops(ras_batch *B, cudaStream_t st) {
+    RAS_CK(cudaMemcpyAsync(B->d_ops, B->ops.data(), B->ops.size() * sizeof(BOp), cudaMemcpyHostToDevice, st));
+    return RAS_OK;
+}
+
+// norms of per-reservoir vectors vecs[i] (gathered into B->tmp) for want[i]
+static int b_norms_of(ras_batch *B, const std::vector<const double *> &vecs, const std::vector<unsigned char> &want,
+                      std::vector<double> &res, cudaStream_t st) {
+    for (int i = 0; i < B->n; ++i)
+        if (want[i]) RAS_TRY(vec_copy(B->tmp + B->off[i], vecs[i], B->P[i]->N, st));
+    B->act = want;
+    RAS_TRY(upload_mask(B, st));
+    return b_norms(B, B->tmp, res, st);
+}
+
+// One implicit step of every reservoir (the single-reservoir Newton driver's
+// steps, per reservoir, with the linear solves batched).
+static int bnewton(ras_batch *B, double *const *p, const double *const *pl, const double *const *plm1,
+                   const double *dt, int order, const ras_newton_opts &o, ras_newton_stats *stats,
+                   cudaStream_t st) {
+    const int n = B->n;
+    std::vector<int> cur(n, 0), k(n, 0), nres(n, 0), lin_total(n, 0), status(n, RAS_OK);
+    for (int i = 0; i < n; ++i) {
+        ras_problem *P = B->P[i];
+        RAS_TRY(ensure_newton(P));
+        RAS_TRY(vec_copy(P->nX[0], p[i], P->N, st));
+        RAS_TRY(residual_eval_impl(P, P->nX[0], pl[i], order == 2 ? plm1[i] : nullptr, dt[i], order, P->nF[0],
+                                   P->nJ[0], st));
+        ++nres[i];
+    }
+    std::vector<unsigned char> all(n, 1), live(n, 0);
+    std::vector<const double *> vecs(n);
+    std::vector<double> fnorm(n, 0.0), f0(n, 0.0), tol(n, 0.0), ft(n, 0.0);
+    for (int i = 0; i < n; ++i) vecs[i] = B->P[i]->nF[0];
+    RAS_TRY(b_norms_of(B, vecs, all, fnorm, st));
+    for (int i = 0; i < n; ++i) {
+        if (!std::isfinite(fnorm[i])) return RAS_ENAN;
+        f0[i] = fnorm[i];
+        tol[i] = std::max(o.rtol * f0[i], o.atol);
+        live[i] = fnorm[i] > tol[i];
+        if (stats) {
+            ras_newton_stats &S = stats[i];
+            S.fhistory_len = 0; S.iters = 0; S.lin_iters = 0;
+            if (S.fhistory && S.fhistory_cap > 0) S.fhistory[S.fhistory_len++] = f0[i];
+        }
+    }
+    std::vector<ras_krylov_stats> ks(n);
+    for (;;) {
+        bool any = false;
+        for (int i = 0; i < n; ++i) {
+            if (live[i] && k[i] >= o.maxit) { status[i] = RAS_NEWTON_MAXIT; live[i] = 0; }
+            any = any || live[i];
+        }
+        if (!any) break;
+        for (int i = 0; i < n; ++i) {
+            if (!live[i]) continue;
+            ras_problem *P = B->P[i];
+            ras_stencil Js;
+            for (int s = 0; s < 7; ++s) Js.c[s] = P->nJ[cur[i]][s];
+            RAS_TRY(precond_factor(B->pc[i], &Js, st));
+            RAS_TRY(vec_axpby(B->b + B->off[i], -1.0, P->nF[cur[i]], 0.0, P->N, st));
+            set_ops(B, i, P->nJ[cur[i]]);
+        }
+        RAS_TRY(upload_ops(B, st));
+        RAS_TRY(refresh_opsM(B, st));
+        std::memset(ks.data(), 0, ks.size() * sizeof(ras_krylov_stats));
+        const int ls = bfgmres(B, live, o.lin, ks.data(), st);
+        if (ls < 0) return ls;
+        for (int i = 0; i < n; ++i) {
+            if (!live[i]) continue;
+            lin_total[i] += ks[i].iters;
+            if (stats && stats[i].lin_history && k[i] < stats[i].lin_history_cap) stats[i].lin_history[k[i]] = ks[i].iters;
+        }
+        // slope_i = F_i^T J_i s_i = -(b_i . J_i s_i)
+        B->act = live;
+        RAS_TRY(upload_mask(B, st));
+        RAS_TRY(b_stencil<false>(B, nullptr, B->x, B->tmp, st));
+        RAS_TRY(b_mdot(B, B->b, 1, 0, B->tmp, st));
+        RAS_TRY(b_finalize(B, 1, 0, 0, st));
+        RAS_CK(cudaMemcpyAsync(B->h_out, B->out, (size_t)n * OST * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RAS_CK(cudaStreamSynchronize(st));
+        std::vector<double> slope(n, 0.0), phi0(n, 0.0), lam(n, 1.0), lam_prev(n, 0.0), phi_prev(n, 0.0);
+        std::vector<unsigned char> first(n, 1), search = live;
+        for (int i = 0; i < n; ++i) {
+            if (!live[i]) continue;
+            slope[i] = -B->h_out[(size_t)i * OST];
+            if (!(slope[i] < 0.0)) slope[i] = -fnorm[i] * fnorm[i];
+            phi0[i] = 0.5 * fnorm[i] * fnorm[i];
+        }
+        // line search, all searching reservoirs' trials evaluated together
+        for (;;) {
+            bool anys = false;
+            for (int i = 0; i < n; ++i) anys = anys || search[i];
+            if (!anys) break;
+            for (int i = 0; i < n; ++i) {
+                if (!search[i]) continue;
+                ras_problem *P = B->P[i];
+                const int nxt = 1 - cur[i];
+                RAS_TRY(vec_copy(P->nX[nxt], P->nX[cur[i]], P->N, st));
+                RAS_TRY(vec_axpby(P->nX[nxt], lam[i], B->x + B->off[i], 1.0, P->N, st));
+                RAS_TRY(residual_eval_impl(P, P->nX[nxt], pl[i], order == 2 ? plm1[i] : nullptr, dt[i], order,
+                                           P->nF[nxt], P->nJ[nxt], st));
+                ++nres[i];
+                vecs[i] = P->nF[nxt];
+            }
+            RAS_TRY(b_norms_of(B, vecs, search, ft, st));
+            for (int i = 0; i < n; ++i) {
+                if (!search[i]) continue;
+                if (std::isfinite(ft[i]) && ft[i] <= (1.0 - o.ls_alpha * lam[i]) * fnorm[i]) {
+                    search[i] = 0;
+                    if (stats && stats[i].lambdas && k[i] < stats[i].lin_history_cap) stats[i].lambdas[k[i]] = lam[i];
+                    cur[i] = 1 - cur[i];
+                    fnorm[i] = ft[i];
+                    ++k[i];
+                    if (stats && stats[i].fhistory && stats[i].fhistory_len < stats[i].fhistory_cap)
+                        stats[i].fhistory[stats[i].fhistory_len++] = fnorm[i];
+                    if (fnorm[i] <= tol[i]) live[i] = 0;
+                    continue;
+                }
+                const double phit = std::isfinite(ft[i]) ? 0.5 * ft[i] * ft[i] : 1e300;
+                const double nl = backtrack(lam[i], lam_prev[i], phi0[i], slope[i], phit, phi_prev[i], first[i] != 0);
+                first[i] = 0;
+                lam_prev[i] = lam[i];
+                phi_prev[i] = phit;
+                lam[i] = nl;
+                if (lam[i] < o.ls_min_lambda) { status[i] = RAS_LINESEARCH_FAIL; search[i] = 0; live[i] = 0; }
+            }
+        }
+    }
+    int ret = RAS_OK;
+    for (int i = 0; i < n; ++i) {
+        ras_problem *P = B->P[i];
+        RAS_TRY(vec_copy(p[i], P->nX[cur[i]], P->N, st));
+        if (stats) {
+            stats[i].iters = k[i];
+            stats[i].lin_iters = lin_total[i];
+            stats[i].residual_evals = nres[i];
+            stats[i].f0 = f0[i];
+            stats[i].ffinal = fnorm[i];
+        }
+        if (ret == RAS_OK && status[i] != RAS_OK) ret = status[i];
+    }
+    RAS_CK(cudaStreamSynchronize(st));
+    return ret;
+}
+
+static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pcs, ras_batch **out) {
+    ras_batch *B = new ras_batch();
+    auto fail = [&](int s) { batch_free(B); return s; };
+    B->n = n;
+    B->P.assign(probs, probs + n);
+    B->pc.assign(pcs, pcs + n);
+    std::vector<BChunk> ch;
+    std::vector<ApplyParams> ap(n);
+    std::vector<int> box_inst, box_local;
+    long long off = 0;
+    for (int i = 0; i < n; ++i) {
+        ras_problem *P = probs[i];
+        ras_precond *pc = pcs[i];
+        if (!P || !pc || pc->prob != P) return fail(RAS_EINVAL);
+        for (int q = 0; q < i; ++q)
+            if (probs[q] == P) return fail(RAS_EINVAL);   // every reservoir its own handle
+        // left-RAS with ILU(0) subdomain solves, one level or the two-level V-cycle with
+        // the exact coarse solve; one factor precision and one kind for the batch
+        const bool two = pc->coarse != nullptr;
+        if (pc->icoarse || pc->xfer || pc->use125 || pc->fine.kind != 1) return fail(RAS_EINVAL);
+        if (two && pc->opts.mlevel_type != 0) return fail(RAS_EINVAL);
+        if (i == 0) { B->prec = pc->fine.prec; B->twolevel = two; }
+        else if (pc->fine.prec != B->prec || two != B->twolevel) return fail(RAS_EINVAL);
+        B->off.push_back(off);
+        B->ch0.push_back((int)ch.size());
+        for (int s = 0; s < P->N; s += BCH) ch.push_back(BChunk{i, s, std::min(BCH, P->N - s)});
+        B->chn.push_back((int)ch.size() - B->ch0.back());
+        off += ((long long)P->N + 31) / 32 * 32;
+        BOp op{};
+        op.nx = P->nx; op.ny = P->ny; op.nz = P->nz;
+        op.mx = bmagic(P->nx); op.my = bmagic(P->ny);
+        B->ops.push_back(op);
+        ras1_apply_params(pc->fine, ap[i]);
+        for (int q = 0; q < pc->fine.nsub; ++q) { box_inst.push_back(i); box_local.push_back(q); }
+        B->block = std::max(B->block, pc->fine.block);
+        B->smem = std::max(B->smem, pc->fine.smem_apply);
+    }
+    if (off > 0x7fffffffLL) return fail(RAS_EINVAL);   // the flat vector kernels take int counts
+    B->Ntot = off;
+    B->nch = (int)ch.size();
+    B->nbox = (int)box_inst.size();
+    B->act.assign(n, 1);
+    const size_t Nt = (size_t)B->Ntot;
+    int rc = 0;
+    B->opsM = B->ops;
+    if ((rc = dalloc(&B->d_ops, n)) || (rc = dalloc(&B->d_opsM, n)) || (rc = dalloc(&B->t, Nt)) ||
+        (rc = dalloc(&B->d_ch, ch.size())) || (rc = dalloc(&B->d_off, n)) ||
+        (rc = dalloc(&B->d_ch0, n)) || (rc = dalloc(&B->d_chn, n)) || (rc = dalloc(&B->d_kk, n)) ||
+        (rc = dalloc(&B->d_act, n)) || (rc = dalloc(&B->d_ap, n)) || (rc = dalloc(&B->d_box_inst, box_inst.size())) ||
+        (rc = dalloc(&B->d_box_local, box_local.size())) ||
+        (rc = dalloc(&B->partials, (size_t)(MAX_MDOT + 1) * B->nch)) || (rc = dalloc(&B->out, (size_t)n * OST)) ||
+        (rc = dalloc(&B->d_y, (size_t)n * MAX_MDOT)) || (rc = dalloc(&B->d_beta, n)) || (rc = dalloc(&B->w, Nt)) ||
+        (rc = dalloc(&B->r, Nt)) || (rc = dalloc(&B->b, Nt)) || (rc = dalloc(&B->x, Nt)) || (rc = dalloc(&B->tmp, Nt)))
+        return fail(rc);
+    if (cudaMallocHost((void **)&B->h_out, (size_t)n * OST * sizeof(double)) != cudaSuccess) {
+        B->h_out = nullptr;
+        return fail(RAS_ENOMEM);
+    }
+    auto up = [&](void *d, const void *h, size_t bytes) {
+        return cudaMemcpy(d, h, bytes, cudaMemcpyHostToDevice) == cudaSuccess;
+    };
+    if (!up(B->d_ops, B->ops.data(), n * sizeof(BOp)) || !up(B->d_ch, ch.data(), ch.size() * sizeof(BChunk)) ||
+        !up(B->d_off, B->off.data(), n * sizeof(long long)) || !up(B->d_ch0, B->ch0.data(), n * sizeof(int)) ||
+        !up(B->d_chn, B->chn.data(), n * sizeof(int)) || !up(B->d_act, B->act.data(), n) ||
+        !up(B->d_ap, ap.data(), n * sizeof(ApplyParams)) ||
+        !up(B->d_box_inst, box_inst.data(), box_inst.size() * sizeof(int)) ||
+        !up(B->d_box_local, box_local.data(), box_local.size() * sizeof(int)))
+        return fail(RAS_ECUDA);
+    // the padding between reservoirs stays zero in every vector
+    if (cudaMemset(B->w, 0, Nt * sizeof(double)) != cudaSuccess || cudaMemset(B->r, 0, Nt * sizeof(double)) ||
+        cudaMemset(B->b, 0, Nt * sizeof(double)) || cudaMemset(B->x, 0, Nt * sizeof(double)) ||
+        cudaMemset(B->tmp, 0, Nt * sizeof(double)) || cudaMemset(B->t, 0, Nt * sizeof(double)))
+        return fail(RAS_ECUDA);
+    *out = B;
+    return RAS_OK;
+}
+
+}  // namespace ras
+
+extern "C" int ras_batch_create(int n, ras_problem *const *problems, ras_precond *const *preconds,
+                                ras_batch **out) {
+    if (!out) return RAS_EINVAL;
+    *out = nullptr;
+    if (n < 1 || !problems || !preconds) return RAS_EINVAL;
+    return batch_create(n, problems, preconds, out);
+}
+
+extern "C" void ras_batch_destroy(ras_batch *b) { batch_free(b); }
+
+extern "C" int ras_batch_gmres(ras_batch *b, const ras_stencil *J, const double *const *rhs, double *const *x,
+                               const ras_krylov_opts *opts, ras_krylov_stats *stats, void *stream) {
+    if (!b || !J || !rhs || !x || !opts) return RAS_EINVAL;
+    const cudaStream_t st = S(stream);
+    for (int i = 0; i < b->n; ++i) {
+        if (!rhs[i] || !x[i]) return RAS_EINVAL;
+        for (int s = 0; s < 7; ++s)
+            if (!J[i].c[s]) return RAS_EINVAL;
+        set_ops(b, i, J[i].c);
+        RAS_TRY(vec_copy(b->b + b->off[i], rhs[i], b->P[i]->N, st));
+    }
+    RAS_TRY(upload_ops(b, st));
+    RAS_TRY(refresh_opsM(b, st));
+    std::vector<unsigned char> all(b->n, 1);
+    const int status = bfgmres(b, all, *opts, stats, st);
+    if (status < 0) return status;
+    for (int i = 0; i < b->n; ++i) RAS_TRY(vec_copy(x[i], b->x + b->off[i], b->P[i]->N, st));
+    RAS_CK(cudaStreamSynchronize(st));
+    return status;
+}
+
+extern "C" int ras_batch_newton_step(ras_batch *b, double *const *p, const double *const *p_l,
+                                     const double *const *p_lm1, const double *dt, int bdf_order,
+                                     const ras_newton_opts *opts, ras_newton_stats *stats, void *stream) {
+    if (!b || !p || !p_l || !dt || !opts) return RAS_EINVAL;
+    if (bdf_order != 1 && bdf_order != 2) return RAS_EINVAL;
+    if (bdf_order == 2 && !p_lm1) return RAS_EINVAL;
+    for (int i = 0; i < b->n; ++i) {
+        if (!p[i] || !p_l[i] || !(dt[i] > 0)) return RAS_EINVAL;
+        if (bdf_order == 2 && !p_lm1[i]) return RAS_EINVAL;
+    }
+    return bnewton(b, p, p_l, p_lm1, dt, bdf_order, *opts, stats, S(stream));
+}

@@ -367,7 +367,7 @@ int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const 
 // Newton
 // ---------------------------------------------------------------------------
 
-static int ensure_newton(ras_problem *P) {
+int ensure_newton(ras_problem *P) {
     if (P->nw_ready) return RAS_OK;
     for (int b = 0; b < 2; ++b) {
         RAS_TRY(dalloc(&P->nX[b], P->N));
@@ -382,8 +382,8 @@ static int ensure_newton(ras_problem *P) {
 }
 
 // next trial step length of the cubic backtracking (Dennis-Schnabel)
-static double backtrack(double lam, double lam_prev, double phi0, double slope, double phi_lam,
-                        double phi_prev, bool first) {
+double backtrack(double lam, double lam_prev, double phi0, double slope, double phi_lam,
+                 double phi_prev, bool first) {
     double nl;
     if (first) {
         nl = -slope / (2.0 * (phi_lam - phi0 - slope));

@@ -76,4 +76,10 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st);
 int precond_apply(ras_precond *pc, const double *r, double *z, cudaStream_t st);
 // reports (and clears) an error recorded by the asynchronous coarse solves
 int precond_check(ras_precond *pc, cudaStream_t st);
+// Newton helpers shared by the single and the batched drivers
+int ensure_newton(ras_problem *P);
+double backtrack(double lam, double lam_prev, double phi0, double slope, double phi_lam,
+                 double phi_prev, bool first);
+int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const double *plm1,
+                       double dt, int order, double *F, double *const *J, cudaStream_t st);
 }  // namespace ras

@@ -107,23 +107,12 @@ __device__ __forceinline__ int fast_div(int q, int d, unsigned m) {
 }
 
 
-struct ApplyParams {
-    const SubInfo *subs;
-    const ShapeInfo *shapes;
-    const int *lvl, *chunk;
-    const int *cidx;          // per shape, level order: local natural index of each cell
-    const unsigned char *fwd, *bwd;
-    const double *r;
-    double *z;
-    int nx, ny, nz;
-    int accumulate;
-    int ycap, gcap, lcap, nbuf, chunk_cells;
-    int kind;        // 1 left-RAS; 0 AS, 2 right-RAS (box solutions to zbuf)
-    double *zbuf;
-};
 
+// One subdomain solve (one CTA): box `box` of the handle described by P, input r,
+// output z (whole-grid vectors of that handle).
 template <int PREC, int NBUF>
-__global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
+__device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, const double *r, double *z,
+                                              int accumulate) {
     using R = typename RecT<PREC>::T;
     using Acc = typename RecT<PREC>::Acc;
     constexpr int RB = (int)sizeof(R);
@@ -138,7 +127,7 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
     unsigned char *ring_rec = ring;
     unsigned char *ring_cell = ring + (size_t)NBUF * rcap;
 
-    const SubInfo si = P.subs[blockIdx.x];
+    const SubInfo si = P.subs[box];
     const ShapeInfo sh = P.shapes[si.shape];
     const int *chunk_lev = P.chunk + sh.chunk_off;
     for (int t = threadIdx.x; t <= sh.nlev; t += blockDim.x) lvl_s[t] = P.lvl[sh.lvl_off + t];
@@ -174,7 +163,7 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
     const int bx = sh.bx, by = sh.by, bxy = sh.bx * sh.by;
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
-    const double *rg = P.r + g0;
+    const double *rg = r + g0;
     const unsigned mbx = magic_div(bx), mby = magic_div(by);
     for (int q0 = threadIdx.x; q0 < sh.ncell; q0 += GB * blockDim.x) {
         double v[GB];
@@ -306,7 +295,7 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
     const int owx = si.ox1 - si.ox0, owy = si.oy1 - si.oy0;
     const int nown = owx * owy * (si.oz1 - si.oz0);
     const unsigned mox = magic_div(owx), moy = magic_div(owy);
-    double *zg = P.z + g0;
+    double *zg = z + g0;
     for (int q0 = threadIdx.x; q0 < nown; q0 += GW * blockDim.x) {
         int yq[GW], go[GW];
         double prev[GW];
@@ -320,13 +309,28 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
                 const int i = si.ox0 + q - row * owx, j = si.oy0 + row - k * owy, kk = si.oz0 + k;
                 yq[m] = i + bx * j + bxy * kk;
                 go[m] = i + nx * j + nxy * kk;
-                if (P.accumulate) prev[m] = zg[go[m]];
+                if (accumulate) prev[m] = zg[go[m]];
             }
         }
 #pragma unroll
         for (int m = 0; m < GW; ++m)
             if (yq[m] >= 0) zg[go[m]] = prev[m] + (double)Y[yq[m]];
     }
+}
+
+template <int PREC, int NBUF>
+__global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
+    ras_apply_box<PREC, NBUF>(P, blockIdx.x, P.r, P.z, P.accumulate);
+}
+
+// Left-RAS of many handles in one launch: CTA b solves box box_local[b] of handle
+// box_inst[b] (CTAs of inactive handles return at once); r and z are the handles'
+// vectors concatenated at off[handle].
+template <int PREC, int NBUF>
+__global__ void __launch_bounds__(512, 2) k_ras_apply_batch(BatchApply B) {
+    const int h = B.box_inst[blockIdx.x];
+    if (!B.active[h]) return;
+    ras_apply_box<PREC, NBUF>(B.inst[h], B.box_local[blockIdx.x], B.r + B.off[h], B.z + B.off[h], B.accumulate);
 }
 
 // z (+)= sum over the overlapped boxes covering each cell of their solution
@@ -436,6 +440,8 @@ constexpr int SMEM_OPTIN = 227 * 1024;
 template <int PREC, int NBUF>
 static int set_apply_attr(size_t) {
     RAS_CK(cudaFuncSetAttribute(k_ras_apply<PREC, NBUF>,
+                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
+    RAS_CK(cudaFuncSetAttribute(k_ras_apply_batch<PREC, NBUF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
     return RAS_OK;
 }
@@ -684,6 +690,25 @@ int ras1_check(Ras1 &R, cudaStream_t st) {
         RAS_CK(cudaMemsetAsync(R.d_err, 0, sizeof(int), st));
         return RAS_EZEROPIVOT;
     }
+    return RAS_OK;
+}
+
+void ras1_apply_params(const Ras1 &R, ApplyParams &P) {
+    P = ApplyParams{};
+    P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.chunk = R.d_chunk;
+    P.cidx = R.d_cidx;
+    P.fwd = (const unsigned char *)R.d_fwd; P.bwd = (const unsigned char *)R.d_bwd;
+    P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.accumulate = 0;
+    P.ycap = R.ycap; P.gcap = R.gcap; P.lcap = R.lcap; P.nbuf = R.nbuf; P.chunk_cells = R.chunk_cells;
+    P.kind = R.kind; P.zbuf = R.zbuf;
+}
+
+int ras1_apply_batch(const BatchApply &B, int nblocks, int prec, int block, size_t smem, cudaStream_t st) {
+    if (nblocks <= 0) return RAS_OK;
+    if (prec == 64) k_ras_apply_batch<64, 3><<<nblocks, block, smem, st>>>(B);
+    else if (prec == 32) k_ras_apply_batch<32, 3><<<nblocks, block, smem, st>>>(B);
+    else k_ras_apply_batch<16, 3><<<nblocks, block, smem, st>>>(B);
+    RAS_LAUNCHED();
     return RAS_OK;
 }
 

@@ -73,6 +73,34 @@ int ras1_check(Ras1 &R, cudaStream_t st);
 // sum_i (R_i^delta)^T A_i^{-1} R_i^delta (AS, kind 0) or
 // sum_i (R_i^delta)^T A_i^{-1} R_i^0 (right-RAS, kind 2)
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st);
+
+// parameters of one handle's apply kernel
+struct ApplyParams {
+    const SubInfo *subs;
+    const ShapeInfo *shapes;
+    const int *lvl, *chunk;
+    const int *cidx;          // per shape, level order: local natural index of each cell
+    const unsigned char *fwd, *bwd;
+    const double *r;
+    double *z;
+    int nx, ny, nz;
+    int accumulate;
+    int ycap, gcap, lcap, nbuf, chunk_cells;
+    int kind;        // 1 left-RAS; 0 AS, 2 right-RAS (box solutions to zbuf)
+    double *zbuf;
+};
+// Left-RAS (kind 1) of several handles in one launch (see k_ras_apply_batch)
+struct BatchApply {
+    const ApplyParams *inst;          // [handles] device copies of the handles' parameters
+    const int *box_inst, *box_local;  // [CTAs] handle and box of every CTA
+    const long long *off;             // [handles] offset of the handle's cells in r and z
+    const unsigned char *active;      // [handles] 0: skip
+    const double *r;
+    double *z;
+    int accumulate;                   // z += (instead of =) the correction
+};
+void ras1_apply_params(const Ras1 &R, ApplyParams &P);
+int ras1_apply_batch(const BatchApply &B, int nblocks, int prec, int block, size_t smem, cudaStream_t st);
 double ras1_bytes(const Ras1 &R);
 
 }  // namespace ras

@@ -23,7 +23,8 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
             "ras_setup", "ras_precond_destroy", "ras_factor", "ras_apply", "gmres_solve",
             "newton_step", "ras_status_string", "ras_last_error", "ras_kernel_launches",
             "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc",
-            "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk"]
+            "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk", "ras_batch_create",
+            "ras_batch_destroy", "ras_batch_gmres", "ras_batch_newton_step"]
 
 
 class Grid(C.Structure):
@@ -113,6 +114,10 @@ def lib():
             "ras_stencil_transpose": (i, [vp, C.POINTER(Stencil), C.POINTER(Stencil), vp]),
             "ras_adjoint_rhs": (i, [vp, vp, vp, vp, d, vp, vp, d, vp, vp]),
             "ras_grad_logk": (i, [vp, vp, vp, vp, vp]),
+            "ras_batch_create": (i, [i, vp, vp, C.POINTER(vp)]),
+            "ras_batch_destroy": (None, [vp]),
+            "ras_batch_gmres": (i, [vp, vp, vp, vp, C.POINTER(KrylovOpts), vp, vp]),
+            "ras_batch_newton_step": (i, [vp, vp, vp, vp, vp, i, C.POINTER(NewtonOpts), vp, vp]),
         }
         for name, (res, args) in sig.items():
             f = getattr(L, name)
@@ -304,3 +309,63 @@ class Precond:
 
     def apply_bytes(self) -> float:
         return float(lib().ras_apply_bytes(self.h))
+
+
+class BatchSolver:
+    """ras_batch handle: independent reservoirs whose FGMRES operations run in one
+    launch each (one-level left-RAS preconditioners of one factor precision)."""
+
+    def __init__(self, problems, preconds):
+        n = len(problems)
+        hp = (C.c_void_p * n)(*[q.h.value for q in problems])
+        hc = (C.c_void_p * n)(*[q.h.value for q in preconds])
+        h = C.c_void_p()
+        check(lib().ras_batch_create(n, hp, hc, C.byref(h)), "ras_batch_create")
+        self.h = h
+        self.n = n
+        self.problems, self.preconds = list(problems), list(preconds)   # must outlive the batch
+
+    def __del__(self):
+        if getattr(self, "h", None) and _lib is not None:
+            _lib.ras_batch_destroy(self.h)
+            self.h = None
+
+    @staticmethod
+    def _ptrs(ts):
+        return (C.c_void_p * len(ts))(*[_ptr(t) if t is not None else None for t in ts])
+
+    def gmres(self, Js, bs, xs, restart=30, maxit=1000, rtol=1e-6, atol=0.0, history_cap=4096):
+        n = self.n
+        J = (Stencil * n)(*[stencil_struct(j) for j in Js])
+        ko = KrylovOpts(restart, maxit, rtol, atol)
+        hists = [(C.c_double * history_cap)() for _ in range(n)]
+        ks = (KrylovStats * n)(*[KrylovStats(0, 0, 0.0, 0.0, h, history_cap, 0) for h in hists])
+        st = lib().ras_batch_gmres(self.h, J, self._ptrs(bs), self._ptrs(xs), C.byref(ko), ks, _stream())
+        check(st, "ras_batch_gmres", ok=(RAS_OK, RAS_GMRES_MAXIT))
+        return [{"iters": k.iters, "converged": bool(k.converged), "r0": k.r0, "rfinal": k.rfinal,
+                 "history": list(h[:k.history_len])} for k, h in zip(ks, hists)]
+
+    def newton_step(self, ps, p_ls, p_lm1s, dts, order, rtol=1e-6, atol=1e-10, maxit=50,
+                    lin_rtol=1e-6, lin_atol=1e-8, restart=30, lin_maxit=2000, alpha=1e-4,
+                    lam_min=1e-8):
+        n = self.n
+        no = NewtonOpts(maxit, rtol, atol, alpha, lam_min, KrylovOpts(restart, lin_maxit, lin_rtol, lin_atol))
+        cap = 256
+        fh = [(C.c_double * cap)() for _ in range(n)]
+        lh = [(C.c_int * cap)() for _ in range(n)]
+        lams = [(C.c_double * cap)() for _ in range(n)]
+        ns = (NewtonStats * n)(*[NewtonStats(0, 0, 0, 0.0, 0.0, fh[i], cap, 0, lh[i], cap, lams[i])
+                                  for i in range(n)])
+        dt = (C.c_double * n)(*[float(v) for v in dts])
+        st = lib().ras_batch_newton_step(self.h, self._ptrs(ps), self._ptrs(p_ls),
+                                         self._ptrs(p_lm1s) if p_lm1s is not None else None, dt,
+                                         int(order), C.byref(no), ns, _stream())
+        check(st, "ras_batch_newton_step", ok=(RAS_OK, RAS_NEWTON_MAXIT, RAS_LINESEARCH_FAIL))
+        out = []
+        for i in range(n):
+            k = ns[i].iters
+            out.append({"newton_iters": k, "lin_iters": list(lh[i][:k]),
+                        "fnorm_history": list(fh[i][:ns[i].fhistory_len]), "lambdas": list(lams[i][:k]),
+                        "lin_total": ns[i].lin_iters, "residual_evals": ns[i].residual_evals,
+                        "f0": ns[i].f0, "ffinal": ns[i].ffinal})
+        return st, out

@@ -28,8 +28,8 @@ def make(n, i):
 def test_concurrent_equals_sequential(ras):
     from paper_2007_13966_gb300 import batch
     res = batch.random_batch(6, 12, 24, 7, make)
-    seq = batch.solve_batch(res, 2, batch.BatchOpts(box=8, threads=1))
-    con = batch.solve_batch(res, 2, batch.BatchOpts(box=8, threads=4))
+    seq = batch.solve_batch(res, 2, batch.BatchOpts(box=8, threads=1, fused=False))
+    con = batch.solve_batch(res, 2, batch.BatchOpts(box=8, threads=4, fused=False))
     for (ps, its), (pc, itc) in zip(seq, con):
         assert its == itc
         assert torch.equal(ps, pc)                      # deterministic per instance
@@ -38,7 +38,7 @@ def test_concurrent_equals_sequential(ras):
 def test_batch_states_meet_newton_test(ras):
     from paper_2007_13966_gb300 import batch
     res = batch.random_batch(4, 10, 20, 3, make)
-    out = batch.solve_batch(res, 1, batch.BatchOpts(box=8, threads=4))
+    out = batch.solve_batch(res, 1, batch.BatchOpts(box=8, threads=4, fused=False))
     for r, (p, _) in zip(res, out):
         prob = disc.Problem(r)
         p0 = np.full(r.grid.n, r.p0)
