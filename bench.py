@@ -537,8 +537,9 @@ def c4_arm(args):
 
     res = batch.random_batch(64, 32, 96, 7, make)
     opts = batch.BatchOpts(box=16, overlap=1, factor_prec=args.factor_prec, threads=16, fused=True,
-                           nlevels=2, coarsen=(4, 4, 4))
+                           nlevels=2, coarsen=(4, 4, 4), tune=True)
     b = batch.Batch(res, opts)
+    tuned = {"chunk_cells": b.schedule, "table": b.tune_table}
     b.advance(max(args.warmup, 1))
     sampler = ClockSampler(local)
     sampler.start()
@@ -570,6 +571,7 @@ def c4_arm(args):
         "cell_steps_per_s": cells * args.steps / t,
         "newton_iters_mean": float(np.mean([a for a, _ in iters])),
         "fgmres_iters_mean": float(np.mean([c for _, c in iters])),
+        "schedule_autotune": tuned,
         "streams_sec_per_step": ts,
         "fused_speedup_over_streams": ts / (t / args.steps),
         "clocks": clocks, "gpu_launches": int(launches), "e2e": None,

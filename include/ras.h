@@ -357,6 +357,21 @@ int ras_timing_read(ras_precond *pc, double *total_ms, long long *launches, int 
  * reporting. */
 double ras_apply_bytes(const ras_precond *pc);
 
+/* Level schedule of the fine-level subdomain solves (a performance setting; the
+ * preconditioner's values do not depend on it): consecutive wavefront levels are
+ * staged into shared memory in chunks of at most chunk_cells cells (at least the
+ * widest level), and each box is solved by `threads` threads (a multiple of 32,
+ * <= 512). 0 keeps the default of that argument (1024 cells, 384 for FP64
+ * factors; the widest level rounded up to a warp). Smaller chunks use less shared
+ * memory per box, so more boxes run per SM: worth it when there are many more
+ * boxes than SMs. Synchronous; no apply of this handle may be in flight; a batch
+ * created before the call keeps the old launch settings (create it again).
+ * RAS_EINVAL for ILU(k > 0) handles, negative or invalid values, or a schedule
+ * whose shared memory exceeds the per-block limit (the old schedule stays). */
+int ras_set_apply_schedule(ras_precond *pc, int chunk_cells, int threads);
+/* The current schedule (chunk_cells after raising it to the widest level). */
+int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads);
+
 #ifdef __cplusplus
 }
 #endif

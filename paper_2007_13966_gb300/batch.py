@@ -34,6 +34,7 @@ class BatchOpts:
     fused: bool = True            # one batch handle; False: one stream per reservoir
     nlevels: int = 1              # 2: two-level V-cycle with the exact coarse solve
     coarsen: tuple = (4, 4, 4)
+    tune: bool = False            # fused: pick the subdomain solves' chunk size by timing
 
 
 def parts_for(res, box):
@@ -81,6 +82,10 @@ class Batch:
         if self.opts.fused:
             self.inst = [_Instance(r, self.opts, own_stream=False) for r in reservoirs]
             self.solver = ras.BatchSolver([i.gp for i in self.inst], [i.pc for i in self.inst])
+            self.schedule, self.tune_table = None, None
+            if self.opts.tune:
+                from .autotune import tune_batch_schedule
+                self.schedule, self.tune_table = tune_batch_schedule(self)
         else:
             self.inst = self._map(lambda r: _Instance(r, self.opts), reservoirs)
 

@@ -207,6 +207,7 @@ struct ras_batch {
     int prec = 32, block = 0;
     size_t smem = 0;
     bool twolevel = false;                   // two-level V-cycle preconditioners
+    CoarseBatch *cb = nullptr;               // their coarse corrections in one launch (or null: one each)
     std::vector<BOp> ops, opsM;              // host copies: FGMRES operators, V-cycle operators
     std::vector<unsigned char> act;          // host copy of the mask
     // device tables
@@ -228,6 +229,7 @@ namespace ras {
 
 static void batch_free(ras_batch *B) {
     if (!B) return;
+    coarse_batch_free(B->cb);
     dfree(B->d_ops); dfree(B->d_opsM); dfree(B->t); dfree(B->d_ch); dfree(B->d_off); dfree(B->d_ch0); dfree(B->d_chn); dfree(B->d_kk);
     dfree(B->d_act); dfree(B->d_ap); dfree(B->d_box_inst); dfree(B->d_box_local);
     dfree(B->partials); dfree(B->out); dfree(B->d_y); dfree(B->d_beta);
@@ -311,8 +313,12 @@ static int b_precond(ras_batch *B, const double *v, double *z, cudaStream_t st) 
     RAS_TRY(ras1_apply_batch(A, B->nbox, B->prec, B->block, B->smem, st));
     if (!B->twolevel) return RAS_OK;
     RAS_TRY(b_stencil<true>(B, v, z, B->t, st, B->d_opsM));
-    for (int i = 0; i < B->n; ++i)
-        if (B->act[i]) RAS_TRY(coarse_correct(B->pc[i]->coarse, B->t + B->off[i], z + B->off[i], 1, st));
+    if (B->cb) {
+        RAS_TRY(coarse_correct_batch(B->cb, B->d_off, B->d_act, B->t, z, st));
+    } else {
+        for (int i = 0; i < B->n; ++i)
+            if (B->act[i]) RAS_TRY(coarse_correct(B->pc[i]->coarse, B->t + B->off[i], z + B->off[i], 1, st));
+    }
     RAS_TRY(b_stencil<true>(B, v, z, B->t, st, B->d_opsM));
     A.r = B->t;
     A.accumulate = 1;
@@ -513,6 +519,46 @@ static int b_norms_of(ras_batch *B, const std::vector<const double *> &vecs, con
     return b_norms(B, B->tmp, res, st);
 }
 
+// ras_factor of the live reservoirs on their current Jacobians. Two-level batches:
+// per reservoir the operator copy, the subdomain ILU(0) and the Galerkin coarse
+// operator with its blocks, then all block eliminations in one cooperative launch,
+// then each reservoir's checks (the steps of precond_factor).
+static int b_factor(ras_batch *B, const std::vector<int> &cur, const std::vector<unsigned char> &live,
+                    cudaStream_t st) {
+    const int n = B->n;
+    if (!B->cb) {
+        for (int i = 0; i < n; ++i) {
+            if (!live[i]) continue;
+            ras_stencil Js;
+            for (int s = 0; s < 7; ++s) Js.c[s] = B->P[i]->nJ[cur[i]][s];
+            RAS_TRY(precond_factor(B->pc[i], &Js, st));
+        }
+        return RAS_OK;
+    }
+    for (int i = 0; i < n; ++i) {
+        if (!live[i]) continue;
+        ras_precond *pc = B->pc[i];
+        const ras_problem *P = B->P[i];
+        Stencil7 A;
+        for (int s = 0; s < 7; ++s) {
+            A.c[s] = P->nJ[cur[i]][s];
+            RAS_CK(cudaMemcpyAsync(pc->Acopy[s], A.c[s], (size_t)P->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+            pc->A.c[s] = pc->Acopy[s];
+        }
+        RAS_TRY(ras1_factor(pc->fine, A, st));
+        RAS_TRY(coarse_factor_prepare(pc->coarse, A, st));
+    }
+    B->act = live;
+    RAS_TRY(upload_mask(B, st));
+    RAS_TRY(coarse_factor_batch(B->cb, B->d_act, st));
+    for (int i = 0; i < n; ++i) {
+        if (!live[i]) continue;
+        RAS_TRY(ras1_check(B->pc[i]->fine, st));
+        RAS_TRY(coarse_check(B->pc[i]->coarse, st));
+    }
+    return RAS_OK;
+}
+
 // One implicit step of every reservoir (the single-reservoir Newton driver's
 // steps, per reservoir, with the linear solves batched).
 static int bnewton(ras_batch *B, double *const *p, const double *const *pl, const double *const *plm1,
@@ -552,12 +598,10 @@ static int bnewton(ras_batch *B, double *const *p, const double *const *pl, cons
             any = any || live[i];
         }
         if (!any) break;
+        RAS_TRY(b_factor(B, cur, live, st));
         for (int i = 0; i < n; ++i) {
             if (!live[i]) continue;
             ras_problem *P = B->P[i];
-            ras_stencil Js;
-            for (int s = 0; s < 7; ++s) Js.c[s] = P->nJ[cur[i]][s];
-            RAS_TRY(precond_factor(B->pc[i], &Js, st));
             RAS_TRY(vec_axpby(B->b + B->off[i], -1.0, P->nF[cur[i]], 0.0, P->N, st));
             set_ops(B, i, P->nJ[cur[i]]);
         }
@@ -717,6 +761,14 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
         cudaMemset(B->b, 0, Nt * sizeof(double)) || cudaMemset(B->x, 0, Nt * sizeof(double)) ||
         cudaMemset(B->tmp, 0, Nt * sizeof(double)) || cudaMemset(B->t, 0, Nt * sizeof(double)))
         return fail(RAS_ECUDA);
+    if (B->twolevel) {
+        // one cooperative launch for all coarse corrections when the handles fit in one
+        // co-resident grid; otherwise one launch per handle
+        std::vector<Coarse *> cs(n);
+        for (int i = 0; i < n; ++i) cs[i] = B->pc[i]->coarse;
+        if (coarse_batch_setup(cs.data(), n, &B->cb) != RAS_OK) B->cb = nullptr;
+        cudaGetLastError();
+    }
     *out = B;
     return RAS_OK;
 }

@@ -419,9 +419,10 @@ __device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
 // limit. `epoch` is the caller's count of barriers passed (same in every thread);
 // counter and gen are reset to zero before every launch. The error word is read at
 // entry without waiting for it (its value is consulted after the barrier) and every
-// 1024 polls. Returns false if this or any CTA has flagged an error or the wait ran
-// out (ERR_TIMEOUT is then set).
-__device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch) {
+// 1024 polls. G: the number of CTAs that take part (default: the grid; a group of
+// co-resident CTAs with a barrier word of its own). Returns false if this or any
+// CTA has flagged an error or the wait ran out (ERR_TIMEOUT is then set).
+__device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch, unsigned G = 0) {
     __shared__ int s_ok;
     ++epoch;
     __syncthreads();
@@ -430,7 +431,7 @@ __device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch) {
         int ok = 1;
         const long long lim = bar->polls > 0 ? bar->polls : BAR_POLLS;
         __threadfence();
-        const unsigned target = epoch * gridDim.x;
+        const unsigned target = epoch * (G ? G : gridDim.x);
         if (atom_add_acq_rel(&bar->count, 1u) == target - 1) {
             st_release(&bar->gen, epoch);
         } else {
@@ -887,12 +888,12 @@ __device__ void sparse_row_times(const AT *Inv, const int *lq, const AT *lv, int
 // inverted by a CTA of its own (when the grid has more CTAs than chains).
 template <typename AT>
 __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT> &ts, const int *blk, int nblk,
-                              unsigned &epoch) {
-    const int T = a.T, nt = a.nt, G = gridDim.x, b = blockIdx.x;
+                              unsigned &epoch, int b, int G) {
+    const int T = a.T, nt = a.nt;
     const long long bsz = (long long)T * T;
     // prologue: pivot tile 0 and the row panel of step 0
     for (int c = b; c < nblk; c += G) tile_invert(ts, a.D + blk[c] * bsz, T, 0, a.err);
-    if (!grid_barrier(a.bar, a.err, epoch)) return false;
+    if (!grid_barrier(a.bar, a.err, epoch, G)) return false;
     {
         const int n0 = 4 * (nt - 1);
         for (int it = b; it < nblk * n0; it += G) {
@@ -901,7 +902,7 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
             subtile_product<AT, 64, 16, 2, 2>(ts, Dk, Dk, Dk, T, 0, 0, 0, j, 0, j, 0, 16 * q, (AT)1, false);
         }
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) return false;
+    if (!grid_barrier(a.bar, a.err, epoch, G)) return false;
     const bool own = G > nblk;              // CTAs 0..nblk-1 do only the pivot tiles
     for (int p = 0; p < nt; ++p) {
         const bool nxt = p + 1 < nt;
@@ -944,7 +945,7 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
                 else regular(it - ns);
             }
         }
-        if (!grid_barrier(a.bar, a.err, epoch)) return false;
+        if (!grid_barrier(a.bar, a.err, epoch, G)) return false;
         // phase B: column panel of step p (D_ip = -D_ip P_p, i != p, p+1),
         // row panel of step p+1 (D_{p+1,j} = P_{p+1} D_{p+1,j}, j != p, p+1),
         // and tile (p+1, p) = P_{p+1} (-D_{p+1,p} P_p)
@@ -971,7 +972,7 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
                                                   p + 1, 0, 0, p + 1, p, 0, 16 * q, (AT)1, false);
             }
         }
-        if (!grid_barrier(a.bar, a.err, epoch)) return false;
+        if (!grid_barrier(a.bar, a.err, epoch, G)) return false;
     }
     return true;
 }
@@ -980,12 +981,14 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
 // inverts block s and the bottom chain block nb-1-s, then both form C_e, F_e
 // of their edge and update their target block; the middle block is inverted
 // last.
+// The factorisation of one handle by a group of G co-resident CTAs (b: this CTA's
+// index in the group).
 template <typename AT>
-__global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
+__device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, int G) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<AT> &ts = *reinterpret_cast<TileSmem<AT> *>(smem_raw);
     AT *rows = reinterpret_cast<AT *>(smem_raw);
-    const int T = a.T, G = gridDim.x, b = blockIdx.x, nb = a.nb, mid = a.mid;
+    const int T = a.T, nb = a.nb, mid = a.mid;
     const long long bsz = (long long)T * T;
     const int ntop = mid, nbot = nb - 1 - mid;
     const int nsteps = max(ntop, nbot);
@@ -998,7 +1001,7 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
         } else {
             blk[nblk++] = mid;
         }
-        if (!invert_blocks(a, ts, blk, nblk, epoch)) return;
+        if (!invert_blocks(a, ts, blk, nblk, epoch, b, G)) return;
         if (s == nsteps) break;
         const long long ell = (long long)T * ELLW;
         const int nchunk = T / FROWS;
@@ -1016,14 +1019,31 @@ __global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
                               a.up_n + (long long)e * T, T, (it - T) * FROWS, false);
             }
         }
-        if (!grid_barrier(a.bar, a.err, epoch)) return;
+        if (!grid_barrier(a.bar, a.err, epoch, G)) return;
         for (int it2 = b; it2 < ne * nchunk; it2 += G) {    // S_target -= C_e A(pivot, target)
             const int e = edg[it2 / nchunk], it = it2 % nchunk;
             rows_times_up(rows, a.C + e * bsz, a.D + edge_target(e, mid) * bsz, a.up_q + e * ell,
                           a.up_v + e * ell, a.up_n + (long long)e * T, T, it * FROWS, true);
         }
-        if (!grid_barrier(a.bar, a.err, epoch)) return;
+        if (!grid_barrier(a.bar, a.err, epoch, G)) return;
     }
+}
+
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
+    coarse_factor_body(a, blockIdx.x, gridDim.x);
+}
+
+// The factorisations of several handles in one cooperative launch: handle h takes
+// CTAs first[h] .. first[h] + size[h] - 1 and its own barrier word; handles off in
+// `active` return at once.
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_factor_batch(const FacArgs<AT> *args, const int *cta_inst,
+                                                             const int *first, const int *size,
+                                                             const unsigned char *active) {
+    const int h = cta_inst[blockIdx.x];
+    if (!active[h]) return;
+    coarse_factor_body(args[h], blockIdx.x - first[h], size[h]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1121,8 +1141,10 @@ __device__ void stage_vector(const AT *xsrc, AT *xs, int T) {
     __syncthreads();
 }
 
+// The coarse correction of one handle by a group of ng co-resident CTAs (b: this
+// CTA's index in the group); t: fine residual, z: fine correction.
 template <typename AT>
-__global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
+__device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, int ng, const double *t, double *z) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     AT *xs = reinterpret_cast<AT *>(smem_raw);
     const CGeom &G = a.G;
@@ -1140,7 +1162,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     // vector staging); further rows are read directly.
     const int nb = G.nb, mid = G.mid, ntop = mid, nbot = nb - 1 - mid;
     const int nsteps = max(ntop, nbot), nstage = 2 * nsteps + 1;
-    const int wg = blockIdx.x * wpb + (threadIdx.x >> 5), nwt = gridDim.x * wpb;
+    const int wg = b * wpb + (threadIdx.x >> 5), nwt = ng * wpb;
     AT *rbuf = xs + 2 * (long long)T + (long long)(threadIdx.x >> 5) * a.npf * T;
     constexpr int VEC = 16 / sizeof(AT);
     auto edges_of = [&](int st, int *edg) {
@@ -1180,19 +1202,19 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
     };
     prefetch(0);   // lands during the restriction
     // g = R t with R = P^T = Pz^T Py^T Px^T, one axis per pass
-    const long long gtid = blockIdx.x * (long long)blockDim.x + threadIdx.x;
-    const long long gstride = (long long)gridDim.x * blockDim.x;
+    const long long gtid = b * (long long)blockDim.x + threadIdx.x;
+    const long long gstride = (long long)ng * blockDim.x;
     const long long n1 = (long long)G.cx * G.ny * G.nz;
     for (long long e = gtid; e < n1; e += gstride) {          // x pass
         const int Ix = (int)(e % G.cx);
         const long long yz = e / G.cx;
-        const double *src = a.t + yz * G.nx;
+        const double *src = t + yz * G.nx;
         AT acc = 0;
         const int x0 = P.lo[0][Ix], x1 = P.hi[0][Ix];
         for (int ax = x0; ax < x1; ++ax) acc += (AT)w1(P, 0, ax, Ix) * (AT)__ldg(src + ax);
         a.rx[e] = acc;
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
+    if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     const long long n2 = (long long)G.cx * G.cy * G.nz;
     for (long long e = gtid; e < n2; e += gstride) {          // y pass
         const int Ix = (int)(e % G.cx), Iy = (int)((e / G.cx) % G.cy);
@@ -1203,7 +1225,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
             acc += (AT)w1(P, 1, ay, Iy) * __ldcg(a.rx + Ix + (long long)G.cx * (ay + (long long)G.ny * az));
         a.ry[e] = acc;
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
+    if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     for (long long I = gtid; I < G.Nc; I += gstride) {         // z pass
         const int Ix = (int)(I % G.cx), Iy = (int)((I / G.cx) % G.cy), Iz = (int)(I / ((long long)G.cx * G.cy));
         AT acc = 0;
@@ -1212,7 +1234,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
             acc += (AT)w1(P, 2, az, Iz) * __ldcg(a.ry + Ix + (long long)G.cx * (Iy + (long long)G.cy * az));
         a.g[a.pos[I]] = acc;
     }
-    if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
+    if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     for (int st = 0; st < nstage; ++st) {
         int edg[2];
         const int ne = edges_of(st, edg);
@@ -1251,7 +1273,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
         }
         __syncwarp();                      // this warp's reads of its row buffer are done
         prefetch(st + 1);
-        if (!grid_barrier(a.bar, a.err, epoch)) { cp_async_wait_all(); return; }
+        if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     }
     // z (+)= P x, four fine cells per thread with their loads in flight together
     const long long N = (long long)G.nx * G.ny * G.nz;
@@ -1286,9 +1308,28 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
 #pragma unroll
         for (int m = 0; m < 4; ++m) {
             const long long p = p0 + m * gstride;
-            if (p < N) { if (a.accumulate) a.z[p] += (double)sv[m]; else a.z[p] = (double)sv[m]; }
+            if (p < N) { if (a.accumulate) z[p] += (double)sv[m]; else z[p] = (double)sv[m]; }
         }
     }
+}
+
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
+    coarse_solve_body(a, blockIdx.x, gridDim.x, a.t, a.z);
+}
+
+// The coarse corrections of several handles in one cooperative launch: handle h
+// takes CTAs first[h] .. first[h] + size[h] - 1 and its own barrier word; t and z
+// are the handles' fine vectors concatenated at off[h]; a handle switched off in
+// `active` returns at once (all its CTAs).
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_solve_batch(const SolArgs<AT> *args, const int *cta_inst,
+                                                            const int *first, const int *size,
+                                                            const long long *off, const unsigned char *active,
+                                                            const double *t, double *z) {
+    const int h = cta_inst[blockIdx.x];
+    if (!active[h]) return;
+    coarse_solve_body(args[h], blockIdx.x - first[h], size[h], t + off[h], z + off[h]);
 }
 
 // ---------------------------------------------------------------------------
@@ -1379,7 +1420,9 @@ static int configure_t(Coarse *c) {
     RAS_CK(cudaFuncSetAttribute(k_rap<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_rap125<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_factor<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_coarse_factor_batch<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_solve<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_coarse_solve_batch<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
     const int WM = std::max(WX, std::max(WY, WZ));
     const size_t tables = sizeof(int) * (size_t)(5 * WY * WX + 25 * WX);
@@ -1551,7 +1594,7 @@ void coarse_free(Coarse *c) {
 
 // dense block factorisation of the Galerkin operator already in c->Ac
 template <typename AT>
-static int factor_blocks_t(Coarse *c, cudaStream_t st) {
+static int assemble_blocks_t(Coarse *c, cudaStream_t st) {
     const CGeom G = geom_of(c);
     AT *Ac = (AT *)c->Ac, *D = (AT *)c->D;
     const size_t bsz = (size_t)c->T * c->T;
@@ -1564,9 +1607,20 @@ static int factor_blocks_t(Coarse *c, cudaStream_t st) {
             c->up_n, c->d_err);
         RAS_LAUNCHED();
     }
+    return RAS_OK;
+}
+
+template <typename AT>
+static FacArgs<AT> fac_args(Coarse *c, GridBar *bar) {
+    return FacArgs<AT>{(AT *)c->D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n,
+                       (const AT *)c->lo_v, (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, bar, c->d_err};
+}
+
+template <typename AT>
+static int factor_blocks_t(Coarse *c, cudaStream_t st) {
+    RAS_TRY(assemble_blocks_t<AT>(c, st));
     RAS_TRY(reset_bar(c, st));
-    FacArgs<AT> fa{D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n, (const AT *)c->lo_v,
-                   (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, c->d_bar, c->d_err};
+    FacArgs<AT> fa = fac_args<AT>(c, c->d_bar);
     void *args[] = {&fa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor<AT>, dim3(c->fac_grid),
                                        dim3(256), args, c->fac_smem, st));
@@ -1595,6 +1649,18 @@ int coarse_factor(Coarse *c, const Stencil7 &A, cudaStream_t st) {
     return c->prec == 64 ? factor_t<double>(c, A, st) : factor_t<float>(c, A, st);
 }
 
+template <typename AT>
+static int prepare_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
+    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
+    k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, (AT *)c->Ac);
+    RAS_LAUNCHED();
+    return assemble_blocks_t<AT>(c, st);
+}
+
+int coarse_factor_prepare(Coarse *c, const Stencil7 &A, cudaStream_t st) {
+    return c->prec == 64 ? prepare_t<double>(c, A, st) : prepare_t<float>(c, A, st);
+}
+
 int coarse_factor125(Coarse *c, const double *Af, cudaStream_t st) {
     return c->prec == 64 ? factor125_t<double>(c, Af, st) : factor125_t<float>(c, Af, st);
 }
@@ -1619,6 +1685,164 @@ static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cuda
     void *args[] = {&sa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve<AT>, dim3(c->sol_grid),
                                        dim3(256), args, c->sol_smem, st));
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+// ---------------------------------------------------------------------------
+// coarse corrections of many handles in one cooperative launch
+// ---------------------------------------------------------------------------
+
+struct CoarseBatch {
+    int n = 0, prec = 32, grid = 0, fgrid = 0;
+    size_t smem = 0, fsmem = 0;
+    void *d_args = nullptr;                 // SolArgs<AT>[n]
+    int *d_cta_inst = nullptr, *d_first = nullptr, *d_size = nullptr;
+    void *d_fargs = nullptr;                // FacArgs<AT>[n]
+    int *d_fcta_inst = nullptr, *d_ffirst = nullptr, *d_fsize = nullptr;
+    GridBar *d_bars = nullptr;              // [n], one barrier word per handle
+};
+
+void coarse_batch_free(CoarseBatch *cb) {
+    if (!cb) return;
+    if (cb->d_args) cudaFree(cb->d_args);
+    if (cb->d_fargs) cudaFree(cb->d_fargs);
+    dfree(cb->d_cta_inst); dfree(cb->d_first); dfree(cb->d_size); dfree(cb->d_bars);
+    dfree(cb->d_fcta_inst); dfree(cb->d_ffirst); dfree(cb->d_fsize);
+    delete cb;
+}
+
+// CTA groups of a batched cooperative launch: `total` CTAs split over n handles in
+// proportion to w (at least one each); cta[k] = handle of CTA k.
+static int partition(const std::vector<double> &w, int total, std::vector<int> &cta, std::vector<int> &first,
+                     std::vector<int> &size) {
+    const int n = (int)w.size();
+    if (n > total) return RAS_EINVAL;
+    double wsum = 0.0;
+    for (double v : w) wsum += v;
+    size.assign(n, 1);
+    first.assign(n, 0);
+    int used = 0;
+    for (int i = 0; i < n; ++i) {
+        size[i] = std::max(1, (int)((total - n) * (wsum > 0 ? w[i] / wsum : 0.0)) + 1);
+        used += size[i];
+    }
+    while (used > total) {                  // rounding: take from the largest groups
+        const int j = (int)(std::max_element(size.begin(), size.end()) - size.begin());
+        --size[j];
+        --used;
+    }
+    cta.clear();
+    for (int i = 0; i < n; ++i) {
+        first[i] = (int)cta.size();
+        for (int q = 0; q < size[i]; ++q) cta.push_back(i);
+    }
+    return RAS_OK;
+}
+
+template <typename AT>
+static int batch_setup_t(Coarse *const *cs, int n, CoarseBatch *cb) {
+    int dev = 0, sms = 0, bs = 0, bf = 0;
+    size_t smem = 0, fsmem = 0;
+    for (int i = 0; i < n; ++i) {
+        smem = std::max(smem, cs[i]->sol_smem);
+        fsmem = std::max(fsmem, cs[i]->fac_smem);
+    }
+    RAS_CK(cudaGetDevice(&dev));
+    RAS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bs, k_coarse_solve_batch<AT>, 256, smem));
+    RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&bf, k_coarse_factor_batch<AT>, 256, fsmem));
+    if (bs < 1 || bf < 1) return RAS_EINVAL;
+    // solve: CTAs in proportion to the fine cells (the restriction and prolongation
+    // scale with them, the block sweeps' latency-bound rows with the coarse cells);
+    // factorisation: in proportion to the block elimination's work T^3 nb
+    std::vector<double> ws(n), wf(n);
+    for (int i = 0; i < n; ++i) {
+        ws[i] = (double)cs[i]->N;
+        wf[i] = (double)cs[i]->T * cs[i]->T * cs[i]->T * cs[i]->nb;
+    }
+    std::vector<int> cta, first, size, fcta, ffirst, fsize;
+    RAS_TRY(partition(ws, sms * std::min(bs, 2), cta, first, size));
+    RAS_TRY(partition(wf, sms * std::min(bf, 2), fcta, ffirst, fsize));
+    std::vector<SolArgs<AT>> args(n);
+    std::vector<FacArgs<AT>> fargs(n);
+    RAS_TRY(dalloc(&cb->d_bars, n));
+    for (int i = 0; i < n; ++i) {
+        Coarse *c = cs[i];
+        args[i] = SolArgs<AT>{nullptr, nullptr, 1, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
+                              (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
+                              (AT *)c->ry, cb->d_bars + i, c->d_err, c->sol_npf};
+        fargs[i] = fac_args<AT>(c, cb->d_bars + i);
+    }
+    RAS_CK(cudaMalloc(&cb->d_args, n * sizeof(SolArgs<AT>)));
+    RAS_CK(cudaMalloc(&cb->d_fargs, n * sizeof(FacArgs<AT>)));
+    RAS_TRY(dalloc(&cb->d_cta_inst, cta.size()));
+    RAS_TRY(dalloc(&cb->d_first, n));
+    RAS_TRY(dalloc(&cb->d_size, n));
+    RAS_TRY(dalloc(&cb->d_fcta_inst, fcta.size()));
+    RAS_TRY(dalloc(&cb->d_ffirst, n));
+    RAS_TRY(dalloc(&cb->d_fsize, n));
+    RAS_CK(cudaMemcpy(cb->d_args, args.data(), n * sizeof(SolArgs<AT>), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_fargs, fargs.data(), n * sizeof(FacArgs<AT>), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_cta_inst, cta.data(), cta.size() * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_first, first.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_size, size.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_fcta_inst, fcta.data(), fcta.size() * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_ffirst, ffirst.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemcpy(cb->d_fsize, fsize.data(), n * sizeof(int), cudaMemcpyHostToDevice));
+    RAS_CK(cudaMemset(cb->d_bars, 0, n * sizeof(GridBar)));
+    cb->grid = (int)cta.size();
+    cb->smem = smem;
+    cb->fgrid = (int)fcta.size();
+    cb->fsmem = fsmem;
+    return RAS_OK;
+}
+
+int coarse_batch_setup(Coarse *const *cs, int n, CoarseBatch **out) {
+    *out = nullptr;
+    if (n < 1) return RAS_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (!cs[i] || cs[i]->prec != cs[0]->prec) return RAS_EINVAL;
+    CoarseBatch *cb = new CoarseBatch();
+    cb->n = n;
+    cb->prec = cs[0]->prec;
+    const int rc = cb->prec == 64 ? batch_setup_t<double>(cs, n, cb) : batch_setup_t<float>(cs, n, cb);
+    if (rc) { coarse_batch_free(cb); return rc; }
+    *out = cb;
+    return RAS_OK;
+}
+
+int coarse_factor_batch(CoarseBatch *cb, const unsigned char *d_active, cudaStream_t st) {
+    RAS_CK(cudaMemsetAsync(cb->d_bars, 0, cb->n * sizeof(GridBar), st));
+    if (cb->prec == 64) {
+        const FacArgs<double> *a = (const FacArgs<double> *)cb->d_fargs;
+        void *args[] = {&a, &cb->d_fcta_inst, &cb->d_ffirst, &cb->d_fsize, &d_active};
+        RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor_batch<double>, dim3(cb->fgrid),
+                                           dim3(256), args, cb->fsmem, st));
+    } else {
+        const FacArgs<float> *a = (const FacArgs<float> *)cb->d_fargs;
+        void *args[] = {&a, &cb->d_fcta_inst, &cb->d_ffirst, &cb->d_fsize, &d_active};
+        RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor_batch<float>, dim3(cb->fgrid),
+                                           dim3(256), args, cb->fsmem, st));
+    }
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+int coarse_correct_batch(CoarseBatch *cb, const long long *d_off, const unsigned char *d_active, const double *t,
+                         double *z, cudaStream_t st) {
+    RAS_CK(cudaMemsetAsync(cb->d_bars, 0, cb->n * sizeof(GridBar), st));
+    if (cb->prec == 64) {
+        const SolArgs<double> *a = (const SolArgs<double> *)cb->d_args;
+        void *args[] = {&a, &cb->d_cta_inst, &cb->d_first, &cb->d_size, &d_off, &d_active, &t, &z};
+        RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve_batch<double>, dim3(cb->grid), dim3(256),
+                                           args, cb->smem, st));
+    } else {
+        const SolArgs<float> *a = (const SolArgs<float> *)cb->d_args;
+        void *args[] = {&a, &cb->d_cta_inst, &cb->d_first, &cb->d_size, &d_off, &d_active, &t, &z};
+        RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve_batch<float>, dim3(cb->grid), dim3(256),
+                                           args, cb->smem, st));
+    }
     RAS_LAUNCHED();
     return RAS_OK;
 }

@@ -250,3 +250,15 @@ extern "C" double ras_apply_bytes(const ras_precond *pc) {
     if (!pc) return 0.0;
     return pc->use125 ? ras125_bytes(pc->fine125) : ras1_bytes(pc->fine);
 }
+
+extern "C" int ras_set_apply_schedule(ras_precond *pc, int chunk_cells, int threads) {
+    if (!pc || pc->use125) return RAS_EINVAL;
+    return ras1_set_schedule(pc->fine, chunk_cells, threads);
+}
+
+extern "C" int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads) {
+    if (!pc || pc->use125 || !chunk_cells || !threads) return RAS_EINVAL;
+    *chunk_cells = pc->fine.chunk_cells;
+    *threads = pc->fine.block;
+    return RAS_OK;
+}

@@ -20,6 +20,22 @@ int coarse_check(Coarse *c, cudaStream_t st);
 double coarse_bytes(const Coarse *c);
 // ec = A_c^{-1} R t, then z (+)= P ec  (accumulate selects += )
 int coarse_correct(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st);
+// z += P A_c^{-1} P^T t for several handles in one cooperative launch (a group of
+// CTAs and a barrier word per handle); t, z: the handles' fine vectors
+// concatenated at off[h] (device); handles off in `active` (device) do nothing.
+// The coarse factors must be current (coarse_factor); errors go to each handle's
+// flag (coarse_check). RAS_EINVAL when the handles' precisions differ or there are
+// more handles than co-resident CTAs.
+struct CoarseBatch;
+int coarse_batch_setup(Coarse *const *cs, int n, CoarseBatch **out);
+void coarse_batch_free(CoarseBatch *cb);
+int coarse_correct_batch(CoarseBatch *cb, const long long *d_off, const unsigned char *d_active, const double *t,
+                         double *z, cudaStream_t st);
+// The first part of coarse_factor (Galerkin product, block assembly, couplings),
+// then the block eliminations of several handles in one cooperative launch
+// (handles off in `active` skip it); coarse_check per handle afterwards.
+int coarse_factor_prepare(Coarse *c, const Stencil7 &A, cudaStream_t st);
+int coarse_factor_batch(CoarseBatch *cb, const unsigned char *d_active, cudaStream_t st);
 
 // grid transfer to the next coarser level (linear interpolation P, R = P^T)
 struct Transfer;

@@ -452,6 +452,77 @@ static int set_factor_attr(size_t) {
     return RAS_OK;
 }
 
+// Level schedule of the subdomain solves: chunks of consecutive levels with at most
+// chunk_cells cells (staged into the shared-memory ring together) and threads per
+// box. 0 takes the default (chunk 1024 cells, 384 in FP64; threads: the widest
+// level rounded up to a warp), or the RAS_APPLY_CHUNK / RAS_APPLY_THREADS tuning
+// knobs. Fills the shapes' chunk offsets, chunk_tab, block and smem_apply.
+static int schedule_tables(Ras1 &R, int chunk_cells, int threads, std::vector<int> &chunk_tab) {
+    int base_chunk = R.prec == 64 ? 384 : 1024;
+    if (const char *e = getenv("RAS_APPLY_CHUNK")) {     // tuning knob
+        const int v = atoi(e);
+        if (v >= 64 && v <= 8192) base_chunk = v;
+    }
+    if (chunk_cells > 0) base_chunk = chunk_cells;
+    const int cc = std::max(base_chunk, R.maxw);
+    int block = std::min(512, std::max(64, ((R.maxw + 31) / 32) * 32));
+    if (const char *e = getenv("RAS_APPLY_THREADS")) {   // tuning knob
+        const int v = atoi(e);
+        if (v >= 32 && v <= 512 && v % 32 == 0) block = v;
+    }
+    if (threads > 0) {
+        if (threads > 512 || threads % 32) return RAS_EINVAL;
+        block = threads;
+    }
+    const size_t acc = R.prec == 64 ? 8 : 4;
+    const size_t rcap = ((cc * R.rec_bytes + 32) + 15) & ~15;
+    const size_t ccap = ((cc * 4 + 32) + 15) & ~15;
+    const size_t smem = (R.ycap + 2 * (size_t)R.gcap) * acc + R.lcap * sizeof(int) + R.nbuf * (rcap + ccap);
+    if (smem > 227 * 1024) return RAS_EINVAL;
+    chunk_tab.clear();
+    for (auto &sh : R.shapes) {
+        sh.chunk_off = (int)chunk_tab.size();
+        const int *lv = &R.h_lvl[sh.lvl_off];
+        int l = 0;
+        chunk_tab.push_back(0);
+        int nch = 0;
+        while (l < sh.nlev) {
+            int l1 = l + 1;
+            while (l1 < sh.nlev && lv[l1 + 1] - lv[l] <= cc) ++l1;
+            chunk_tab.push_back(l1);
+            ++nch;
+            l = l1;
+        }
+        sh.nchunk = nch;
+    }
+    R.chunk_cells = cc;
+    R.block = block;
+    R.smem_apply = smem;
+    return RAS_OK;
+}
+
+int ras1_set_schedule(Ras1 &R, int chunk_cells, int threads) {
+    if (chunk_cells < 0 || threads < 0) return RAS_EINVAL;
+    Ras1 T = R;                 // the tables only change if the new schedule is valid
+    std::vector<int> chunk_tab;
+    RAS_TRY(schedule_tables(T, chunk_cells, threads, chunk_tab));
+    int *d = nullptr;
+    RAS_TRY(dalloc(&d, chunk_tab.size()));
+    if (cudaMemcpy(d, chunk_tab.data(), chunk_tab.size() * sizeof(int), cudaMemcpyHostToDevice) != cudaSuccess ||
+        cudaMemcpy(R.d_shapes, T.shapes.data(), T.shapes.size() * sizeof(ShapeInfo), cudaMemcpyHostToDevice) !=
+            cudaSuccess) {
+        dfree(d);
+        return RAS_ECUDA;
+    }
+    dfree(R.d_chunk);
+    R.d_chunk = d;
+    R.shapes = T.shapes;
+    R.chunk_cells = T.chunk_cells;
+    R.block = T.block;
+    R.smem_apply = T.smem_apply;
+    return RAS_OK;
+}
+
 int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec,
                int kind) {
     if (px < 1 || py < 1 || pz < 1 || overlap < 0) return RAS_EINVAL;
@@ -468,7 +539,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     for (int a = 0; a < 3; ++a) cuts[a] = split_axis(dims[a], parts[a]);
 
     std::map<std::tuple<int, int, int>, int> shape_id;
-    std::vector<int> lvl_tab, chunk_tab;
+    std::vector<int> lvl_tab;
     std::vector<unsigned> cell_tab;
     std::vector<int> cidx_tab;        // same positions as cell_tab: i + bx (j + by k)
     R.subs.clear();
@@ -571,41 +642,13 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
             return RAS_EINVAL;
     }
     R.nrec = foff;
-    // chunks of consecutive levels with at most chunk_cells cells
-    int base_chunk = prec == 64 ? 384 : 1024;
-    if (const char *e = getenv("RAS_APPLY_CHUNK")) {     // tuning knob
-        const int v = atoi(e);
-        if (v >= 64 && v <= 8192) base_chunk = v;
-    }
-    R.chunk_cells = std::max(base_chunk, maxw_all);
-    R.nbuf = 3;
-    for (auto &sh : R.shapes) {
-        sh.chunk_off = (int)chunk_tab.size();
-        const int *lv = &lvl_tab[sh.lvl_off];
-        int l = 0;
-        chunk_tab.push_back(0);
-        int nch = 0;
-        while (l < sh.nlev) {
-            int l1 = l + 1;
-            while (l1 < sh.nlev && lv[l1 + 1] - lv[l] <= R.chunk_cells) ++l1;
-            chunk_tab.push_back(l1);
-            ++nch;
-            l = l1;
-        }
-        sh.nchunk = nch;
-    }
-    R.block = std::min(512, std::max(64, ((maxw_all + 31) / 32) * 32));
-    if (const char *e = getenv("RAS_APPLY_THREADS")) {   // tuning knob
-        const int v = atoi(e);
-        if (v >= 32 && v <= 512 && v % 32 == 0) R.block = v;
-    }
     R.ycap = (ycap + 3) & ~3;
     R.gcap = (gcap + 3) & ~3;
     R.lcap = (lcap + 3) & ~3;
-    const size_t acc = prec == 64 ? 8 : 4;
-    const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
-    const size_t ccap = ((R.chunk_cells * 4 + 32) + 15) & ~15;
-    R.smem_apply = (R.ycap + 2 * (size_t)R.gcap) * acc + R.lcap * sizeof(int) + R.nbuf * (rcap + ccap);
+    R.maxw = maxw_all;
+    R.h_lvl = lvl_tab;
+    std::vector<int> chunk_tab;
+    RAS_TRY(schedule_tables(R, 0, 0, chunk_tab));
     R.smem_factor = (size_t)R.ycap * sizeof(double);
     if (R.smem_apply > 227 * 1024 || R.smem_factor > 227 * 1024) return RAS_EINVAL;
 

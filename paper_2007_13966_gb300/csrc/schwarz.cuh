@@ -40,6 +40,8 @@ struct Ras1 {
     int nbuf = 3;           // staged chunks in flight
     int ycap = 0, lcap = 0; // smem capacities (cells, levels + 1)
     int gcap = 0;           // zero guard band on each side of the apply's vector (cells)
+    int maxw = 0;           // widest level over the box shapes
+    std::vector<int> h_lvl; // host copy of the level starts (rescheduling)
     size_t smem_apply = 0, smem_factor = 0;
     long long nrec = 0;     // factor records (incl. padding)
     long long ncell_total = 0;  // sum of overlapped cells
@@ -73,6 +75,8 @@ int ras1_check(Ras1 &R, cudaStream_t st);
 // sum_i (R_i^delta)^T A_i^{-1} R_i^delta (AS, kind 0) or
 // sum_i (R_i^delta)^T A_i^{-1} R_i^0 (right-RAS, kind 2)
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st);
+// new chunk size / threads per box for the subdomain solves (0: default); synchronous
+int ras1_set_schedule(Ras1 &R, int chunk_cells, int threads);
 
 // parameters of one handle's apply kernel
 struct ApplyParams {

@@ -24,7 +24,8 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
             "newton_step", "ras_status_string", "ras_last_error", "ras_kernel_launches",
             "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc",
             "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk", "ras_batch_create",
-            "ras_batch_destroy", "ras_batch_gmres", "ras_batch_newton_step"]
+            "ras_batch_destroy", "ras_batch_gmres", "ras_batch_newton_step", "ras_set_apply_schedule",
+            "ras_get_apply_schedule"]
 
 
 class Grid(C.Structure):
@@ -114,6 +115,8 @@ def lib():
             "ras_stencil_transpose": (i, [vp, C.POINTER(Stencil), C.POINTER(Stencil), vp]),
             "ras_adjoint_rhs": (i, [vp, vp, vp, vp, d, vp, vp, d, vp, vp]),
             "ras_grad_logk": (i, [vp, vp, vp, vp, vp]),
+            "ras_set_apply_schedule": (i, [vp, i, i]),
+            "ras_get_apply_schedule": (i, [vp, C.POINTER(i), C.POINTER(i)]),
             "ras_batch_create": (i, [i, vp, vp, C.POINTER(vp)]),
             "ras_batch_destroy": (None, [vp]),
             "ras_batch_gmres": (i, [vp, vp, vp, vp, C.POINTER(KrylovOpts), vp, vp]),
@@ -309,6 +312,15 @@ class Precond:
 
     def apply_bytes(self) -> float:
         return float(lib().ras_apply_bytes(self.h))
+
+    def set_schedule(self, chunk_cells=0, threads=0):
+        """Level schedule of the subdomain solves (performance only; 0 = default)."""
+        check(lib().ras_set_apply_schedule(self.h, int(chunk_cells), int(threads)), "ras_set_apply_schedule")
+
+    def schedule(self):
+        c, t = C.c_int(0), C.c_int(0)
+        check(lib().ras_get_apply_schedule(self.h, C.byref(c), C.byref(t)), "ras_get_apply_schedule")
+        return c.value, t.value
 
 
 class BatchSolver:
