@@ -514,7 +514,8 @@ WORKLOAD_C4 = ("64 independent 3d lognormal reservoirs, edges uniform in 32..96 
                "per-instance seeds, two-level V-cycle: left-RAS ILU(0) with ~16^3 subdomains, overlap 1, "
                "exact coarse solve on the 4x coarsened grid, FP32 factors inside FP64 FGMRES(30), all "
                "reservoirs in one batch handle (one launch per fine-level FGMRES operation for the whole "
-               "batch, one cooperative coarse solve per reservoir)")
+               "batch; coarse solves of all reservoirs in one cooperative launch, coarse block "
+               "eliminations in waves of at least 16 CTAs per reservoir)")
 
 
 def c4_arm(args):

@@ -37,6 +37,7 @@ namespace ras {
 constexpr int TILE = 64;
 constexpr int ELLW = 64;    // max couplings of one cell into the neighbouring block (<= 50)
 constexpr int FROWS = 8;    // rows of a dense block staged per CTA in the sparse products
+constexpr int FWAVE_CTAS = 16;   // least CTAs per handle in a batched block elimination
 constexpr int ERR_PIVOT = 1, ERR_ELL = 2, ERR_TIMEOUT = 7;
 constexpr long long BAR_POLLS = 1LL << 22;   // ~1-2 s of polling before a barrier gives up
 
@@ -1700,6 +1701,7 @@ struct CoarseBatch {
     int *d_cta_inst = nullptr, *d_first = nullptr, *d_size = nullptr;
     void *d_fargs = nullptr;                // FacArgs<AT>[n]
     int *d_fcta_inst = nullptr, *d_ffirst = nullptr, *d_fsize = nullptr;
+    std::vector<int> fwave0, fwaven;        // factorisation waves: CTA range in d_fcta_inst
     GridBar *d_bars = nullptr;              // [n], one barrier word per handle
 };
 
@@ -1761,9 +1763,30 @@ static int batch_setup_t(Coarse *const *cs, int n, CoarseBatch *cb) {
         ws[i] = (double)cs[i]->N;
         wf[i] = (double)cs[i]->T * cs[i]->T * cs[i]->T * cs[i]->nb;
     }
-    std::vector<int> cta, first, size, fcta, ffirst, fsize;
+    std::vector<int> cta, first, size, fcta, ffirst(n, 0), fsize(n, 1);
     RAS_TRY(partition(ws, sms * std::min(bs, 2), cta, first, size));
-    RAS_TRY(partition(wf, sms * std::min(bf, 2), fcta, ffirst, fsize));
+    // The block elimination is a chain of latency-bound panel steps whose trailing
+    // work needs CTAs: handles are factored in waves (largest first) of at most
+    // total / FWAVE_CTAS handles, so every handle gets at least FWAVE_CTAS CTAs.
+    const int ftotal = sms * std::min(bf, 2);
+    const int per = std::max(1, ftotal / FWAVE_CTAS);
+    std::vector<int> order(n);
+    for (int i = 0; i < n; ++i) order[i] = i;
+    std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wf[x] > wf[y]; });
+    for (int w0 = 0; w0 < n; w0 += per) {
+        const int m = std::min(per, n - w0);
+        std::vector<double> ww(m);
+        for (int q = 0; q < m; ++q) ww[q] = wf[order[w0 + q]];
+        std::vector<int> wc, wfirst, wsize;
+        RAS_TRY(partition(ww, ftotal, wc, wfirst, wsize));
+        cb->fwave0.push_back((int)fcta.size());
+        cb->fwaven.push_back((int)wc.size());
+        for (int q = 0; q < m; ++q) {
+            ffirst[order[w0 + q]] = wfirst[q];
+            fsize[order[w0 + q]] = wsize[q];
+        }
+        for (int k : wc) fcta.push_back(order[w0 + k]);
+    }
     std::vector<SolArgs<AT>> args(n);
     std::vector<FacArgs<AT>> fargs(n);
     RAS_TRY(dalloc(&cb->d_bars, n));
@@ -1793,7 +1816,7 @@ static int batch_setup_t(Coarse *const *cs, int n, CoarseBatch *cb) {
     RAS_CK(cudaMemset(cb->d_bars, 0, n * sizeof(GridBar)));
     cb->grid = (int)cta.size();
     cb->smem = smem;
-    cb->fgrid = (int)fcta.size();
+    cb->fgrid = (int)fcta.size();   // all waves
     cb->fsmem = fsmem;
     return RAS_OK;
 }
@@ -1814,18 +1837,22 @@ int coarse_batch_setup(Coarse *const *cs, int n, CoarseBatch **out) {
 
 int coarse_factor_batch(CoarseBatch *cb, const unsigned char *d_active, cudaStream_t st) {
     RAS_CK(cudaMemsetAsync(cb->d_bars, 0, cb->n * sizeof(GridBar), st));
-    if (cb->prec == 64) {
-        const FacArgs<double> *a = (const FacArgs<double> *)cb->d_fargs;
-        void *args[] = {&a, &cb->d_fcta_inst, &cb->d_ffirst, &cb->d_fsize, &d_active};
-        RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor_batch<double>, dim3(cb->fgrid),
-                                           dim3(256), args, cb->fsmem, st));
-    } else {
-        const FacArgs<float> *a = (const FacArgs<float> *)cb->d_fargs;
-        void *args[] = {&a, &cb->d_fcta_inst, &cb->d_ffirst, &cb->d_fsize, &d_active};
-        RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor_batch<float>, dim3(cb->fgrid),
-                                           dim3(256), args, cb->fsmem, st));
+    for (size_t w = 0; w < cb->fwave0.size(); ++w) {
+        const int *cta = cb->d_fcta_inst + cb->fwave0[w];
+        const dim3 grid(cb->fwaven[w]);
+        if (cb->prec == 64) {
+            const FacArgs<double> *a = (const FacArgs<double> *)cb->d_fargs;
+            void *args[] = {&a, &cta, &cb->d_ffirst, &cb->d_fsize, &d_active};
+            RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor_batch<double>, grid, dim3(256), args,
+                                               cb->fsmem, st));
+        } else {
+            const FacArgs<float> *a = (const FacArgs<float> *)cb->d_fargs;
+            void *args[] = {&a, &cta, &cb->d_ffirst, &cb->d_fsize, &d_active};
+            RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor_batch<float>, grid, dim3(256), args,
+                                               cb->fsmem, st));
+        }
+        RAS_LAUNCHED();
     }
-    RAS_LAUNCHED();
     return RAS_OK;
 }
 
