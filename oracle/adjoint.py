@@ -72,12 +72,17 @@ def storage_coef(prob, p):
 def dF_dtheta_T(prob, res, p, lam):
     """(dF/dtheta)^T lam at state p."""
     g = prob.grid
-    _, _, _, _, m, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    Z, _, _, _, m, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    fl = prob.fluid
+    rho = p * fl.W / (Z * fl.R * fl.T)
     out = np.zeros(g.n)
-    for T, k, sh in ((prob.Tx, res.kx, 1), (prob.Ty, res.ky, g.nx), (prob.Tz, res.kz, g.nx * g.ny)):
+    for T, k, sh, dh in ((prob.Tx, res.kx, 1, 0.0), (prob.Ty, res.ky, g.nx, 0.0),
+                         (prob.Tz, res.kz, g.nx * g.ny, -g.hz)):
         i = np.nonzero(T > 0)[0]
         j = i + sh
-        flux = T[i] * 0.5 * (m[i] + m[j]) * (p[i] - p[j])
+        # the face flux of the residual (gravity term included): only T_f depends on theta
+        phi_ij = p[i] - p[j] - 0.5 * (rho[i] + rho[j]) * prob.gravity * dh
+        flux = T[i] * 0.5 * (m[i] + m[j]) * phi_ij
         w = (lam[i] - lam[j]) * flux / (k[i] + k[j])
         np.add.at(out, i, w * k[j])
         np.add.at(out, j, w * k[i])

@@ -3,19 +3,25 @@
 Oracle; test infrastructure only.
 
 Residual of cell i (Eq. gover_sys integrated over the cell, times its volume V,
-time derivative by Eq. implicit-method-bdf1 / implicit-method-bdf2, gravity off):
+time derivative by Eq. implicit-method-bdf1 / implicit-method-bdf2):
 
-    F_i = V phi_i c(p_i) D_t p_i + sum_faces T_f mbar_f (p_i - p_j)
+    F_i = V phi_i c(p_i) D_t p_i + sum_faces T_f mbar_f (p_i - p_j - rhobar_f g (h_i - h_j))
           + sum_conns T_q mbar_q (p_i - p_q)
 
 with c(p) = (p/Z)(1/p - Z'/Z) evaluated at the new level, m(p) = p / (mu Z),
-D_t p = (p - p^l)/dt (BDF1) or (3p - 4p^l + p^{l-1})/(2 dt) (BDF2).
+D_t p = (p - p^l)/dt (BDF1) or (3p - 4p^l + p^{l-1})/(2 dt) (BDF2), and the gravity
+term of Eq. gover_sys: rho(p) = p W / (Z R T) (Eq. equ:density), h the depth of the
+cell centre, g = Reservoir.gravity along the z axis with depth increasing with the z
+index (h_j - h_i = hz across a +z face; x and y faces are level). gravity = 0 is the
+gravity-free model.
 
 Readings (the paper defers CCFD details to its references):
 * geometric face transmissibility T_f = A_f / (h/(2 k_i) + h/(2 k_j)) (harmonic);
 * mbar_f = (m_i + m_j)/2 (arithmetic mean of the two cells);
 * wells and Dirichlet faces are fixed-pressure connections with a half-cell
-  transmissibility and mbar = (m_i + m(p_q))/2; faces without one are no-flow.
+  transmissibility and mbar = (m_i + m(p_q))/2, at the depth of their cell (no
+  gravity term); faces without one are no-flow;
+* rhobar_f = (rho_i + rho_j)/2 (arithmetic mean, like mbar_f).
 The source term -qRT/W of Eq. gover_sys is carried by the connections.
 
 Jacobian storage: seven arrays (centre, -x, +x, -y, +y, -z, +z) of length N,
@@ -55,6 +61,7 @@ class Problem:
     def __init__(self, res):
         self.res = res
         self.grid = res.grid
+        self.gravity = float(getattr(res, "gravity", 0.0))
         self.fluid = res.fluid
         self.a, self.b = eos.pr_constants(res.fluid)
         self.Tx, self.Ty, self.Tz = face_transmissibilities(res.grid, res.kx, res.ky, res.kz)
@@ -83,25 +90,29 @@ def residual(prob: Problem, p, p_l, p_lm1, dt, order, want_jac=False):
     g = prob.grid
     N = g.n
     p = np.asarray(p, dtype=np.float64)
-    _, _, c, dc, m, dm = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    Z, _, c, dc, m, dm = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    fl = prob.fluid
+    rho = p * fl.W / (Z * fl.R * fl.T)         # Eq. equ:density
+    drho = fl.W * c / (fl.R * fl.T)             # d rho / dp = (W / RT)(1/Z - p Z'/Z^2)
     Dt, dDt = bdf_terms(p, p_l, p_lm1, dt, order)
     F = prob.V * prob.phi * c * Dt
     Jc = prob.V * prob.phi * (dc * Dt + c * dDt)
     J = {s: np.zeros(N) for s in STENCIL}
     # interior faces, one axis at a time (+ side of cell i joins i and i+shift)
-    for T, sh, minus, plus in ((prob.Tx, 1, "-x", "+x"),
-                               (prob.Ty, g.nx, "-y", "+y"),
-                               (prob.Tz, g.nx * g.ny, "-z", "+z")):
+    for T, sh, minus, plus, dh in ((prob.Tx, 1, "-x", "+x", 0.0),
+                                   (prob.Ty, g.nx, "-y", "+y", 0.0),
+                                   (prob.Tz, g.nx * g.ny, "-z", "+z", -g.hz)):
         i = np.nonzero(T > 0)[0]
         j = i + sh
         mbar = 0.5 * (m[i] + m[j])
-        dp = p[i] - p[j]
-        flux = T[i] * mbar * dp
+        gdh = prob.gravity * dh                  # g (h_i - h_j)
+        phi_ij = p[i] - p[j] - 0.5 * (rho[i] + rho[j]) * gdh
+        flux = T[i] * mbar * phi_ij
         np.add.at(F, i, flux)
         np.add.at(F, j, -flux)
         # d flux / d p_i and d flux / d p_j
-        dfi = T[i] * (0.5 * dm[i] * dp + mbar)
-        dfj = T[i] * (0.5 * dm[j] * dp - mbar)
+        dfi = T[i] * (0.5 * dm[i] * phi_ij + mbar * (1.0 - 0.5 * drho[i] * gdh))
+        dfj = T[i] * (0.5 * dm[j] * phi_ij + mbar * (-1.0 - 0.5 * drho[j] * gdh))
         np.add.at(Jc, i, dfi)
         np.add.at(Jc, j, -dfj)
         J[plus][i] += dfj

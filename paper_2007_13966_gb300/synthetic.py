@@ -110,6 +110,7 @@ class Reservoir:
     p0: float = ATM
     dt: float = 0.1 * DAY
     name: str = ""
+    gravity: float = 0.0   # m/s^2 along the z axis, depth increasing with the z index
 
 
 def _gauss_kernel(corr: float) -> np.ndarray:
