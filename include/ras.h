@@ -43,6 +43,11 @@ enum ras_status {
 typedef struct {
     int nx, ny, nz;
     double hx, hy, hz;
+    double gz;             /* gravitational acceleration (m/s^2) along the z axis, depth
+                              increasing with the z index (Eq. gover_sys's rho g grad h
+                              term, rho = pW/(ZRT) of Eq. equ:density, arithmetic mean
+                              over a face); 0 = no gravity. Fixed-pressure connections
+                              are at their cell's depth. */
 } ras_grid;
 
 /* Fluid (Section 2, Eq. attrfactor and the m(omega), omega(T_br) fits;
