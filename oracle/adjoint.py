@@ -82,13 +82,14 @@ def dF_dtheta_T(prob, res, p, lam):
         j = i + sh
         # the face flux of the residual (gravity term included): only T_f depends on theta
         phi_ij = p[i] - p[j] - 0.5 * (rho[i] + rho[j]) * prob.gravity * dh
-        flux = T[i] * 0.5 * (m[i] + m[j]) * phi_ij
+        mf = np.where(phi_ij >= 0, m[i], m[j]) if prob.upwind else 0.5 * (m[i] + m[j])
+        flux = T[i] * mf * phi_ij
         w = (lam[i] - lam[j]) * flux / (k[i] + k[j])
         np.add.at(out, i, w * k[j])
         np.add.at(out, j, w * k[i])
     q = prob.conn_cell
     if q.size:
-        np.add.at(out, q, lam[q] * prob.conn_T * 0.5 * (m[q] + prob.conn_m) * (p[q] - prob.conn_p))
+        np.add.at(out, q, lam[q] * disc.connection_flux(prob, p))
     return out
 
 

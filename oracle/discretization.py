@@ -21,7 +21,11 @@ Readings (the paper defers CCFD details to its references):
 * wells and Dirichlet faces are fixed-pressure connections with a half-cell
   transmissibility and mbar = (m_i + m(p_q))/2, at the depth of their cell (no
   gravity term); faces without one are no-flow;
-* rhobar_f = (rho_i + rho_j)/2 (arithmetic mean, like mbar_f).
+* rhobar_f = (rho_i + rho_j)/2 (arithmetic mean, like mbar_f);
+* Reservoir.upwind = True replaces mbar_f by the mobility of the upstream cell, the
+  one the face potential points away from (i if p_i - p_j - rhobar g (h_i - h_j) >= 0,
+  else j), for faces and connections alike (a fixed pressure upstream: m(p_q)); the
+  density in the gravity term stays the mean.
 The source term -qRT/W of Eq. gover_sys is carried by the connections.
 
 Jacobian storage: seven arrays (centre, -x, +x, -y, +y, -z, +z) of length N,
@@ -62,6 +66,7 @@ class Problem:
         self.res = res
         self.grid = res.grid
         self.gravity = float(getattr(res, "gravity", 0.0))
+        self.upwind = bool(getattr(res, "upwind", False))
         self.fluid = res.fluid
         self.a, self.b = eos.pr_constants(res.fluid)
         self.Tx, self.Ty, self.Tz = face_transmissibilities(res.grid, res.kx, res.ky, res.kz)
@@ -104,15 +109,20 @@ def residual(prob: Problem, p, p_l, p_lm1, dt, order, want_jac=False):
                                    (prob.Tz, g.nx * g.ny, "-z", "+z", -g.hz)):
         i = np.nonzero(T > 0)[0]
         j = i + sh
-        mbar = 0.5 * (m[i] + m[j])
         gdh = prob.gravity * dh                  # g (h_i - h_j)
         phi_ij = p[i] - p[j] - 0.5 * (rho[i] + rho[j]) * gdh
-        flux = T[i] * mbar * phi_ij
+        if prob.upwind:
+            wi = (phi_ij >= 0).astype(np.float64)  # weight of cell i in the face mobility
+        else:
+            wi = np.full(i.size, 0.5)
+        wj = 1.0 - wi
+        mf = wi * m[i] + wj * m[j] if prob.upwind else 0.5 * (m[i] + m[j])
+        flux = T[i] * mf * phi_ij
         np.add.at(F, i, flux)
         np.add.at(F, j, -flux)
         # d flux / d p_i and d flux / d p_j
-        dfi = T[i] * (0.5 * dm[i] * phi_ij + mbar * (1.0 - 0.5 * drho[i] * gdh))
-        dfj = T[i] * (0.5 * dm[j] * phi_ij + mbar * (-1.0 - 0.5 * drho[j] * gdh))
+        dfi = T[i] * (wi * dm[i] * phi_ij + mf * (1.0 - 0.5 * drho[i] * gdh))
+        dfj = T[i] * (wj * dm[j] * phi_ij + mf * (-1.0 - 0.5 * drho[j] * gdh))
         np.add.at(Jc, i, dfi)
         np.add.at(Jc, j, -dfj)
         J[plus][i] += dfj
@@ -120,10 +130,15 @@ def residual(prob: Problem, p, p_l, p_lm1, dt, order, want_jac=False):
     # fixed-pressure connections (wells, Dirichlet faces)
     q = prob.conn_cell
     if q.size:
-        mbar = 0.5 * (m[q] + prob.conn_m)
         dp = p[q] - prob.conn_p
-        np.add.at(F, q, prob.conn_T * mbar * dp)
-        np.add.at(Jc, q, prob.conn_T * (0.5 * dm[q] * dp + mbar))
+        if prob.upwind:
+            wq = (dp >= 0).astype(np.float64)
+            mf = wq * m[q] + (1.0 - wq) * prob.conn_m
+        else:
+            wq = np.full(q.size, 0.5)
+            mf = 0.5 * (m[q] + prob.conn_m)
+        np.add.at(F, q, prob.conn_T * mf * dp)
+        np.add.at(Jc, q, prob.conn_T * (wq * dm[q] * dp + mf))
     J["c"] = Jc
     if want_jac:
         return F, J
@@ -164,7 +179,9 @@ def storage(prob: Problem, p, p_l, p_lm1, dt, order):
 
 
 def connection_flux(prob: Problem, p):
-    """Per-connection outflow T mbar (p_i - p_q) (positive out of the cell)."""
+    """Per-connection outflow T m_f (p_i - p_q) (positive out of the cell)."""
     _, _, _, _, m, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
     q = prob.conn_cell
-    return prob.conn_T * 0.5 * (m[q] + prob.conn_m) * (p[q] - prob.conn_p)
+    dp = p[q] - prob.conn_p
+    mf = np.where(dp >= 0, m[q], prob.conn_m) if prob.upwind else 0.5 * (m[q] + prob.conn_m)
+    return prob.conn_T * mf * dp

@@ -111,6 +111,7 @@ class Reservoir:
     dt: float = 0.1 * DAY
     name: str = ""
     gravity: float = 0.0   # m/s^2 along the z axis, depth increasing with the z index
+    upwind: bool = False   # face mobility of the upstream cell instead of the mean
 
 
 def _gauss_kernel(corr: float) -> np.ndarray:
