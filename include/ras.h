@@ -48,6 +48,10 @@ typedef struct {
                               term, rho = pW/(ZRT) of Eq. equ:density, arithmetic mean
                               over a face); 0 = no gravity. Fixed-pressure connections
                               are at their cell's depth. */
+    int upwind;            /* face mobility: 0 = arithmetic mean of the two cells (default);
+                              1 = the upstream cell's, by the sign of the face potential
+                              (fixed-pressure connections alike; the density of the
+                              gravity term stays the mean) */
 } ras_grid;
 
 /* Fluid (Section 2, Eq. attrfactor and the m(omega), omega(T_br) fits;

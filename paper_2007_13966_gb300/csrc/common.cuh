@@ -109,6 +109,7 @@ struct ras_problem {
     int nx, ny, nz, N;
     double hx, hy, hz, V;
     double a, b, R, T, mu, inv_mu;
+    int upwind = 0;       // face mobility of the upstream cell instead of the mean
     double ghz = 0.0;     // g hz W mu / (R T): rho g hz across a z face = ghz * mbar (rho = that / (g hz) * m)
     double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *phi = nullptr;
     double *kx = nullptr, *ky = nullptr, *kz = nullptr;   // permeabilities (sensitivities)

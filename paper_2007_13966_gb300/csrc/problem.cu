@@ -335,7 +335,7 @@ __global__ void __launch_bounds__(128) k_flux(
     const double *__restrict__ dm, const double *__restrict__ Tx, const double *__restrict__ Ty,
     const double *__restrict__ Tz, const int *__restrict__ conn_ptr,
     const double *__restrict__ conn_p, const double *__restrict__ conn_T,
-    const double *__restrict__ conn_m, double ghz, double *__restrict__ F, JacOut J) {
+    const double *__restrict__ conn_m, double ghz, int upwind, double *__restrict__ F, JacOut J) {
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
     const int j = blockIdx.y, k = blockIdx.z;
     if (i >= nx) return;
@@ -347,14 +347,18 @@ __global__ void __launch_bounds__(128) k_flux(
     double jn[6] = {0, 0, 0, 0, 0, 0};
     // potential difference p_n - p_q - rhobar g (h_n - h_q), rhobar g hz = ghz * mbar;
     // gz: +1 towards the deeper neighbour (+z), -1 towards the shallower, 0 level faces
+    // face mobility: the mean, or the upstream cell's (weights wn, wq of m_n, m_q)
     auto face = [&](double T, int q, int slot, double gz) {
-        const double mbar = 0.5 * (mn + m[q]);
+        const double mq = m[q], mbar = 0.5 * (mn + mq);
         const double gh = gz * ghz;
         const double dphi = (pn - p[q]) + gh * mbar;
-        f += T * mbar * dphi;
+        const bool up_n = dphi >= 0.0;
+        const double mf = upwind ? (up_n ? mn : mq) : mbar;
+        const double wn = upwind ? (up_n ? 1.0 : 0.0) : 0.5, wq = upwind ? 1.0 - wn : 0.5;
+        f += T * mf * dphi;
         if (WANT_J) {
-            jc += T * (0.5 * dmn * dphi + mbar * (1.0 + 0.5 * gh * dmn));
-            jn[slot] = T * (0.5 * dm[q] * dphi + mbar * (-1.0 + 0.5 * gh * dm[q]));
+            jc += T * (wn * dmn * dphi + mf * (1.0 + 0.5 * gh * dmn));
+            jn[slot] = T * (wq * dm[q] * dphi + mf * (-1.0 + 0.5 * gh * dm[q]));
         }
     };
     if (i < nx - 1) face(Tx[n], n + 1, 1, 0.0);
@@ -364,10 +368,11 @@ __global__ void __launch_bounds__(128) k_flux(
     if (k < nz - 1) face(Tz[n], n + nxy, 5, 1.0);
     if (k > 0) face(Tz[n - nxy], n - nxy, 4, -1.0);
     for (int q = conn_ptr[n]; q < conn_ptr[n + 1]; ++q) {
-        const double mbar = 0.5 * (mn + conn_m[q]);
         const double dp = pn - conn_p[q];
-        f += conn_T[q] * mbar * dp;
-        if (WANT_J) jc += conn_T[q] * (0.5 * dmn * dp + mbar);
+        const double mf = upwind ? (dp >= 0.0 ? mn : conn_m[q]) : 0.5 * (mn + conn_m[q]);
+        const double wn = upwind ? (dp >= 0.0 ? 1.0 : 0.0) : 0.5;
+        f += conn_T[q] * mf * dp;
+        if (WANT_J) jc += conn_T[q] * (wn * dmn * dp + mf);
     }
     F[n] = f;
     if (WANT_J) {
@@ -439,7 +444,7 @@ __global__ void __launch_bounds__(256) k_grad_logk(
     const double *__restrict__ kz, const double *__restrict__ Tx, const double *__restrict__ Ty,
     const double *__restrict__ Tz, const int *__restrict__ conn_ptr,
     const double *__restrict__ conn_p, const double *__restrict__ conn_T,
-    const double *__restrict__ conn_m, double ghz, double *__restrict__ grad) {
+    const double *__restrict__ conn_m, double ghz, int upwind, double *__restrict__ grad) {
     const int N = nx * ny * nz, nxy = nx * ny;
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
         const int i = n % nx, j = (n / nx) % ny, k = n / nxy;
@@ -447,7 +452,9 @@ __global__ void __launch_bounds__(256) k_grad_logk(
         double g = 0.0;
         auto face = [&](double T, int q, const double *ka, double gz) {
             const double mbar = 0.5 * (mn + m[q]);
-            const double flux = T * mbar * ((pn - p[q]) + gz * ghz * mbar);   // the residual's face flux
+            const double dphi = (pn - p[q]) + gz * ghz * mbar;
+            const double mf = upwind ? (dphi >= 0.0 ? mn : m[q]) : mbar;
+            const double flux = T * mf * dphi;   // the residual's face flux
             g += (ln - lam[q]) * flux * ka[q] / (ka[n] + ka[q]);
         };
         if (i < nx - 1) face(Tx[n], n + 1, kx, 0.0);
@@ -456,8 +463,11 @@ __global__ void __launch_bounds__(256) k_grad_logk(
         if (j > 0) face(Ty[n - nx], n - nx, ky, 0.0);
         if (k < nz - 1) face(Tz[n], n + nxy, kz, 1.0);
         if (k > 0) face(Tz[n - nxy], n - nxy, kz, -1.0);
-        for (int q = conn_ptr[n]; q < conn_ptr[n + 1]; ++q)
-            g += ln * conn_T[q] * 0.5 * (mn + conn_m[q]) * (pn - conn_p[q]);
+        for (int q = conn_ptr[n]; q < conn_ptr[n + 1]; ++q) {
+            const double dp = pn - conn_p[q];
+            const double mf = upwind ? (dp >= 0.0 ? mn : conn_m[q]) : 0.5 * (mn + conn_m[q]);
+            g += ln * (conn_T[q] * mf * dp);
+        }
         grad[n] += g;
     }
 }
@@ -494,6 +504,7 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     if (grid->nx < 1 || grid->ny < 1 || grid->nz < 1) return RAS_EINVAL;
     if (!(grid->hx > 0 && grid->hy > 0 && grid->hz > 0)) return RAS_EINVAL;
     if (!std::isfinite(grid->gz) || (grid->gz != 0.0 && !(eos->W > 0 && std::isfinite(eos->W)))) return RAS_EINVAL;
+    if (grid->upwind != 0 && grid->upwind != 1) return RAS_EINVAL;
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > (1LL << 30)) return RAS_EINVAL;
     if (!rock->kx || !rock->ky || !rock->kz || !rock->phi) return RAS_EINVAL;
@@ -507,6 +518,7 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     P->V = grid->hx * grid->hy * grid->hz;
     P->R = eos->R; P->T = eos->T; P->mu = eos->mu; P->inv_mu = 1.0 / eos->mu;
     P->ghz = grid->gz * grid->hz * eos->W * eos->mu / (eos->R * eos->T);
+    P->upwind = grid->upwind;
     // Eq. attrfactor and the m(omega) fit (first branch at omega = 0.491)
     const double omega = eos->omega_from_Tb ? acentric_factor(eos->Tc, eos->pc, eos->Tb) : eos->omega;
     const double mfit = omega <= 0.491 ? 0.37464 + 1.54226 * omega - 0.26992 * omega * omega
@@ -592,10 +604,10 @@ int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const 
     for (int s = 0; s < 7; ++s) jo.c[s] = J ? J[s] : nullptr;
     if (J) {
         k_flux<true><<<g, t, 0, st>>>(P->nx, P->ny, P->nz, p, P->eos_m, P->eos_dm, P->Tx, P->Ty,
-                                      P->Tz, P->conn_ptr, P->conn_p, P->conn_T, P->conn_m, P->ghz, F, jo);
+                                      P->Tz, P->conn_ptr, P->conn_p, P->conn_T, P->conn_m, P->ghz, P->upwind, F, jo);
     } else {
         k_flux<false><<<g, t, 0, st>>>(P->nx, P->ny, P->nz, p, P->eos_m, P->eos_dm, P->Tx, P->Ty,
-                                       P->Tz, P->conn_ptr, P->conn_p, P->conn_T, P->conn_m, P->ghz, F, jo);
+                                       P->Tz, P->conn_ptr, P->conn_p, P->conn_T, P->conn_m, P->ghz, P->upwind, F, jo);
     }
     RAS_LAUNCHED();
     return RAS_OK;
@@ -684,7 +696,7 @@ extern "C" int ras_grad_logk(ras_problem *P, const double *p, const double *lam,
     RAS_LAUNCHED();
     k_grad_logk<<<grid_for(P->N), 256, 0, st>>>(P->nx, P->ny, P->nz, p, P->eos_m, lam, P->kx, P->ky,
                                                  P->kz, P->Tx, P->Ty, P->Tz, P->conn_ptr, P->conn_p,
-                                                 P->conn_T, P->conn_m, P->ghz, grad);
+                                                 P->conn_T, P->conn_m, P->ghz, P->upwind, grad);
     RAS_LAUNCHED();
     return RAS_OK;
 }

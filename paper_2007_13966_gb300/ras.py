@@ -30,7 +30,8 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
 
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
-                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double), ("gz", C.c_double)]
+                ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double), ("gz", C.c_double),
+                ("upwind", C.c_int)]
 
 
 class Eos(C.Structure):
@@ -196,7 +197,8 @@ class Problem:
         self._cp = torch.as_tensor(res.conns.p, **f64).contiguous()
         self._cT = torch.as_tensor(res.conns.T, **f64).contiguous()
         fl = res.fluid
-        grid = Grid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, float(getattr(res, "gravity", 0.0)))
+        grid = Grid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, float(getattr(res, "gravity", 0.0)),
+                    1 if getattr(res, "upwind", False) else 0)
         eos = Eos(fl.Tc, fl.pc, 0.0 if fl.omega_from_Tb else fl.omega, fl.Tb,
                   1 if fl.omega_from_Tb else 0, fl.T, fl.R, fl.W, fl.mu)
         rock = Rock(self._kx.data_ptr(), self._ky.data_ptr(), self._kz.data_ptr(),
