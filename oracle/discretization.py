@@ -25,7 +25,12 @@ Readings (the paper defers CCFD details to its references):
 * Reservoir.upwind = True replaces mbar_f by the mobility of the upstream cell, the
   one the face potential points away from (i if p_i - p_j - rhobar g (h_i - h_j) >= 0,
   else j), for faces and connections alike (a fixed pressure upstream: m(p_q)); the
-  density in the gravity term stays the mean.
+  density in the gravity term stays the mean;
+* fixed injection rates (the paper's Case-2 alternative to a fixed injection pressure): a
+  Darcy velocity v into the domain through boundary faces of total area A of a cell
+  carries (p/Z) v A of the equation's transported quantity (Eq. gover_sys divided by
+  W / (RT)), the cell's own p/Z for the injected gas: F_i -= mu m(p_i) Q_i with
+  Q_i = v A (Reservoir.rate_Q, m^3/s per cell; positive into the cell). Oracle only.
 The source term -qRT/W of Eq. gover_sys is carried by the connections.
 
 Jacobian storage: seven arrays (centre, -x, +x, -y, +y, -z, +z) of length N,
@@ -67,6 +72,8 @@ class Problem:
         self.grid = res.grid
         self.gravity = float(getattr(res, "gravity", 0.0))
         self.upwind = bool(getattr(res, "upwind", False))
+        rq = getattr(res, "rate_Q", None)
+        self.rate_Q = None if rq is None else np.asarray(rq, dtype=np.float64)
         self.fluid = res.fluid
         self.a, self.b = eos.pr_constants(res.fluid)
         self.Tx, self.Ty, self.Tz = face_transmissibilities(res.grid, res.kx, res.ky, res.kz)
@@ -139,6 +146,11 @@ def residual(prob: Problem, p, p_l, p_lm1, dt, order, want_jac=False):
             mf = 0.5 * (m[q] + prob.conn_m)
         np.add.at(F, q, prob.conn_T * mf * dp)
         np.add.at(Jc, q, prob.conn_T * (wq * dm[q] * dp + mf))
+    # fixed injection rates: the cell's p/Z = mu m enters with the Darcy volume rate
+    if prob.rate_Q is not None:
+        mu = prob.fluid.mu
+        F -= mu * m * prob.rate_Q
+        Jc -= mu * dm * prob.rate_Q
     J["c"] = Jc
     if want_jac:
         return F, J
@@ -185,3 +197,11 @@ def connection_flux(prob: Problem, p):
     dp = p[q] - prob.conn_p
     mf = np.where(dp >= 0, m[q], prob.conn_m) if prob.upwind else 0.5 * (m[q] + prob.conn_m)
     return prob.conn_T * mf * dp
+
+
+def rate_inflow(prob: Problem, p):
+    """Per-cell inflow mu m(p) Q of the fixed injection rates (zero without them)."""
+    if prob.rate_Q is None:
+        return np.zeros(prob.grid.n)
+    _, _, _, _, m, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    return prob.fluid.mu * m * prob.rate_Q

@@ -183,6 +183,8 @@ class Problem:
     """ras_problem handle built from a synthetic.Reservoir."""
 
     def __init__(self, res, device="cuda"):
+        if getattr(res, "rate_Q", None) is not None:
+            raise NotImplementedError("fixed injection rates (Reservoir.rate_Q) are not in the library")
         g = res.grid
         self.res = res
         self.N = g.n

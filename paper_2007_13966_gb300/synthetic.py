@@ -112,6 +112,7 @@ class Reservoir:
     name: str = ""
     gravity: float = 0.0   # m/s^2 along the z axis, depth increasing with the z index
     upwind: bool = False   # face mobility of the upstream cell instead of the mean
+    rate_Q: np.ndarray | None = None   # [N] m^3/s of Darcy inflow through boundary faces per cell
 
 
 def _gauss_kernel(corr: float) -> np.ndarray:
