@@ -30,7 +30,12 @@ Readings (the paper defers CCFD details to its references):
   Darcy velocity v into the domain through boundary faces of total area A of a cell
   carries (p/Z) v A of the equation's transported quantity (Eq. gover_sys divided by
   W / (RT)), the cell's own p/Z for the injected gas: F_i -= mu m(p_i) Q_i with
-  Q_i = v A (Reservoir.rate_Q, m^3/s per cell; positive into the cell). Oracle only.
+  Q_i = v A (Reservoir.rate_Q, m^3/s per cell; positive into the cell). Oracle only;
+* Reservoir.conservative = True takes the accumulation in conservative form,
+  V phi D_t (p/Z) (the time derivative of Eq. mass conservation's phi rho, divided by
+  W / (RT)), instead of Eq. gover_sys's V phi c(p) D_t p; the two agree for an ideal
+  gas (Z = 1) and differ at O(dt) otherwise; the conservative form keeps the discrete
+  mass of a closed domain exactly. Oracle only.
 The source term -qRT/W of Eq. gover_sys is carried by the connections.
 
 Jacobian storage: seven arrays (centre, -x, +x, -y, +y, -z, +z) of length N,
@@ -72,6 +77,7 @@ class Problem:
         self.grid = res.grid
         self.gravity = float(getattr(res, "gravity", 0.0))
         self.upwind = bool(getattr(res, "upwind", False))
+        self.conservative = bool(getattr(res, "conservative", False))
         rq = getattr(res, "rate_Q", None)
         self.rate_Q = None if rq is None else np.asarray(rq, dtype=np.float64)
         self.fluid = res.fluid
@@ -107,8 +113,15 @@ def residual(prob: Problem, p, p_l, p_lm1, dt, order, want_jac=False):
     rho = p * fl.W / (Z * fl.R * fl.T)         # Eq. equ:density
     drho = fl.W * c / (fl.R * fl.T)             # d rho / dp = (W / RT)(1/Z - p Z'/Z^2)
     Dt, dDt = bdf_terms(p, p_l, p_lm1, dt, order)
-    F = prob.V * prob.phi * c * Dt
-    Jc = prob.V * prob.phi * (dc * Dt + c * dDt)
+    if prob.conservative:
+        # D_t of P = p/Z with the same BDF weights; dP/dp = c
+        P = lambda q: q / eos.eos_state(q, prob.fluid, prob.a, prob.b)[0]
+        DtP, _ = bdf_terms(p / Z, P(p_l), P(p_lm1) if order == 2 else None, dt, order)
+        F = prob.V * prob.phi * DtP
+        Jc = prob.V * prob.phi * c * dDt
+    else:
+        F = prob.V * prob.phi * c * Dt
+        Jc = prob.V * prob.phi * (dc * Dt + c * dDt)
     J = {s: np.zeros(N) for s in STENCIL}
     # interior faces, one axis at a time (+ side of cell i joins i and i+shift)
     for T, sh, minus, plus, dh in ((prob.Tx, 1, "-x", "+x", 0.0),
@@ -184,8 +197,13 @@ def stencil_matvec(grid, J, x):
 
 
 def storage(prob: Problem, p, p_l, p_lm1, dt, order):
-    """The accumulation part V phi c D_t p of each cell."""
-    _, _, c, _, _, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    """The accumulation part of each cell: V phi c D_t p, or V phi D_t (p/Z) in the
+    conservative form."""
+    Z, _, c, _, _, _ = eos.eos_state(p, prob.fluid, prob.a, prob.b)
+    if prob.conservative:
+        P = lambda q: q / eos.eos_state(q, prob.fluid, prob.a, prob.b)[0]
+        DtP, _ = bdf_terms(p / Z, P(p_l), P(p_lm1) if order == 2 else None, dt, order)
+        return prob.V * prob.phi * DtP
     Dt, _ = bdf_terms(p, p_l, p_lm1, dt, order)
     return prob.V * prob.phi * c * Dt
 

@@ -185,6 +185,8 @@ class Problem:
     def __init__(self, res, device="cuda"):
         if getattr(res, "rate_Q", None) is not None:
             raise NotImplementedError("fixed injection rates (Reservoir.rate_Q) are not in the library")
+        if getattr(res, "conservative", False):
+            raise NotImplementedError("the conservative accumulation form is not in the library")
         g = res.grid
         self.res = res
         self.N = g.n

@@ -113,6 +113,7 @@ class Reservoir:
     gravity: float = 0.0   # m/s^2 along the z axis, depth increasing with the z index
     upwind: bool = False   # face mobility of the upstream cell instead of the mean
     rate_Q: np.ndarray | None = None   # [N] m^3/s of Darcy inflow through boundary faces per cell
+    conservative: bool = False          # accumulation as phi D_t(p/Z) instead of phi c(p) D_t p
 
 
 def _gauss_kernel(corr: float) -> np.ndarray:
