@@ -107,10 +107,15 @@ def adjoint_gradient(res, nsteps, cells, rtol=1e-12):
         A = disc.jacobian_csr(prob.grid, J)
         rhs = np.zeros(prob.grid.n)
         rhs[cells] -= 2.0 * P[l][cells]
+        # dF^{l+1}/dp^l = -(2/dt) s and dF^{l+2}/dp^l = (1/(2 dt)) s, with s = V phi c at
+        # the newer state in Eq. gover_sys's form (c(p) D_t p) and at p^l itself in the
+        # conservative form (D_t (p/Z), d(p/Z)/dp = c)
         if l + 1 <= L:
-            rhs += (2.0 / dt) * storage_coef(prob, P[l + 1]) * lam[l + 1]
+            s1 = storage_coef(prob, P[l] if prob.conservative else P[l + 1])
+            rhs += (2.0 / dt) * s1 * lam[l + 1]
         if l + 2 <= L:
-            rhs -= (0.5 / dt) * storage_coef(prob, P[l + 2]) * lam[l + 2]
+            s2 = storage_coef(prob, P[l] if prob.conservative else P[l + 2])
+            rhs -= (0.5 / dt) * s2 * lam[l + 2]
         lam[l] = spla.spsolve(A.T.tocsc(), rhs)
         grad += dF_dtheta_T(prob, res, P[l], lam[l])
     return objective(P, cells), grad, lam[1:L + 1]
