@@ -5,9 +5,10 @@
 // updates -- while the scalar logic of each reservoir (Givens rotations, stop
 // tests, cubic backtracking) stays on the host. One host synchronisation per
 // Arnoldi step serves the whole batch. With two-level V-cycle preconditioners
-// (Eq. equ:v-cycle) the fine-level solves and residuals are batched the same way
-// and each reservoir's exact coarse correction is one cooperative launch of its
-// own.
+// (Eq. equ:v-cycle) the fine-level solves and residuals are batched the same way,
+// the exact coarse corrections of all reservoirs run in one cooperative launch (a
+// group of CTAs and a barrier word per reservoir), and their coarse block
+// eliminations in a few such launches (waves of reservoirs).
 //
 // Vectors of the batch are the reservoirs' vectors concatenated (each starting
 // at a multiple of 32 cells). The vector kernels run on chunks of BCH cells of
