@@ -299,16 +299,20 @@ const char *ras_status_string(int status);
 /* ||x||_2 of a device vector, written to the DEVICE scalar *result, without
  * allocating any memory. The paper has no counterpart: this is library
  * plumbing for callers that cannot allocate device memory at call time (a
- * framework that owns all device memory through its own pool, a caller
- * recording a CUDA stream capture, a latency-critical loop). It computes the
- * same deterministic reduction as the norm of residual_eval, with its
- * partial sums (608 doubles) in a static device array inside the library
- * that every device which loads the library keeps until the process exits.
- * x: device [n], 0 <= n <= 2^31 - 1 (larger n: RAS_EINVAL). Asynchronous on
- * `stream`. The first call on a device looks up that array's device address
- * (once per device, with the device current); make that first call before
- * any stream capture. All calls share the one array: calls that overlap on
- * the GPU (different streams, or different host threads) race and must be
+ * framework that owns all device memory through its own pool, where a raw
+ * cudaMalloc behind its back fragments memory or breaks its budget; a
+ * latency-critical loop that cannot afford an allocation, its implicit
+ * synchronisation or its failure). It computes the same deterministic
+ * reduction as the norm of residual_eval (bit for bit), with its partial sums
+ * (608 doubles, 4.75 KB) in a static device array inside the library that
+ * every device which loads the library keeps until the process exits.
+ * x: device [n], 0 <= n <= 2^31 - 1 (larger n or n < 0: RAS_EINVAL, checked
+ * before any CUDA call). Asynchronous on `stream`. The first call in a
+ * device's context looks up that array's device address (once per device
+ * and context, with the device current; a context created after
+ * cudaDeviceReset looks it up again); make that first call before any
+ * stream capture. All calls share the one array: calls that overlap on the
+ * GPU (different streams, or different host threads) race and must be
  * serialised by the caller. Nothing in the array needs clearing: every call
  * overwrites all of it before reading it. */
 int ras_norm2_noalloc(const double *x, long long n, double *result, void *stream);

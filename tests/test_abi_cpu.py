@@ -47,3 +47,15 @@ def test_binding_covers_the_header(lib):
 def test_status_strings_without_gpu(lib):
     assert lib.ras_status_string(0) == b"ok"
     assert b"pivot" in lib.ras_status_string(-5)
+
+
+def test_noalloc_rejects_out_of_range_sizes_on_the_host(lib):
+    """ras_norm2_noalloc refuses n < 0 and n > 2^31 - 1 before any CUDA call
+    (its reduction loop has a 64-bit index, so sizes up to the limit cannot
+    overflow a stride step); nothing is launched, so this runs without a GPU."""
+    import ctypes as C
+    from paper_2007_13966_gb300 import ras
+    fake = C.c_void_p(0x1000)   # never dereferenced: the size check comes first
+    for n in (2 ** 31, 2 ** 40, -1):
+        assert lib.ras_norm2_noalloc(fake, C.c_longlong(n), fake, None) == ras.RAS_EINVAL
+    assert lib.ras_norm2_noalloc(fake, C.c_longlong(8), None, None) == ras.RAS_EINVAL
