@@ -279,25 +279,34 @@ def gb300_arm(args):
         return {"p_l": st["p_l"].clone(), "p_lm1": st["p_lm1"].clone(), "step": st["step"]}
 
     s0 = clone(state)   # the state the timed steps start from
-    # timed region: K implicit steps on resident state
+    # timed region: K implicit steps on resident state (no per-launch events inside)
     sampler = ClockSampler(local)
     sampler.start()
-    pc.timing(True)
-    pc.timing_read(reset=True)
     n0 = ras.kernel_launches()
     t, outs = timed(lambda: run_steps(gp, pc, res, state, args.steps, torch), torch, dist_on)
     launches = ras.kernel_launches() - n0
-    apply_ms, apply_n = pc.timing_read(reset=True)
-    pc.timing(False)
     clocks = sampler.stop()
     t = max_over_ranks(t, dist_on)
     sec_per_step = t / args.steps
 
-    # e2e: same steps through the public API with host-resident inputs
-    pin = {"p_l": state["p_l"].cpu().pin_memory(), "p_lm1": state["p_lm1"].cpu().pin_memory()}
-    te, _ = timed(lambda: run_steps(gp, pc, res, state, args.steps, torch, e2e_host=pin), torch,
-                  dist_on)
+    # e2e: the SAME K steps again from the same starting state, through the public
+    # API with each step's inputs copied from pinned host memory and the new state
+    # copied back inside the timed region
+    se = clone(s0)
+    pin = {"p_l": s0["p_l"].cpu().pin_memory(), "p_lm1": s0["p_lm1"].cpu().pin_memory()}
+    te, outs_e = timed(lambda: run_steps(gp, pc, res, se, args.steps, torch, e2e_host=pin), torch,
+                       dist_on)
     te = max_over_ranks(te, dist_on)
+
+    # the subdomain-solve kernel's launch times: the same K steps a third time with
+    # CUDA events recorded around every launch of it (kept out of the timed step)
+    sa_ = clone(s0)
+    pc.timing(True)
+    pc.timing_read(reset=True)
+    run_steps(gp, pc, res, sa_, args.steps, torch)
+    torch.cuda.synchronize()
+    apply_ms, apply_n = pc.timing_read(reset=True)
+    pc.timing(False)
 
     # the all-FP64 form on the same step sequence, for the FP32-vs-FP64 comparison
     fp64 = None
@@ -368,7 +377,10 @@ def gb300_arm(args):
         "fgmres_iters": [o["lin_total"] for o in outs],
         "clocks": clocks,
         "e2e": {"value": te / args.steps, "unit": "s/step",
-                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8},
+                "h2d_bytes_per_step": 2 * N * 8, "d2h_bytes_per_step": N * 8,
+                "same_steps_as_value": True,
+                "newton_iters": [o["newton_iters"] for o in outs_e],
+                "fgmres_iters": [o["lin_total"] for o in outs_e]},
         "gpu_launches": int(launches),
         "roofline": {
             "kernel": "k_ras_apply (fine-level subdomain ILU(0) solves, %s factors)"
@@ -379,6 +391,8 @@ def gb300_arm(args):
             "peak_kind": peak_kind,
             "bytes_per_launch": bytes_per_launch,
             "avg_launch_us": avg_s * 1e6, "launches": int(apply_n),
+            "launch_times": "CUDA events around every launch of the kernel, on its stream, in a "
+                            "separate pass over the same K steps (not inside the timed steps)",
         },
         "fp64_form": fp64,
     }
@@ -427,6 +441,27 @@ def oracle_step_seconds():
     return dt * (1048576 / g.n), dt
 
 
+def oracle_residual_anchor():
+    """Times one oracle residual + Jacobian evaluation on the full 128x128x64 grid
+    and on the 32x32x16 sample grid: a measured anchor for scaling the sample's
+    step time by the cell ratio (returns both times and their ratio)."""
+    import numpy as np
+    from oracle import discretization as disc
+    from paper_2007_13966_gb300 import synthetic as syn
+    out = {}
+    for name, res in (("1m", syn.config_3d_1m()),
+                      ("sample", syn.lognormal_reservoir(32, 32, 16, 25.0, 25.0, 12.5, sigma=1.5,
+                                                         corr=8.0, seed_k=3, seed_phi=4))):
+        prob = disc.Problem(res)
+        p = syn.random_pressure(res, 3, 1.0, 3.0)
+        disc.residual(prob, p, 0.99 * p, 0.98 * p, res.dt, 2, want_jac=True)   # warm-up
+        t0 = time.perf_counter()
+        disc.residual(prob, p, 0.99 * p, 0.98 * p, res.dt, 2, want_jac=True)
+        out[name] = time.perf_counter() - t0
+    return {"residual_jacobian_1m_s": out["1m"], "residual_jacobian_sample_s": out["sample"],
+            "measured_ratio": out["1m"] / out["sample"], "cell_ratio": 64}
+
+
 def cpu_baseline_subprocess(args):
     env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
                CUDA_VISIBLE_DEVICES="")
@@ -438,12 +473,13 @@ def cpu_baseline_subprocess(args):
         return {"value": None, "unit": "s/step", "cores": 1, "kind": "oracle",
                 "sample": SAMPLE, "error": str(e)[:200]}
     return {"value": d["value"], "unit": "s/step", "cores": 1, "kind": "oracle",
-            "sample": SAMPLE, "sample_seconds": d["raw"]}
+            "sample": SAMPLE, "sample_seconds": d["raw"], "host_cores": os.cpu_count(),
+            "anchor": d.get("anchor")}
 
 
 def cpu_sample_main():
     v, raw = oracle_step_seconds()
-    print(json.dumps({"value": v, "raw": raw}))
+    print(json.dumps({"value": v, "raw": raw, "anchor": oracle_residual_anchor()}))
 
 
 def reference_arm(args):

@@ -168,7 +168,8 @@ typedef struct ras_precond ras_precond;
  * (Eq. attrfactor), the harmonic-average face transmissibilities of the
  * two-point flux scheme (Section 2, CCFD) and copies phi and the connections.
  * The grid must have nx, ny >= 1, nz >= 1 and positive spacings; N = nx*ny*nz
- * must fit in int32. Returns RAS_EINVAL on bad arguments. */
+ * must fit in int32. Returns RAS_EINVAL on bad arguments, RAS_ENOROOT if a
+ * fixed connection pressure has no admissible root (see residual_eval). */
 int ras_problem_create(const ras_grid *grid, const ras_eos *eos, const ras_rock *rock,
                        void *stream, ras_problem **out);
 void ras_problem_destroy(ras_problem *prob);
@@ -182,7 +183,13 @@ void ras_problem_destroy(ras_problem *prob);
  * closed form under Eq. gover_sys. p, p_l, p_lm1: device [N] (p_lm1 unused
  * for bdf_order 1). F: device [N] output. J: if non-NULL, its seven arrays
  * (device [N] each) receive the exact Jacobian. normF: if non-NULL, HOST
- * pointer that receives ||F||_2 (the call then synchronises the stream). */
+ * pointer that receives ||F||_2 (the call then synchronises the stream).
+ * Root selection (the paper defers it to its references): Z is the largest
+ * real root, chosen in FP64; a cell whose root is not admissible (Z not finite,
+ * Z <= B, or a multiple root where dZ/dp is unbounded) gets F_n = NaN and sets
+ * the problem's no-root flag, which this call reports as RAS_ENOROOT when
+ * normF is requested (the flag is then cleared), else the next synchronising
+ * call on the problem does. */
 int residual_eval(ras_problem *prob, const double *p, const double *p_l, const double *p_lm1,
                   double dt, int bdf_order, double *F, const ras_stencil *J, double *normF,
                   void *stream);
@@ -240,7 +247,9 @@ int gmres_solve(ras_problem *prob, const ras_stencil *J, ras_precond *pc, const 
  * gmres_solve with pc refactored every iteration, cubic backtracking line
  * search with sufficient decrease ||F(X + lambda s)|| <= (1 - alpha lambda)||F||,
  * stop on Eq. equ:nonlinear_stop. p: device [N], in: initial guess, out:
- * p^{l+1}. stats may be NULL. */
+ * p^{l+1}. stats may be NULL. A starting state with a cell without an
+ * admissible EOS root returns RAS_ENOROOT; a line-search trial state without
+ * one is treated as a failed trial (the step is shortened). */
 int newton_step(ras_problem *prob, ras_precond *pc, double *p, const double *p_l,
                 const double *p_lm1, double dt, int bdf_order, const ras_newton_opts *opts,
                 ras_newton_stats *stats, void *stream);

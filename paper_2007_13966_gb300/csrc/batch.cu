@@ -581,6 +581,7 @@ static int bnewton(ras_batch *B, double *const *p, const double *const *pl, cons
     for (int i = 0; i < n; ++i) vecs[i] = B->P[i]->nF[0];
     RAS_TRY(b_norms_of(B, vecs, all, fnorm, st));
     for (int i = 0; i < n; ++i) {
+        if (noroot_take(B->P[i])) return RAS_ENOROOT;
         if (!std::isfinite(fnorm[i])) return RAS_ENAN;
         f0[i] = fnorm[i];
         tol[i] = std::max(o.rtol * f0[i], o.atol);
@@ -651,6 +652,7 @@ static int bnewton(ras_batch *B, double *const *p, const double *const *pl, cons
             RAS_TRY(b_norms_of(B, vecs, search, ft, st));
             for (int i = 0; i < n; ++i) {
                 if (!search[i]) continue;
+                if (noroot_take(B->P[i])) ft[i] = NAN;
                 if (std::isfinite(ft[i]) && ft[i] <= (1.0 - o.ls_alpha * lam[i]) * fnorm[i]) {
                     search[i] = 0;
                     if (stats && stats[i].lambdas && k[i] < stats[i].lin_history_cap) stats[i].lambdas[k[i]] = lam[i];

@@ -117,6 +117,9 @@ struct ras_problem {
     int *conn_ptr = nullptr;       // [N+1] CSR of connections per cell
     double *conn_p = nullptr, *conn_T = nullptr, *conn_m = nullptr;
     double *eos_m = nullptr, *eos_dm = nullptr;  // per-cell scratch of the residual
+    // set by the EOS kernels when a cell (or a fixed connection pressure) has no
+    // admissible root; mapped pinned host memory, read after a synchronisation
+    int *noroot_h = nullptr, *noroot_d = nullptr;
     ras::ReduceWs red;
     // Krylov workspace (allocated on first use for the largest restart seen)
     int kr_m = 0;

@@ -415,6 +415,7 @@ int newton(ras_problem *P, ras_precond *pc, double *p, const double *pl, const d
     RAS_TRY(residual_eval_impl(P, P->nX[cur], pl, plm1, dt, order, P->nF[cur], P->nJ[cur], st));
     ++nres;
     RAS_TRY(norm2_sync(P->red, P->nF[cur], N, &fnorm, st));
+    if (noroot_take(P)) return RAS_ENOROOT;   // the starting state has no admissible EOS root
     if (!std::isfinite(fnorm)) return RAS_ENAN;
     const double f0 = fnorm;
     const double tol = std::max(o.rtol * f0, o.atol);
@@ -453,6 +454,7 @@ int newton(ras_problem *P, ras_precond *pc, double *p, const double *pl, const d
             RAS_TRY(residual_eval_impl(P, P->nX[nxt], pl, plm1, dt, order, P->nF[nxt], P->nJ[nxt], st));
             ++nres;
             RAS_TRY(norm2_sync(P->red, P->nF[nxt], N, &ft, st));
+            if (noroot_take(P)) ft = NAN;   // an inadmissible trial state: shorten the step
             if (std::isfinite(ft) && ft <= (1.0 - o.ls_alpha * lam) * fnorm) break;
             const double phit = std::isfinite(ft) ? 0.5 * ft * ft : 1e300;
             const double nl = backtrack(lam, lam_prev, phi0, slope, phit, phi_prev, first);

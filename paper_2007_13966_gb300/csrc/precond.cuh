@@ -98,4 +98,6 @@ double backtrack(double lam, double lam_prev, double phi0, double slope, double 
                  double phi_prev, bool first);
 int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const double *plm1,
                        double dt, int order, double *F, double *const *J, cudaStream_t st);
+// reads and clears the problem's no-admissible-EOS-root flag (after a synchronisation)
+bool noroot_take(ras_problem *P);
 }  // namespace ras

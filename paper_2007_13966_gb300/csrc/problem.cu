@@ -262,6 +262,7 @@ __device__ __forceinline__ float cubic_root_f32(float c2, float c1, float c0) {
 
 struct EosOut {
     double c, dc, m, dm;
+    bool ok;   // an admissible root: Z finite, Z > B, f_Z != 0
 };
 
 __device__ __forceinline__ EosOut eos_cell(double p, const EosConst &E) {
@@ -277,6 +278,28 @@ __device__ __forceinline__ EosOut eos_cell(double p, const EosConst &E) {
         const double f = ((Z + c2) * Z + c1) * Z + c0;
         const double fz = (3.0 * Z + 2.0 * c2) * Z + c1;
         Z -= f / fz;
+    }
+    // Root selection in FP64: the FP32 closed form decides between one and three
+    // real roots in FP32, and near a pair of close roots it can start Newton on
+    // another root than the largest. The other two roots solve the deflated
+    // quadratic t^2 + (c2 + Z) t + (c1 + (c2 + Z) Z) = 0; if it has a real root
+    // above Z, that root is the largest: take it and polish it.
+    {
+        const double q1 = c2 + Z, q0 = c1 + q1 * Z;
+        const double dq = q1 * q1 - 4.0 * q0;
+        if (dq >= 0.0) {
+            double Zq = 0.5 * (-q1 + sqrt(dq));
+            if (Zq > Z) {
+#pragma unroll
+                for (int it = 0; it < 2; ++it) {
+                    const double f = ((Zq + c2) * Zq + c1) * Zq + c0;
+                    const double fz = (3.0 * Zq + 2.0 * c2) * Zq + c1;
+                    const double step = f / fz;
+                    if (isfinite(step)) Zq -= step;
+                }
+                Z = Zq;
+            }
+        }
     }
     // partial derivatives of f(Z, p) with A = alpha p, B = beta p
     const double fZ = 3.0 * Z * Z - 2.0 * (1.0 - B) * Z + (A - 3.0 * B * B - 2.0 * B);
@@ -295,6 +318,7 @@ __device__ __forceinline__ EosOut eos_cell(double p, const EosConst &E) {
     o.dc = -2.0 * dZ * iZ2 - p * d2Z * iZ2 + 2.0 * p * dZ * dZ * iZ2 * iZ;
     o.m = p * iZ * E.inv_mu;                                       // p / (mu Z)
     o.dm = o.c * E.inv_mu;
+    o.ok = isfinite(Z) && Z > B && fZ != 0.0 && isfinite(o.c) && isfinite(o.dc);
     return o;
 }
 
@@ -303,10 +327,14 @@ __global__ void __launch_bounds__(256) k_eos_storage(
     int N, EosConst E, double Vol, double inv_dt, int order, const double *__restrict__ p,
     const double *__restrict__ pl, const double *__restrict__ plm1, const double *__restrict__ phi,
     double *__restrict__ F, double *__restrict__ Jc, double *__restrict__ m_out,
-    double *__restrict__ dm_out) {
+    double *__restrict__ dm_out, int *__restrict__ noroot) {
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
         const double pn = p[n];
-        const EosOut o = eos_cell(pn, E);
+        EosOut o = eos_cell(pn, E);
+        if (!o.ok) {   // no admissible root: flag it and poison the cell's residual
+            *noroot = 1;
+            o.c = o.dc = o.m = o.dm = __longlong_as_double(0x7ff8000000000000LL);
+        }
         double Dt, g;
         if (order == 1) {
             Dt = (pn - pl[n]) * inv_dt;
@@ -383,9 +411,12 @@ __global__ void __launch_bounds__(128) k_flux(
 }
 
 __global__ void k_conn_mobility(int nconn, EosConst E, const double *__restrict__ cp,
-                                double *__restrict__ cm) {
-    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nconn; q += gridDim.x * blockDim.x)
-        cm[q] = eos_cell(cp[q], E).m;
+                                double *__restrict__ cm, int *__restrict__ noroot) {
+    for (int q = blockIdx.x * blockDim.x + threadIdx.x; q < nconn; q += gridDim.x * blockDim.x) {
+        const EosOut o = eos_cell(cp[q], E);
+        if (!o.ok) *noroot = 1;
+        cm[q] = o.m;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -472,6 +503,14 @@ __global__ void __launch_bounds__(256) k_grad_logk(
     }
 }
 
+// reads and clears the problem's no-admissible-root flag (the stream must have
+// been synchronised after the kernels that may set it)
+bool noroot_take(ras_problem *P) {
+    if (!P->noroot_h || !*reinterpret_cast<volatile int *>(P->noroot_h)) return false;
+    *reinterpret_cast<volatile int *>(P->noroot_h) = 0;
+    return true;
+}
+
 static EosConst eos_const(const ras_problem *P) {
     EosConst E;
     E.alpha = P->a / (P->R * P->R * P->T * P->T);
@@ -536,6 +575,10 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
         (rc = dalloc(&P->kx, N)) || (rc = dalloc(&P->ky, N)) || (rc = dalloc(&P->kz, N)))
         return fail(rc);
     if ((rc = reduce_ws_init(P->red))) return fail(rc);
+    if (cudaHostAlloc((void **)&P->noroot_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
+        cudaHostGetDevicePointer((void **)&P->noroot_d, P->noroot_h, 0) != cudaSuccess)
+        return fail(RAS_ENOMEM);
+    *P->noroot_h = 0;
     P->nconn = rock->nconn;
     int *cell = nullptr;
     if ((rc = dalloc(&cell, rock->nconn))) return fail(rc);
@@ -564,12 +607,13 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     counted();
     if (rock->nconn > 0) {
         k_conn_mobility<<<grid_for(rock->nconn), 256, 0, st>>>(rock->nconn, eos_const(P), P->conn_p,
-                                                               P->conn_m);
+                                                               P->conn_m, P->noroot_d);
         counted();
     }
     ok = ck(cudaGetLastError()) && ck(cudaStreamSynchronize(st));
     dfree(cell);
     if (!ok) return fail(RAS_ECUDA);
+    if (noroot_take(P)) return fail(RAS_ENOROOT);   // a fixed connection pressure has no admissible Z
     *out = P;
     return RAS_OK;
 }
@@ -587,6 +631,7 @@ extern "C" void ras_problem_destroy(ras_problem *P) {
         for (int s = 0; s < 7; ++s) dfree(P->nJ[b][s]);
     }
     dfree(P->ns); dfree(P->nrhs); dfree(P->ntmp);
+    if (P->noroot_h) cudaFreeHost(P->noroot_h);
     delete P;
 }
 
@@ -596,7 +641,8 @@ int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const 
     const EosConst E = eos_const(P);
     k_eos_storage<<<grid_for(P->N), 256, 0, st>>>(P->N, E, P->V, 1.0 / dt, order, p, pl,
                                                    order == 2 ? plm1 : pl, P->phi, F,
-                                                   J ? J[0] : nullptr, P->eos_m, P->eos_dm);
+                                                   J ? J[0] : nullptr, P->eos_m, P->eos_dm,
+                                                   P->noroot_d);
     RAS_LAUNCHED();
     const int t = stencil_threads(P->nx);
     const dim3 g = stencil_grid(P->nx, P->ny, P->nz, t);
@@ -624,6 +670,7 @@ extern "C" int residual_eval(ras_problem *P, const double *p, const double *p_l,
     RAS_TRY(residual_eval_impl(P, p, p_l, p_lm1, dt, bdf_order, F, J ? J->c : nullptr, st));
     if (normF) {
         RAS_TRY(norm2_sync(P->red, F, P->N, normF, st));
+        if (noroot_take(P)) return RAS_ENOROOT;
         if (!std::isfinite(*normF)) return RAS_ENAN;
     }
     return RAS_OK;

@@ -18,6 +18,7 @@ LIB_PATH = os.path.join(_HERE, "_lib", "libras.so")
 
 RAS_OK, RAS_GMRES_MAXIT, RAS_NEWTON_MAXIT, RAS_LINESEARCH_FAIL = 0, 1, 2, 3
 RAS_EINVAL, RAS_ECUDA, RAS_ENOMEM, RAS_ENAN, RAS_EZEROPIVOT = -1, -2, -3, -4, -5
+RAS_ENOROOT, RAS_ETIMEOUT = -6, -7
 
 EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_stencil_matvec",
             "ras_setup", "ras_precond_destroy", "ras_factor", "ras_apply", "gmres_solve",

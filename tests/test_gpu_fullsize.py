@@ -67,7 +67,20 @@ def test_full_ras_apply_sampled_subdomains(ras, full, prec, tol):
     zh = host(z)
     assert np.all(np.isfinite(zh))
     boxes = schwarz.partition((g.nx, g.ny, g.nz), PARTS, OVERLAP)
-    for i in (0, 91, 255):               # corner, interior, opposite corner
+    # one box of every distinct overlapped-box shape (18 or 20 cells per axis: at
+    # the grid's edge or inside), with low and high edges both represented, plus
+    # the two opposite corners and an interior box
+    picks = {0, 91, 255}
+    for ex in (0, 1):
+        for ey in (0, 1):
+            for ez in (0, 1):
+                ix = (0 if (ey + ez) % 2 == 0 else 7) if ex else 3
+                iy = (7 if (ex + ez) % 2 == 0 else 0) if ey else 4
+                iz = (0 if (ex + ey) % 2 == 0 else 3) if ez else 1
+                picks.add(ix + PARTS[0] * (iy + PARTS[1] * iz))
+    shapes = {tuple(boxes[i].e1[a] - boxes[i].e0[a] for a in range(3)) for i in picks}
+    assert len(shapes) == 8, shapes
+    for i in sorted(picks):
         b = boxes[i]
         Ai = A[b.idx][:, b.idx].tocsr()
         Ai.sort_indices()
