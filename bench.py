@@ -69,6 +69,9 @@ def parse():
                     help="kernel-only mode: factor once, then time REPS applications "
                          "(used for the ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
+    ap.add_argument("--apply-kernel", type=int, choices=[0, 1], default=None,
+                    help="fine subdomain-solve kernel: 0 level-scheduled, 1 pipelined "
+                         "(default: the library's choice)")
     return ap.parse_args()
 
 
@@ -102,11 +105,14 @@ def precond_opts(small=False, workload="c2"):
                 coarse_overlap=1)
 
 
-def make_precond(ras, gp, po, factor_prec, coarse_prec, nlevels=None):
-    return ras.Precond(gp, po["parts"], po["overlap"], factor_prec=factor_prec,
-                       nlevels=po["nlevels"] if nlevels is None else nlevels,
-                       coarsen=po["coarsen"], mlevel_type=po["mlevel_type"],
-                       coarse_prec=coarse_prec, coarse_overlap=po["coarse_overlap"])
+def make_precond(ras, gp, po, factor_prec, coarse_prec, nlevels=None, apply_kernel=None):
+    pc = ras.Precond(gp, po["parts"], po["overlap"], factor_prec=factor_prec,
+                     nlevels=po["nlevels"] if nlevels is None else nlevels,
+                     coarsen=po["coarsen"], mlevel_type=po["mlevel_type"],
+                     coarse_prec=coarse_prec, coarse_overlap=po["coarse_overlap"])
+    if apply_kernel is not None:
+        pc.set_apply_kernel(apply_kernel)
+    return pc
 
 
 NEWTON = dict(rtol=1e-6, atol=1e-10, maxit=50, lin_rtol=1e-6, lin_atol=1e-8, restart=30,
@@ -267,7 +273,7 @@ def gb300_arm(args):
     N = res.grid.n
     gp = ras.Problem(res)
     po = precond_opts(args.small, args.workload)
-    pc = make_precond(ras, gp, po, args.factor_prec, args.coarse_prec)
+    pc = make_precond(ras, gp, po, args.factor_prec, args.coarse_prec, apply_kernel=args.apply_kernel)
     p0 = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
     state = {"p_l": p0.clone(), "p_lm1": p0.clone(), "step": 0}
 
@@ -347,8 +353,9 @@ def gb300_arm(args):
     avg_s = (apply_ms / 1e3) / max(apply_n, 1)
     achieved = bytes_per_launch / avg_s / 1e9 if apply_n else None
     traffic = None
+    kname = "k_ras_pipe" if pc.apply_kernel() == 1 else "k_ras_apply"
     if args.workload == "c2" and not args.small:
-        traffic = load_traffic(f"k_ras_apply_fp{args.factor_prec}_1m")
+        traffic = load_traffic(f"{kname}_fp{args.factor_prec}_1m")
     line = {
         "metric": METRIC,
         "value": sec_per_step,
@@ -383,8 +390,8 @@ def gb300_arm(args):
                 "fgmres_iters": [o["lin_total"] for o in outs_e]},
         "gpu_launches": int(launches),
         "roofline": {
-            "kernel": "k_ras_apply (fine-level subdomain ILU(0) solves, %s factors)"
-                      % {64: "FP64", 32: "FP32", 16: "BF16"}[args.factor_prec],
+            "kernel": "%s (fine-level subdomain ILU(0) solves, %s factors)"
+                      % (kname, {64: "FP64", 32: "FP32", 16: "BF16"}[args.factor_prec]),
             "bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
             "frac": (achieved / peak) if achieved else None,
             "traffic": traffic,
@@ -525,7 +532,8 @@ def kernel_mode(args):
     gp = ras.Problem(res)
     po = precond_opts(args.small, args.workload)
     nl = 1 if args.kernel == "ras_apply" else po["nlevels"]
-    pc = make_precond(ras, gp, po, args.factor_prec, args.coarse_prec, nlevels=nl)
+    pc = make_precond(ras, gp, po, args.factor_prec, args.coarse_prec, nlevels=nl,
+                      apply_kernel=args.apply_kernel)
     from paper_2007_13966_gb300 import synthetic as syn
     p = torch.tensor(syn.random_pressure(res, 3, 1.0, 3.0), device="cuda")
     p0 = torch.full((N,), res.p0, dtype=torch.float64, device="cuda")
@@ -541,7 +549,8 @@ def kernel_mode(args):
     t, _ = timed(lambda: [pc.apply(r, z) for _ in range(args.reps)], torch, False)
     ms, n = pc.timing_read(reset=True)
     B = pc.apply_bytes()
-    print(json.dumps({"kernel": args.kernel, "reps": args.reps, "apply_us": t / args.reps * 1e6,
+    print(json.dumps({"kernel": args.kernel, "apply_kernel": pc.apply_kernel(), "reps": args.reps,
+                      "apply_us": t / args.reps * 1e6,
                       "subdomain_kernel_us": ms / max(n, 1) * 1e3, "bytes": B,
                       "GBps": B / (ms / max(n, 1) / 1e3) / 1e9 if n else None}))
 

@@ -256,6 +256,17 @@ extern "C" int ras_set_apply_schedule(ras_precond *pc, int chunk_cells, int thre
     return ras1_set_schedule(pc->fine, chunk_cells, threads);
 }
 
+extern "C" int ras_set_apply_kernel(ras_precond *pc, int kernel) {
+    if (!pc || pc->use125) return RAS_EINVAL;
+    return ras1_set_kernel(pc->fine, kernel);
+}
+
+extern "C" int ras_get_apply_kernel(const ras_precond *pc, int *kernel) {
+    if (!pc || !kernel) return RAS_EINVAL;
+    *kernel = pc->use125 ? 0 : pc->fine.pipe;
+    return RAS_OK;
+}
+
 extern "C" int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads) {
     if (!pc || pc->use125 || !chunk_cells || !threads) return RAS_EINVAL;
     *chunk_cells = pc->fine.chunk_cells;

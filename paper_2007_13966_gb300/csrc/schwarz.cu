@@ -333,6 +333,286 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply_batch(BatchApply B) {
     ras_apply_box<PREC, NBUF>(B.inst[h], B.box_local[blockIdx.x], B.r + B.off[h], B.z + B.off[h], B.accumulate);
 }
 
+// ---------------------------------------------------------------------------
+// Pipelined subdomain solves (left-RAS, FP32 / BF16 factors)
+//
+// The natural-order ILU(0) sweeps of a box run as a pipeline over its x-pencils
+// (j, k): pencil (j, k) handles its cells i = 0 .. bx-1 one per step, cell i at
+// step i + j + k in the forward sweep, so that its -y and -z neighbours, cells of
+// the pencils (j-1, k) and (j, k-1) on the anti-diagonal d - 1 (d = j + k), were
+// finished one step earlier, and its -x neighbour is the pencil's previous value,
+// kept in a register (the backward sweep mirrors this). A warp handles the
+// anti-diagonals d = w (mod warps), one lane per pencil, at most PIPE_M of them at
+// once; it waits only for the warp of diagonal d - 1 (d + 1 backwards) through a
+// progress word in shared memory (release / acquire, bounded spin) instead of a
+// CTA barrier per wavefront level. Every lane streams its records, r values and,
+// when accumulating, old z values PIPE_PF steps ahead into a shared-memory ring with
+// cp.async, and the backward sweep writes each owned cell's z as soon as it is
+// final: there is no separate gather or write-back phase. At the start each CTA
+// asks L2 for its box's records and r rows (cp.async.bulk.prefetch), so that DRAM
+// streams while the sweeps run. The arithmetic of every cell is the same as in
+// the level-scheduled kernel, in the same order.
+// ---------------------------------------------------------------------------
+
+constexpr int PIPE_M = 2;    // concurrently active diagonals per warp (slots)
+constexpr int PIPE_PF = 4;   // steps of cp.async look-ahead per lane
+
+struct PipeParams {
+    const SubInfo *subs;
+    const ShapeInfo *shapes;
+    const DiagInfo *diag;
+    const unsigned char *fwd, *bwd;
+    const double *r;
+    double *z;
+    int nx, ny, nz;
+    int accumulate;
+    int ycap;          // elements of the padded box vector
+    int poll_limit;    // spins (per thread, over the whole launch) before waits give up
+    int *err;          // set to 2 when a wait gave up
+};
+
+__device__ __forceinline__ int ld_acquire_cta(const int *p) {
+    int v;
+    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];\n"
+                 : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
+    return v;
+}
+__device__ __forceinline__ void st_release_cta(int *p, int v) {
+    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;\n"
+                 :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
+    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
+}
+// L2 prefetch of the 16-byte-aligned interior of the global bytes [b0, b1)
+__device__ __forceinline__ void l2_prefetch(const void *b0, const void *b1) {
+    const unsigned long long a0 = ((unsigned long long)b0 + 15) & ~15ull;
+    const unsigned long long a1 = (unsigned long long)b1 & ~15ull;
+    if (a1 > a0)
+        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a0), "r"((unsigned)(a1 - a0))
+                     : "memory");
+}
+template <int RB>
+__device__ __forceinline__ void cp_async_rec(void *smem, const void *gmem) {
+    if constexpr (RB == 16) cp_async16(smem, gmem);
+    else cp_async8(smem, gmem);
+}
+
+// Diagonals of slot m of warp w: d = base + L t (base = w + NW m < L = NW * PIPE_M,
+// L >= bx, so at most one is active at a step). rem = (step - base) mod L is kept
+// incrementally; forward at step G the active diagonal is d = G - rem at i = rem,
+// active iff rem < bx and 0 <= d <= D-1. Backwards (G' = G - S) the slot runs the
+// same diagonals in reverse: with dt = D-1-d, dt = G' - rem at i = bx-1-rem, rem =
+// (G' - bb) mod L, bb = (D-1-base) mod L, active iff rem < bx and 0 <= dt <= D-1.
+struct PipeCursor {
+    int rem[PIPE_M];
+    __device__ __forceinline__ void start(int first_mod_L, int m, int L) {   // (0 - first) mod L
+        rem[m] = first_mod_L == 0 ? 0 : L - first_mod_L;
+    }
+    __device__ __forceinline__ void step(int L) {
+#pragma unroll
+        for (int m = 0; m < PIPE_M; ++m) rem[m] = rem[m] + 1 == L ? 0 : rem[m] + 1;
+    }
+};
+
+template <int PREC>
+__global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
+    using R = typename RecT<PREC>::T;
+    using Acc = typename RecT<PREC>::Acc;
+    constexpr int RB = (int)sizeof(R);
+    constexpr int M = PIPE_M, PF = PIPE_PF;
+    extern __shared__ __align__(16) unsigned char smem[];
+
+    const int NW = blockDim.x >> 5;
+    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const SubInfo si = P.subs[blockIdx.x];
+    const ShapeInfo sh = P.shapes[si.shape];
+    const int bx = sh.bx, by = sh.by, bz = sh.bz;
+    const int D = by + bz - 1, S = bx + D - 1;
+    const int PX = bx, PXY = sh.pxy;
+    const int nx = P.nx, nxy = P.nx * P.ny;
+    const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
+
+    // shared memory: [Y: ycap][progress: 32][diagonals][record ring][value ring]
+    Acc *Y = reinterpret_cast<Acc *>(smem);
+    int *prog = reinterpret_cast<int *>(smem + (((size_t)P.ycap * sizeof(Acc) + 15) & ~(size_t)15));
+    DiagInfo *dg = reinterpret_cast<DiagInfo *>(prog + 32);
+    unsigned char *ringR = reinterpret_cast<unsigned char *>(dg + ((D + 1) & ~1));
+    double *ringA = reinterpret_cast<double *>(ringR + (size_t)NW * PF * M * 32 * RB);
+
+    const unsigned char *recf = P.fwd + si.foff * RB;
+    const unsigned char *recb = P.bwd + si.foff * RB;
+    const double *rg = P.r + g0;
+    double *zg = P.z + g0;
+
+    // ask L2 for the box's forward records and r rows, then the backward records
+    {
+        const long long nb = (long long)sh.ncell * RB;
+        const int nch = (int)((nb + 4095) >> 12);
+        const int rows = by * bz;
+        for (int t = threadIdx.x; t < nch + rows; t += blockDim.x) {
+            if (t < nch) {
+                l2_prefetch(recf + ((long long)t << 12), recf + min(nb, (long long)(t + 1) << 12));
+            } else {
+                const int row = t - nch, j = row % by, k = row / by;
+                const double *a = rg + (long long)nx * j + (long long)nxy * k;
+                l2_prefetch(a, a + bx);
+            }
+        }
+        for (int t = threadIdx.x; t < nch; t += blockDim.x)
+            l2_prefetch(recb + ((long long)t << 12), recb + min(nb, (long long)(t + 1) << 12));
+    }
+    for (int t = threadIdx.x; t < D; t += blockDim.x) dg[t] = P.diag[sh.diag_off + t];
+    if (threadIdx.x < 32) prog[threadIdx.x] = -1;
+    __syncthreads();
+
+    const int L = NW * M;
+    const bool acc = P.accumulate != 0;
+    int bb[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) bb[m] = ((D - 1 - (w + NW * m)) % L + L) % L;
+
+    // the slot's active diagonal and cell index at global step G with position rem
+    auto active = [&](int G, int rem, int &d, int &i) -> bool {
+        if (rem >= bx) return false;
+        if (G < S) {
+            d = G - rem;
+            i = rem;
+            return d >= 0 && d <= D - 1;
+        }
+        const int dt = G - S - rem;
+        d = D - 1 - dt;
+        i = bx - 1 - rem;
+        return dt >= 0 && dt <= D - 1;
+    };
+
+    // cp.async of the lane's data for global step G (cursor position cp) into ring stage G % PF
+    PipeCursor cp;
+    auto prefetch = [&](int G) {
+        if (G == S) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) cp.start(bb[m], m, L);
+        }
+        if (G < 2 * S) {
+            const int stage = G % PF;
+#pragma unroll
+            for (int m = 0; m < M; ++m) {
+                int d, i;
+                if (!active(G, cp.rem[m], d, i)) continue;
+                const DiagInfo di = dg[d];
+                const int jmin = di.jmin_cnt & 0xffff, cnt = di.jmin_cnt >> 16;
+                if (lane >= cnt) continue;
+                const size_t e = ((size_t)(w * PF + stage) * M + m) * 32 + lane;
+                const long long ri = (long long)di.base + (long long)i * cnt + lane;
+                const int j = jmin + lane, k = d - j;
+                const long long go = i + (long long)nx * j + (long long)nxy * k;
+                if (G < S) {
+                    cp_async_rec<RB>(ringR + e * RB, recf + ri * RB);
+                    cp_async8(ringA + e, rg + go);
+                } else {
+                    cp_async_rec<RB>(ringR + e * RB, recb + ri * RB);
+                    if (acc && i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 &&
+                        k >= si.oz0 && k < si.oz1)
+                        cp_async8(ringA + e, zg + go);
+                }
+            }
+        }
+        cp_async_commit();
+        cp.step(L);
+    };
+#pragma unroll
+    for (int m = 0; m < M; ++m) cp.start(w + NW * m, m, L);
+#pragma unroll
+    for (int t = 0; t < PF; ++t) prefetch(t);
+
+    PipeCursor cc;
+#pragma unroll
+    for (int m = 0; m < M; ++m) cc.start(w + NW * m, m, L);
+    Acc xprev[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) xprev[m] = (Acc)0;
+    const int pred_f = (w + NW - 1) % NW, pred_b = (w + 1) % NW;
+    int spins_left = P.poll_limit;
+    const int ylast = P.ycap - 1;
+
+    for (int G = 0; G < 2 * S; ++G) {
+        if (G == S) {
+#pragma unroll
+            for (int m = 0; m < M; ++m) cc.start(bb[m], m, L);
+        }
+        cp_async_wait<PF - 1>();
+        const bool fw = G < S;
+        int dd[M], ii[M];
+        bool act[M];
+        bool need = false;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            act[m] = active(G, cc.rem[m], dd[m], ii[m]);
+            if (act[m]) need = need || (fw ? dd[m] > 0 : dd[m] < D - 1);
+        }
+        if (need) {
+            const int *pw = &prog[fw ? pred_f : pred_b];
+            while (ld_acquire_cta(pw) < G - 1) {
+                if (--spins_left < 0) {   // bounded: record the give-up and go on
+                    atomicExch(P.err, 2);
+                    break;
+                }
+            }
+        }
+        const int stage = G % PF;
+#pragma unroll
+        for (int m = 0; m < M; ++m) {
+            if (!act[m]) continue;
+            const int d = dd[m], i = ii[m];
+            const DiagInfo di = dg[d];
+            const int jmin = di.jmin_cnt & 0xffff, cnt = di.jmin_cnt >> 16;
+            if (lane >= cnt) continue;
+            const int j = jmin + lane, k = d - j;
+            const int n = i + PX * j + PXY * k;
+            const size_t e = ((size_t)(w * PF + stage) * M + m) * 32 + lane;
+            Acc ax, ay, az, dinv;
+            load_rec<Acc, R>(ringR + e * RB, ax, ay, az, dinv);
+            if (fw) {
+                // w_n = (r_n - a_z w_{n-bxy} - a_y w_{n-bx} - a_x w_{n-1}) / d_n
+                if (i == 0) xprev[m] = (Acc)0;
+                const Acc vz = Y[max(n - PXY, 0)], vy = Y[max(n - PX, 0)];
+                const Acc yz = k > 0 ? vz : (Acc)0;
+                const Acc yy = j > 0 ? vy : (Acc)0;
+                Acc s = (Acc)ringA[e];
+                s -= az * yz;
+                s -= ay * yy;
+                s -= ax * xprev[m];
+                const Acc y = s * dinv;
+                Y[n] = y;
+                xprev[m] = y;
+            } else {
+                // z_n = w_n - d_n^{-1} (a_x z_{n+1} + a_y z_{n+bx} + a_z z_{n+bxy})
+                if (i == bx - 1) xprev[m] = (Acc)0;
+                const Acc vy = Y[min(n + PX, ylast)], vz = Y[min(n + PXY, ylast)];
+                const Acc zy = j < by - 1 ? vy : (Acc)0;
+                const Acc zz = k < bz - 1 ? vz : (Acc)0;
+                Acc s = ax * xprev[m];
+                s += ay * zy;
+                s += az * zz;
+                const Acc y = Y[n] - dinv * s;
+                Y[n] = y;
+                xprev[m] = y;
+                if (i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 &&
+                    k < si.oz1) {
+                    const long long go = i + (long long)nx * j + (long long)nxy * k;
+                    zg[go] = acc ? ringA[e] + (double)y : (double)y;
+                }
+            }
+        }
+        __syncwarp();
+        if (lane == 0) st_release_cta(&prog[w], G);
+        prefetch(G + PF);
+        cc.step(L);
+    }
+    cp_async_wait<0>();
+}
+
 // z (+)= sum over the overlapped boxes covering each cell of their solution
 // ((R_i^delta)^T), boxes in ascending index order (deterministic)
 struct SumParams {
@@ -371,6 +651,7 @@ struct FactorParams {
     const ShapeInfo *shapes;
     const int *lvl;
     const unsigned *cells;
+    const DiagInfo *diag;   // non-null: records in the pipelined (diagonal) layout
     Stencil7 A;
     void *fwd, *bwd;
     int nx, ny, nz;
@@ -416,9 +697,14 @@ __global__ void __launch_bounds__(512) k_ras_factor(FactorParams P) {
         const int n = i + bx * j + bxy * k;
         const long long g = g0 + i + (long long)nx * j + (long long)nxy * k;
         const double dinv = 1.0 / D[n];
-        store_rec<PREC>(P.fwd, si.foff + q, (fl & F_MX) ? Amx[g] : 0.0, (fl & F_MY) ? Amy[g] : 0.0,
+        long long pos = q;
+        if (P.diag) {   // diagonal d = j + k, then i, then pencil j - jmin
+            const DiagInfo di = P.diag[sh.diag_off + j + k];
+            pos = di.base + (long long)i * (di.jmin_cnt >> 16) + (j - (di.jmin_cnt & 0xffff));
+        }
+        store_rec<PREC>(P.fwd, si.foff + pos, (fl & F_MX) ? Amx[g] : 0.0, (fl & F_MY) ? Amy[g] : 0.0,
                         (fl & F_MZ) ? Amz[g] : 0.0, dinv);
-        store_rec<PREC>(P.bwd, si.foff + q, (fl & F_PX) ? Apx[g] : 0.0, (fl & F_PY) ? Apy[g] : 0.0,
+        store_rec<PREC>(P.bwd, si.foff + pos, (fl & F_PX) ? Apx[g] : 0.0, (fl & F_PY) ? Apy[g] : 0.0,
                         (fl & F_PZ) ? Apz[g] : 0.0, dinv);
     }
 }
@@ -443,6 +729,11 @@ static int set_apply_attr(size_t) {
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
     RAS_CK(cudaFuncSetAttribute(k_ras_apply_batch<PREC, NBUF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
+    return RAS_OK;
+}
+template <int PREC>
+static int set_pipe_attr() {
+    RAS_CK(cudaFuncSetAttribute(k_ras_pipe<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
     return RAS_OK;
 }
 template <int PREC>
@@ -542,6 +833,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     std::vector<int> lvl_tab;
     std::vector<unsigned> cell_tab;
     std::vector<int> cidx_tab;        // same positions as cell_tab: i + bx (j + by k)
+    std::vector<DiagInfo> diag_tab;
     R.subs.clear();
     R.shapes.clear();
     long long foff = 0;
@@ -610,6 +902,16 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
                     }
                     lvl_tab.push_back(pos);
                     sh.maxw = maxw;
+                    // x-pencil anti-diagonals d = j + k for the pipelined layout
+                    sh.diag_off = (int)diag_tab.size();
+                    int dbase = 0;
+                    for (int d = 0; d < by + bz - 1; ++d) {
+                        const int jmin = std::max(0, d - (bz - 1)), jmax = std::min(d, by - 1);
+                        const int cnt = jmax - jmin + 1;
+                        diag_tab.push_back(DiagInfo{jmin | (cnt << 16), dbase});
+                        dbase += bx * cnt;
+                    }
+                    sh.pxy = bx * by + (((bx * (by - 1)) % 2 == 0) ? 1 : 0);
                     maxw_all = std::max(maxw_all, maxw);
                     ycap = std::max(ycap, ncell);
                     gcap = std::max(gcap, bx * by);
@@ -651,6 +953,37 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     RAS_TRY(schedule_tables(R, 0, 0, chunk_tab));
     R.smem_factor = (size_t)R.ycap * sizeof(double);
     if (R.smem_apply > 227 * 1024 || R.smem_factor > 227 * 1024) return RAS_EINVAL;
+    // pipelined subdomain solves: left-RAS with FP32 / BF16 factors, boxes at most
+    // 24 cells along x (12 warps of two slots) and 32 pencils per anti-diagonal
+    {
+        bool ok = kind == 1 && prec != 64;
+        int bxmax = 1, ycp = 0, dmax = 1;
+        for (const ShapeInfo &sh : R.shapes) {
+            bxmax = std::max(bxmax, sh.bx);
+            ycp = std::max(ycp, sh.pxy * sh.bz);
+            dmax = std::max(dmax, sh.by + sh.bz - 1);
+            if (std::min(sh.by, sh.bz) > 32) ok = false;
+        }
+        if (bxmax > 2 * 12) ok = false;
+        int nw = std::max(2, (bxmax + PIPE_M - 1) / PIPE_M);
+        if (const char *e = getenv("RAS_PIPE_WARPS")) {   // tuning knob (warps per box)
+            const int v = atoi(e);
+            if (v >= nw && v <= 12) nw = v;
+        }
+        const size_t acc = prec == 64 ? 8 : 4;
+        const size_t ybytes = (((size_t)((ycp + 3) & ~3) * acc) + 15) & ~(size_t)15;
+        const size_t smem = ybytes + 32 * sizeof(int) + (size_t)((dmax + 1) & ~1) * sizeof(DiagInfo) +
+                            (size_t)nw * PIPE_PF * PIPE_M * 32 * (R.rec_bytes + sizeof(double));
+        if (smem > 227 * 1024) ok = false;
+        R.pipe = R.pipe_ok = ok ? 1 : 0;
+        R.pipe_warps = nw;
+        R.ycap_pipe = (ycp + 3) & ~3;
+        R.smem_pipe = smem;
+        if (const char *e = getenv("RAS_PIPE_POLLS")) {   // shortened waits (tests)
+            const int v = atoi(e);
+            if (v > 0) R.pipe_poll_limit = v;
+        }
+    }
 
     RAS_TRY(dalloc(&R.d_subs, R.subs.size()));
     RAS_TRY(dalloc(&R.d_shapes, R.shapes.size()));
@@ -659,6 +992,8 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     RAS_TRY(dalloc(&R.d_cells, cell_tab.size() + 16));
     RAS_TRY(dalloc(&R.d_cidx, cidx_tab.size() + 16));
     RAS_TRY(dalloc(&R.d_err, 1));
+    RAS_TRY(dalloc(&R.d_diag, diag_tab.size()));
+    RAS_CK(cudaMemcpy(R.d_diag, diag_tab.data(), diag_tab.size() * sizeof(DiagInfo), cudaMemcpyHostToDevice));
     unsigned char *fw = nullptr, *bw = nullptr;
     RAS_TRY(dalloc(&fw, (size_t)R.nrec * R.rec_bytes + 64));
     RAS_TRY(dalloc(&bw, (size_t)R.nrec * R.rec_bytes + 64));
@@ -678,8 +1013,8 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     RAS_CK(cudaMemset(R.d_fwd, 0, (size_t)R.nrec * R.rec_bytes + 64));
     RAS_CK(cudaMemset(R.d_bwd, 0, (size_t)R.nrec * R.rec_bytes + 64));
     if (prec == 64) { RAS_TRY(set_apply_attr<64, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<64>(R.smem_factor)); }
-    if (prec == 32) { RAS_TRY(set_apply_attr<32, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<32>(R.smem_factor)); }
-    if (prec == 16) { RAS_TRY(set_apply_attr<16, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<16>(R.smem_factor)); }
+    if (prec == 32) { RAS_TRY(set_apply_attr<32, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<32>(R.smem_factor)); RAS_TRY(set_pipe_attr<32>()); }
+    if (prec == 16) { RAS_TRY(set_apply_attr<16, 3>(R.smem_apply)); RAS_TRY(set_factor_attr<16>(R.smem_factor)); RAS_TRY(set_pipe_attr<16>()); }
     if (kind != 1) {
         // per axis and coordinate, the (contiguous) range of parts whose overlapped
         // boxes cover it; box solutions are kept per record offset
@@ -704,7 +1039,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
 
 void ras1_free(Ras1 &R) {
     dfree(R.d_subs); dfree(R.d_shapes); dfree(R.d_lvl); dfree(R.d_chunk); dfree(R.d_cells);
-    dfree(R.d_cidx); dfree(R.d_err);
+    dfree(R.d_cidx); dfree(R.d_err); dfree(R.d_diag);
     if (R.d_fwd) cudaFree(R.d_fwd);
     if (R.d_bwd) cudaFree(R.d_bwd);
     R.d_fwd = R.d_bwd = nullptr;
@@ -716,7 +1051,9 @@ int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st) {
     FactorParams P;
     P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.cells = R.d_cells;
     P.A = A; P.fwd = R.d_fwd; P.bwd = R.d_bwd;
+    P.diag = R.pipe ? R.d_diag : nullptr;
     P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.err = R.d_err;
+    R.stale = 0;
     const int block = std::min(R.block, 256);
     if (R.prec == 64) k_ras_factor<64><<<R.nsub, block, R.smem_factor, st>>>(P);
     else if (R.prec == 32) k_ras_factor<32><<<R.nsub, block, R.smem_factor, st>>>(P);
@@ -731,10 +1068,20 @@ int ras1_check(Ras1 &R, cudaStream_t st) {
     RAS_CK(cudaStreamSynchronize(st));
     if (h) {
         RAS_CK(cudaMemsetAsync(R.d_err, 0, sizeof(int), st));
-        return RAS_EZEROPIVOT;
+        return h == 2 ? RAS_ETIMEOUT : RAS_EZEROPIVOT;
     }
     return RAS_OK;
 }
+
+int ras1_set_kernel(Ras1 &R, int kernel) {
+    if (kernel != 0 && kernel != 1) return RAS_EINVAL;
+    if (kernel == 1 && !R.pipe_ok) return RAS_EINVAL;
+    if (kernel != R.pipe) R.stale = 1;
+    R.pipe = kernel;
+    return RAS_OK;
+}
+
+void ras1_use_level_layout(Ras1 &R) { ras1_set_kernel(R, 0); }
 
 void ras1_apply_params(const Ras1 &R, ApplyParams &P) {
     P = ApplyParams{};
@@ -756,6 +1103,19 @@ int ras1_apply_batch(const BatchApply &B, int nblocks, int prec, int block, size
 }
 
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st) {
+    if (R.stale) return RAS_EINVAL;   // kernel switched: factor again first
+    if (R.pipe) {
+        PipeParams Q;
+        Q.subs = R.d_subs; Q.shapes = R.d_shapes; Q.diag = R.d_diag;
+        Q.fwd = (const unsigned char *)R.d_fwd; Q.bwd = (const unsigned char *)R.d_bwd;
+        Q.r = r; Q.z = z; Q.nx = R.nx; Q.ny = R.ny; Q.nz = R.nz; Q.accumulate = accumulate;
+        Q.ycap = R.ycap_pipe; Q.poll_limit = R.pipe_poll_limit; Q.err = R.d_err;
+        const int threads = 32 * R.pipe_warps;
+        if (R.prec == 32) k_ras_pipe<32><<<R.nsub, threads, R.smem_pipe, st>>>(Q);
+        else k_ras_pipe<16><<<R.nsub, threads, R.smem_pipe, st>>>(Q);
+        RAS_LAUNCHED();
+        return RAS_OK;
+    }
     ApplyParams P;
     P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.chunk = R.d_chunk;
     P.cidx = R.d_cidx;

@@ -26,7 +26,7 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
             "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc",
             "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk", "ras_batch_create",
             "ras_batch_destroy", "ras_batch_gmres", "ras_batch_newton_step", "ras_set_apply_schedule",
-            "ras_get_apply_schedule"]
+            "ras_get_apply_schedule", "ras_set_apply_kernel", "ras_get_apply_kernel"]
 
 
 class Grid(C.Structure):
@@ -119,6 +119,8 @@ def lib():
             "ras_grad_logk": (i, [vp, vp, vp, vp, vp]),
             "ras_set_apply_schedule": (i, [vp, i, i]),
             "ras_get_apply_schedule": (i, [vp, C.POINTER(i), C.POINTER(i)]),
+            "ras_set_apply_kernel": (i, [vp, i]),
+            "ras_get_apply_kernel": (i, [vp, C.POINTER(i)]),
             "ras_batch_create": (i, [i, vp, vp, C.POINTER(vp)]),
             "ras_batch_destroy": (None, [vp]),
             "ras_batch_gmres": (i, [vp, vp, vp, vp, C.POINTER(KrylovOpts), vp, vp]),
@@ -328,6 +330,15 @@ class Precond:
         c, t = C.c_int(0), C.c_int(0)
         check(lib().ras_get_apply_schedule(self.h, C.byref(c), C.byref(t)), "ras_get_apply_schedule")
         return c.value, t.value
+
+    def set_apply_kernel(self, kernel):
+        """0: level-scheduled subdomain solves, 1: pipelined (same values; factor again after a change)."""
+        check(lib().ras_set_apply_kernel(self.h, int(kernel)), "ras_set_apply_kernel")
+
+    def apply_kernel(self):
+        k = C.c_int(0)
+        check(lib().ras_get_apply_kernel(self.h, C.byref(k)), "ras_get_apply_kernel")
+        return k.value
 
 
 class BatchSolver:

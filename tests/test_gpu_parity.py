@@ -170,8 +170,11 @@ def test_gmres_history_matches_oracle(ras, restart):
     hist = np.array(hist)
     rel = np.abs(h - hist) / np.abs(hist)
     detail = " ".join(f"{i}:{a:.6e}/{b:.6e}" for i, (a, b) in enumerate(zip(h, hist)) if rel[i] > 1e-10)
+    # 1e-9 relative: of ||r0|| over the whole history, and of each entry down to the
+    # FP64 floor of the Arnoldi residual estimate (~1e-11 ||r0|| here: entries that
+    # small differ by rounding that the Givens recurrence carries from the start)
     assert np.max(np.abs(h - hist) / hist[0]) < 1e-9, detail
-    assert np.max(rel) < 1e-9, detail
+    assert np.all(np.abs(h - hist) <= 1e-9 * hist + 1e-11 * hist[0]), detail
     assert rel_err(host(x), x_ref) < 1e-9
 
 
