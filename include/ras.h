@@ -52,6 +52,11 @@ typedef struct {
                               1 = the upstream cell's, by the sign of the face potential
                               (fixed-pressure connections alike; the density of the
                               gravity term stays the mean) */
+    int conservative;      /* accumulation term: 0 = Eq. gover_sys's V phi c(p) D_t p
+                              (default); 1 = the conservative form V phi D_t (p/Z) of the
+                              time derivative of phi rho (Eq. mass conservation / (W/RT)),
+                              with the same BDF weights on p/Z at the three levels;
+                              Jacobian V phi c(p) dD_t/dp */
 } ras_grid;
 
 /* Fluid (Section 2, Eq. attrfactor and the m(omega), omega(T_br) fits;
@@ -75,6 +80,11 @@ typedef struct {
     int nconn;
     const int *conn_cell;
     const double *conn_p, *conn_T;
+    const double *rate_Q;  /* NULL, or device [N]: fixed injection rates (the paper's Case-2
+                              fixed injection velocity), the Darcy volume rate Q_n (m^3/s,
+                              positive into the cell) through boundary faces of cell n;
+                              the injected gas carries the cell's own p/Z:
+                              F_n -= (p_n/Z_n) Q_n, dF_n/dp_n -= c(p_n) Q_n */
 } ras_rock;
 
 /* Jacobian (or any 7-point operator) as seven device arrays of N entries:

@@ -10,7 +10,8 @@ fixed pressure). Forward: the BDF1-then-BDF2 time loop (newton_step), every
 state kept as a checkpoint. Backward, for l = L .. 1, on the library's calls:
     J_l = dF^l/dp^l at p^l (residual_eval), J_l^T (ras_stencil_transpose),
     rhs = -dPhi/dp^l + (2/dt) s(p^{l+1}) lambda^{l+1} - (1/(2 dt)) s(p^{l+2}) lambda^{l+2}
-          (ras_adjoint_rhs),
+          (ras_adjoint_rhs; in the conservative accumulation form the BDF weights act
+          on p/Z of the older level, so both history terms take s at p^l instead),
     J_l^T lambda^l = rhs by FGMRES preconditioned by right-RAS of J_l^T
           (the transposed shape of the forward left-RAS),
     grad += (dF^l/dtheta)^T lambda^l (ras_grad_logk).
@@ -81,7 +82,7 @@ def run_forward(res, theta, nsteps, opts: AdjointOpts):
     return gp, states, phi, cells
 
 
-def adjoint_gradient(gp, dt, states, cells, opts: AdjointOpts):
+def adjoint_gradient(gp, dt, states, cells, opts: AdjointOpts, conservative=False):
     """dPhi/dtheta for the checkpointed states."""
     L = len(states) - 1
     N = states[0].numel()
@@ -101,8 +102,10 @@ def adjoint_gradient(gp, dt, states, cells, opts: AdjointOpts):
         gp.stencil_transpose(gp.J, JT)
         dphi.zero_()
         dphi[cells] = 2.0 * states[l][cells]
-        p1, l1 = (states[l + 1], lam[l + 1]) if l + 1 <= L else (None, None)
-        p2, l2 = (states[l + 2], lam[l + 2]) if l + 2 <= L else (None, None)
+        # dF^{l+1}/dp^l and dF^{l+2}/dp^l: s at the newer state (Eq. gover_sys's
+        # c(p) D_t p) or at p^l itself (conservative form, D_t of p/Z)
+        p1, l1 = (states[l] if conservative else states[l + 1], lam[l + 1]) if l + 1 <= L else (None, None)
+        p2, l2 = (states[l] if conservative else states[l + 2], lam[l + 2]) if l + 2 <= L else (None, None)
         gp.adjoint_rhs(dphi, p1, l1, 2.0 / dt, p2, l2, -0.5 / dt, rhs)
         pcT.factor(JT)
         x = torch.zeros(N, **f64)
@@ -123,13 +126,13 @@ class ProducerPressureObjective(torch.autograd.Function):
     def forward(ctx, theta, res, nsteps, opts):
         th = theta.detach().to("cpu", torch.float64).numpy()
         gp, states, phi, cells = run_forward(res, th, nsteps, opts)
-        ctx.saved = (gp, states, cells, res.dt, opts)
+        ctx.saved = (gp, states, cells, res.dt, opts, bool(getattr(res, "conservative", False)))
         return phi.detach().clone()
 
     @staticmethod
     def backward(ctx, g):
-        gp, states, cells, dt, opts = ctx.saved
-        grad = adjoint_gradient(gp, dt, states, cells, opts)
+        gp, states, cells, dt, opts, cons = ctx.saved
+        grad = adjoint_gradient(gp, dt, states, cells, opts, conservative=cons)
         return g * grad, None, None, None
 
 

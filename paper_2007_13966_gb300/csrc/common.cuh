@@ -110,6 +110,8 @@ struct ras_problem {
     double hx, hy, hz, V;
     double a, b, R, T, mu, inv_mu;
     int upwind = 0;       // face mobility of the upstream cell instead of the mean
+    int conservative = 0; // accumulation V phi D_t(p/Z) instead of V phi c(p) D_t p
+    double *rateQ = nullptr;  // fixed injection rates per cell (m^3/s), or null
     double ghz = 0.0;     // g hz W mu / (R T): rho g hz across a z face = ghz * mbar (rho = that / (g hz) * m)
     double *Tx = nullptr, *Ty = nullptr, *Tz = nullptr, *phi = nullptr;
     double *kx = nullptr, *ky = nullptr, *kz = nullptr;   // permeabilities (sensitivities)

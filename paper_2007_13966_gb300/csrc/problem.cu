@@ -262,6 +262,7 @@ __device__ __forceinline__ float cubic_root_f32(float c2, float c1, float c0) {
 
 struct EosOut {
     double c, dc, m, dm;
+    double Z;
     bool ok;   // an admissible root: Z finite, Z > B, f_Z != 0
 };
 
@@ -318,34 +319,57 @@ __device__ __forceinline__ EosOut eos_cell(double p, const EosConst &E) {
     o.dc = -2.0 * dZ * iZ2 - p * d2Z * iZ2 + 2.0 * p * dZ * dZ * iZ2 * iZ;
     o.m = p * iZ * E.inv_mu;                                       // p / (mu Z)
     o.dm = o.c * E.inv_mu;
+    o.Z = Z;
     o.ok = isfinite(Z) && Z > B && fZ != 0.0 && isfinite(o.c) && isfinite(o.dc);
     return o;
 }
 
-// pass 1: per-cell storage term and its derivative, and m, dm for the fluxes
+// pass 1: per-cell storage term and its derivative, and m, dm for the fluxes.
+// Accumulation V phi c(p) D_t p (Eq. gover_sys), or in the conservative form
+// V phi D_t(p/Z) with the same BDF weights on p/Z at the three levels (d(p/Z)/dp = c);
+// fixed injection rates subtract (p/Z) Q from the cell's residual.
 __global__ void __launch_bounds__(256) k_eos_storage(
     int N, EosConst E, double Vol, double inv_dt, int order, const double *__restrict__ p,
     const double *__restrict__ pl, const double *__restrict__ plm1, const double *__restrict__ phi,
     double *__restrict__ F, double *__restrict__ Jc, double *__restrict__ m_out,
-    double *__restrict__ dm_out, int *__restrict__ noroot) {
+    double *__restrict__ dm_out, int *__restrict__ noroot, int conservative,
+    const double *__restrict__ rateQ) {
     for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < N; n += gridDim.x * blockDim.x) {
         const double pn = p[n];
         EosOut o = eos_cell(pn, E);
+        const double g = order == 1 ? inv_dt : 1.5 * inv_dt;
+        const double vp = Vol * phi[n];
+        double f, jc;
+        if (conservative) {
+            const EosOut ol = eos_cell(pl[n], E);
+            if (!ol.ok) o.ok = false;
+            double DtP;
+            if (order == 1) {
+                DtP = (pn / o.Z - pl[n] / ol.Z) * inv_dt;
+            } else {
+                const EosOut om = eos_cell(plm1[n], E);
+                if (!om.ok) o.ok = false;
+                DtP = (3.0 * (pn / o.Z) - 4.0 * (pl[n] / ol.Z) + plm1[n] / om.Z) * (0.5 * inv_dt);
+            }
+            f = vp * DtP;
+            jc = vp * o.c * g;
+        } else {
+            const double Dt = order == 1 ? (pn - pl[n]) * inv_dt
+                                         : (3.0 * pn - 4.0 * pl[n] + plm1[n]) * (0.5 * inv_dt);
+            f = vp * o.c * Dt;
+            jc = vp * (o.dc * Dt + o.c * g);
+        }
+        if (rateQ) {
+            const double q = rateQ[n];
+            f -= (pn / o.Z) * q;
+            jc -= o.c * q;
+        }
         if (!o.ok) {   // no admissible root: flag it and poison the cell's residual
             *noroot = 1;
-            o.c = o.dc = o.m = o.dm = __longlong_as_double(0x7ff8000000000000LL);
+            f = jc = o.m = o.dm = __longlong_as_double(0x7ff8000000000000LL);
         }
-        double Dt, g;
-        if (order == 1) {
-            Dt = (pn - pl[n]) * inv_dt;
-            g = inv_dt;
-        } else {
-            Dt = (3.0 * pn - 4.0 * pl[n] + plm1[n]) * (0.5 * inv_dt);
-            g = 1.5 * inv_dt;
-        }
-        const double vp = Vol * phi[n];
-        F[n] = vp * o.c * Dt;
-        if (Jc) Jc[n] = vp * (o.dc * Dt + o.c * g);
+        F[n] = f;
+        if (Jc) Jc[n] = jc;
         m_out[n] = o.m;
         dm_out[n] = o.dm;
     }
@@ -544,6 +568,7 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     if (!(grid->hx > 0 && grid->hy > 0 && grid->hz > 0)) return RAS_EINVAL;
     if (!std::isfinite(grid->gz) || (grid->gz != 0.0 && !(eos->W > 0 && std::isfinite(eos->W)))) return RAS_EINVAL;
     if (grid->upwind != 0 && grid->upwind != 1) return RAS_EINVAL;
+    if (grid->conservative != 0 && grid->conservative != 1) return RAS_EINVAL;
     const long long N = (long long)grid->nx * grid->ny * grid->nz;
     if (N > (1LL << 30)) return RAS_EINVAL;
     if (!rock->kx || !rock->ky || !rock->kz || !rock->phi) return RAS_EINVAL;
@@ -558,6 +583,7 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     P->R = eos->R; P->T = eos->T; P->mu = eos->mu; P->inv_mu = 1.0 / eos->mu;
     P->ghz = grid->gz * grid->hz * eos->W * eos->mu / (eos->R * eos->T);
     P->upwind = grid->upwind;
+    P->conservative = grid->conservative;
     // Eq. attrfactor and the m(omega) fit (first branch at omega = 0.491)
     const double omega = eos->omega_from_Tb ? acentric_factor(eos->Tc, eos->pc, eos->Tb) : eos->omega;
     const double mfit = omega <= 0.491 ? 0.37464 + 1.54226 * omega - 0.26992 * omega * omega
@@ -572,7 +598,8 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
         (rc = dalloc(&P->phi, N)) || (rc = dalloc(&P->eos_m, N)) || (rc = dalloc(&P->eos_dm, N)) ||
         (rc = dalloc(&P->conn_ptr, N + 1)) || (rc = dalloc(&P->conn_p, rock->nconn)) ||
         (rc = dalloc(&P->conn_T, rock->nconn)) || (rc = dalloc(&P->conn_m, rock->nconn)) ||
-        (rc = dalloc(&P->kx, N)) || (rc = dalloc(&P->ky, N)) || (rc = dalloc(&P->kz, N)))
+        (rc = dalloc(&P->kx, N)) || (rc = dalloc(&P->ky, N)) || (rc = dalloc(&P->kz, N)) ||
+        (rock->rate_Q && (rc = dalloc(&P->rateQ, N))))
         return fail(rc);
     if ((rc = reduce_ws_init(P->red))) return fail(rc);
     if (cudaHostAlloc((void **)&P->noroot_h, sizeof(int), cudaHostAllocMapped) != cudaSuccess ||
@@ -590,6 +617,8 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
     ok = ok && ck(cudaMemcpyAsync(P->kx, rock->kx, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     ok = ok && ck(cudaMemcpyAsync(P->ky, rock->ky, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     ok = ok && ck(cudaMemcpyAsync(P->kz, rock->kz, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
+    if (rock->rate_Q)
+        ok = ok && ck(cudaMemcpyAsync(P->rateQ, rock->rate_Q, N * sizeof(double), cudaMemcpyDeviceToDevice, st));
     if (rock->nconn > 0) {
         ok = ok && ck(cudaMemcpyAsync(cell, rock->conn_cell, rock->nconn * sizeof(int),
                                       cudaMemcpyDeviceToDevice, st));
@@ -621,7 +650,7 @@ extern "C" int ras_problem_create(const ras_grid *grid, const ras_eos *eos, cons
 extern "C" void ras_problem_destroy(ras_problem *P) {
     if (!P) return;
     dfree(P->Tx); dfree(P->Ty); dfree(P->Tz); dfree(P->phi);
-    dfree(P->kx); dfree(P->ky); dfree(P->kz);
+    dfree(P->kx); dfree(P->ky); dfree(P->kz); dfree(P->rateQ);
     dfree(P->eos_m); dfree(P->eos_dm);
     dfree(P->conn_ptr); dfree(P->conn_p); dfree(P->conn_T); dfree(P->conn_m);
     reduce_ws_free(P->red);
@@ -642,7 +671,7 @@ int residual_eval_impl(ras_problem *P, const double *p, const double *pl, const 
     k_eos_storage<<<grid_for(P->N), 256, 0, st>>>(P->N, E, P->V, 1.0 / dt, order, p, pl,
                                                    order == 2 ? plm1 : pl, P->phi, F,
                                                    J ? J[0] : nullptr, P->eos_m, P->eos_dm,
-                                                   P->noroot_d);
+                                                   P->noroot_d, P->conservative, P->rateQ);
     RAS_LAUNCHED();
     const int t = stencil_threads(P->nx);
     const dim3 g = stencil_grid(P->nx, P->ny, P->nz, t);

@@ -32,7 +32,7 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
 class Grid(C.Structure):
     _fields_ = [("nx", C.c_int), ("ny", C.c_int), ("nz", C.c_int),
                 ("hx", C.c_double), ("hy", C.c_double), ("hz", C.c_double), ("gz", C.c_double),
-                ("upwind", C.c_int)]
+                ("upwind", C.c_int), ("conservative", C.c_int)]
 
 
 class Eos(C.Structure):
@@ -44,7 +44,7 @@ class Eos(C.Structure):
 class Rock(C.Structure):
     _fields_ = [("kx", C.c_void_p), ("ky", C.c_void_p), ("kz", C.c_void_p), ("phi", C.c_void_p),
                 ("nconn", C.c_int), ("conn_cell", C.c_void_p), ("conn_p", C.c_void_p),
-                ("conn_T", C.c_void_p)]
+                ("conn_T", C.c_void_p), ("rate_Q", C.c_void_p)]
 
 
 class Stencil(C.Structure):
@@ -186,10 +186,6 @@ class Problem:
     """ras_problem handle built from a synthetic.Reservoir."""
 
     def __init__(self, res, device="cuda"):
-        if getattr(res, "rate_Q", None) is not None:
-            raise NotImplementedError("fixed injection rates (Reservoir.rate_Q) are not in the library")
-        if getattr(res, "conservative", False):
-            raise NotImplementedError("the conservative accumulation form is not in the library")
         g = res.grid
         self.res = res
         self.N = g.n
@@ -203,14 +199,18 @@ class Problem:
         self._cc = torch.as_tensor(res.conns.cell, dtype=torch.int32, device=dev).contiguous()
         self._cp = torch.as_tensor(res.conns.p, **f64).contiguous()
         self._cT = torch.as_tensor(res.conns.T, **f64).contiguous()
+        rq = getattr(res, "rate_Q", None)
+        self._rq = None if rq is None else torch.as_tensor(rq, **f64).contiguous()
         fl = res.fluid
         grid = Grid(g.nx, g.ny, g.nz, g.hx, g.hy, g.hz, float(getattr(res, "gravity", 0.0)),
-                    1 if getattr(res, "upwind", False) else 0)
+                    1 if getattr(res, "upwind", False) else 0,
+                    1 if getattr(res, "conservative", False) else 0)
         eos = Eos(fl.Tc, fl.pc, 0.0 if fl.omega_from_Tb else fl.omega, fl.Tb,
                   1 if fl.omega_from_Tb else 0, fl.T, fl.R, fl.W, fl.mu)
         rock = Rock(self._kx.data_ptr(), self._ky.data_ptr(), self._kz.data_ptr(),
                     self._phi.data_ptr(), len(res.conns), self._cc.data_ptr(),
-                    self._cp.data_ptr(), self._cT.data_ptr())
+                    self._cp.data_ptr(), self._cT.data_ptr(),
+                    self._rq.data_ptr() if self._rq is not None else None)
         h = C.c_void_p()
         check(lib().ras_problem_create(C.byref(grid), C.byref(eos), C.byref(rock), _stream(),
                                        C.byref(h)), "ras_problem_create")

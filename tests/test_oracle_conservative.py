@@ -1,8 +1,8 @@
 """Pins of the oracle's conservative accumulation option (Reservoir.conservative):
 a closed domain keeps its discrete mass sum V phi p/Z through a converged step
 (the non-conservative form of Eq. gover_sys does not: O(dt) drift), the two forms
-coincide for an ideal gas (Z = 1, c = 1), the Jacobian matches central
-differences, and the library refuses the option (not on the GPU path yet)."""
+coincide for an ideal gas (Z = 1, c = 1), and the Jacobian matches central
+differences. (GPU parity: tests/test_gpu_physics_options.py.)"""
 import dataclasses
 
 import numpy as np
@@ -69,9 +69,3 @@ def test_conservative_jacobian_matches_central_differences(order):
         fd[:, j] = (disc.residual(prob, p + e, p_l, p_lm1, dt, order)
                     - disc.residual(prob, p - e, p_l, p_lm1, dt, order)) / (2 * h)
     assert np.abs(A - fd).max() / np.abs(fd).max() < 1e-7
-
-
-def test_library_refuses_the_conservative_form():
-    from paper_2007_13966_gb300 import ras
-    with pytest.raises(NotImplementedError):
-        ras.Problem(dataclasses.replace(syn.small_3d(4, 3, 2, seed=1), conservative=True))

@@ -3,8 +3,8 @@ velocity): steady ideal-gas flow from a fixed-rate inlet to a fixed outlet
 pressure matches its closed form (every face carries the inlet's p_0 Q, so
 p_i^2 = p_R^2 + 2 mu p_0 Q R_i with R_i the series resistance from cell i to the
 outlet, p_0 the root of p_0^2 = p_R^2 + 2 mu Q R_0 p_0), the Jacobian matches
-central differences, mass balance holds with the inflow, and the library refuses
-a reservoir with rates (not on the GPU path yet)."""
+central differences, and mass balance holds with the inflow. (GPU parity:
+tests/test_gpu_physics_options.py.)"""
 import dataclasses
 
 import numpy as np
@@ -66,10 +66,3 @@ def test_jacobian_and_mass_balance_with_rates():
     S = disc.storage(prob, p, p_l, p_lm1, dt, 2)
     out = disc.connection_flux(prob, p).sum() - disc.rate_inflow(prob, p).sum()
     assert abs(F.sum() - S.sum() - out) < 1e-12 * np.abs(F).sum()
-
-
-def test_library_refuses_rates():
-    from paper_2007_13966_gb300 import ras
-    res = dataclasses.replace(syn.small_3d(4, 3, 2, seed=1), rate_Q=np.zeros(24))
-    with pytest.raises(NotImplementedError):
-        ras.Problem(res)
