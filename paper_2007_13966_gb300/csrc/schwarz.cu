@@ -67,6 +67,13 @@ __device__ __forceinline__ void load_rec(const unsigned char *p, Acc &a, Acc &b,
     }
 }
 
+// Multiply-adds of the triangular sweeps, fused explicitly so that every kernel
+// that runs them rounds identically: fmsub(a, b, s) = s - a b, fmadd(a, b, s) = s + a b.
+__device__ __forceinline__ float fmsub(float a, float b, float s) { return __fmaf_rn(-a, b, s); }
+__device__ __forceinline__ double fmsub(double a, double b, double s) { return __fma_rn(-a, b, s); }
+__device__ __forceinline__ float fmadd(float a, float b, float s) { return __fmaf_rn(a, b, s); }
+__device__ __forceinline__ double fmadd(double a, double b, double s) { return __fma_rn(a, b, s); }
+
 // ---------------------------------------------------------------------------
 // cp.async staging
 // ---------------------------------------------------------------------------
@@ -223,9 +230,9 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
                         load_rec<Acc, R>(rec_t + (size_t)RB * lo, ax, ay, az, dinv);
                         Acc *yn = Y + n;
                         Acc s = yn[0];
-                        s -= az * yn[-bxy];
-                        s -= ay * yn[-bx];
-                        s -= ax * yn[-1];
+                        s = fmsub(az, yn[-bxy], s);
+                        s = fmsub(ay, yn[-bx], s);
+                        s = fmsub(ax, yn[-1], s);
                         yn[0] = s * dinv;
                     }
                     __syncthreads();
@@ -240,9 +247,9 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
                         load_rec<Acc, R>(rec_t + (size_t)RB * lo, ax, ay, az, dinv);
                         Acc *yn = Y + n;
                         Acc s = ax * yn[1];
-                        s += ay * yn[bx];
-                        s += az * yn[bxy];
-                        yn[0] = yn[0] - dinv * s;
+                        s = fmadd(ay, yn[bx], s);
+                        s = fmadd(az, yn[bxy], s);
+                        yn[0] = fmsub(dinv, s, yn[0]);
                     }
                     __syncthreads();
                 }
@@ -258,9 +265,9 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
                     Acc ax, ay, az, dinv;
                     load_rec<Acc, R>(rec + (size_t)RB * (q - qa), ax, ay, az, dinv);
                     Acc s = Y[n];
-                    s -= az * Y[n - bxy];
-                    s -= ay * Y[n - bx];
-                    s -= ax * Y[n - 1];
+                    s = fmsub(az, Y[n - bxy], s);
+                    s = fmsub(ay, Y[n - bx], s);
+                    s = fmsub(ax, Y[n - 1], s);
                     Y[n] = s * dinv;
                 }
                 __syncthreads();
@@ -274,9 +281,9 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
                     Acc ax, ay, az, dinv;
                     load_rec<Acc, R>(rec + (size_t)RB * (q - qa), ax, ay, az, dinv);
                     Acc s = ax * Y[n + 1];
-                    s += ay * Y[n + bx];
-                    s += az * Y[n + bxy];
-                    Y[n] = Y[n] - dinv * s;
+                    s = fmadd(ay, Y[n + bx], s);
+                    s = fmadd(az, Y[n + bxy], s);
+                    Y[n] = fmsub(dinv, s, Y[n]);
                 }
                 __syncthreads();
             }
@@ -580,9 +587,9 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                 const Acc yz = k > 0 ? vz : (Acc)0;
                 const Acc yy = j > 0 ? vy : (Acc)0;
                 Acc s = (Acc)ringA[e];
-                s -= az * yz;
-                s -= ay * yy;
-                s -= ax * xprev[m];
+                s = fmsub(az, yz, s);
+                s = fmsub(ay, yy, s);
+                s = fmsub(ax, xprev[m], s);
                 const Acc y = s * dinv;
                 Y[n] = y;
                 xprev[m] = y;
@@ -593,9 +600,9 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                 const Acc zy = j < by - 1 ? vy : (Acc)0;
                 const Acc zz = k < bz - 1 ? vz : (Acc)0;
                 Acc s = ax * xprev[m];
-                s += ay * zy;
-                s += az * zz;
-                const Acc y = Y[n] - dinv * s;
+                s = fmadd(ay, zy, s);
+                s = fmadd(az, zz, s);
+                const Acc y = fmsub(dinv, s, Y[n]);
                 Y[n] = y;
                 xprev[m] = y;
                 if (i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 &&
