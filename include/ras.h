@@ -405,20 +405,20 @@ int ras_set_apply_schedule(ras_precond *pc, int chunk_cells, int threads);
 int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads);
 
 /* Kernel of the fine-level subdomain solves of Eq. equ:as-left (a performance
- * setting: both give the same values, bit for bit, in the same arithmetic order).
+ * setting: both give the same values, bit for bit, in the same arithmetic order,
+ * from the same factor records; the switch takes effect at the next ras_apply).
  * 0: level-scheduled, every wavefront level i + j + k of a box separated by a CTA
  * barrier (the schedule above applies). 1: pipelined, the default where allowed:
  * a box's x-pencils (j, k) advance one cell per step, each warp handling the
  * anti-diagonals j + k = w (mod warps) and waiting only for the warp of the
  * neighbouring diagonal through a bounded progress wait in shared memory; the
- * records, r and old z values are streamed per lane a few steps ahead and z is
- * written as soon as it is final. Allowed for left-RAS (ras_type 1) ILU(0) with
- * FP32 or BF16 factors when every overlapped box has at most 24 cells along x and
- * at most 32 along y or z (RAS_EINVAL otherwise). The kernels store the factors in
- * different orders, so a change takes effect at the next ras_factor and ras_apply
- * returns RAS_EINVAL until then. A bounded wait of the pipelined kernel that runs
- * out (RAS_PIPE_POLLS in the environment at ras_setup shortens it, for tests)
- * makes the next ras_factor of the handle return RAS_ETIMEOUT. */
+ * records are staged in chunks of levels (the schedule's chunk size) and, without
+ * accumulation, z is written as soon as it is final. Allowed for left-RAS
+ * (ras_type 1) ILU(0) with FP32 or BF16 factors when every overlapped box has at
+ * most 24 cells along x and at most 32 along y or z (RAS_EINVAL otherwise). A
+ * bounded wait of the pipelined kernel that runs out (RAS_PIPE_POLLS in the
+ * environment at ras_setup shortens it, for tests) makes the next ras_factor of
+ * the handle return RAS_ETIMEOUT. */
 int ras_set_apply_kernel(ras_precond *pc, int kernel);
 int ras_get_apply_kernel(const ras_precond *pc, int *kernel);
 

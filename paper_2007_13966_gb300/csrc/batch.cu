@@ -723,7 +723,6 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
         op.nx = P->nx; op.ny = P->ny; op.nz = P->nz;
         op.mx = bmagic(P->nx); op.my = bmagic(P->ny);
         B->ops.push_back(op);
-        ras1_use_level_layout(pc->fine);   // the batched launch runs the level-scheduled solves
         ras1_apply_params(pc->fine, ap[i]);
         for (int q = 0; q < pc->fine.nsub; ++q) { box_inst.push_back(i); box_local.push_back(q); }
         B->block = std::max(B->block, pc->fine.block);

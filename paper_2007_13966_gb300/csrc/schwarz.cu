@@ -352,28 +352,29 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply_batch(BatchApply B) {
 // anti-diagonals d = w (mod warps), one lane per pencil, at most PIPE_M of them at
 // once; it waits only for the warp of diagonal d - 1 (d + 1 backwards) through a
 // progress word in shared memory (release / acquire, bounded spin) instead of a
-// CTA barrier per wavefront level. Every lane streams its records, r values and,
-// when accumulating, old z values PIPE_PF steps ahead into a shared-memory ring with
-// cp.async, and the backward sweep writes each owned cell's z as soon as it is
-// final: there is no separate gather or write-back phase. At the start each CTA
-// asks L2 for its box's records and r rows (cp.async.bulk.prefetch), so that DRAM
-// streams while the sweeps run. The arithmetic of every cell is the same as in
-// the level-scheduled kernel, in the same order.
+// CTA barrier per wavefront level. The factor records are in level order with the
+// cells of a level grouped by anti-diagonal (the layout both solve kernels read);
+// chunks of consecutive levels are staged into a shared-memory ring with cp.async
+// two chunks ahead, one CTA barrier per chunk. Without accumulation the backward
+// sweep writes each owned cell's z as soon as it is final. The arithmetic of every
+// cell is the same as in the level-scheduled kernel, in the same order.
 // ---------------------------------------------------------------------------
 
 constexpr int PIPE_M = 2;    // concurrently active diagonals per warp (slots)
-constexpr int PIPE_PF = 4;   // steps of cp.async look-ahead per lane
 
 struct PipeParams {
     const SubInfo *subs;
     const ShapeInfo *shapes;
     const DiagInfo *diag;
+    const int *lvl, *chunk;
     const unsigned char *fwd, *bwd;
     const double *r;
     double *z;
     int nx, ny, nz;
     int accumulate;
     int ycap;          // elements of the padded box vector
+    int lcap;          // level starts (incl. the end) capacity
+    int chunk_cells;   // ring slot capacity (cells)
     int poll_limit;    // spins (per thread, over the whole launch) before waits give up
     int *err;          // set to 2 when a wait gave up
 };
@@ -388,47 +389,20 @@ __device__ __forceinline__ void st_release_cta(int *p, int v) {
     asm volatile("st.release.cta.shared::cta.b32 [%0], %1;\n"
                  :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
 }
-__device__ __forceinline__ void cp_async8(void *smem, const void *gmem) {
-    const unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(s), "l"(gmem) : "memory");
-}
-// L2 prefetch of the 16-byte-aligned interior of the global bytes [b0, b1)
-__device__ __forceinline__ void l2_prefetch(const void *b0, const void *b1) {
-    const unsigned long long a0 = ((unsigned long long)b0 + 15) & ~15ull;
-    const unsigned long long a1 = (unsigned long long)b1 & ~15ull;
-    if (a1 > a0)
-        asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;\n" ::"l"(a0), "r"((unsigned)(a1 - a0))
-                     : "memory");
-}
-template <int RB>
-__device__ __forceinline__ void cp_async_rec(void *smem, const void *gmem) {
-    if constexpr (RB == 16) cp_async16(smem, gmem);
-    else cp_async8(smem, gmem);
-}
 
-// Diagonals of slot m of warp w: d = base + L t (base = w + NW m < L = NW * PIPE_M,
-// L >= bx, so at most one is active at a step). rem = (step - base) mod L is kept
-// incrementally; forward at step G the active diagonal is d = G - rem at i = rem,
-// active iff rem < bx and 0 <= d <= D-1. Backwards (G' = G - S) the slot runs the
-// same diagonals in reverse: with dt = D-1-d, dt = G' - rem at i = bx-1-rem, rem =
-// (G' - bb) mod L, bb = (D-1-base) mod L, active iff rem < bx and 0 <= dt <= D-1.
-struct PipeCursor {
-    int rem[PIPE_M];
-    __device__ __forceinline__ void start(int first_mod_L, int m, int L) {   // (0 - first) mod L
-        rem[m] = first_mod_L == 0 ? 0 : L - first_mod_L;
-    }
-    __device__ __forceinline__ void step(int L) {
-#pragma unroll
-        for (int m = 0; m < PIPE_M; ++m) rem[m] = rem[m] + 1 == L ? 0 : rem[m] + 1;
-    }
-};
+// Slot m of warp w runs the diagonals d = base + L t (base = w + NW m < L = NW *
+// PIPE_M, L >= bx, so at most one is active at a step); rem = (step - base) mod L is
+// kept incrementally. Forward at step G: d = G - rem at i = rem, active iff rem < bx
+// and 0 <= d <= D-1. Backwards (G' = G - S) the same diagonals in reverse order:
+// dt = D-1-d = G' - rem at i = bx-1-rem, rem = (G' - bb) mod L, bb = (D-1-base) mod L,
+// active iff rem < bx and 0 <= dt <= D-1.
 
 template <int PREC>
 __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     using R = typename RecT<PREC>::T;
     using Acc = typename RecT<PREC>::Acc;
     constexpr int RB = (int)sizeof(R);
-    constexpr int M = PIPE_M, PF = PIPE_PF;
+    constexpr int M = PIPE_M, NBUF = 3;
     extern __shared__ __align__(16) unsigned char smem[];
 
     const int NW = blockDim.x >> 5;
@@ -441,101 +415,72 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
 
-    // shared memory: [Y: ycap][progress: 32][diagonals][record ring][value ring]
+    // shared memory: [Y: ycap][level starts: lcap][progress: 32][diagonals: dcap][ring]
     Acc *Y = reinterpret_cast<Acc *>(smem);
-    int *prog = reinterpret_cast<int *>(smem + (((size_t)P.ycap * sizeof(Acc) + 15) & ~(size_t)15));
+    int *lvl_s = reinterpret_cast<int *>(smem + (((size_t)P.ycap * sizeof(Acc) + 15) & ~(size_t)15));
+    int *prog = lvl_s + P.lcap;
     DiagInfo *dg = reinterpret_cast<DiagInfo *>(prog + 32);
-    unsigned char *ringR = reinterpret_cast<unsigned char *>(dg + ((D + 1) & ~1));
-    double *ringA = reinterpret_cast<double *>(ringR + (size_t)NW * PF * M * 32 * RB);
+    unsigned char *ring = reinterpret_cast<unsigned char *>(dg + ((D + 1) & ~1));
+    const int rcap = ((P.chunk_cells * RB + 32) + 15) & ~15;
 
-    const unsigned char *recf = P.fwd + si.foff * RB;
-    const unsigned char *recb = P.bwd + si.foff * RB;
-    const double *rg = P.r + g0;
-    double *zg = P.z + g0;
-
-    // ask L2 for the box's forward records and r rows, then the backward records
-    {
-        const long long nb = (long long)sh.ncell * RB;
-        const int nch = (int)((nb + 4095) >> 12);
-        const int rows = by * bz;
-        for (int t = threadIdx.x; t < nch + rows; t += blockDim.x) {
-            if (t < nch) {
-                l2_prefetch(recf + ((long long)t << 12), recf + min(nb, (long long)(t + 1) << 12));
-            } else {
-                const int row = t - nch, j = row % by, k = row / by;
-                const double *a = rg + (long long)nx * j + (long long)nxy * k;
-                l2_prefetch(a, a + bx);
-            }
-        }
-        for (int t = threadIdx.x; t < nch; t += blockDim.x)
-            l2_prefetch(recb + ((long long)t << 12), recb + min(nb, (long long)(t + 1) << 12));
-    }
+    const int *chunk_lev = P.chunk + sh.chunk_off;
+    const int nchunk = sh.nchunk, nstage = 2 * nchunk;
+    for (int t = threadIdx.x; t <= S; t += blockDim.x) lvl_s[t] = P.lvl[sh.lvl_off + t];
     for (int t = threadIdx.x; t < D; t += blockDim.x) dg[t] = P.diag[sh.diag_off + t];
     if (threadIdx.x < 32) prog[threadIdx.x] = -1;
     __syncthreads();
 
-    const int L = NW * M;
-    const bool acc = P.accumulate != 0;
-    int bb[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) bb[m] = ((D - 1 - (w + NW * m)) % L + L) % L;
-
-    // the slot's active diagonal and cell index at global step G with position rem
-    auto active = [&](int G, int rem, int &d, int &i) -> bool {
-        if (rem >= bx) return false;
-        if (G < S) {
-            d = G - rem;
-            i = rem;
-            return d >= 0 && d <= D - 1;
-        }
-        const int dt = G - S - rem;
-        d = D - 1 - dt;
-        i = bx - 1 - rem;
-        return dt >= 0 && dt <= D - 1;
-    };
-
-    // cp.async of the lane's data for global step G (cursor position cp) into ring stage G % PF
-    PipeCursor cp;
-    auto prefetch = [&](int G) {
-        if (G == S) {
-#pragma unroll
-            for (int m = 0; m < M; ++m) cp.start(bb[m], m, L);
-        }
-        if (G < 2 * S) {
-            const int stage = G % PF;
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                int d, i;
-                if (!active(G, cp.rem[m], d, i)) continue;
-                const DiagInfo di = dg[d];
-                const int jmin = di.jmin_cnt & 0xffff, cnt = di.jmin_cnt >> 16;
-                if (lane >= cnt) continue;
-                const size_t e = ((size_t)(w * PF + stage) * M + m) * 32 + lane;
-                const long long ri = (long long)di.base + (long long)i * cnt + lane;
-                const int j = jmin + lane, k = d - j;
-                const long long go = i + (long long)nx * j + (long long)nxy * k;
-                if (G < S) {
-                    cp_async_rec<RB>(ringR + e * RB, recf + ri * RB);
-                    cp_async8(ringA + e, rg + go);
-                } else {
-                    cp_async_rec<RB>(ringR + e * RB, recb + ri * RB);
-                    if (acc && i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 &&
-                        k >= si.oz0 && k < si.oz1)
-                        cp_async8(ringA + e, zg + go);
-                }
-            }
+    // stage t < nchunk: forward chunk t; t >= nchunk: backward chunk 2 nchunk - 1 - t
+    auto issue = [&](int t) {
+        if (t < nstage) {
+            const bool fw = t < nchunk;
+            const int c = fw ? t : nstage - 1 - t;
+            const int qa = lvl_s[chunk_lev[c]], qb = lvl_s[chunk_lev[c + 1]];
+            stage_bytes(ring + (size_t)(t % NBUF) * rcap, fw ? P.fwd : P.bwd,
+                        (si.foff + qa) * (long long)RB, (si.foff + qb) * (long long)RB);
         }
         cp_async_commit();
-        cp.step(L);
     };
 #pragma unroll
-    for (int m = 0; m < M; ++m) cp.start(w + NW * m, m, L);
-#pragma unroll
-    for (int t = 0; t < PF; ++t) prefetch(t);
+    for (int t = 0; t < NBUF - 1; ++t) issue(t);
 
-    PipeCursor cc;
+    // gather R_i^delta r into the padded box vector (GB loads in flight per thread)
+    {
+        constexpr int GB = 12;
+        const double *rg = P.r + g0;
+        const unsigned mbx = magic_div(bx), mby = magic_div(by);
+        const int ncell = sh.ncell;
+        for (int q0 = threadIdx.x; q0 < ncell; q0 += GB * blockDim.x) {
+            double v[GB];
+            int yo[GB];
 #pragma unroll
-    for (int m = 0; m < M; ++m) cc.start(w + NW * m, m, L);
+            for (int m = 0; m < GB; ++m) {
+                const int q = q0 + m * (int)blockDim.x;
+                if (q < ncell) {
+                    const int row = fast_div(q, bx, mbx), k = fast_div(row, by, mby);
+                    const int i = q - row * bx, j = row - k * by;
+                    v[m] = __ldg(rg + i + (long long)nx * j + (long long)nxy * k);
+                    yo[m] = i + PX * j + PXY * k;
+                }
+            }
+#pragma unroll
+            for (int m = 0; m < GB; ++m) {
+                const int q = q0 + m * (int)blockDim.x;
+                if (q < ncell) Y[yo[m]] = (Acc)v[m];
+            }
+        }
+    }
+
+    const int L = NW * M;
+    const bool acc = P.accumulate != 0;
+    double *zg = P.z + g0;
+    int rem[M], bb[M];
+#pragma unroll
+    for (int m = 0; m < M; ++m) {
+        const int base = w + NW * m;
+        rem[m] = base == 0 ? 0 : L - base;              // (0 - base) mod L
+        bb[m] = ((D - 1 - base) % L + L) % L;
+    }
     Acc xprev[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) xprev[m] = (Acc)0;
@@ -543,19 +488,44 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     int spins_left = P.poll_limit;
     const int ylast = P.ycap - 1;
 
+    int t = -1, lev_lo = 0, lev_hi = -1;   // current stage and its level range
+    long long roff = 0;                     // ring byte offset of record 0 of the box
     for (int G = 0; G < 2 * S; ++G) {
+        const bool fw = G < S;
         if (G == S) {
 #pragma unroll
-            for (int m = 0; m < M; ++m) cc.start(bb[m], m, L);
+            for (int m = 0; m < M; ++m) rem[m] = bb[m] == 0 ? 0 : L - bb[m];
         }
-        cp_async_wait<PF - 1>();
-        const bool fw = G < S;
+        const int lev = fw ? G : 2 * S - 1 - G;
+        if (G == S || lev < lev_lo || lev > lev_hi) {   // next stage of the ring (all warps together)
+            ++t;
+            cp_async_wait<NBUF - 2>();
+            __syncthreads();
+            issue(t + NBUF - 1);
+            const int c = t < nchunk ? t : nstage - 1 - t;
+            lev_lo = chunk_lev[c];
+            lev_hi = chunk_lev[c + 1] - 1;
+            const int qa = lvl_s[lev_lo];
+            roff = (long long)(t % NBUF) * rcap + (((si.foff + qa) * (long long)RB) & 15) - (long long)RB * qa;
+        }
         int dd[M], ii[M];
         bool act[M];
         bool need = false;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            act[m] = active(G, cc.rem[m], dd[m], ii[m]);
+            act[m] = false;
+            if (rem[m] < bx) {
+                if (fw) {
+                    dd[m] = G - rem[m];
+                    ii[m] = rem[m];
+                    act[m] = dd[m] >= 0 && dd[m] <= D - 1;
+                } else {
+                    const int dt = G - S - rem[m];
+                    dd[m] = D - 1 - dt;
+                    ii[m] = bx - 1 - rem[m];
+                    act[m] = dt >= 0 && dt <= D - 1;
+                }
+            }
             if (act[m]) need = need || (fw ? dd[m] > 0 : dd[m] < D - 1);
         }
         if (need) {
@@ -567,7 +537,9 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                 }
             }
         }
-        const int stage = G % PF;
+        // cells of level lev: diagonals dlo .. ; diagonal d starts at cum(d) - cum(dlo)
+        const int dlo = max(0, lev - bx + 1);
+        const long long rlev = roff + (long long)RB * (lvl_s[lev] - dg[dlo].base);
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             if (!act[m]) continue;
@@ -577,16 +549,15 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
             if (lane >= cnt) continue;
             const int j = jmin + lane, k = d - j;
             const int n = i + PX * j + PXY * k;
-            const size_t e = ((size_t)(w * PF + stage) * M + m) * 32 + lane;
             Acc ax, ay, az, dinv;
-            load_rec<Acc, R>(ringR + e * RB, ax, ay, az, dinv);
+            load_rec<Acc, R>(ring + (rlev + (long long)RB * (di.base + lane)), ax, ay, az, dinv);
             if (fw) {
                 // w_n = (r_n - a_z w_{n-bxy} - a_y w_{n-bx} - a_x w_{n-1}) / d_n
                 if (i == 0) xprev[m] = (Acc)0;
                 const Acc vz = Y[max(n - PXY, 0)], vy = Y[max(n - PX, 0)];
                 const Acc yz = k > 0 ? vz : (Acc)0;
                 const Acc yy = j > 0 ? vy : (Acc)0;
-                Acc s = (Acc)ringA[e];
+                Acc s = Y[n];
                 s = fmsub(az, yz, s);
                 s = fmsub(ay, yy, s);
                 s = fmsub(ax, xprev[m], s);
@@ -605,19 +576,45 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                 const Acc y = fmsub(dinv, s, Y[n]);
                 Y[n] = y;
                 xprev[m] = y;
-                if (i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 &&
-                    k < si.oz1) {
-                    const long long go = i + (long long)nx * j + (long long)nxy * k;
-                    zg[go] = acc ? ringA[e] + (double)y : (double)y;
-                }
+                if (!acc && i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 &&
+                    k < si.oz1)
+                    zg[i + (long long)nx * j + (long long)nxy * k] = (double)y;
             }
         }
         __syncwarp();
         if (lane == 0) st_release_cta(&prog[w], G);
-        prefetch(G + PF);
-        cc.step(L);
+#pragma unroll
+        for (int m = 0; m < M; ++m) rem[m] = rem[m] + 1 == L ? 0 : rem[m] + 1;
     }
     cp_async_wait<0>();
+    if (!acc) return;
+    // z += (R_i^0)^T y: flat over the owned box, GW old values in flight per thread
+    __syncthreads();
+    constexpr int GW = 8;
+    const int owx = si.ox1 - si.ox0, owy = si.oy1 - si.oy0;
+    const int nown = owx * owy * (si.oz1 - si.oz0);
+    const unsigned mox = magic_div(owx), moy = magic_div(owy);
+    for (int q0 = threadIdx.x; q0 < nown; q0 += GW * blockDim.x) {
+        int yq[GW];
+        long long go[GW];
+        double prev[GW];
+#pragma unroll
+        for (int m = 0; m < GW; ++m) {
+            const int q = q0 + m * (int)blockDim.x;
+            yq[m] = -1;
+            prev[m] = 0.0;
+            if (q < nown) {
+                const int row = fast_div(q, owx, mox), k = fast_div(row, owy, moy);
+                const int i = si.ox0 + q - row * owx, j = si.oy0 + row - k * owy, kk = si.oz0 + k;
+                yq[m] = i + PX * j + PXY * kk;
+                go[m] = i + (long long)nx * j + (long long)nxy * kk;
+                prev[m] = zg[go[m]];
+            }
+        }
+#pragma unroll
+        for (int m = 0; m < GW; ++m)
+            if (yq[m] >= 0) zg[go[m]] = prev[m] + (double)Y[yq[m]];
+    }
 }
 
 // z (+)= sum over the overlapped boxes covering each cell of their solution
@@ -658,7 +655,6 @@ struct FactorParams {
     const ShapeInfo *shapes;
     const int *lvl;
     const unsigned *cells;
-    const DiagInfo *diag;   // non-null: records in the pipelined (diagonal) layout
     Stencil7 A;
     void *fwd, *bwd;
     int nx, ny, nz;
@@ -704,14 +700,9 @@ __global__ void __launch_bounds__(512) k_ras_factor(FactorParams P) {
         const int n = i + bx * j + bxy * k;
         const long long g = g0 + i + (long long)nx * j + (long long)nxy * k;
         const double dinv = 1.0 / D[n];
-        long long pos = q;
-        if (P.diag) {   // diagonal d = j + k, then i, then pencil j - jmin
-            const DiagInfo di = P.diag[sh.diag_off + j + k];
-            pos = di.base + (long long)i * (di.jmin_cnt >> 16) + (j - (di.jmin_cnt & 0xffff));
-        }
-        store_rec<PREC>(P.fwd, si.foff + pos, (fl & F_MX) ? Amx[g] : 0.0, (fl & F_MY) ? Amy[g] : 0.0,
+        store_rec<PREC>(P.fwd, si.foff + q, (fl & F_MX) ? Amx[g] : 0.0, (fl & F_MY) ? Amy[g] : 0.0,
                         (fl & F_MZ) ? Amz[g] : 0.0, dinv);
-        store_rec<PREC>(P.bwd, si.foff + pos, (fl & F_PX) ? Apx[g] : 0.0, (fl & F_PY) ? Apy[g] : 0.0,
+        store_rec<PREC>(P.bwd, si.foff + q, (fl & F_PX) ? Apx[g] : 0.0, (fl & F_PY) ? Apy[g] : 0.0,
                         (fl & F_PZ) ? Apz[g] : 0.0, dinv);
     }
 }
@@ -748,6 +739,16 @@ static int set_factor_attr(size_t) {
     RAS_CK(cudaFuncSetAttribute(k_ras_factor<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 SMEM_OPTIN));
     return RAS_OK;
+}
+
+// shared memory of the pipelined solves for the handle's current chunk size
+static size_t pipe_smem(Ras1 &R) {
+    const size_t acc = R.prec == 64 ? 8 : 4;
+    const size_t ybytes = (((size_t)R.ycap_pipe * acc) + 15) & ~(size_t)15;
+    const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
+    R.smem_pipe = ybytes + (size_t)R.lcap * sizeof(int) + 32 * sizeof(int) +
+                  (size_t)R.dcap_pipe * sizeof(DiagInfo) + 3 * rcap;
+    return R.smem_pipe;
 }
 
 // Level schedule of the subdomain solves: chunks of consecutive levels with at most
@@ -818,6 +819,7 @@ int ras1_set_schedule(Ras1 &R, int chunk_cells, int threads) {
     R.chunk_cells = T.chunk_cells;
     R.block = T.block;
     R.smem_apply = T.smem_apply;
+    if (R.pipe_ok && pipe_smem(R) > 227 * 1024) R.pipe = R.pipe_ok = 0;
     return RAS_OK;
 }
 
@@ -884,14 +886,16 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
                                 levels[i + j + k].push_back((unsigned)i | ((unsigned)j << 8) |
                                                             ((unsigned)k << 16) | (fl << 24));
                             }
-                    // natural order inside a level: sort by n = i + bx (j + by k)
+                    // inside a level, cells grouped by x-pencil anti-diagonal d = j + k,
+                    // then by j (the pipelined solves read a diagonal's cells contiguously;
+                    // the cells of a level are independent, so the order is free)
                     for (auto &L : levels)
                         std::sort(L.begin(), L.end(), [&](unsigned a, unsigned b) {
-                            auto nat = [&](unsigned e) {
-                                return (int)(e & 255u) + bx * ((int)((e >> 8) & 255u) +
-                                                               by * (int)((e >> 16) & 255u));
+                            auto key = [&](unsigned e) {
+                                const int j = (int)((e >> 8) & 255u), k = (int)((e >> 16) & 255u);
+                                return (j + k) * 256 + j;
                             };
-                            return nat(a) < nat(b);
+                            return key(a) < key(b);
                         });
                     while (cell_tab.size() % 4) { cell_tab.push_back(0); cidx_tab.push_back(0); }
                     sh.cell_off = (int)cell_tab.size();
@@ -916,7 +920,7 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
                         const int jmin = std::max(0, d - (bz - 1)), jmax = std::min(d, by - 1);
                         const int cnt = jmax - jmin + 1;
                         diag_tab.push_back(DiagInfo{jmin | (cnt << 16), dbase});
-                        dbase += bx * cnt;
+                        dbase += cnt;
                     }
                     sh.pxy = bx * by + (((bx * (by - 1)) % 2 == 0) ? 1 : 0);
                     maxw_all = std::max(maxw_all, maxw);
@@ -977,15 +981,11 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
             const int v = atoi(e);
             if (v >= nw && v <= 12) nw = v;
         }
-        const size_t acc = prec == 64 ? 8 : 4;
-        const size_t ybytes = (((size_t)((ycp + 3) & ~3) * acc) + 15) & ~(size_t)15;
-        const size_t smem = ybytes + 32 * sizeof(int) + (size_t)((dmax + 1) & ~1) * sizeof(DiagInfo) +
-                            (size_t)nw * PIPE_PF * PIPE_M * 32 * (R.rec_bytes + sizeof(double));
-        if (smem > 227 * 1024) ok = false;
-        R.pipe = R.pipe_ok = ok ? 1 : 0;
         R.pipe_warps = nw;
         R.ycap_pipe = (ycp + 3) & ~3;
-        R.smem_pipe = smem;
+        R.dcap_pipe = (dmax + 1) & ~1;
+        if (pipe_smem(R) > 227 * 1024) ok = false;
+        R.pipe = R.pipe_ok = ok ? 1 : 0;
         if (const char *e = getenv("RAS_PIPE_POLLS")) {   // shortened waits (tests)
             const int v = atoi(e);
             if (v > 0) R.pipe_poll_limit = v;
@@ -1058,9 +1058,7 @@ int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st) {
     FactorParams P;
     P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.cells = R.d_cells;
     P.A = A; P.fwd = R.d_fwd; P.bwd = R.d_bwd;
-    P.diag = R.pipe ? R.d_diag : nullptr;
     P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.err = R.d_err;
-    R.stale = 0;
     const int block = std::min(R.block, 256);
     if (R.prec == 64) k_ras_factor<64><<<R.nsub, block, R.smem_factor, st>>>(P);
     else if (R.prec == 32) k_ras_factor<32><<<R.nsub, block, R.smem_factor, st>>>(P);
@@ -1083,12 +1081,10 @@ int ras1_check(Ras1 &R, cudaStream_t st) {
 int ras1_set_kernel(Ras1 &R, int kernel) {
     if (kernel != 0 && kernel != 1) return RAS_EINVAL;
     if (kernel == 1 && !R.pipe_ok) return RAS_EINVAL;
-    if (kernel != R.pipe) R.stale = 1;
     R.pipe = kernel;
     return RAS_OK;
 }
 
-void ras1_use_level_layout(Ras1 &R) { ras1_set_kernel(R, 0); }
 
 void ras1_apply_params(const Ras1 &R, ApplyParams &P) {
     P = ApplyParams{};
@@ -1110,13 +1106,14 @@ int ras1_apply_batch(const BatchApply &B, int nblocks, int prec, int block, size
 }
 
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st) {
-    if (R.stale) return RAS_EINVAL;   // kernel switched: factor again first
     if (R.pipe) {
         PipeParams Q;
         Q.subs = R.d_subs; Q.shapes = R.d_shapes; Q.diag = R.d_diag;
+        Q.lvl = R.d_lvl; Q.chunk = R.d_chunk;
         Q.fwd = (const unsigned char *)R.d_fwd; Q.bwd = (const unsigned char *)R.d_bwd;
         Q.r = r; Q.z = z; Q.nx = R.nx; Q.ny = R.ny; Q.nz = R.nz; Q.accumulate = accumulate;
-        Q.ycap = R.ycap_pipe; Q.poll_limit = R.pipe_poll_limit; Q.err = R.d_err;
+        Q.ycap = R.ycap_pipe; Q.lcap = R.lcap; Q.chunk_cells = R.chunk_cells;
+        Q.poll_limit = R.pipe_poll_limit; Q.err = R.d_err;
         const int threads = 32 * R.pipe_warps;
         if (R.prec == 32) k_ras_pipe<32><<<R.nsub, threads, R.smem_pipe, st>>>(Q);
         else k_ras_pipe<16><<<R.nsub, threads, R.smem_pipe, st>>>(Q);

@@ -15,16 +15,16 @@ struct ShapeInfo {
     int cell_off;    // into cell_tab: ncell packed entries (multiple of 4 aligned)
     int chunk_off;   // into chunk_tab: nchunk + 1 level indices
     int maxw;        // widest level
-    int diag_off;    // into diag_tab: by + bz - 1 anti-diagonals of (j, k) x-pencils
+    int diag_off;    // into diag_tab: by + bz - 1 anti-diagonals d = j + k of the x-pencils (j, k)
     int pxy;         // plane stride of the pipelined apply's vector (bx*by or bx*by + 1)
 };
 
 // One anti-diagonal d = j + k of a box's x-pencils (j, k): its first j, its
-// pencil count and the offset of its records (the pipelined layout stores a
-// box's records by diagonal, then i, then pencil: base + i*cnt + (j - jmin)).
+// pencil count, and the number of pencils on the diagonals before it (inside a
+// wavefront level the cells are grouped by diagonal, then ordered by j).
 struct DiagInfo {
     int jmin_cnt;    // jmin | cnt << 16
-    int base;
+    int base;        // sum of cnt over the diagonals d' < d
 };
 
 // One subdomain: overlapped box origin, its shape, owned box (relative to the
@@ -71,12 +71,12 @@ struct Ras1 {
     int parts[3] = {1, 1, 1};
     std::vector<SubInfo> subs;
     std::vector<ShapeInfo> shapes;
-    // pipelined subdomain solves (left-RAS, FP32 / BF16 factors): records in the
-    // diagonal layout, one warp per group of anti-diagonals
+    // pipelined subdomain solves (left-RAS, FP32 / BF16 factors): one warp per
+    // group of x-pencil anti-diagonals
     int pipe = 0;
     int pipe_ok = 0;          // the handle's shapes and options allow the pipelined solves
-    int stale = 0;            // the record layout changed since the last factorisation
     int pipe_warps = 0;       // warps per box
+    int dcap_pipe = 0;        // anti-diagonal table capacity
     size_t smem_pipe = 0;
     int ycap_pipe = 0;        // floats of the padded box vector
     DiagInfo *d_diag = nullptr;
@@ -98,11 +98,8 @@ int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t
 // new chunk size / threads per box for the subdomain solves (0: default); synchronous
 int ras1_set_schedule(Ras1 &R, int chunk_cells, int threads);
 // subdomain-solve kernel: 0 level-scheduled (CTA barrier per wavefront level),
-// 1 pipelined (records in the diagonal layout); takes effect at the next
-// ras1_factor (applies before it are refused). RAS_EINVAL if not eligible.
+// 1 pipelined (both read the same records); RAS_EINVAL if not eligible
 int ras1_set_kernel(Ras1 &R, int kernel);
-// the level-scheduled layout (batched launches use it)
-void ras1_use_level_layout(Ras1 &R);
 
 // parameters of one handle's apply kernel
 struct ApplyParams {
