@@ -408,17 +408,15 @@ int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads
  * setting: both give the same values, bit for bit, in the same arithmetic order,
  * from the same factor records; the switch takes effect at the next ras_apply).
  * 0: level-scheduled, every wavefront level i + j + k of a box separated by a CTA
- * barrier (the schedule above applies). 1: pipelined, the default where allowed:
- * a box's x-pencils (j, k) advance one cell per step, each warp handling the
- * anti-diagonals j + k = w (mod warps) and waiting only for the warp of the
- * neighbouring diagonal through a bounded progress wait in shared memory; the
- * records are staged in chunks of levels (the schedule's chunk size) and, without
+ * barrier, each thread looking its cell up in the level's table (the schedule
+ * above applies). 1: pencil-wavefront, the default where allowed: each lane owns an
+ * x-pencil (j, k) of a box and advances one cell per level, its -x neighbour kept
+ * in a register, its positions following from the pencil and the level with no
+ * table look-up; one warp per group of anti-diagonals j + k; the records are
+ * staged in chunks of levels (the schedule's chunk size) and, without
  * accumulation, z is written as soon as it is final. Allowed for left-RAS
  * (ras_type 1) ILU(0) with FP32 or BF16 factors when every overlapped box has at
- * most 24 cells along x and at most 32 along y or z (RAS_EINVAL otherwise). A
- * bounded wait of the pipelined kernel that runs out (RAS_PIPE_POLLS in the
- * environment at ras_setup shortens it, for tests) makes the next ras_factor of
- * the handle return RAS_ETIMEOUT. */
+ * most 24 cells along x and at most 32 along y or z (RAS_EINVAL otherwise). */
 int ras_set_apply_kernel(ras_precond *pc, int kernel);
 int ras_get_apply_kernel(const ras_precond *pc, int *kernel);
 

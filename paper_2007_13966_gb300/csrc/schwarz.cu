@@ -341,23 +341,24 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply_batch(BatchApply B) {
 }
 
 // ---------------------------------------------------------------------------
-// Pipelined subdomain solves (left-RAS, FP32 / BF16 factors)
+// Pencil-wavefront subdomain solves (left-RAS, FP32 / BF16 factors)
 //
-// The natural-order ILU(0) sweeps of a box run as a pipeline over its x-pencils
-// (j, k): pencil (j, k) handles its cells i = 0 .. bx-1 one per step, cell i at
-// step i + j + k in the forward sweep, so that its -y and -z neighbours, cells of
-// the pencils (j-1, k) and (j, k-1) on the anti-diagonal d - 1 (d = j + k), were
-// finished one step earlier, and its -x neighbour is the pencil's previous value,
-// kept in a register (the backward sweep mirrors this). A warp handles the
-// anti-diagonals d = w (mod warps), one lane per pencil, at most PIPE_M of them at
-// once; it waits only for the warp of diagonal d - 1 (d + 1 backwards) through a
-// progress word in shared memory (release / acquire, bounded spin) instead of a
-// CTA barrier per wavefront level. The factor records are in level order with the
+// The natural-order ILU(0) sweeps of a box run over its x-pencils (j, k): pencil
+// (j, k) handles its cells i = 0 .. bx-1 one per step, cell i at step i + j + k in
+// the forward sweep (the wavefront level of the cell), so that its -y and -z
+// neighbours, cells of the pencils (j-1, k) and (j, k-1) on the anti-diagonal
+// d - 1 (d = j + k), were finished one step earlier, and its -x neighbour is the
+// pencil's previous value, kept in a register (the backward sweep mirrors this).
+// A warp handles the anti-diagonals d = w (mod warps), one lane per pencil, at most
+// PIPE_M of them at once; consecutive steps are separated by one CTA barrier. Each
+// lane's cell, neighbour and record positions follow from its pencil and the step
+// with no table look-up on the dependent chain (level start -> cell index -> values
+// of the level-scheduled kernel). The factor records are in level order with the
 // cells of a level grouped by anti-diagonal (the layout both solve kernels read);
 // chunks of consecutive levels are staged into a shared-memory ring with cp.async
-// two chunks ahead, one CTA barrier per chunk. Without accumulation the backward
-// sweep writes each owned cell's z as soon as it is final. The arithmetic of every
-// cell is the same as in the level-scheduled kernel, in the same order.
+// two chunks ahead. Without accumulation the backward sweep writes each owned cell's
+// z as soon as it is final. The arithmetic of every cell is the same as in the
+// level-scheduled kernel, in the same order.
 // ---------------------------------------------------------------------------
 
 constexpr int PIPE_M = 2;    // concurrently active diagonals per warp (slots)
@@ -375,20 +376,7 @@ struct PipeParams {
     int ycap;          // elements of the padded box vector
     int lcap;          // level starts (incl. the end) capacity
     int chunk_cells;   // ring slot capacity (cells)
-    int poll_limit;    // spins (per thread, over the whole launch) before waits give up
-    int *err;          // set to 2 when a wait gave up
 };
-
-__device__ __forceinline__ int ld_acquire_cta(const int *p) {
-    int v;
-    asm volatile("ld.acquire.cta.shared::cta.b32 %0, [%1];\n"
-                 : "=r"(v) : "r"((unsigned)__cvta_generic_to_shared(p)) : "memory");
-    return v;
-}
-__device__ __forceinline__ void st_release_cta(int *p, int v) {
-    asm volatile("st.release.cta.shared::cta.b32 [%0], %1;\n"
-                 :: "r"((unsigned)__cvta_generic_to_shared(p)), "r"(v) : "memory");
-}
 
 // Slot m of warp w runs the diagonals d = base + L t (base = w + NW m < L = NW *
 // PIPE_M, L >= bx, so at most one is active at a step); rem = (step - base) mod L is
@@ -415,11 +403,10 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
 
-    // shared memory: [Y: ycap][level starts: lcap][progress: 32][diagonals: dcap][ring]
+    // shared memory: [Y: ycap][level starts: lcap][diagonals: dcap][ring]
     Acc *Y = reinterpret_cast<Acc *>(smem);
     int *lvl_s = reinterpret_cast<int *>(smem + (((size_t)P.ycap * sizeof(Acc) + 15) & ~(size_t)15));
-    int *prog = lvl_s + P.lcap;
-    DiagInfo *dg = reinterpret_cast<DiagInfo *>(prog + 32);
+    DiagInfo *dg = reinterpret_cast<DiagInfo *>(lvl_s + P.lcap);
     unsigned char *ring = reinterpret_cast<unsigned char *>(dg + ((D + 1) & ~1));
     const int rcap = ((P.chunk_cells * RB + 32) + 15) & ~15;
 
@@ -427,7 +414,6 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     const int nchunk = sh.nchunk, nstage = 2 * nchunk;
     for (int t = threadIdx.x; t <= S; t += blockDim.x) lvl_s[t] = P.lvl[sh.lvl_off + t];
     for (int t = threadIdx.x; t < D; t += blockDim.x) dg[t] = P.diag[sh.diag_off + t];
-    if (threadIdx.x < 32) prog[threadIdx.x] = -1;
     __syncthreads();
 
     // stage t < nchunk: forward chunk t; t >= nchunk: backward chunk 2 nchunk - 1 - t
@@ -484,8 +470,6 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     Acc xprev[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) xprev[m] = (Acc)0;
-    const int pred_f = (w + NW - 1) % NW, pred_b = (w + 1) % NW;
-    int spins_left = P.poll_limit;
     const int ylast = P.ycap - 1;
 
     int t = -1, lev_lo = 0, lev_hi = -1;   // current stage and its level range
@@ -510,7 +494,6 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
         }
         int dd[M], ii[M];
         bool act[M];
-        bool need = false;
 #pragma unroll
         for (int m = 0; m < M; ++m) {
             act[m] = false;
@@ -524,16 +507,6 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                     dd[m] = D - 1 - dt;
                     ii[m] = bx - 1 - rem[m];
                     act[m] = dt >= 0 && dt <= D - 1;
-                }
-            }
-            if (act[m]) need = need || (fw ? dd[m] > 0 : dd[m] < D - 1);
-        }
-        if (need) {
-            const int *pw = &prog[fw ? pred_f : pred_b];
-            while (ld_acquire_cta(pw) < G - 1) {
-                if (--spins_left < 0) {   // bounded: record the give-up and go on
-                    atomicExch(P.err, 2);
-                    break;
                 }
             }
         }
@@ -581,8 +554,7 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                     zg[i + (long long)nx * j + (long long)nxy * k] = (double)y;
             }
         }
-        __syncwarp();
-        if (lane == 0) st_release_cta(&prog[w], G);
+        __syncthreads();   // level G done: its values are the next level's neighbours
 #pragma unroll
         for (int m = 0; m < M; ++m) rem[m] = rem[m] + 1 == L ? 0 : rem[m] + 1;
     }
@@ -746,8 +718,8 @@ static size_t pipe_smem(Ras1 &R) {
     const size_t acc = R.prec == 64 ? 8 : 4;
     const size_t ybytes = (((size_t)R.ycap_pipe * acc) + 15) & ~(size_t)15;
     const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
-    R.smem_pipe = ybytes + (size_t)R.lcap * sizeof(int) + 32 * sizeof(int) +
-                  (size_t)R.dcap_pipe * sizeof(DiagInfo) + 3 * rcap;
+    R.smem_pipe = ybytes + (size_t)R.lcap * sizeof(int) + (size_t)R.dcap_pipe * sizeof(DiagInfo) +
+                  3 * rcap;
     return R.smem_pipe;
 }
 
@@ -986,10 +958,6 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
         R.dcap_pipe = (dmax + 1) & ~1;
         if (pipe_smem(R) > 227 * 1024) ok = false;
         R.pipe = R.pipe_ok = ok ? 1 : 0;
-        if (const char *e = getenv("RAS_PIPE_POLLS")) {   // shortened waits (tests)
-            const int v = atoi(e);
-            if (v > 0) R.pipe_poll_limit = v;
-        }
     }
 
     RAS_TRY(dalloc(&R.d_subs, R.subs.size()));
@@ -1073,7 +1041,7 @@ int ras1_check(Ras1 &R, cudaStream_t st) {
     RAS_CK(cudaStreamSynchronize(st));
     if (h) {
         RAS_CK(cudaMemsetAsync(R.d_err, 0, sizeof(int), st));
-        return h == 2 ? RAS_ETIMEOUT : RAS_EZEROPIVOT;
+        return RAS_EZEROPIVOT;
     }
     return RAS_OK;
 }
@@ -1113,7 +1081,6 @@ int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t
         Q.fwd = (const unsigned char *)R.d_fwd; Q.bwd = (const unsigned char *)R.d_bwd;
         Q.r = r; Q.z = z; Q.nx = R.nx; Q.ny = R.ny; Q.nz = R.nz; Q.accumulate = accumulate;
         Q.ycap = R.ycap_pipe; Q.lcap = R.lcap; Q.chunk_cells = R.chunk_cells;
-        Q.poll_limit = R.pipe_poll_limit; Q.err = R.d_err;
         const int threads = 32 * R.pipe_warps;
         if (R.prec == 32) k_ras_pipe<32><<<R.nsub, threads, R.smem_pipe, st>>>(Q);
         else k_ras_pipe<16><<<R.nsub, threads, R.smem_pipe, st>>>(Q);

@@ -71,8 +71,8 @@ struct Ras1 {
     int parts[3] = {1, 1, 1};
     std::vector<SubInfo> subs;
     std::vector<ShapeInfo> shapes;
-    // pipelined subdomain solves (left-RAS, FP32 / BF16 factors): one warp per
-    // group of x-pencil anti-diagonals
+    // pencil-wavefront subdomain solves (left-RAS, FP32 / BF16 factors): one warp
+    // per group of x-pencil anti-diagonals
     int pipe = 0;
     int pipe_ok = 0;          // the handle's shapes and options allow the pipelined solves
     int pipe_warps = 0;       // warps per box
@@ -80,7 +80,6 @@ struct Ras1 {
     size_t smem_pipe = 0;
     int ycap_pipe = 0;        // floats of the padded box vector
     DiagInfo *d_diag = nullptr;
-    int pipe_poll_limit = 1 << 22;
 };
 
 int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int overlap, int prec,
@@ -97,8 +96,8 @@ int ras1_check(Ras1 &R, cudaStream_t st);
 int ras1_apply(Ras1 &R, const double *r, double *z, int accumulate, cudaStream_t st);
 // new chunk size / threads per box for the subdomain solves (0: default); synchronous
 int ras1_set_schedule(Ras1 &R, int chunk_cells, int threads);
-// subdomain-solve kernel: 0 level-scheduled (CTA barrier per wavefront level),
-// 1 pipelined (both read the same records); RAS_EINVAL if not eligible
+// subdomain-solve kernel: 0 level-scheduled, 1 pencil-wavefront (both read the
+// same records and give the same bits); RAS_EINVAL if not eligible
 int ras1_set_kernel(Ras1 &R, int kernel);
 
 // parameters of one handle's apply kernel

@@ -332,7 +332,7 @@ class Precond:
         return c.value, t.value
 
     def set_apply_kernel(self, kernel):
-        """0: level-scheduled subdomain solves, 1: pipelined (same values from the same factors)."""
+        """0: level-scheduled subdomain solves, 1: pencil-wavefront (same values from the same factors)."""
         check(lib().ras_set_apply_kernel(self.h, int(kernel)), "ras_set_apply_kernel")
 
     def apply_kernel(self):
