@@ -460,25 +460,35 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     const int L = NW * M;
     const bool acc = P.accumulate != 0;
     double *zg = P.z + g0;
+    const int ylast = P.ycap - 1;
+    const unsigned owx = (unsigned)(si.ox1 - si.ox0);
+    // per slot: position in its period and, for the diagonal it is running, the
+    // lane's pencil state (set when the diagonal starts)
     int rem[M], bb[M];
+    int n0[M], go0[M], rq[M];     // Y index and global offset at i = 0; record index in its level
+    bool live[M], own[M], lo1[M], lo2[M];   // lane has a pencil; (j, k) owned; -y / -z (or +y / +z) inside
+    Acc xprev[M];
 #pragma unroll
     for (int m = 0; m < M; ++m) {
         const int base = w + NW * m;
-        rem[m] = base == 0 ? 0 : L - base;              // (0 - base) mod L
+        rem[m] = base == 0 ? 0 : L - base;               // (0 - base) mod L
         bb[m] = ((D - 1 - base) % L + L) % L;
+        live[m] = false;
+        n0[m] = go0[m] = rq[m] = 0;
+        own[m] = lo1[m] = lo2[m] = false;
+        xprev[m] = (Acc)0;
     }
-    Acc xprev[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) xprev[m] = (Acc)0;
-    const int ylast = P.ycap - 1;
 
-    int t = -1, lev_lo = 0, lev_hi = -1;   // current stage and its level range
+    int t = -1, lev_lo = 0, lev_hi = -1;   // current ring stage and its level range
     long long roff = 0;                     // ring byte offset of record 0 of the box
     for (int G = 0; G < 2 * S; ++G) {
         const bool fw = G < S;
-        if (G == S) {
+        if (G == S) {   // the backward sweep: the slots start their reversed periods
 #pragma unroll
-            for (int m = 0; m < M; ++m) rem[m] = bb[m] == 0 ? 0 : L - bb[m];
+            for (int m = 0; m < M; ++m) {
+                rem[m] = bb[m] == 0 ? 0 : L - bb[m];
+                live[m] = false;
+            }
         }
         const int lev = fw ? G : 2 * S - 1 - G;
         if (G == S || lev < lev_lo || lev > lev_hi) {   // next stage of the ring (all warps together)
@@ -492,44 +502,40 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
             const int qa = lvl_s[lev_lo];
             roff = (long long)(t % NBUF) * rcap + (((si.foff + qa) * (long long)RB) & 15) - (long long)RB * qa;
         }
-        int dd[M], ii[M];
-        bool act[M];
+        // records of level lev: diagonal d's cells start at cum(d) - cum(dlo)
+        const unsigned char *rl =
+            ring + (roff + (long long)RB * (lvl_s[lev] - dg[max(0, lev - bx + 1)].base));
 #pragma unroll
         for (int m = 0; m < M; ++m) {
-            act[m] = false;
-            if (rem[m] < bx) {
-                if (fw) {
-                    dd[m] = G - rem[m];
-                    ii[m] = rem[m];
-                    act[m] = dd[m] >= 0 && dd[m] <= D - 1;
-                } else {
-                    const int dt = G - S - rem[m];
-                    dd[m] = D - 1 - dt;
-                    ii[m] = bx - 1 - rem[m];
-                    act[m] = dt >= 0 && dt <= D - 1;
+            if (rem[m] == 0) {   // a diagonal of this slot may start: set the lane's pencil
+                const int d = fw ? G : D - 1 - (G - S);
+                live[m] = false;
+                if (d >= 0 && d <= D - 1) {
+                    const DiagInfo di = dg[d];
+                    const int jmin = di.jmin_cnt & 0xffff, cnt = di.jmin_cnt >> 16;
+                    if (lane < cnt) {
+                        const int j = jmin + lane, k = d - j;
+                        live[m] = true;
+                        n0[m] = PX * j + PXY * k;
+                        go0[m] = nx * j + nxy * k;
+                        rq[m] = di.base + lane;
+                        own[m] = j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1;
+                        lo1[m] = fw ? j > 0 : j < by - 1;
+                        lo2[m] = fw ? k > 0 : k < bz - 1;
+                    }
                 }
+                xprev[m] = (Acc)0;
             }
-        }
-        // cells of level lev: diagonals dlo .. ; diagonal d starts at cum(d) - cum(dlo)
-        const int dlo = max(0, lev - bx + 1);
-        const long long rlev = roff + (long long)RB * (lvl_s[lev] - dg[dlo].base);
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            if (!act[m]) continue;
-            const int d = dd[m], i = ii[m];
-            const DiagInfo di = dg[d];
-            const int jmin = di.jmin_cnt & 0xffff, cnt = di.jmin_cnt >> 16;
-            if (lane >= cnt) continue;
-            const int j = jmin + lane, k = d - j;
-            const int n = i + PX * j + PXY * k;
+            if (!live[m] || rem[m] >= bx) continue;
+            const int i = fw ? rem[m] : bx - 1 - rem[m];
+            const int n = n0[m] + i;
             Acc ax, ay, az, dinv;
-            load_rec<Acc, R>(ring + (rlev + (long long)RB * (di.base + lane)), ax, ay, az, dinv);
+            load_rec<Acc, R>(rl + (size_t)RB * rq[m], ax, ay, az, dinv);
             if (fw) {
                 // w_n = (r_n - a_z w_{n-bxy} - a_y w_{n-bx} - a_x w_{n-1}) / d_n
-                if (i == 0) xprev[m] = (Acc)0;
                 const Acc vz = Y[max(n - PXY, 0)], vy = Y[max(n - PX, 0)];
-                const Acc yz = k > 0 ? vz : (Acc)0;
-                const Acc yy = j > 0 ? vy : (Acc)0;
+                const Acc yz = lo2[m] ? vz : (Acc)0;
+                const Acc yy = lo1[m] ? vy : (Acc)0;
                 Acc s = Y[n];
                 s = fmsub(az, yz, s);
                 s = fmsub(ay, yy, s);
@@ -539,54 +545,27 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
                 xprev[m] = y;
             } else {
                 // z_n = w_n - d_n^{-1} (a_x z_{n+1} + a_y z_{n+bx} + a_z z_{n+bxy})
-                if (i == bx - 1) xprev[m] = (Acc)0;
                 const Acc vy = Y[min(n + PX, ylast)], vz = Y[min(n + PXY, ylast)];
-                const Acc zy = j < by - 1 ? vy : (Acc)0;
-                const Acc zz = k < bz - 1 ? vz : (Acc)0;
+                const Acc zy = lo1[m] ? vy : (Acc)0;
+                const Acc zz = lo2[m] ? vz : (Acc)0;
                 Acc s = ax * xprev[m];
                 s = fmadd(ay, zy, s);
                 s = fmadd(az, zz, s);
                 const Acc y = fmsub(dinv, s, Y[n]);
                 Y[n] = y;
                 xprev[m] = y;
-                if (!acc && i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 &&
-                    k < si.oz1)
-                    zg[i + (long long)nx * j + (long long)nxy * k] = (double)y;
+                if (own[m] && (unsigned)(i - si.ox0) < owx) {
+                    double *zp = zg + (go0[m] + i);
+                    if (acc) atomicAdd(zp, (double)y);   // one owner per cell: a fire-and-forget add
+                    else *zp = (double)y;
+                }
             }
         }
-        __syncthreads();   // level G done: its values are the next level's neighbours
+        __syncthreads();   // level done: its values are the next level's neighbours
 #pragma unroll
         for (int m = 0; m < M; ++m) rem[m] = rem[m] + 1 == L ? 0 : rem[m] + 1;
     }
     cp_async_wait<0>();
-    if (!acc) return;
-    // z += (R_i^0)^T y: flat over the owned box, GW old values in flight per thread
-    __syncthreads();
-    constexpr int GW = 8;
-    const int owx = si.ox1 - si.ox0, owy = si.oy1 - si.oy0;
-    const int nown = owx * owy * (si.oz1 - si.oz0);
-    const unsigned mox = magic_div(owx), moy = magic_div(owy);
-    for (int q0 = threadIdx.x; q0 < nown; q0 += GW * blockDim.x) {
-        int yq[GW];
-        long long go[GW];
-        double prev[GW];
-#pragma unroll
-        for (int m = 0; m < GW; ++m) {
-            const int q = q0 + m * (int)blockDim.x;
-            yq[m] = -1;
-            prev[m] = 0.0;
-            if (q < nown) {
-                const int row = fast_div(q, owx, mox), k = fast_div(row, owy, moy);
-                const int i = si.ox0 + q - row * owx, j = si.oy0 + row - k * owy, kk = si.oz0 + k;
-                yq[m] = i + PX * j + PXY * kk;
-                go[m] = i + (long long)nx * j + (long long)nxy * kk;
-                prev[m] = zg[go[m]];
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < GW; ++m)
-            if (yq[m] >= 0) zg[go[m]] = prev[m] + (double)Y[yq[m]];
-    }
 }
 
 // z (+)= sum over the overlapped boxes covering each cell of their solution
