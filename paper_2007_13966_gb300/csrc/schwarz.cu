@@ -343,25 +343,26 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply_batch(BatchApply B) {
 // ---------------------------------------------------------------------------
 // Pencil-wavefront subdomain solves (left-RAS, FP32 / BF16 factors)
 //
-// The natural-order ILU(0) sweeps of a box run over its x-pencils (j, k): pencil
-// (j, k) handles its cells i = 0 .. bx-1 one per step, cell i at step i + j + k in
-// the forward sweep (the wavefront level of the cell), so that its -y and -z
-// neighbours, cells of the pencils (j-1, k) and (j, k-1) on the anti-diagonal
-// d - 1 (d = j + k), were finished one step earlier, and its -x neighbour is the
-// pencil's previous value, kept in a register (the backward sweep mirrors this).
-// A warp handles the anti-diagonals d = w (mod warps), one lane per pencil, at most
-// PIPE_M of them at once; consecutive steps are separated by one CTA barrier. Each
-// lane's cell, neighbour and record positions follow from its pencil and the step
-// with no table look-up on the dependent chain (level start -> cell index -> values
-// of the level-scheduled kernel). The factor records are in level order with the
-// cells of a level grouped by anti-diagonal (the layout both solve kernels read);
-// chunks of consecutive levels are staged into a shared-memory ring with cp.async
-// two chunks ahead. Without accumulation the backward sweep writes each owned cell's
-// z as soon as it is final. The arithmetic of every cell is the same as in the
-// level-scheduled kernel, in the same order.
+// The natural-order ILU(0) sweeps of a box run over its x-pencils (j, k), one
+// thread per pencil: pencil (j, k) handles its cells i = 0 .. bx-1 one per
+// wavefront level, cell i at level i + j + k, so that its -y and -z neighbours,
+// cells of the pencils (j-1, k) and (j, k-1), were finished at the previous level
+// and its -x neighbour is the pencil's previous value, kept in a register (the
+// backward sweep mirrors this). Consecutive levels are separated by one CTA
+// barrier. Pencils are numbered by anti-diagonal d = j + k, then j, so that a warp
+// holds pencils of one or two neighbouring diagonals: it is busy for about bx + 2
+// levels of a sweep with most lanes active and idles (only the barrier) otherwise.
+// A thread's cell, neighbour and record positions follow from its pencil and the
+// level with no table look-up on the dependent chain (level start -> cell index ->
+// values in the level-scheduled kernel). The factor records are in level order with
+// the cells of a level grouped by anti-diagonal, then j (the layout both solve
+// kernels read): the record of pencil number p at level l is record lb[l] + p with
+// lb[l] = (start of level l) - (pencils on the diagonals below the level's first).
+// Chunks of consecutive levels are staged into a shared-memory ring with cp.async
+// two chunks ahead. The backward sweep writes each owned cell's z as soon as it is
+// final (an add when accumulating: one owner per cell). The arithmetic of every
+// cell is the same as in the level-scheduled kernel, in the same order.
 // ---------------------------------------------------------------------------
-
-constexpr int PIPE_M = 2;    // concurrently active diagonals per warp (slots)
 
 struct PipeParams {
     const SubInfo *subs;
@@ -378,23 +379,14 @@ struct PipeParams {
     int chunk_cells;   // ring slot capacity (cells)
 };
 
-// Slot m of warp w runs the diagonals d = base + L t (base = w + NW m < L = NW *
-// PIPE_M, L >= bx, so at most one is active at a step); rem = (step - base) mod L is
-// kept incrementally. Forward at step G: d = G - rem at i = rem, active iff rem < bx
-// and 0 <= d <= D-1. Backwards (G' = G - S) the same diagonals in reverse order:
-// dt = D-1-d = G' - rem at i = bx-1-rem, rem = (G' - bb) mod L, bb = (D-1-base) mod L,
-// active iff rem < bx and 0 <= dt <= D-1.
-
 template <int PREC>
-__global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
+__global__ void __launch_bounds__(1024, 1) k_ras_pipe(PipeParams P) {
     using R = typename RecT<PREC>::T;
     using Acc = typename RecT<PREC>::Acc;
     constexpr int RB = (int)sizeof(R);
-    constexpr int M = PIPE_M, NBUF = 3;
+    constexpr int NBUF = 3;
     extern __shared__ __align__(16) unsigned char smem[];
 
-    const int NW = blockDim.x >> 5;
-    const int w = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const SubInfo si = P.subs[blockIdx.x];
     const ShapeInfo sh = P.shapes[si.shape];
     const int bx = sh.bx, by = sh.by, bz = sh.bz;
@@ -403,10 +395,11 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
 
-    // shared memory: [Y: ycap][level starts: lcap][diagonals: dcap][ring]
+    // shared memory: [Y: ycap][level starts: lcap][lb: lcap][diagonals: dcap][ring]
     Acc *Y = reinterpret_cast<Acc *>(smem);
     int *lvl_s = reinterpret_cast<int *>(smem + (((size_t)P.ycap * sizeof(Acc) + 15) & ~(size_t)15));
-    DiagInfo *dg = reinterpret_cast<DiagInfo *>(lvl_s + P.lcap);
+    int *lb = lvl_s + P.lcap;
+    DiagInfo *dg = reinterpret_cast<DiagInfo *>(lb + P.lcap);
     unsigned char *ring = reinterpret_cast<unsigned char *>(dg + ((D + 1) & ~1));
     const int rcap = ((P.chunk_cells * RB + 32) + 15) & ~15;
 
@@ -414,14 +407,13 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
     const int nchunk = sh.nchunk, nstage = 2 * nchunk;
     for (int t = threadIdx.x; t <= S; t += blockDim.x) lvl_s[t] = P.lvl[sh.lvl_off + t];
     for (int t = threadIdx.x; t < D; t += blockDim.x) dg[t] = P.diag[sh.diag_off + t];
-    __syncthreads();
 
     // stage t < nchunk: forward chunk t; t >= nchunk: backward chunk 2 nchunk - 1 - t
     auto issue = [&](int t) {
         if (t < nstage) {
             const bool fw = t < nchunk;
             const int c = fw ? t : nstage - 1 - t;
-            const int qa = lvl_s[chunk_lev[c]], qb = lvl_s[chunk_lev[c + 1]];
+            const int qa = P.lvl[sh.lvl_off + chunk_lev[c]], qb = P.lvl[sh.lvl_off + chunk_lev[c + 1]];
             stage_bytes(ring + (size_t)(t % NBUF) * rcap, fw ? P.fwd : P.bwd,
                         (si.foff + qa) * (long long)RB, (si.foff + qb) * (long long)RB);
         }
@@ -432,7 +424,7 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
 
     // gather R_i^delta r into the padded box vector (GB loads in flight per thread)
     {
-        constexpr int GB = 12;
+        constexpr int GB = 8;
         const double *rg = P.r + g0;
         const unsigned mbx = magic_div(bx), mby = magic_div(by);
         const int ncell = sh.ncell;
@@ -456,42 +448,33 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
             }
         }
     }
+    __syncthreads();
+    for (int l = threadIdx.x; l < S; l += blockDim.x) lb[l] = lvl_s[l] - dg[max(0, l - bx + 1)].base;
 
-    const int L = NW * M;
-    const bool acc = P.accumulate != 0;
-    double *zg = P.z + g0;
-    const int ylast = P.ycap - 1;
-    const unsigned owx = (unsigned)(si.ox1 - si.ox0);
-    // per slot: position in its period and, for the diagonal it is running, the
-    // lane's pencil state (set when the diagonal starts)
-    int rem[M], bb[M];
-    int n0[M], go0[M], rq[M];     // Y index and global offset at i = 0; record index in its level
-    bool live[M], own[M], lo1[M], lo2[M];   // lane has a pencil; (j, k) owned; -y / -z (or +y / +z) inside
-    Acc xprev[M];
-#pragma unroll
-    for (int m = 0; m < M; ++m) {
-        const int base = w + NW * m;
-        rem[m] = base == 0 ? 0 : L - base;               // (0 - base) mod L
-        bb[m] = ((D - 1 - base) % L + L) % L;
-        live[m] = false;
-        n0[m] = go0[m] = rq[m] = 0;
-        own[m] = lo1[m] = lo2[m] = false;
-        xprev[m] = (Acc)0;
+    // this thread's pencil: number p = threadIdx.x in (d, j) order
+    const int p = threadIdx.x;
+    const bool live = p < by * bz;
+    int d = 0, j = 0, k = 0;
+    if (live) {
+        while (d + 1 < D && dg[d + 1].base <= p) ++d;
+        j = (dg[d].jmin_cnt & 0xffff) + (p - dg[d].base);
+        k = d - j;
     }
+    const int n0 = PX * j + PXY * k;                       // Y index of cell i = 0
+    double *zp0 = P.z + g0 + ((long long)nx * j + (long long)nxy * k);
+    const bool own_jk = live && j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1;
+    const unsigned owx = (unsigned)(si.ox1 - si.ox0);
+    const bool acc = P.accumulate != 0;
+    const int nmy = j > 0 ? PX : 0, nmz = k > 0 ? PXY : 0;           // -y / -z offsets (0: none)
+    const int npy = j < by - 1 ? PX : 0, npz = k < bz - 1 ? PXY : 0; // +y / +z offsets
+    Acc xprev = (Acc)0;
 
     int t = -1, lev_lo = 0, lev_hi = -1;   // current ring stage and its level range
     long long roff = 0;                     // ring byte offset of record 0 of the box
     for (int G = 0; G < 2 * S; ++G) {
         const bool fw = G < S;
-        if (G == S) {   // the backward sweep: the slots start their reversed periods
-#pragma unroll
-            for (int m = 0; m < M; ++m) {
-                rem[m] = bb[m] == 0 ? 0 : L - bb[m];
-                live[m] = false;
-            }
-        }
         const int lev = fw ? G : 2 * S - 1 - G;
-        if (G == S || lev < lev_lo || lev > lev_hi) {   // next stage of the ring (all warps together)
+        if (G == S || lev < lev_lo || lev > lev_hi) {   // next stage of the ring (all threads)
             ++t;
             cp_async_wait<NBUF - 2>();
             __syncthreads();
@@ -502,68 +485,41 @@ __global__ void __launch_bounds__(384, 2) k_ras_pipe(PipeParams P) {
             const int qa = lvl_s[lev_lo];
             roff = (long long)(t % NBUF) * rcap + (((si.foff + qa) * (long long)RB) & 15) - (long long)RB * qa;
         }
-        // records of level lev: diagonal d's cells start at cum(d) - cum(dlo)
-        const unsigned char *rl =
-            ring + (roff + (long long)RB * (lvl_s[lev] - dg[max(0, lev - bx + 1)].base));
-#pragma unroll
-        for (int m = 0; m < M; ++m) {
-            if (rem[m] == 0) {   // a diagonal of this slot may start: set the lane's pencil
-                const int d = fw ? G : D - 1 - (G - S);
-                live[m] = false;
-                if (d >= 0 && d <= D - 1) {
-                    const DiagInfo di = dg[d];
-                    const int jmin = di.jmin_cnt & 0xffff, cnt = di.jmin_cnt >> 16;
-                    if (lane < cnt) {
-                        const int j = jmin + lane, k = d - j;
-                        live[m] = true;
-                        n0[m] = PX * j + PXY * k;
-                        go0[m] = nx * j + nxy * k;
-                        rq[m] = di.base + lane;
-                        own[m] = j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1;
-                        lo1[m] = fw ? j > 0 : j < by - 1;
-                        lo2[m] = fw ? k > 0 : k < bz - 1;
-                    }
-                }
-                xprev[m] = (Acc)0;
-            }
-            if (!live[m] || rem[m] >= bx) continue;
-            const int i = fw ? rem[m] : bx - 1 - rem[m];
-            const int n = n0[m] + i;
+        const int i = lev - d;
+        if (live && (unsigned)i < (unsigned)bx) {
+            const int n = n0 + i;
             Acc ax, ay, az, dinv;
-            load_rec<Acc, R>(rl + (size_t)RB * rq[m], ax, ay, az, dinv);
+            load_rec<Acc, R>(ring + (roff + (long long)RB * (lb[lev] + p)), ax, ay, az, dinv);
             if (fw) {
                 // w_n = (r_n - a_z w_{n-bxy} - a_y w_{n-bx} - a_x w_{n-1}) / d_n
-                const Acc vz = Y[max(n - PXY, 0)], vy = Y[max(n - PX, 0)];
-                const Acc yz = lo2[m] ? vz : (Acc)0;
-                const Acc yy = lo1[m] ? vy : (Acc)0;
+                if (i == 0) xprev = (Acc)0;
+                const Acc yz = nmz ? Y[n - nmz] : (Acc)0;
+                const Acc yy = nmy ? Y[n - nmy] : (Acc)0;
                 Acc s = Y[n];
                 s = fmsub(az, yz, s);
                 s = fmsub(ay, yy, s);
-                s = fmsub(ax, xprev[m], s);
+                s = fmsub(ax, xprev, s);
                 const Acc y = s * dinv;
                 Y[n] = y;
-                xprev[m] = y;
+                xprev = y;
             } else {
                 // z_n = w_n - d_n^{-1} (a_x z_{n+1} + a_y z_{n+bx} + a_z z_{n+bxy})
-                const Acc vy = Y[min(n + PX, ylast)], vz = Y[min(n + PXY, ylast)];
-                const Acc zy = lo1[m] ? vy : (Acc)0;
-                const Acc zz = lo2[m] ? vz : (Acc)0;
-                Acc s = ax * xprev[m];
+                if (i == bx - 1) xprev = (Acc)0;
+                const Acc zy = npy ? Y[n + npy] : (Acc)0;
+                const Acc zz = npz ? Y[n + npz] : (Acc)0;
+                Acc s = ax * xprev;
                 s = fmadd(ay, zy, s);
                 s = fmadd(az, zz, s);
                 const Acc y = fmsub(dinv, s, Y[n]);
                 Y[n] = y;
-                xprev[m] = y;
-                if (own[m] && (unsigned)(i - si.ox0) < owx) {
-                    double *zp = zg + (go0[m] + i);
-                    if (acc) atomicAdd(zp, (double)y);   // one owner per cell: a fire-and-forget add
-                    else *zp = (double)y;
+                xprev = y;
+                if (own_jk && (unsigned)(i - si.ox0) < owx) {
+                    if (acc) atomicAdd(zp0 + i, (double)y);   // one owner per cell
+                    else zp0[i] = (double)y;
                 }
             }
         }
         __syncthreads();   // level done: its values are the next level's neighbours
-#pragma unroll
-        for (int m = 0; m < M; ++m) rem[m] = rem[m] + 1 == L ? 0 : rem[m] + 1;
     }
     cp_async_wait<0>();
 }
@@ -697,7 +653,7 @@ static size_t pipe_smem(Ras1 &R) {
     const size_t acc = R.prec == 64 ? 8 : 4;
     const size_t ybytes = (((size_t)R.ycap_pipe * acc) + 15) & ~(size_t)15;
     const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
-    R.smem_pipe = ybytes + (size_t)R.lcap * sizeof(int) + (size_t)R.dcap_pipe * sizeof(DiagInfo) +
+    R.smem_pipe = ybytes + 2 * (size_t)R.lcap * sizeof(int) + (size_t)R.dcap_pipe * sizeof(DiagInfo) +
                   3 * rcap;
     return R.smem_pipe;
 }
@@ -915,30 +871,23 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
     RAS_TRY(schedule_tables(R, 0, 0, chunk_tab));
     R.smem_factor = (size_t)R.ycap * sizeof(double);
     if (R.smem_apply > 227 * 1024 || R.smem_factor > 227 * 1024) return RAS_EINVAL;
-    // pipelined subdomain solves: left-RAS with FP32 / BF16 factors, boxes at most
-    // 24 cells along x (12 warps of two slots) and 32 pencils per anti-diagonal
+    // pencil-wavefront subdomain solves: left-RAS with FP32 / BF16 factors, at most
+    // 1024 x-pencils per box (one thread each)
     {
         bool ok = kind == 1 && prec != 64;
-        int bxmax = 1, ycp = 0, dmax = 1;
+        int pens = 1, ycp = 0, dmax = 1;
         for (const ShapeInfo &sh : R.shapes) {
-            bxmax = std::max(bxmax, sh.bx);
+            pens = std::max(pens, sh.by * sh.bz);
             ycp = std::max(ycp, sh.pxy * sh.bz);
             dmax = std::max(dmax, sh.by + sh.bz - 1);
-            if (std::min(sh.by, sh.bz) > 32) ok = false;
         }
-        if (bxmax > 2 * 12) ok = false;
-        int nw = std::max(2, (bxmax + PIPE_M - 1) / PIPE_M);
-        if (const char *e = getenv("RAS_PIPE_WARPS")) {   // tuning knob (warps per box)
-            const int v = atoi(e);
-            if (v >= nw && v <= 12) nw = v;
-        }
-        R.pipe_warps = nw;
+        if (pens > 1024) ok = false;
+        R.pipe_warps = (pens + 31) / 32;
         R.ycap_pipe = (ycp + 3) & ~3;
         R.dcap_pipe = (dmax + 1) & ~1;
         if (pipe_smem(R) > 227 * 1024) ok = false;
         R.pipe = R.pipe_ok = ok ? 1 : 0;
     }
-
     RAS_TRY(dalloc(&R.d_subs, R.subs.size()));
     RAS_TRY(dalloc(&R.d_shapes, R.shapes.size()));
     RAS_TRY(dalloc(&R.d_lvl, lvl_tab.size()));
