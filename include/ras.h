@@ -418,6 +418,18 @@ int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads
  * (ras_type 1) ILU(0) with FP32 or BF16 factors when every overlapped box has at
  * most 24 cells along x and at most 32 along y or z (RAS_EINVAL otherwise). */
 int ras_set_apply_kernel(ras_precond *pc, int kernel);
+
+/* Dense FP32 product C = alpha A B + beta C on the tcgen05 tensor cores, the
+ * building block of the dense coarse-level block elimination (Section 3.2: the
+ * exact coarse solve of the two-level methods). FP32 accuracy from the TF32 tensor
+ * path by the three-term split A B ~ Ah Bh + Ah Bl + Al Bh (h: rounded to TF32,
+ * l: the FP32 remainder), accumulated in FP32. Row-major device arrays: A m x k
+ * (lda), B k x n (ldb), C m x n (ldc). m and n multiples of 128, k a positive
+ * multiple of 32, leading dimensions multiples of 4 (>= the row length), 16-byte
+ * aligned bases; else RAS_EINVAL. Synchronises the stream; RAS_ETIMEOUT if a
+ * bounded wait for the tensor core gave up. */
+int ras_gemm_f32(int m, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
+                 float beta, float *C, int ldc, void *stream);
 int ras_get_apply_kernel(const ras_precond *pc, int *kernel);
 
 #ifdef __cplusplus

@@ -18,7 +18,7 @@ OUT_DIR = os.path.join(HERE, "_lib")
 LIB = os.path.join(OUT_DIR, "libras.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["problem.cu", "schwarz.cu", "precond.cu", "krylov.cu", "coarse.cu", "ras125.cu",
-           "noalloc.cu", "batch.cu"]
+           "noalloc.cu", "batch.cu", "tc_gemm.cu"]
 
 
 def source_hash(files=None) -> str:

@@ -395,9 +395,9 @@ __global__ void __launch_bounds__(1024, 1) k_ras_pipe(PipeParams P) {
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
 
-    // shared memory: [Y: ycap][level starts: lcap][lb: lcap][diagonals: dcap][ring]
+    // shared memory: [Y: ycap, zero cell, pad][level starts: lcap][lb: lcap][diagonals: dcap][ring]
     Acc *Y = reinterpret_cast<Acc *>(smem);
-    int *lvl_s = reinterpret_cast<int *>(smem + (((size_t)P.ycap * sizeof(Acc) + 15) & ~(size_t)15));
+    int *lvl_s = reinterpret_cast<int *>(smem + (((size_t)(P.ycap + 4) * sizeof(Acc) + 15) & ~(size_t)15));
     int *lb = lvl_s + P.lcap;
     DiagInfo *dg = reinterpret_cast<DiagInfo *>(lb + P.lcap);
     unsigned char *ring = reinterpret_cast<unsigned char *>(dg + ((D + 1) & ~1));
@@ -460,66 +460,95 @@ __global__ void __launch_bounds__(1024, 1) k_ras_pipe(PipeParams P) {
         j = (dg[d].jmin_cnt & 0xffff) + (p - dg[d].base);
         k = d - j;
     }
+    // -y / -z (forward) and +y / +z (backward) neighbour rows of the pencil; a
+    // neighbour outside the box reads the zero cell Y[ycap] (stride 0 along i)
+    Acc *Yz = Y + P.ycap;
     const int n0 = PX * j + PXY * k;                       // Y index of cell i = 0
+    Acc *const my = j > 0 ? Y + n0 - PX : Yz, *const mz = k > 0 ? Y + n0 - PXY : Yz;
+    Acc *const py = j < by - 1 ? Y + n0 + PX : Yz, *const pz = k < bz - 1 ? Y + n0 + PXY : Yz;
+    const int smy = j > 0, smz = k > 0, spy = j < by - 1, spz = k < bz - 1;
+    Acc *const yp = Y + n0;
     double *zp0 = P.z + g0 + ((long long)nx * j + (long long)nxy * k);
     const bool own_jk = live && j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1;
     const unsigned owx = (unsigned)(si.ox1 - si.ox0);
     const bool acc = P.accumulate != 0;
-    const int nmy = j > 0 ? PX : 0, nmz = k > 0 ? PXY : 0;           // -y / -z offsets (0: none)
-    const int npy = j < by - 1 ? PX : 0, npz = k < bz - 1 ? PXY : 0; // +y / +z offsets
-    Acc xprev = (Acc)0;
+    if (threadIdx.x == 0) *Yz = (Acc)0;
 
     int t = -1, lev_lo = 0, lev_hi = -1;   // current ring stage and its level range
-    long long roff = 0;                     // ring byte offset of record 0 of the box
-    for (int G = 0; G < 2 * S; ++G) {
-        const bool fw = G < S;
-        const int lev = fw ? G : 2 * S - 1 - G;
-        if (G == S || lev < lev_lo || lev > lev_hi) {   // next stage of the ring (all threads)
-            ++t;
-            cp_async_wait<NBUF - 2>();
-            __syncthreads();
-            issue(t + NBUF - 1);
-            const int c = t < nchunk ? t : nstage - 1 - t;
-            lev_lo = chunk_lev[c];
-            lev_hi = chunk_lev[c + 1] - 1;
-            const int qa = lvl_s[lev_lo];
-            roff = (long long)(t % NBUF) * rcap + (((si.foff + qa) * (long long)RB) & 15) - (long long)RB * qa;
-        }
-        const int i = lev - d;
-        if (live && (unsigned)i < (unsigned)bx) {
-            const int n = n0 + i;
-            Acc ax, ay, az, dinv;
-            load_rec<Acc, R>(ring + (roff + (long long)RB * (lb[lev] + p)), ax, ay, az, dinv);
-            if (fw) {
-                // w_n = (r_n - a_z w_{n-bxy} - a_y w_{n-bx} - a_x w_{n-1}) / d_n
-                if (i == 0) xprev = (Acc)0;
-                const Acc yz = nmz ? Y[n - nmz] : (Acc)0;
-                const Acc yy = nmy ? Y[n - nmy] : (Acc)0;
-                Acc s = Y[n];
+    const unsigned char *rp = ring;         // this pencil's record base in the current stage
+    // a new ring stage: wait for its chunk, refill the slot two stages back
+    auto next_stage = [&]() {
+        ++t;
+        cp_async_wait<NBUF - 2>();
+        __syncthreads();
+        issue(t + NBUF - 1);
+        const int c = t < nchunk ? t : nstage - 1 - t;
+        lev_lo = chunk_lev[c];
+        lev_hi = chunk_lev[c + 1] - 1;
+        const int qa = lvl_s[lev_lo];
+        rp = ring + ((long long)(t % NBUF) * rcap + (((si.foff + qa) * (long long)RB) & 15) +
+                     (long long)RB * (p - qa));
+    };
+    // forward sweep: w_n = (r_n - a_z w_{n-bxy} - a_y w_{n-bx} - a_x w_{n-1}) / d_n
+    {
+        Acc xprev = (Acc)0;
+        Acc ax = 0, ay = 0, az = 0, dinv = 0;
+        bool have = false;                   // the record of the coming level is in registers
+        for (int lev = 0; lev < S; ++lev) {
+            if (lev > lev_hi) { next_stage(); have = false; }
+            const int i = lev - d;
+            const bool on = live && (unsigned)i < (unsigned)bx;
+            if (on) {
+                if (!have) load_rec<Acc, R>(rp + (long long)RB * lb[lev], ax, ay, az, dinv);
+                const Acc yz = mz[i * smz], yy = my[i * smy];
+                Acc s = yp[i];
                 s = fmsub(az, yz, s);
                 s = fmsub(ay, yy, s);
                 s = fmsub(ax, xprev, s);
                 const Acc y = s * dinv;
-                Y[n] = y;
+                yp[i] = y;
                 xprev = y;
-            } else {
-                // z_n = w_n - d_n^{-1} (a_x z_{n+1} + a_y z_{n+bx} + a_z z_{n+bxy})
-                if (i == bx - 1) xprev = (Acc)0;
-                const Acc zy = npy ? Y[n + npy] : (Acc)0;
-                const Acc zz = npz ? Y[n + npz] : (Acc)0;
+            }
+            // the next level's record (independent of this level's values), if staged
+            have = false;
+            if (lev + 1 <= lev_hi && live && (unsigned)(i + 1) < (unsigned)bx) {
+                load_rec<Acc, R>(rp + (long long)RB * lb[lev + 1], ax, ay, az, dinv);
+                have = true;
+            }
+            __syncthreads();   // level done: its values are the next level's neighbours
+        }
+    }
+    // backward sweep: z_n = w_n - d_n^{-1} (a_x z_{n+1} + a_y z_{n+bx} + a_z z_{n+bxy})
+    {
+        Acc xprev = (Acc)0;
+        Acc ax = 0, ay = 0, az = 0, dinv = 0;
+        bool have = false;
+        next_stage();
+        for (int lev = S - 1; lev >= 0; --lev) {
+            if (lev < lev_lo) { next_stage(); have = false; }
+            const int i = lev - d;
+            const bool on = live && (unsigned)i < (unsigned)bx;
+            if (on) {
+                if (!have) load_rec<Acc, R>(rp + (long long)RB * lb[lev], ax, ay, az, dinv);
+                const Acc zy = py[i * spy], zz = pz[i * spz];
                 Acc s = ax * xprev;
                 s = fmadd(ay, zy, s);
                 s = fmadd(az, zz, s);
-                const Acc y = fmsub(dinv, s, Y[n]);
-                Y[n] = y;
+                const Acc y = fmsub(dinv, s, yp[i]);
+                yp[i] = y;
                 xprev = y;
                 if (own_jk && (unsigned)(i - si.ox0) < owx) {
                     if (acc) atomicAdd(zp0 + i, (double)y);   // one owner per cell
                     else zp0[i] = (double)y;
                 }
             }
+            have = false;
+            if (lev - 1 >= lev_lo && live && (unsigned)(i - 1) < (unsigned)bx) {
+                load_rec<Acc, R>(rp + (long long)RB * lb[lev - 1], ax, ay, az, dinv);
+                have = true;
+            }
+            __syncthreads();
         }
-        __syncthreads();   // level done: its values are the next level's neighbours
     }
     cp_async_wait<0>();
 }
@@ -651,7 +680,7 @@ static int set_factor_attr(size_t) {
 // shared memory of the pipelined solves for the handle's current chunk size
 static size_t pipe_smem(Ras1 &R) {
     const size_t acc = R.prec == 64 ? 8 : 4;
-    const size_t ybytes = (((size_t)R.ycap_pipe * acc) + 15) & ~(size_t)15;
+    const size_t ybytes = (((size_t)(R.ycap_pipe + 4) * acc) + 15) & ~(size_t)15;
     const size_t rcap = ((R.chunk_cells * R.rec_bytes + 32) + 15) & ~15;
     R.smem_pipe = ybytes + 2 * (size_t)R.lcap * sizeof(int) + (size_t)R.dcap_pipe * sizeof(DiagInfo) +
                   3 * rcap;

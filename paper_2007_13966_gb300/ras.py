@@ -26,7 +26,7 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
             "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc",
             "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk", "ras_batch_create",
             "ras_batch_destroy", "ras_batch_gmres", "ras_batch_newton_step", "ras_set_apply_schedule",
-            "ras_get_apply_schedule", "ras_set_apply_kernel", "ras_get_apply_kernel"]
+            "ras_get_apply_schedule", "ras_set_apply_kernel", "ras_get_apply_kernel", "ras_gemm_f32"]
 
 
 class Grid(C.Structure):
@@ -121,6 +121,7 @@ def lib():
             "ras_get_apply_schedule": (i, [vp, C.POINTER(i), C.POINTER(i)]),
             "ras_set_apply_kernel": (i, [vp, i]),
             "ras_get_apply_kernel": (i, [vp, C.POINTER(i)]),
+            "ras_gemm_f32": (i, [i, i, i, C.c_float, vp, i, vp, i, C.c_float, vp, i, vp]),
             "ras_batch_create": (i, [i, vp, vp, C.POINTER(vp)]),
             "ras_batch_destroy": (None, [vp]),
             "ras_batch_gmres": (i, [vp, vp, vp, vp, C.POINTER(KrylovOpts), vp, vp]),
@@ -176,6 +177,14 @@ def norm2_noalloc(x, out, stream=None):
     (partial sums in the library's static device array)."""
     check(lib().ras_norm2_noalloc(_ptr(x), x.numel(), _ptr(out), _stream(stream)),
           "ras_norm2_noalloc")
+
+
+def gemm_f32(A, B, C, alpha=1.0, beta=0.0, stream=None):
+    """C = alpha A B + beta C (FP32 row-major device tensors) on the tensor cores."""
+    m, k = A.shape
+    n = B.shape[1]
+    check(lib().ras_gemm_f32(m, n, k, float(alpha), _ptr(A), A.stride(0), _ptr(B), B.stride(0),
+                             float(beta), _ptr(C), C.stride(0), _stream(stream)), "ras_gemm_f32")
 
 
 def kernel_launches() -> int:
