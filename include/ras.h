@@ -407,16 +407,16 @@ int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads
 /* Kernel of the fine-level subdomain solves of Eq. equ:as-left (a performance
  * setting: both give the same values, bit for bit, in the same arithmetic order,
  * from the same factor records; the switch takes effect at the next ras_apply).
- * 0: level-scheduled, every wavefront level i + j + k of a box separated by a CTA
- * barrier, each thread looking its cell up in the level's table (the schedule
- * above applies). 1: pencil-wavefront, the default where allowed: each lane owns an
- * x-pencil (j, k) of a box and advances one cell per level, its -x neighbour kept
- * in a register, its positions following from the pencil and the level with no
- * table look-up; one warp per group of anti-diagonals j + k; the records are
- * staged in chunks of levels (the schedule's chunk size) and, without
- * accumulation, z is written as soon as it is final. Allowed for left-RAS
- * (ras_type 1) ILU(0) with FP32 or BF16 factors when every overlapped box has at
- * most 24 cells along x and at most 32 along y or z (RAS_EINVAL otherwise). */
+ * 0 (the default): level-scheduled, every wavefront level i + j + k of a box
+ * separated by a CTA barrier, each thread looking its cell up in the level's
+ * table (the schedule above applies), each owned z written as soon as the
+ * backward sweep has it. 1: pencil-wavefront: each thread owns an x-pencil
+ * (j, k) of a box and advances one cell per level, its -x neighbour kept in a
+ * register, its positions following from the pencil and the level with no table
+ * look-up; pencils numbered by anti-diagonal j + k; the records are staged in
+ * chunks of levels (the schedule's chunk size) and z is written as soon as it is
+ * final. Allowed for left-RAS (ras_type 1) ILU(0) with FP32 or BF16 factors when
+ * no overlapped box has more than 1024 x-pencils (RAS_EINVAL otherwise). */
 int ras_set_apply_kernel(ras_precond *pc, int kernel);
 
 /* Dense FP32 product C = alpha A B + beta C on the tcgen05 tensor cores, the

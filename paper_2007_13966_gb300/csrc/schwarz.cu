@@ -166,7 +166,7 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
     // gather R_i^delta r into shared memory, flat over the box's cells with GB
     // loads in flight per thread before any is consumed (the gather is bound by
     // the bytes in flight per SM, not by bandwidth)
-    constexpr int GB = 12;   // the largest batch without spills at 64 registers
+    constexpr int GB = 10;   // a batch that stays in 64 registers with the direct z stores
     const int bx = sh.bx, by = sh.by, bxy = sh.bx * sh.by;
     const int nx = P.nx, nxy = P.nx * P.ny;
     const long long g0 = si.e0x + (long long)nx * (si.e0y + (long long)P.ny * si.e0z);
@@ -197,6 +197,20 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
             }
         }
     }
+
+    // Left-RAS writes each owned cell's z as soon as the backward sweep has it
+    // ((R_i^0)^T: one owner per cell, so an add when accumulating is a plain update)
+    const bool direct = P.kind == 1;
+    double *zg = z + g0;
+    auto put = [&](int n, Acc y) {
+        const int row = fast_div(n, bx, mbx), k = fast_div(row, by, mby);
+        const int i = n - row * bx, j = row - k * by;
+        if (i >= si.ox0 && i < si.ox1 && j >= si.oy0 && j < si.oy1 && k >= si.oz0 && k < si.oz1) {
+            double *zp = zg + (i + nx * j + nxy * k);
+            if (accumulate) atomicAdd(zp, (double)y);
+            else *zp = (double)y;
+        }
+    };
 
     // Sweeps, level by level. A neighbour outside the box has a zero factor value and
     // reads a finite value (a cell of the box or the zero guard band on either side
@@ -249,7 +263,9 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
                         Acc s = ax * yn[1];
                         s = fmadd(ay, yn[bx], s);
                         s = fmadd(az, yn[bxy], s);
-                        yn[0] = fmsub(dinv, s, yn[0]);
+                        const Acc y = fmsub(dinv, s, yn[0]);
+                        yn[0] = y;
+                        if (direct) put(n, y);
                     }
                     __syncthreads();
                 }
@@ -283,7 +299,9 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
                     Acc s = ax * Y[n + 1];
                     s = fmadd(ay, Y[n + bx], s);
                     s = fmadd(az, Y[n + bxy], s);
-                    Y[n] = fmsub(dinv, s, Y[n]);
+                    const Acc y = fmsub(dinv, s, Y[n]);
+                    Y[n] = y;
+                    if (direct) put(n, y);
                 }
                 __syncthreads();
             }
@@ -295,33 +313,6 @@ __device__ __forceinline__ void ras_apply_box(const ApplyParams &P, int box, con
         double *dst = P.zbuf + si.foff;
         for (int q = threadIdx.x; q < sh.ncell; q += blockDim.x) dst[q] = (double)Y[q];
         return;
-    }
-    // (R_i^0)^T: write the owned cells, flat over the owned box (GW old values in
-    // flight per thread when accumulating)
-    constexpr int GW = 8;
-    const int owx = si.ox1 - si.ox0, owy = si.oy1 - si.oy0;
-    const int nown = owx * owy * (si.oz1 - si.oz0);
-    const unsigned mox = magic_div(owx), moy = magic_div(owy);
-    double *zg = z + g0;
-    for (int q0 = threadIdx.x; q0 < nown; q0 += GW * blockDim.x) {
-        int yq[GW], go[GW];
-        double prev[GW];
-#pragma unroll
-        for (int m = 0; m < GW; ++m) {
-            const int q = q0 + m * (int)blockDim.x;
-            yq[m] = -1;
-            prev[m] = 0.0;
-            if (q < nown) {
-                const int row = fast_div(q, owx, mox), k = fast_div(row, owy, moy);
-                const int i = si.ox0 + q - row * owx, j = si.oy0 + row - k * owy, kk = si.oz0 + k;
-                yq[m] = i + bx * j + bxy * kk;
-                go[m] = i + nx * j + nxy * kk;
-                if (accumulate) prev[m] = zg[go[m]];
-            }
-        }
-#pragma unroll
-        for (int m = 0; m < GW; ++m)
-            if (yq[m] >= 0) zg[go[m]] = prev[m] + (double)Y[yq[m]];
     }
 }
 
@@ -915,7 +906,8 @@ int ras1_setup(Ras1 &R, int nx, int ny, int nz, int px, int py, int pz, int over
         R.ycap_pipe = (ycp + 3) & ~3;
         R.dcap_pipe = (dmax + 1) & ~1;
         if (pipe_smem(R) > 227 * 1024) ok = false;
-        R.pipe = R.pipe_ok = ok ? 1 : 0;
+        R.pipe_ok = ok ? 1 : 0;
+        R.pipe = 0;   // the level-scheduled solves are faster on the measured workloads
     }
     RAS_TRY(dalloc(&R.d_subs, R.subs.size()));
     RAS_TRY(dalloc(&R.d_shapes, R.shapes.size()));

@@ -62,9 +62,9 @@ def test_pencil_equals_level_scheduled(ras, case, prec):
     gp = ras.Problem(res)
     a = ras.Precond(gp, parts, ov, factor_prec=prec)
     b = ras.Precond(gp, parts, ov, factor_prec=prec)
-    assert a.apply_kernel() == 1          # the default where allowed
-    b.set_apply_kernel(0)
-    assert b.apply_kernel() == 0
+    assert b.apply_kernel() == 0          # the default
+    a.set_apply_kernel(1)
+    assert a.apply_kernel() == 1
     Jd = j_to_dev(J)
     a.factor(Jd)
     b.factor(Jd)
@@ -87,7 +87,7 @@ def test_pencil_matches_oracle_emulation(ras, prec, tol):
     emu = schwarz.Schwarz(A, (g.nx, g.ny, g.nz), parts, ov, prec=prec)(r)
     gp = ras.Problem(res)
     pc = ras.Precond(gp, parts, ov, factor_prec=prec)
-    assert pc.apply_kernel() == 1
+    pc.set_apply_kernel(1)
     pc.factor(j_to_dev(J))
     z = torch.zeros(g.n, dtype=torch.float64, device="cuda")
     pc.apply(dev(r), z)
@@ -125,9 +125,9 @@ def test_kernel_switch_on_the_same_factors(ras):
     r = dev(syn.random_vector(res.grid.n, 1))
     z = [torch.zeros_like(r) for _ in range(3)]
     pc.apply(r, z[0])
-    pc.set_apply_kernel(0)
-    pc.apply(r, z[1])
     pc.set_apply_kernel(1)
+    pc.apply(r, z[1])
+    pc.set_apply_kernel(0)
     pc.apply(r, z[2])
     assert torch.equal(z[0], z[1]) and torch.equal(z[1], z[2])
     # FP64 factors and AS / right-RAS stay on the level-scheduled kernel
