@@ -80,6 +80,7 @@ struct Coarse {
     int rap125_ng = 25;             // offsets staged per round in k_rap125
     int fac_grid = 0, sol_grid = 0;
     int sol_npf = 0;                // rows per warp prefetched by the solve
+    int use_tc = 0;                 // FP32 inverses: trailing updates on the tcgen05 tensor cores
 };
 
 // ---------------------------------------------------------------------------
@@ -749,6 +750,160 @@ __device__ void subtile_product(TileSmem<AT> &sm, const AT *Xb, const AT *Yb, AT
 }
 
 // ---------------------------------------------------------------------------
+// trailing updates of the FP32 Gauss-Jordan inverses on the tcgen05 tensor cores
+//
+// Two vertically adjacent 64 x 64 tiles of a block, rows 128 x columns of tile j,
+// are updated together: Out -= X Y with X the 128 x 64 column strip of the pivot
+// panel and Y the 64 x 64 pivot-row tile, one group of MMAs (M = 128, N = 64,
+// K = 8 per instruction) with FP32 accuracy from the TF32 path by the three-term
+// split X Y ~ Xh Yh + Xh Yl + Xl Yh (h: rounded to TF32, l: the FP32 remainder),
+// accumulated in FP32 in tensor memory (64 columns per CTA, allocated for the
+// launch). Operands are split and written by the CTA's threads into shared memory
+// in the canonical K-major layout without swizzle (8-row x 16-byte core matrices,
+// 128 B apart along k, 2048 B apart along rows); one thread issues the MMAs and
+// commits them to an mbarrier that the CTA waits on (bounded).
+// ---------------------------------------------------------------------------
+
+struct TcSmem {
+    alignas(128) unsigned char xh[128 * 64 * 4], xl[128 * 64 * 4];   // X: 128 rows x 64 k
+    alignas(128) unsigned char yh[64 * 64 * 4], yl[64 * 64 * 4];     // Y^T: 64 columns x 64 k
+};
+
+struct TcState {
+    unsigned tmem;               // accumulator base (64 columns), 0 without the tensor path
+    unsigned long long *mbar;    // MMA completion
+    unsigned phase;              // completed waits of this CTA
+};
+
+constexpr unsigned TC_LBO = 128, TC_SBO = 2048;
+constexpr unsigned TC_IDESC = (1u << 4) | (2u << 7) | (2u << 10) | ((64u >> 3) << 17) | ((128u >> 4) << 24);
+constexpr long long TC_POLLS = 1LL << 26;
+
+__device__ __forceinline__ int tc_off(int row, int k) {
+    return (row >> 3) * TC_SBO + (k >> 2) * TC_LBO + (row & 7) * 16 + (k & 3) * 4;
+}
+__device__ __forceinline__ unsigned long long tc_desc(unsigned addr) {
+    unsigned long long d = (unsigned long long)((addr & 0x3FFFFu) >> 4);
+    d |= (unsigned long long)((TC_LBO >> 4) & 0x3FFF) << 16;
+    d |= (unsigned long long)((TC_SBO >> 4) & 0x3FFF) << 32;
+    d |= 1ull << 46;
+    return d;
+}
+__device__ __forceinline__ float tc_head(float x) {
+    unsigned r;
+    asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+    return __uint_as_float(r);
+}
+__device__ __forceinline__ void tc_put(unsigned char *h, unsigned char *l, int off, float v) {
+    const float vh = tc_head(v);
+    *reinterpret_cast<float *>(h + off) = vh;
+    *reinterpret_cast<float *>(l + off) = v - vh;
+}
+
+// Out(tiles i0, i0 + 1; tile column j) -= D(same rows, tile column p) D(p, j), T x T
+// row-major block M. All 256 threads; the CTA's smem overlay is free on entry.
+__device__ void tc_pair_update(TcSmem &ts, TcState &st, float *M, int T, int i0, int p, int j, int *err) {
+    const int tid = threadIdx.x;
+    {   // X: rows 64 i0 .. + 127, columns 64 p .. + 63; thread t: row t / 2, k half (t & 1)
+        const int r = tid >> 1, k0 = (tid & 1) * 32;
+        const float4 *src = reinterpret_cast<const float4 *>(M + (long long)(i0 * TILE + r) * T + p * TILE + k0);
+        float4 v[8];
+#pragma unroll
+        for (int q = 0; q < 8; ++q) v[q] = __ldcg(src + q);
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float *e = reinterpret_cast<const float *>(&v[q]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tc_put(ts.xh, ts.xl, tc_off(r, k0 + 4 * q + u), e[u]);
+        }
+    }
+    {   // Y^T: Y = D(p, j), element (k, n) to row n, column k; thread t: k = t / 4, n block (t & 3)
+        const int k = tid >> 2, n0 = (tid & 3) * 16;
+        const float4 *src = reinterpret_cast<const float4 *>(M + (long long)(p * TILE + k) * T + j * TILE + n0);
+        float4 v[4];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) v[q] = __ldcg(src + q);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float *e = reinterpret_cast<const float *>(&v[q]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tc_put(ts.yh, ts.yl, tc_off(n0 + 4 * q + u, k), e[u]);
+        }
+    }
+    asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+    __syncthreads();
+    if (tid == 0) {
+        asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+        const unsigned xh = (unsigned)__cvta_generic_to_shared(ts.xh), xl = (unsigned)__cvta_generic_to_shared(ts.xl);
+        const unsigned yh = (unsigned)__cvta_generic_to_shared(ts.yh), yl = (unsigned)__cvta_generic_to_shared(ts.yl);
+#pragma unroll
+        for (int s = 0; s < 8; ++s) {
+            const unsigned o = s * 2 * TC_LBO;   // k-step of 8: two core matrices along k
+            const unsigned long long d[3][2] = {{tc_desc(xl + o), tc_desc(yh + o)},
+                                                {tc_desc(xh + o), tc_desc(yl + o)},
+                                                {tc_desc(xh + o), tc_desc(yh + o)}};
+#pragma unroll
+            for (int t3 = 0; t3 < 3; ++t3) {
+                const unsigned acc = (s > 0 || t3 > 0) ? 1u : 0u;
+                asm volatile(
+                    "{\n.reg .pred pp;\n"
+                    "setp.ne.b32 pp, %4, 0;\n"
+                    "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, pp;\n}\n"
+                    ::"r"(st.tmem), "l"(d[t3][0]), "l"(d[t3][1]), "r"(TC_IDESC), "r"(acc) : "memory");
+            }
+        }
+        asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                     ::"r"((unsigned)__cvta_generic_to_shared(st.mbar)) : "memory");
+    }
+    {   // bounded wait for the MMAs
+        const unsigned a = (unsigned)__cvta_generic_to_shared(st.mbar), par = st.phase & 1;
+        bool done = false;
+        for (long long it = 0; it < TC_POLLS && !done; ++it) {
+            unsigned ok;
+            asm volatile(
+                "{\n.reg .pred pp;\n"
+                "mbarrier.try_wait.parity.shared::cta.b64 pp, [%1], %2;\n"
+                "selp.u32 %0, 1, 0, pp;\n}\n"
+                : "=r"(ok) : "r"(a), "r"(par) : "memory");
+            done = ok != 0;
+        }
+        if (!done) atomicExch(err, ERR_TIMEOUT);
+        ++st.phase;
+    }
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {   // warp w: rows 32 (w % 4) + lane, columns 32 (w / 4) .. + 31
+        const int w = tid >> 5, lane = tid & 31, q = w & 3, h = w >> 2;
+        unsigned r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+              "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(st.tmem + ((unsigned)(32 * q) << 16) + 32u * h));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        float *out = M + (long long)(i0 * TILE + 32 * q + lane) * T + j * TILE + 32 * h;
+        float4 prev[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) prev[u] = __ldcg(reinterpret_cast<const float4 *>(out) + u);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            float4 o = prev[u];
+            o.x -= __uint_as_float(r[4 * u]);
+            o.y -= __uint_as_float(r[4 * u + 1]);
+            o.z -= __uint_as_float(r[4 * u + 2]);
+            o.w -= __uint_as_float(r[4 * u + 3]);
+            reinterpret_cast<float4 *>(out)[u] = o;
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // the smem overlay and the accumulator are free again
+}
+
+// ---------------------------------------------------------------------------
 // cooperative factorisation: block Thomas with in-place Gauss-Jordan inverses
 // ---------------------------------------------------------------------------
 
@@ -889,7 +1044,7 @@ __device__ void sparse_row_times(const AT *Inv, const int *lq, const AT *lv, int
 // inverted by a CTA of its own (when the grid has more CTAs than chains).
 template <typename AT>
 __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT> &ts, const int *blk, int nblk,
-                              unsigned &epoch, int b, int G) {
+                              unsigned &epoch, int b, int G, TcState &tcs) {
     const int T = a.T, nt = a.nt;
     const long long bsz = (long long)T * T;
     // prologue: pivot tile 0 and the row panel of step 0
@@ -919,16 +1074,42 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
             const int i = bi < p ? bi : bi + 1, j = bj < p ? bj : bj + 1;
             subtile_product<AT, 64, 64, 4, 4>(ts, Dk, Dk, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
         };
-        auto regular = [&](int q) {            // q in 0..nblk*nreg
-            const int c = q / nreg, r = q % nreg;
-            if (r >= nreg - nz) {
-                AT *Dk = a.D + blk[c] * bsz;
-                const int z = r - (nreg - nz);
-                subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, a.Z + (long long)c * TILE * T, T, p + 1, p,
-                                                  p, p, 0, 0, 16 * z, 0, (AT)-1, false);
+        // FP32 with the tensor path: the items are pairs of vertically adjacent tiles
+        // (rows 2 pb, 2 pb + 1) of a tile column j != p, one MMA group per pair; a pair
+        // with the pivot row or the next pivot tile (updated by its own CTA) in it
+        // keeps its other tile on the CUDA-core product
+        const bool tcp = sizeof(AT) == 4 && tcs.tmem != 0;
+        const int npair = (nt + 1) / 2, npi = (nt - 1) * npair;
+        const int nitem = tcp ? npi + nz : nreg;
+        auto z_item = [&](int c, int z) {
+            AT *Dk = a.D + blk[c] * bsz;
+            subtile_product<AT, 16, 64, 2, 2>(ts, Dk, Dk, a.Z + (long long)c * TILE * T, T, p + 1, p,
+                                              p, p, 0, 0, 16 * z, 0, (AT)-1, false);
+        };
+        auto regular = [&](int q) {            // q in 0..nblk*nitem
+            const int c = q / nitem, r = q % nitem;
+            if (r >= nitem - nz) {
+                z_item(c, r - (nitem - nz));
                 return;
             }
-            update(c, nxt && r >= dpiv ? r + 1 : r);
+            if (!tcp) {
+                update(c, nxt && r >= dpiv ? r + 1 : r);
+                return;
+            }
+            if constexpr (sizeof(AT) == 4) {
+                AT *Dk = a.D + blk[c] * bsz;
+                const int bj = r / npair, pb = r % npair;
+                const int j = bj < p ? bj : bj + 1;
+                auto ok = [&](int i) { return i < nt && i != p && !(nxt && i == p + 1 && j == p + 1); };
+                const int i0 = 2 * pb, i1 = 2 * pb + 1;
+                const bool o0 = ok(i0), o1 = ok(i1);
+                if (o0 && o1) {
+                    tc_pair_update(*reinterpret_cast<TcSmem *>(&ts), tcs, Dk, T, i0, p, j, a.err);
+                } else if (o0 || o1) {
+                    const int i = o0 ? i0 : i1;
+                    subtile_product<AT, 64, 64, 4, 4>(ts, Dk, Dk, Dk, T, i, p, p, j, i, j, 0, 0, (AT)-1, true);
+                }
+            }
         };
         auto special = [&](int c) {
             update(c, dpiv);
@@ -938,10 +1119,10 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
         if (nxt && own) {
             if (b < nblk) special(b);
             else
-                for (int q = b - nblk; q < nblk * nreg; q += G - nblk) regular(q);
+                for (int q = b - nblk; q < nblk * nitem; q += G - nblk) regular(q);
         } else {
             const int ns = nxt ? nblk : 0;
-            for (int it = b; it < ns + nblk * nreg; it += G) {
+            for (int it = b; it < ns + nblk * nitem; it += G) {
                 if (it < ns) special(it);
                 else regular(it - ns);
             }
@@ -985,7 +1166,7 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
 // The factorisation of one handle by a group of G co-resident CTAs (b: this CTA's
 // index in the group).
 template <typename AT>
-__device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, int G) {
+__device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, int G, TcState &tcs) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<AT> &ts = *reinterpret_cast<TileSmem<AT> *>(smem_raw);
     AT *rows = reinterpret_cast<AT *>(smem_raw);
@@ -1002,7 +1183,7 @@ __device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, 
         } else {
             blk[nblk++] = mid;
         }
-        if (!invert_blocks(a, ts, blk, nblk, epoch, b, G)) return;
+        if (!invert_blocks(a, ts, blk, nblk, epoch, b, G, tcs)) return;
         if (s == nsteps) break;
         const long long ell = (long long)T * ELLW;
         const int nchunk = T / FROWS;
@@ -1030,9 +1211,46 @@ __device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, 
     }
 }
 
+// Tensor memory and the MMA mbarrier of a factorisation CTA (FP32 with the tensor
+// path): allocated before the body, freed after it on every return path.
 template <typename AT>
-__global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a) {
-    coarse_factor_body(a, blockIdx.x, gridDim.x);
+__device__ __forceinline__ void tc_begin(TcState &tcs, unsigned *slot, unsigned long long *mbar, bool want) {
+    tcs.tmem = 0;
+    tcs.mbar = mbar;
+    tcs.phase = 0;
+    if (sizeof(AT) != 4 || !want) return;
+    if (threadIdx.x < 32) {
+        asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], 64;"
+                     ::"r"((unsigned)__cvta_generic_to_shared(slot)) : "memory");
+        asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+    }
+    if (threadIdx.x == 0) {
+        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;"
+                     ::"r"((unsigned)__cvta_generic_to_shared(mbar)) : "memory");
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    tcs.tmem = *slot;
+}
+template <typename AT>
+__device__ __forceinline__ void tc_end(const TcState &tcs) {
+    if (sizeof(AT) != 4 || tcs.tmem == 0) return;
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();
+    if (threadIdx.x < 32)
+        asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, 64;" ::"r"(tcs.tmem) : "memory");
+}
+
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_factor(FacArgs<AT> a, int use_tc) {
+    __shared__ unsigned tmem_slot;
+    __shared__ unsigned long long mbar;
+    TcState tcs;
+    tc_begin<AT>(tcs, &tmem_slot, &mbar, use_tc != 0);
+    coarse_factor_body(a, blockIdx.x, gridDim.x, tcs);
+    tc_end<AT>(tcs);
 }
 
 // The factorisations of several handles in one cooperative launch: handle h takes
@@ -1044,7 +1262,11 @@ __global__ void __launch_bounds__(256) k_coarse_factor_batch(const FacArgs<AT> *
                                                              const unsigned char *active) {
     const int h = cta_inst[blockIdx.x];
     if (!active[h]) return;
-    coarse_factor_body(args[h], blockIdx.x - first[h], size[h]);
+    TcState tcs;
+    tcs.tmem = 0;   // the batched eliminations keep the CUDA-core products
+    tcs.mbar = nullptr;
+    tcs.phase = 0;
+    coarse_factor_body(args[h], blockIdx.x - first[h], size[h], tcs);
 }
 
 // ---------------------------------------------------------------------------
@@ -1435,6 +1657,10 @@ static int configure_t(Coarse *c) {
         if (c->rap125_smem <= (size_t)big || c->rap125_ng == 1) break;
     }
     c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
+    // FP32: trailing updates of the inverses on the tensor cores (RAS_COARSE_TC=0: CUDA cores)
+    c->use_tc = sizeof(AT) == 4 ? 1 : 0;
+    if (const char *e = getenv("RAS_COARSE_TC")) c->use_tc = c->use_tc && atoi(e) != 0;
+    if (c->use_tc) c->fac_smem = std::max(c->fac_smem, sizeof(TcSmem));
     // the solve prefetches up to two (FP32) or one (FP64) matrix rows per warp
     c->sol_npf = sizeof(AT) == 4 ? 2 : 1;
     while (c->sol_npf > 0 && sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T > (size_t)big) --c->sol_npf;
@@ -1622,7 +1848,8 @@ static int factor_blocks_t(Coarse *c, cudaStream_t st) {
     RAS_TRY(assemble_blocks_t<AT>(c, st));
     RAS_TRY(reset_bar(c, st));
     FacArgs<AT> fa = fac_args<AT>(c, c->d_bar);
-    void *args[] = {&fa};
+    int use_tc = c->use_tc;
+    void *args[] = {&fa, &use_tc};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_factor<AT>, dim3(c->fac_grid),
                                        dim3(256), args, c->fac_smem, st));
     RAS_LAUNCHED();
