@@ -770,7 +770,8 @@ struct TcSmem {
 };
 
 struct TcState {
-    unsigned tmem;               // accumulator base (64 columns), 0 without the tensor path
+    bool on;                     // tensor memory held: the tensor path is in use
+    unsigned tmem;               // accumulator base (64 columns; any value, 0 included)
     unsigned long long *mbar;    // MMA completion
     unsigned phase;              // completed waits of this CTA
 };
@@ -1078,7 +1079,7 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
         // (rows 2 pb, 2 pb + 1) of a tile column j != p, one MMA group per pair; a pair
         // with the pivot row or the next pivot tile (updated by its own CTA) in it
         // keeps its other tile on the CUDA-core product
-        const bool tcp = sizeof(AT) == 4 && tcs.tmem != 0;
+        const bool tcp = sizeof(AT) == 4 && tcs.on;
         const int npair = (nt + 1) / 2, npi = (nt - 1) * npair;
         const int nitem = tcp ? npi + nz : nreg;
         auto z_item = [&](int c, int z) {
@@ -1215,6 +1216,7 @@ __device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, 
 // path): allocated before the body, freed after it on every return path.
 template <typename AT>
 __device__ __forceinline__ void tc_begin(TcState &tcs, unsigned *slot, unsigned long long *mbar, bool want) {
+    tcs.on = false;
     tcs.tmem = 0;
     tcs.mbar = mbar;
     tcs.phase = 0;
@@ -1233,10 +1235,11 @@ __device__ __forceinline__ void tc_begin(TcState &tcs, unsigned *slot, unsigned 
     __syncthreads();
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
     tcs.tmem = *slot;
+    tcs.on = true;
 }
 template <typename AT>
 __device__ __forceinline__ void tc_end(const TcState &tcs) {
-    if (sizeof(AT) != 4 || tcs.tmem == 0) return;
+    if (sizeof(AT) != 4 || !tcs.on) return;
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();
     if (threadIdx.x < 32)
@@ -1263,7 +1266,8 @@ __global__ void __launch_bounds__(256) k_coarse_factor_batch(const FacArgs<AT> *
     const int h = cta_inst[blockIdx.x];
     if (!active[h]) return;
     TcState tcs;
-    tcs.tmem = 0;   // the batched eliminations keep the CUDA-core products
+    tcs.on = false;   // the batched eliminations keep the CUDA-core products
+    tcs.tmem = 0;
     tcs.mbar = nullptr;
     tcs.phase = 0;
     coarse_factor_body(args[h], blockIdx.x - first[h], size[h], tcs);
