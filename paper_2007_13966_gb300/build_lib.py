@@ -36,8 +36,9 @@ def source_hash(files=None) -> str:
     return h.hexdigest()[:16]
 
 
-# files that define the fine-level subdomain-solve kernel k_ras_apply
-RAS_APPLY_FILES = ("common.cuh", "schwarz.cuh", "schwarz.cu")
+# files that define the fine-level subdomain-solve kernels (k_ras_apply, k_ras_pipe):
+# their own source; the shared header holds host-side declarations only
+RAS_APPLY_FILES = ("schwarz.cuh", "schwarz.cu")
 
 
 def nvcc() -> str:
