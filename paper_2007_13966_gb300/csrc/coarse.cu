@@ -74,7 +74,6 @@ struct Coarse {
     void *rx = nullptr, *ry = nullptr;               // restriction passes [cx][ny][nz], [cx][cy][nz]
     int *d_err = nullptr;
     GridBar *d_bar = nullptr;
-    long long bar_polls = 0;        // poll limit currently held by d_bar
     size_t esz = 8;
     size_t rap_smem = 0, rap125_smem = 0, fac_smem = 0, sol_smem = 0;
     int rap125_ng = 25;             // offsets staged per round in k_rap125
@@ -1604,20 +1603,28 @@ static void interp_axis(int n, int r, std::vector<int> &ia, std::vector<int> &ib
     }
 }
 
-// Zero the grid barrier of a cooperative launch and set its poll limit:
-// RAS_BARRIER_POLLS (environment, read at every launch) shortens the bounded
-// wait, so that a test can make it run out and check the RAS_ETIMEOUT path.
-static int reset_bar(Coarse *c, cudaStream_t st) {
+// Zero the grid barriers of a cooperative launch (counter and release word of n
+// barrier words) and set their poll limit, by a kernel rather than a host copy so
+// that the reset can be captured in a graph. RAS_BARRIER_POLLS (environment, read
+// at every launch) shortens the bounded wait, so that a test can make it run out
+// and check the RAS_ETIMEOUT path.
+__global__ void k_reset_bars(GridBar *bars, int n, long long polls) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
+        bars[i].count = 0;
+        bars[i].gen = 0;
+        bars[i].polls = polls;
+    }
+}
+
+static long long barrier_polls() {
     long long polls = 0;
     if (const char *e = getenv("RAS_BARRIER_POLLS")) polls = atoll(e);
-    if (polls != c->bar_polls) {        // the limit stays on the device between launches
-        GridBar b{};
-        b.polls = polls;
-        RAS_CK(cudaMemcpyAsync(c->d_bar, &b, sizeof(GridBar), cudaMemcpyHostToDevice, st));
-        c->bar_polls = polls;
-    } else {
-        RAS_CK(cudaMemsetAsync(c->d_bar, 0, offsetof(GridBar, polls), st));
-    }
+    return polls;
+}
+
+static int reset_bar(Coarse *c, cudaStream_t st) {
+    k_reset_bars<<<1, 32, 0, st>>>(c->d_bar, 1, barrier_polls());
+    RAS_LAUNCHED();
     return RAS_OK;
 }
 
@@ -2067,7 +2074,8 @@ int coarse_batch_setup(Coarse *const *cs, int n, CoarseBatch **out) {
 }
 
 int coarse_factor_batch(CoarseBatch *cb, const unsigned char *d_active, cudaStream_t st) {
-    RAS_CK(cudaMemsetAsync(cb->d_bars, 0, cb->n * sizeof(GridBar), st));
+    k_reset_bars<<<(cb->n + 127) / 128, 128, 0, st>>>(cb->d_bars, cb->n, barrier_polls());
+    RAS_LAUNCHED();
     for (size_t w = 0; w < cb->fwave0.size(); ++w) {
         const int *cta = cb->d_fcta_inst + cb->fwave0[w];
         const dim3 grid(cb->fwaven[w]);
@@ -2089,7 +2097,8 @@ int coarse_factor_batch(CoarseBatch *cb, const unsigned char *d_active, cudaStre
 
 int coarse_correct_batch(CoarseBatch *cb, const long long *d_off, const unsigned char *d_active, const double *t,
                          double *z, cudaStream_t st) {
-    RAS_CK(cudaMemsetAsync(cb->d_bars, 0, cb->n * sizeof(GridBar), st));
+    k_reset_bars<<<(cb->n + 127) / 128, 128, 0, st>>>(cb->d_bars, cb->n, barrier_polls());
+    RAS_LAUNCHED();
     if (cb->prec == 64) {
         const SolArgs<double> *a = (const SolArgs<double> *)cb->d_args;
         void *args[] = {&a, &cb->d_cta_inst, &cb->d_first, &cb->d_size, &d_off, &d_active, &t, &z};
