@@ -193,6 +193,93 @@ __global__ void __launch_bounds__(256) k_bcombine(double *__restrict__ x, const 
     }
 }
 
+// Per-reservoir FGMRES scalars of one restart cycle, on the device: the Hessenberg
+// matrix, the Givens rotations, the rotated right-hand side g, the stop tolerance,
+// the residual estimate after each Arnoldi step, the iteration counts.
+struct BKrylov {
+    double *H;       // [n][(m+1) m]
+    double *cs, *sn; // [n][m]
+    double *g;       // [n][m+1]
+    double *tol;     // [n]
+    double *res;     // [n][m]
+    int *it;         // [n] Arnoldi steps so far (all cycles)
+    int *jend;       // [n] Arnoldi steps of this cycle
+    int *bad;        // [n] NaN / Inf met
+    int m, maxit;
+};
+
+// start of a cycle: H = 0, g = beta e_1 for the reservoirs of the cycle
+__global__ void k_bcycle_init(BKrylov K, const double *__restrict__ beta, const unsigned char *__restrict__ cyc,
+                              int n) {
+    const int i = blockIdx.x;
+    if (i >= n || !cyc[i]) return;
+    const int m = K.m;
+    for (int q = threadIdx.x; q < (m + 1) * m; q += blockDim.x) K.H[(long long)i * (m + 1) * m + q] = 0.0;
+    for (int q = threadIdx.x; q <= m; q += blockDim.x) K.g[(long long)i * (m + 1) + q] = q == 0 ? beta[i] : 0.0;
+    if (threadIdx.x == 0) K.jend[i] = 0;
+}
+
+// Arnoldi step j, one thread per reservoir (the arithmetic of the single-reservoir
+// routine, in its order): the column of H from the two CGS passes, the earlier
+// rotations applied to it, a new rotation, the residual estimate |g_{j+1}| and the
+// stop test; a reservoir that stops (converged, breakdown, iteration limit, NaN) is
+// switched off in the mask, so the remaining steps of the cycle skip it.
+__global__ void k_bgivens(BKrylov K, const double *__restrict__ out, unsigned char *__restrict__ act, int j, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n || !act[i]) return;
+    const int m = K.m, k = j + 1;
+    const double *hh = out + (long long)i * OST;
+    double *Hi = K.H + (long long)i * (m + 1) * m;
+    double *csi = K.cs + (long long)i * m, *sni = K.sn + (long long)i * m, *gi = K.g + (long long)i * (m + 1);
+    for (int a = 0; a < k; ++a) Hi[(long long)a * m + j] = hh[a] + hh[k + 1 + a];
+    const double wnorm0 = sqrt(hh[k]);
+    const double hn = hh[2 * k + 1];
+    Hi[(long long)(j + 1) * m + j] = hn;
+    if (!isfinite(hn) || !isfinite(wnorm0)) {
+        K.bad[i] = 1;
+        act[i] = 0;
+        return;
+    }
+    const bool breakdown = hn <= 1e-14 * wnorm0;
+    for (int a = 0; a < j; ++a) {
+        const double t = csi[a] * Hi[(long long)a * m + j] + sni[a] * Hi[(long long)(a + 1) * m + j];
+        Hi[(long long)(a + 1) * m + j] = -sni[a] * Hi[(long long)a * m + j] + csi[a] * Hi[(long long)(a + 1) * m + j];
+        Hi[(long long)a * m + j] = t;
+    }
+    const double hjj = Hi[(long long)j * m + j], hj1 = Hi[(long long)(j + 1) * m + j];
+    const double den = hypot(hjj, hj1);
+    csi[j] = hjj / den;
+    sni[j] = hj1 / den;
+    Hi[(long long)j * m + j] = den;
+    Hi[(long long)(j + 1) * m + j] = 0.0;
+    gi[j + 1] = -sni[j] * gi[j];
+    gi[j] = csi[j] * gi[j];
+    const int itn = ++K.it[i];
+    const double r = fabs(gi[j + 1]);
+    K.res[(long long)i * m + j] = r;
+    K.jend[i] = j + 1;
+    if (r <= K.tol[i] || breakdown || itn >= K.maxit) act[i] = 0;
+}
+
+// end of a cycle: y = H^{-1} g on the cycle's Krylov dimension, per reservoir
+__global__ void k_btrisolve(BKrylov K, const unsigned char *__restrict__ cyc, double *__restrict__ y,
+                            int *__restrict__ kk, double *__restrict__ lastg, int n) {
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= n) return;
+    kk[i] = 0;
+    if (!cyc[i]) return;
+    const int m = K.m, kq = K.jend[i];
+    const double *Hi = K.H + (long long)i * (m + 1) * m, *gi = K.g + (long long)i * (m + 1);
+    double *yi = y + (long long)i * MAX_MDOT;
+    for (int a = kq - 1; a >= 0; --a) {
+        double s = gi[a];
+        for (int l = a + 1; l < kq; ++l) s -= Hi[(long long)a * m + l] * yi[l];
+        yi[a] = s / Hi[(long long)a * m + a];
+    }
+    kk[i] = kq;
+    lastg[i] = gi[kq];
+}
+
 }  // namespace ras
 
 using namespace ras;
@@ -203,7 +290,8 @@ struct ras_batch {
     std::vector<ras_precond *> pc;
     std::vector<long long> off;              // cell offset of each reservoir
     long long Ntot = 0;
-    int nch = 0, nbox = 0;
+    int nch = 0, nbox = 0, qgrid = 0;       // chunks; boxes in the work queue; persistent CTAs
+    int *d_qcount = nullptr;                 // work counter of the batched subdomain solves
     std::vector<int> ch0, chn;               // per reservoir: first chunk, chunks
     int prec = 32, block = 0;
     size_t smem = 0;
@@ -220,6 +308,17 @@ struct ras_batch {
     ApplyParams *d_ap = nullptr;
     int *d_box_inst = nullptr, *d_box_local = nullptr;
     double *partials = nullptr, *out = nullptr, *h_out = nullptr, *d_y = nullptr, *d_beta = nullptr;
+    // per-reservoir FGMRES scalars on the device, and the restart cycle as a CUDA graph
+    BKrylov K{};
+    int Km = 0;                              // m the device scalars were sized for
+    unsigned char *d_cyc = nullptr;          // reservoirs of the current cycle
+    double *d_lastg = nullptr;
+    cudaGraphExec_t cycle_exec = nullptr;    // the m Arnoldi steps of a cycle, captured
+    int cycle_m = 0;                         // m of the captured cycle
+    long long cycle_launches = 0;            // kernels in it (counted at every replay)
+    bool graph_off = false;                  // capture failed or disabled: direct launches
+    cudaStream_t gstream = nullptr;          // the graph's own stream (joined to the caller's by events)
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     // Krylov and batch vectors
     int m = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *b = nullptr, *x = nullptr,
@@ -232,10 +331,16 @@ static void batch_free(ras_batch *B) {
     if (!B) return;
     coarse_batch_free(B->cb);
     dfree(B->d_ops); dfree(B->d_opsM); dfree(B->t); dfree(B->d_ch); dfree(B->d_off); dfree(B->d_ch0); dfree(B->d_chn); dfree(B->d_kk);
-    dfree(B->d_act); dfree(B->d_ap); dfree(B->d_box_inst); dfree(B->d_box_local);
+    dfree(B->d_act); dfree(B->d_ap); dfree(B->d_box_inst); dfree(B->d_box_local); dfree(B->d_qcount);
     dfree(B->partials); dfree(B->out); dfree(B->d_y); dfree(B->d_beta);
     if (B->h_out) cudaFreeHost(B->h_out);
     dfree(B->V); dfree(B->Z); dfree(B->w); dfree(B->r); dfree(B->b); dfree(B->x); dfree(B->tmp);
+    dfree(B->K.H); dfree(B->K.cs); dfree(B->K.sn); dfree(B->K.g); dfree(B->K.tol); dfree(B->K.res);
+    dfree(B->K.it); dfree(B->K.jend); dfree(B->K.bad); dfree(B->d_cyc); dfree(B->d_lastg);
+    if (B->cycle_exec) cudaGraphExecDestroy(B->cycle_exec);
+    if (B->ev_fork) cudaEventDestroy(B->ev_fork);
+    if (B->ev_join) cudaEventDestroy(B->ev_join);
+    if (B->gstream) cudaStreamDestroy(B->gstream);
     delete B;
 }
 
@@ -310,8 +415,8 @@ static int b_scale(ras_batch *B, double *y, const double *x, const double *s, in
 //   z = M v;  t = v - A z;  z += P A_c^{-1} R t;  t = v - A z;  z += M t
 // (A: the operator of each reservoir's last factorisation)
 static int b_precond(ras_batch *B, const double *v, double *z, cudaStream_t st) {
-    BatchApply A{B->d_ap, B->d_box_inst, B->d_box_local, B->d_off, B->d_act, v, z, 0};
-    RAS_TRY(ras1_apply_batch(A, B->nbox, B->prec, B->block, B->smem, st));
+    BatchApply A{B->d_ap, B->d_box_inst, B->d_box_local, B->d_off, B->d_act, v, z, 0, B->nbox, B->d_qcount};
+    RAS_TRY(ras1_apply_batch(A, B->qgrid, B->prec, B->block, B->smem, st));
     if (!B->twolevel) return RAS_OK;
     RAS_TRY(b_stencil<true>(B, v, z, B->t, st, B->d_opsM));
     if (B->cb) {
@@ -323,7 +428,7 @@ static int b_precond(ras_batch *B, const double *v, double *z, cudaStream_t st) 
     RAS_TRY(b_stencil<true>(B, v, z, B->t, st, B->d_opsM));
     A.r = B->t;
     A.accumulate = 1;
-    return ras1_apply_batch(A, B->nbox, B->prec, B->block, B->smem, st);
+    return ras1_apply_batch(A, B->qgrid, B->prec, B->block, B->smem, st);
 }
 
 // the V-cycle operators of the reservoirs factored since the last upload
@@ -345,14 +450,124 @@ static int b_norms(ras_batch *B, const double *v, std::vector<double> &res, cuda
     return RAS_OK;
 }
 
+static int ensure_krylov_dev(ras_batch *B, int m) {
+    if (B->Km == m) return RAS_OK;
+    BKrylov &K = B->K;
+    dfree(K.H); dfree(K.cs); dfree(K.sn); dfree(K.g); dfree(K.tol); dfree(K.res);
+    dfree(K.it); dfree(K.jend); dfree(K.bad);
+    B->Km = 0;
+    const int n = B->n;
+    RAS_TRY(dalloc(&K.H, (size_t)n * (m + 1) * m));
+    RAS_TRY(dalloc(&K.cs, (size_t)n * m));
+    RAS_TRY(dalloc(&K.sn, (size_t)n * m));
+    RAS_TRY(dalloc(&K.g, (size_t)n * (m + 1)));
+    RAS_TRY(dalloc(&K.tol, n));
+    RAS_TRY(dalloc(&K.res, (size_t)n * m));
+    RAS_TRY(dalloc(&K.it, n));
+    RAS_TRY(dalloc(&K.jend, n));
+    RAS_TRY(dalloc(&K.bad, n));
+    if (!B->d_cyc) RAS_TRY(dalloc(&B->d_cyc, n));
+    if (!B->d_lastg) RAS_TRY(dalloc(&B->d_lastg, n));
+    K.m = m;
+    B->Km = m;
+    if (B->cycle_exec) {   // a captured cycle of another m is stale
+        cudaGraphExecDestroy(B->cycle_exec);
+        B->cycle_exec = nullptr;
+        B->cycle_m = 0;
+    }
+    return RAS_OK;
+}
+
+// The m Arnoldi steps of one restart cycle for every reservoir in the device mask:
+// preconditioner, operator, two CGS passes with their norms, the next basis vector,
+// and the device-side Hessenberg / Givens step that switches a stopping reservoir off.
+// No host data enters: the same launches serve every cycle.
+static int b_cycle(ras_batch *B, int m, cudaStream_t st) {
+    const long long Nt = B->Ntot;
+    for (int j = 0; j < m; ++j) {
+        const int k = j + 1;
+        double *Vj = B->V + (size_t)j * Nt, *Zj = B->Z + (size_t)j * Nt;
+        RAS_TRY(b_precond(B, Vj, Zj, st));
+        RAS_TRY(b_stencil<false>(B, nullptr, Zj, B->w, st));
+        RAS_TRY(b_mdot(B, B->V, k, 1, B->w, st));
+        RAS_TRY(b_finalize(B, k + 1, 0, 0, st));
+        RAS_TRY(b_update<false>(B, k, 0, B->w, st));
+        RAS_TRY(b_mdot(B, B->V, k, 0, B->w, st));
+        RAS_TRY(b_finalize(B, k, k + 1, 0, st));
+        RAS_TRY(b_update<true>(B, k, k + 1, B->w, st));
+        RAS_TRY(b_finalize(B, 1, 2 * k + 1, 1, st));
+        RAS_TRY(b_scale(B, B->V + (size_t)(j + 1) * Nt, B->w, B->out + 2 * k + 1, OST, st));
+        k_bgivens<<<(B->n + 63) / 64, 64, 0, st>>>(B->K, B->out, B->d_act, j, B->n);
+        RAS_LAUNCHED();
+    }
+    return RAS_OK;
+}
+
+// Runs the cycle: replays its CUDA graph (captured on the first cycle of this m) on
+// the batch's own stream, joined to the caller's stream by events; or launches it
+// directly (RAS_BATCH_GRAPH=0, a batch whose coarse corrections are launched per
+// reservoir from host state, or a capture that failed).
+static int b_run_cycle(ras_batch *B, int m, cudaStream_t st) {
+    bool use_graph = !B->graph_off && (!B->twolevel || B->cb);
+    if (const char *e = getenv("RAS_BATCH_GRAPH")) use_graph = use_graph && atoi(e) != 0;
+    if (use_graph && !B->gstream) {
+        if (cudaStreamCreateWithFlags(&B->gstream, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&B->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+            cudaGetLastError();
+            B->graph_off = true;
+            use_graph = false;
+        }
+    }
+    if (!use_graph) return b_cycle(B, m, st);
+    if (!B->cycle_exec || B->cycle_m != m) {
+        if (B->cycle_exec) {
+            cudaGraphExecDestroy(B->cycle_exec);
+            B->cycle_exec = nullptr;
+        }
+        const long long n0 = g_launches.load();
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(B->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            B->graph_off = true;
+            return b_cycle(B, m, st);
+        }
+        const int rc = b_cycle(B, m, B->gstream);
+        const cudaError_t ec = cudaStreamEndCapture(B->gstream, &graph);
+        if (rc < 0 || ec != cudaSuccess || !graph ||
+            cudaGraphInstantiate(&B->cycle_exec, graph, 0) != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            cudaGetLastError();
+            B->cycle_exec = nullptr;
+            B->graph_off = true;
+            g_launches.store(n0);
+            return b_cycle(B, m, st);   // nothing ran during the capture: run the cycle now
+        }
+        cudaGraphDestroy(graph);
+        B->cycle_m = m;
+        B->cycle_launches = g_launches.load() - n0;
+        g_launches.store(n0);
+    }
+    RAS_CK(cudaEventRecord(B->ev_fork, st));
+    RAS_CK(cudaStreamWaitEvent(B->gstream, B->ev_fork, 0));
+    RAS_CK(cudaGraphLaunch(B->cycle_exec, B->gstream));
+    RAS_CK(cudaEventRecord(B->ev_join, B->gstream));
+    RAS_CK(cudaStreamWaitEvent(st, B->ev_join, 0));
+    g_launches.fetch_add(B->cycle_launches, std::memory_order_relaxed);
+    return RAS_OK;
+}
+
 // Batched right-preconditioned FGMRES(m) (the steps of the single-reservoir
 // routine, per reservoir) on B->b -> B->x for the reservoirs with want[i];
-// operators in B->ops (uploaded by the caller).
+// operators in B->ops (uploaded by the caller). The Arnoldi scalars of every
+// reservoir are updated on the device, so a restart cycle runs without the host
+// (one CUDA graph); the host reads the cycle's outcome once per restart.
 static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const ras_krylov_opts &o,
                    ras_krylov_stats *stats, cudaStream_t st) {
     const int n = B->n, m = o.restart;
     if (m < 1 || m > MAX_MDOT - 1 || o.maxit < 1) return RAS_EINVAL;
     RAS_TRY(ensure_krylov_b(B, m));
+    RAS_TRY(ensure_krylov_dev(B, m));
     const long long Nt = B->Ntot;
     auto push = [&](int i, double v) {
         if (!stats) return;
@@ -373,15 +588,17 @@ static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const r
         beta[i] = bnorm[i];
         push(i, beta[i]);
     }
+    BKrylov &K = B->K;
+    K.maxit = o.maxit;
+    RAS_CK(cudaMemcpyAsync(K.tol, tol.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
+    RAS_CK(cudaMemsetAsync(K.it, 0, n * sizeof(int), st));
+    RAS_CK(cudaMemsetAsync(K.bad, 0, n * sizeof(int), st));
     RAS_TRY(vec_set(B->x, 0.0, (int)Nt, st));
     RAS_TRY(vec_copy(B->r, B->b, (int)Nt, st));
-    std::vector<int> it(n, 0), jend(n, 0);
+    std::vector<int> it(n, 0), jend(n, 0), bad(n, 0);
     std::vector<unsigned char> conv(n, 0), cyc(n, 0);
     for (int i = 0; i < n; ++i) conv[i] = want[i] && beta[i] <= tol[i];
-    std::vector<double> H((size_t)n * (m + 1) * m), cs((size_t)n * m), sn((size_t)n * m), g((size_t)n * (m + 1));
-    std::vector<double> y((size_t)n * MAX_MDOT, 0.0);
-    std::vector<int> kk(n, 0);
-    std::vector<double> lastg(n, 0.0);
+    std::vector<double> res((size_t)n * m), lastg(n, 0.0);
     for (;;) {
         bool any = false;
         for (int i = 0; i < n; ++i) {
@@ -389,96 +606,35 @@ static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const r
             any = any || cyc[i];
         }
         if (!any) break;
-        // V_0 = r / beta
+        // V_0 = r / beta; g = beta e_1
         RAS_CK(cudaMemcpyAsync(B->d_beta, beta.data(), n * sizeof(double), cudaMemcpyHostToDevice, st));
         B->act = cyc;
         RAS_TRY(upload_mask(B, st));
+        RAS_CK(cudaMemcpyAsync(B->d_cyc, cyc.data(), n, cudaMemcpyHostToDevice, st));
         RAS_TRY(b_scale(B, B->V, B->r, B->d_beta, 1, st));
-        std::fill(H.begin(), H.end(), 0.0);
-        std::fill(g.begin(), g.end(), 0.0);
-        for (int i = 0; i < n; ++i) { g[(size_t)i * (m + 1)] = beta[i]; jend[i] = 0; }
-        std::vector<unsigned char> live = cyc;
-        for (int j = 0; j < m; ++j) {
-            bool anyl = false;
-            for (int i = 0; i < n; ++i) anyl = anyl || live[i];
-            if (!anyl) break;
-            const int k = j + 1;
-            double *Vj = B->V + (size_t)j * Nt, *Zj = B->Z + (size_t)j * Nt;
-            RAS_TRY(b_precond(B, Vj, Zj, st));
-            RAS_TRY(b_stencil<false>(B, nullptr, Zj, B->w, st));
-            RAS_TRY(b_mdot(B, B->V, k, 1, B->w, st));
-            RAS_TRY(b_finalize(B, k + 1, 0, 0, st));
-            RAS_TRY(b_update<false>(B, k, 0, B->w, st));
-            RAS_TRY(b_mdot(B, B->V, k, 0, B->w, st));
-            RAS_TRY(b_finalize(B, k, k + 1, 0, st));
-            RAS_TRY(b_update<true>(B, k, k + 1, B->w, st));
-            RAS_TRY(b_finalize(B, 1, 2 * k + 1, 1, st));
-            RAS_TRY(b_scale(B, B->V + (size_t)(j + 1) * Nt, B->w, B->out + 2 * k + 1, OST, st));
-            RAS_CK(cudaMemcpyAsync(B->h_out, B->out, (size_t)n * OST * sizeof(double), cudaMemcpyDeviceToHost, st));
-            RAS_CK(cudaStreamSynchronize(st));
-            bool changed = false;
-            for (int i = 0; i < n; ++i) {
-                if (!live[i]) continue;
-                const double *hh = B->h_out + (size_t)i * OST;
-                double *Hi = &H[(size_t)i * (m + 1) * m];
-                auto Hc = [&](int a, int c) -> double & { return Hi[(size_t)a * m + c]; };
-                double *csi = &cs[(size_t)i * m], *sni = &sn[(size_t)i * m], *gi = &g[(size_t)i * (m + 1)];
-                for (int a = 0; a < k; ++a) Hc(a, j) = hh[a] + hh[k + 1 + a];
-                const double wnorm0 = std::sqrt(hh[k]);
-                const double hn = hh[2 * k + 1];
-                Hc(j + 1, j) = hn;
-                if (!std::isfinite(hn) || !std::isfinite(wnorm0)) return RAS_ENAN;
-                const bool breakdown = hn <= 1e-14 * wnorm0;
-                for (int a = 0; a < j; ++a) {
-                    const double t = csi[a] * Hc(a, j) + sni[a] * Hc(a + 1, j);
-                    Hc(a + 1, j) = -sni[a] * Hc(a, j) + csi[a] * Hc(a + 1, j);
-                    Hc(a, j) = t;
-                }
-                const double den = std::hypot(Hc(j, j), Hc(j + 1, j));
-                csi[j] = Hc(j, j) / den;
-                sni[j] = Hc(j + 1, j) / den;
-                Hc(j, j) = den;
-                Hc(j + 1, j) = 0.0;
-                gi[j + 1] = -sni[j] * gi[j];
-                gi[j] = csi[j] * gi[j];
-                ++it[i];
-                const double res = std::fabs(gi[j + 1]);
-                push(i, res);
-                jend[i] = j + 1;
-                if (res <= tol[i] || breakdown || it[i] >= o.maxit) { live[i] = 0; changed = true; }
-            }
-            if (changed) {
-                B->act = live;
-                RAS_TRY(upload_mask(B, st));
-            }
-        }
-        // x += Z y per reservoir (its own Krylov dimension)
-        for (int i = 0; i < n; ++i) {
-            kk[i] = 0;
-            if (!cyc[i]) continue;
-            const int kq = jend[i];
-            const double *Hi = &H[(size_t)i * (m + 1) * m];
-            const double *gi = &g[(size_t)i * (m + 1)];
-            double *yi = &y[(size_t)i * MAX_MDOT];
-            for (int a = kq - 1; a >= 0; --a) {
-                double s = gi[a];
-                for (int l = a + 1; l < kq; ++l) s -= Hi[(size_t)a * m + l] * yi[l];
-                yi[a] = s / Hi[(size_t)a * m + a];
-            }
-            kk[i] = kq;
-            lastg[i] = gi[kq];
-        }
-        RAS_CK(cudaMemcpyAsync(B->d_y, y.data(), y.size() * sizeof(double), cudaMemcpyHostToDevice, st));
-        RAS_CK(cudaMemcpyAsync(B->d_kk, kk.data(), n * sizeof(int), cudaMemcpyHostToDevice, st));
+        k_bcycle_init<<<n, 64, 0, st>>>(K, B->d_beta, B->d_cyc, n);
+        RAS_LAUNCHED();
+        RAS_TRY(b_run_cycle(B, m, st));
+        // x += Z y per reservoir (its own Krylov dimension); mask back to the cycle's reservoirs
+        k_btrisolve<<<(n + 63) / 64, 64, 0, st>>>(K, B->d_cyc, B->d_y, B->d_kk, B->d_lastg, n);
+        RAS_LAUNCHED();
+        RAS_CK(cudaMemcpyAsync(B->d_act, B->d_cyc, n, cudaMemcpyDeviceToDevice, st));
         B->act = cyc;
-        RAS_TRY(upload_mask(B, st));
         k_bcombine<<<B->nch, 256, 0, st>>>(B->x, B->Z, Nt, B->d_y, B->d_kk, B->d_ch, B->d_off, B->d_act);
         RAS_LAUNCHED();
         RAS_TRY(b_stencil<true>(B, B->b, B->x, B->r, st));
+        // the cycle's outcome: iteration counts, steps, residual estimates, NaN flags
+        RAS_CK(cudaMemcpyAsync(it.data(), K.it, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RAS_CK(cudaMemcpyAsync(jend.data(), K.jend, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RAS_CK(cudaMemcpyAsync(bad.data(), K.bad, n * sizeof(int), cudaMemcpyDeviceToHost, st));
+        RAS_CK(cudaMemcpyAsync(res.data(), K.res, res.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        RAS_CK(cudaMemcpyAsync(lastg.data(), B->d_lastg, n * sizeof(double), cudaMemcpyDeviceToHost, st));
         std::vector<double> nb(n, 0.0);
-        RAS_TRY(b_norms(B, B->r, nb, st));
+        RAS_TRY(b_norms(B, B->r, nb, st));   // synchronises
         for (int i = 0; i < n; ++i) {
             if (!cyc[i]) continue;
+            if (bad[i]) return RAS_ENAN;
+            for (int j = 0; j < jend[i]; ++j) push(i, res[(size_t)i * m + j]);
             beta[i] = nb[i];
             if (!std::isfinite(beta[i])) return RAS_ENAN;
             conv[i] = beta[i] <= tol[i] || std::fabs(lastg[i]) <= tol[i];
@@ -699,7 +855,7 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
     B->pc.assign(pcs, pcs + n);
     std::vector<BChunk> ch;
     std::vector<ApplyParams> ap(n);
-    std::vector<int> box_inst, box_local;
+    std::vector<int> box_inst, box_local, box_cells;
     long long off = 0;
     for (int i = 0; i < n; ++i) {
         ras_problem *P = probs[i];
@@ -724,14 +880,31 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
         op.mx = bmagic(P->nx); op.my = bmagic(P->ny);
         B->ops.push_back(op);
         ras1_apply_params(pc->fine, ap[i]);
-        for (int q = 0; q < pc->fine.nsub; ++q) { box_inst.push_back(i); box_local.push_back(q); }
+        for (int q = 0; q < pc->fine.nsub; ++q) {
+            box_inst.push_back(i);
+            box_local.push_back(q);
+            box_cells.push_back(pc->fine.shapes[pc->fine.subs[q].shape].ncell);
+        }
         B->block = std::max(B->block, pc->fine.block);
         B->smem = std::max(B->smem, pc->fine.smem_apply);
     }
     if (off > 0x7fffffffLL) return fail(RAS_EINVAL);   // the flat vector kernels take int counts
+    {
+        const int rq = ras1_batch_grid(B->prec, B->block, B->smem, (int)box_inst.size(), &B->qgrid);
+        if (rq < 0) return fail(rq);
+    }
     B->Ntot = off;
     B->nch = (int)ch.size();
     B->nbox = (int)box_inst.size();
+    {   // the work queue of the batched subdomain solves: largest box first
+        std::vector<int> ord(B->nbox);
+        for (int q = 0; q < B->nbox; ++q) ord[q] = q;
+        std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return box_cells[a] > box_cells[b]; });
+        std::vector<int> bi(B->nbox), bl(B->nbox);
+        for (int q = 0; q < B->nbox; ++q) { bi[q] = box_inst[ord[q]]; bl[q] = box_local[ord[q]]; }
+        box_inst.swap(bi);
+        box_local.swap(bl);
+    }
     B->act.assign(n, 1);
     const size_t Nt = (size_t)B->Ntot;
     int rc = 0;
@@ -740,7 +913,7 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
         (rc = dalloc(&B->d_ch, ch.size())) || (rc = dalloc(&B->d_off, n)) ||
         (rc = dalloc(&B->d_ch0, n)) || (rc = dalloc(&B->d_chn, n)) || (rc = dalloc(&B->d_kk, n)) ||
         (rc = dalloc(&B->d_act, n)) || (rc = dalloc(&B->d_ap, n)) || (rc = dalloc(&B->d_box_inst, box_inst.size())) ||
-        (rc = dalloc(&B->d_box_local, box_local.size())) ||
+        (rc = dalloc(&B->d_box_local, box_local.size())) || (rc = dalloc(&B->d_qcount, 1)) ||
         (rc = dalloc(&B->partials, (size_t)(MAX_MDOT + 1) * B->nch)) || (rc = dalloc(&B->out, (size_t)n * OST)) ||
         (rc = dalloc(&B->d_y, (size_t)n * MAX_MDOT)) || (rc = dalloc(&B->d_beta, n)) || (rc = dalloc(&B->w, Nt)) ||
         (rc = dalloc(&B->r, Nt)) || (rc = dalloc(&B->b, Nt)) || (rc = dalloc(&B->x, Nt)) || (rc = dalloc(&B->tmp, Nt)))

@@ -321,14 +321,24 @@ __global__ void __launch_bounds__(512, 2) k_ras_apply(ApplyParams P) {
     ras_apply_box<PREC, NBUF>(P, blockIdx.x, P.r, P.z, P.accumulate);
 }
 
-// Left-RAS of many handles in one launch: CTA b solves box box_local[b] of handle
-// box_inst[b] (CTAs of inactive handles return at once); r and z are the handles'
-// vectors concatenated at off[handle].
+// Left-RAS of many handles in one persistent launch: every CTA takes the next
+// item of a work queue (an atomic counter over the table of (handle, box), sorted
+// largest box first) until the queue is empty, and solves box box_local[item] of
+// handle box_inst[item] (items of inactive handles are skipped); r and z are the
+// handles' vectors concatenated at off[handle]. No CTA waits on another.
 template <int PREC, int NBUF>
 __global__ void __launch_bounds__(512, 2) k_ras_apply_batch(BatchApply B) {
-    const int h = B.box_inst[blockIdx.x];
-    if (!B.active[h]) return;
-    ras_apply_box<PREC, NBUF>(B.inst[h], B.box_local[blockIdx.x], B.r + B.off[h], B.z + B.off[h], B.accumulate);
+    __shared__ int s_item;
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(B.qcount, 1);
+        __syncthreads();
+        const int it = s_item;
+        __syncthreads();   // every thread holds the item, and the last box's shared memory is free
+        if (it >= B.nitems) return;
+        const int h = B.box_inst[it];
+        if (!B.active[h]) continue;
+        ras_apply_box<PREC, NBUF>(B.inst[h], B.box_local[it], B.r + B.off[h], B.z + B.off[h], B.accumulate);
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -1013,12 +1023,25 @@ void ras1_apply_params(const Ras1 &R, ApplyParams &P) {
     P.kind = R.kind; P.zbuf = R.zbuf;
 }
 
-int ras1_apply_batch(const BatchApply &B, int nblocks, int prec, int block, size_t smem, cudaStream_t st) {
-    if (nblocks <= 0) return RAS_OK;
-    if (prec == 64) k_ras_apply_batch<64, 3><<<nblocks, block, smem, st>>>(B);
-    else if (prec == 32) k_ras_apply_batch<32, 3><<<nblocks, block, smem, st>>>(B);
-    else k_ras_apply_batch<16, 3><<<nblocks, block, smem, st>>>(B);
+int ras1_apply_batch(const BatchApply &B, int grid, int prec, int block, size_t smem, cudaStream_t st) {
+    if (grid <= 0 || B.nitems <= 0) return RAS_OK;
+    RAS_CK(cudaMemsetAsync(B.qcount, 0, sizeof(int), st));
+    if (prec == 64) k_ras_apply_batch<64, 3><<<grid, block, smem, st>>>(B);
+    else if (prec == 32) k_ras_apply_batch<32, 3><<<grid, block, smem, st>>>(B);
+    else k_ras_apply_batch<16, 3><<<grid, block, smem, st>>>(B);
     RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+int ras1_batch_grid(int prec, int block, size_t smem, int nitems, int *grid) {
+    int dev = 0, sms = 0, per = 0;
+    RAS_CK(cudaGetDevice(&dev));
+    RAS_CK(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    if (prec == 64) RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ras_apply_batch<64, 3>, block, smem));
+    else if (prec == 32) RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ras_apply_batch<32, 3>, block, smem));
+    else RAS_CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per, k_ras_apply_batch<16, 3>, block, smem));
+    if (per < 1) return RAS_EINVAL;
+    *grid = std::min(nitems, sms * per);
     return RAS_OK;
 }
 

@@ -115,7 +115,8 @@ struct ApplyParams {
     int kind;        // 1 left-RAS; 0 AS, 2 right-RAS (box solutions to zbuf)
     double *zbuf;
 };
-// Left-RAS (kind 1) of several handles in one launch (see k_ras_apply_batch)
+// Left-RAS (kind 1) of several handles in one launch: a persistent kernel whose CTAs
+// take boxes (handle, box) from a work queue, largest first (see k_ras_apply_batch)
 struct BatchApply {
     const ApplyParams *inst;          // [handles] device copies of the handles' parameters
     const int *box_inst, *box_local;  // [CTAs] handle and box of every CTA
@@ -124,9 +125,14 @@ struct BatchApply {
     const double *r;
     double *z;
     int accumulate;                   // z += (instead of =) the correction
+    int nitems;                       // boxes in the work queue (box_inst / box_local order)
+    int *qcount;                      // device work counter, cleared before each launch
 };
 void ras1_apply_params(const Ras1 &R, ApplyParams &P);
-int ras1_apply_batch(const BatchApply &B, int nblocks, int prec, int block, size_t smem, cudaStream_t st);
+// persistent launch of `grid` CTAs over the B.nitems boxes of the work queue
+int ras1_apply_batch(const BatchApply &B, int grid, int prec, int block, size_t smem, cudaStream_t st);
+// CTAs of the batched solve that are co-resident on the device (its persistent grid)
+int ras1_batch_grid(int prec, int block, size_t smem, int nitems, int *grid);
 double ras1_bytes(const Ras1 &R);
 
 }  // namespace ras

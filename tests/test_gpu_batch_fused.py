@@ -153,3 +153,34 @@ def test_batch_module_fused_equals_streams(ras):
     for (pf, itf), (ps, its) in zip(fused, streams):
         assert rel_err(host(pf), host(ps)) < 1e-7
         assert [a for a, _ in itf] == [a for a, _ in its]    # Newton iterations per step
+
+
+@pytest.mark.parametrize("prec,nlevels", [(32, 1), (32, 2)])
+def test_graph_cycle_equals_direct_launches(ras, prec, nlevels):
+    """A restart cycle of the batched FGMRES (every reservoir's Arnoldi scalars on the
+    device, no host round trip) replayed as a CUDA graph gives the same bits as the
+    same launches issued one by one (RAS_BATCH_GRAPH=0), over several restarts and
+    with reservoirs stopping at different iterations."""
+    import os
+    items = setup(ras, prec, nlevels)
+    outs, xs_all = [], []
+    for graph in ("1", "0"):
+        old = os.environ.get("RAS_BATCH_GRAPH")
+        os.environ["RAS_BATCH_GRAPH"] = graph
+        try:
+            bs = ras.BatchSolver([it[3] for it in items], [it[4] for it in items])
+            xs = [torch.zeros_like(it[6]) for it in items]
+            outs.append(bs.gmres([it[5] for it in items], [it[6] for it in items], xs, restart=8,
+                                 maxit=200, rtol=1e-9))
+            xs_all.append(xs)
+            del bs
+        finally:
+            if old is None:
+                del os.environ["RAS_BATCH_GRAPH"]
+            else:
+                os.environ["RAS_BATCH_GRAPH"] = old
+    for a, b in zip(outs[0], outs[1]):
+        assert a["iters"] == b["iters"] and a["history"] == b["history"]
+    for xa, xb in zip(*xs_all):
+        assert torch.equal(xa, xb)
+    assert len({o["iters"] for o in outs[0]}) > 1
