@@ -292,6 +292,7 @@ struct ras_batch {
     long long Ntot = 0;
     int nch = 0, nbox = 0, qgrid = 0;       // chunks; boxes in the work queue; persistent CTAs
     int *d_qcount = nullptr;                 // work counter of the batched subdomain solves
+    FactorParams *d_fp = nullptr;            // [n] the reservoirs' factorisation parameters
     std::vector<int> ch0, chn;               // per reservoir: first chunk, chunks
     int prec = 32, block = 0;
     size_t smem = 0;
@@ -331,7 +332,7 @@ static void batch_free(ras_batch *B) {
     if (!B) return;
     coarse_batch_free(B->cb);
     dfree(B->d_ops); dfree(B->d_opsM); dfree(B->t); dfree(B->d_ch); dfree(B->d_off); dfree(B->d_ch0); dfree(B->d_chn); dfree(B->d_kk);
-    dfree(B->d_act); dfree(B->d_ap); dfree(B->d_box_inst); dfree(B->d_box_local); dfree(B->d_qcount);
+    dfree(B->d_act); dfree(B->d_ap); dfree(B->d_box_inst); dfree(B->d_box_local); dfree(B->d_qcount); dfree(B->d_fp);
     dfree(B->partials); dfree(B->out); dfree(B->d_y); dfree(B->d_beta);
     if (B->h_out) cudaFreeHost(B->h_out);
     dfree(B->V); dfree(B->Z); dfree(B->w); dfree(B->r); dfree(B->b); dfree(B->x); dfree(B->tmp);
@@ -676,42 +677,54 @@ static int b_norms_of(ras_batch *B, const std::vector<const double *> &vecs, con
     return b_norms(B, B->tmp, res, st);
 }
 
-// ras_factor of the live reservoirs on their current Jacobians. Two-level batches:
-// per reservoir the operator copy, the subdomain ILU(0) and the Galerkin coarse
-// operator with its blocks, then all block eliminations in one cooperative launch,
-// then each reservoir's checks (the steps of precond_factor).
+// ras_factor of the live reservoirs on their current Jacobians: the subdomain
+// ILU(0) factorisations of all of them in one launch (a CTA per (reservoir, box)).
+// Two-level batches also take, per reservoir, the operator copy (the V-cycle's
+// operator) and the Galerkin coarse operator with its blocks, then all block
+// eliminations in a few cooperative launches; then each reservoir's checks (the
+// steps of precond_factor).
 static int b_factor(ras_batch *B, const std::vector<int> &cur, const std::vector<unsigned char> &live,
                     cudaStream_t st) {
     const int n = B->n;
-    if (!B->cb) {
-        for (int i = 0; i < n; ++i) {
-            if (!live[i]) continue;
-            ras_stencil Js;
-            for (int s = 0; s < 7; ++s) Js.c[s] = B->P[i]->nJ[cur[i]][s];
-            RAS_TRY(precond_factor(B->pc[i], &Js, st));
-        }
-        return RAS_OK;
-    }
+    std::vector<FactorParams> fp(n);
+    int fblock = 32;
+    size_t fsmem = 0;
     for (int i = 0; i < n; ++i) {
-        if (!live[i]) continue;
         ras_precond *pc = B->pc[i];
         const ras_problem *P = B->P[i];
         Stencil7 A;
-        for (int s = 0; s < 7; ++s) {
-            A.c[s] = P->nJ[cur[i]][s];
-            RAS_CK(cudaMemcpyAsync(pc->Acopy[s], A.c[s], (size_t)P->N * sizeof(double), cudaMemcpyDeviceToDevice, st));
-            pc->A.c[s] = pc->Acopy[s];
+        for (int s = 0; s < 7; ++s) A.c[s] = P->nJ[cur[i]][s];
+        if (live[i] && B->twolevel) {
+            for (int s = 0; s < 7; ++s) {
+                RAS_CK(cudaMemcpyAsync(pc->Acopy[s], A.c[s], (size_t)P->N * sizeof(double),
+                                       cudaMemcpyDeviceToDevice, st));
+                pc->A.c[s] = pc->Acopy[s];
+                A.c[s] = pc->Acopy[s];
+            }
         }
-        RAS_TRY(ras1_factor(pc->fine, A, st));
-        RAS_TRY(coarse_factor_prepare(pc->coarse, A, st));
+        ras1_factor_params(pc->fine, A, fp[i]);
+        fblock = std::max(fblock, std::min(pc->fine.block, 256));
+        fsmem = std::max(fsmem, pc->fine.smem_factor);
     }
+    RAS_CK(cudaMemcpyAsync(B->d_fp, fp.data(), n * sizeof(FactorParams), cudaMemcpyHostToDevice, st));
     B->act = live;
     RAS_TRY(upload_mask(B, st));
-    RAS_TRY(coarse_factor_batch(B->cb, B->d_act, st));
+    RAS_TRY(ras1_factor_batch(B->d_fp, B->d_box_inst, B->d_box_local, B->d_act, B->nbox, B->prec, fblock, fsmem,
+                              st));
+    if (B->twolevel) {
+        for (int i = 0; i < n; ++i)
+            if (live[i]) RAS_TRY(coarse_factor_prepare(B->pc[i]->coarse, B->pc[i]->A, st));
+        if (B->cb) {
+            RAS_TRY(coarse_factor_batch(B->cb, B->d_act, st));
+        } else {
+            for (int i = 0; i < n; ++i)
+                if (live[i]) RAS_TRY(coarse_factor_blocks(B->pc[i]->coarse, st));
+        }
+    }
     for (int i = 0; i < n; ++i) {
         if (!live[i]) continue;
         RAS_TRY(ras1_check(B->pc[i]->fine, st));
-        RAS_TRY(coarse_check(B->pc[i]->coarse, st));
+        if (B->twolevel) RAS_TRY(coarse_check(B->pc[i]->coarse, st));
     }
     return RAS_OK;
 }
@@ -913,7 +926,7 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
         (rc = dalloc(&B->d_ch, ch.size())) || (rc = dalloc(&B->d_off, n)) ||
         (rc = dalloc(&B->d_ch0, n)) || (rc = dalloc(&B->d_chn, n)) || (rc = dalloc(&B->d_kk, n)) ||
         (rc = dalloc(&B->d_act, n)) || (rc = dalloc(&B->d_ap, n)) || (rc = dalloc(&B->d_box_inst, box_inst.size())) ||
-        (rc = dalloc(&B->d_box_local, box_local.size())) || (rc = dalloc(&B->d_qcount, 1)) ||
+        (rc = dalloc(&B->d_box_local, box_local.size())) || (rc = dalloc(&B->d_qcount, 1)) || (rc = dalloc(&B->d_fp, n)) ||
         (rc = dalloc(&B->partials, (size_t)(MAX_MDOT + 1) * B->nch)) || (rc = dalloc(&B->out, (size_t)n * OST)) ||
         (rc = dalloc(&B->d_y, (size_t)n * MAX_MDOT)) || (rc = dalloc(&B->d_beta, n)) || (rc = dalloc(&B->w, Nt)) ||
         (rc = dalloc(&B->r, Nt)) || (rc = dalloc(&B->b, Nt)) || (rc = dalloc(&B->x, Nt)) || (rc = dalloc(&B->tmp, Nt)))

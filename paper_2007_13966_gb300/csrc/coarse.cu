@@ -1855,8 +1855,17 @@ static FacArgs<AT> fac_args(Coarse *c, GridBar *bar) {
 }
 
 template <typename AT>
+static int eliminate_t(Coarse *c, cudaStream_t st);
+
+template <typename AT>
 static int factor_blocks_t(Coarse *c, cudaStream_t st) {
     RAS_TRY(assemble_blocks_t<AT>(c, st));
+    return eliminate_t<AT>(c, st);
+}
+
+// the block elimination of the assembled blocks (one cooperative launch)
+template <typename AT>
+static int eliminate_t(Coarse *c, cudaStream_t st) {
     RAS_TRY(reset_bar(c, st));
     FacArgs<AT> fa = fac_args<AT>(c, c->d_bar);
     int use_tc = c->use_tc;
@@ -1894,6 +1903,10 @@ static int prepare_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
     k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, (AT *)c->Ac);
     RAS_LAUNCHED();
     return assemble_blocks_t<AT>(c, st);
+}
+
+int coarse_factor_blocks(Coarse *c, cudaStream_t st) {
+    return c->prec == 64 ? eliminate_t<double>(c, st) : eliminate_t<float>(c, st);
 }
 
 int coarse_factor_prepare(Coarse *c, const Stencil7 &A, cudaStream_t st) {

@@ -35,6 +35,8 @@ int coarse_correct_batch(CoarseBatch *cb, const long long *d_off, const unsigned
 // then the block eliminations of several handles in one cooperative launch
 // (handles off in `active` skip it); coarse_check per handle afterwards.
 int coarse_factor_prepare(Coarse *c, const Stencil7 &A, cudaStream_t st);
+// the block elimination of blocks assembled by coarse_factor_prepare
+int coarse_factor_blocks(Coarse *c, cudaStream_t st);
 int coarse_factor_batch(CoarseBatch *cb, const unsigned char *d_active, cudaStream_t st);
 
 // grid transfer to the next coarser level (linear interpolation P, R = P^T)

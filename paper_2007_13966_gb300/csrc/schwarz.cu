@@ -587,24 +587,15 @@ __global__ void __launch_bounds__(256) k_ras_sum(SumParams P) {
     }
 }
 
-struct FactorParams {
-    const SubInfo *subs;
-    const ShapeInfo *shapes;
-    const int *lvl;
-    const unsigned *cells;
-    Stencil7 A;
-    void *fwd, *bwd;
-    int nx, ny, nz;
-    int *err;
-};
 
 // ILU(0) of A_i in natural order: only the diagonal changes,
 // d_n = a_nn - sum_{m<n neighbour} (a_nm / d_m) a_mn   (m: -z, -y, -x).
+// One CTA per box (box `box` of the handle described by P).
 template <int PREC>
-__global__ void __launch_bounds__(512) k_ras_factor(FactorParams P) {
+__device__ __forceinline__ void ras_factor_box(const FactorParams &P, int box) {
     extern __shared__ __align__(16) unsigned char smem[];
     double *D = reinterpret_cast<double *>(smem);
-    const SubInfo si = P.subs[blockIdx.x];
+    const SubInfo si = P.subs[box];
     const ShapeInfo sh = P.shapes[si.shape];
     const int *lvl = P.lvl + sh.lvl_off;
     const unsigned *cells = P.cells + sh.cell_off;
@@ -644,6 +635,23 @@ __global__ void __launch_bounds__(512) k_ras_factor(FactorParams P) {
     }
 }
 
+template <int PREC>
+__global__ void __launch_bounds__(512) k_ras_factor(FactorParams P) {
+    ras_factor_box<PREC>(P, blockIdx.x);
+}
+
+// The subdomain ILU(0) factorisations of several handles in one launch: CTA b
+// factors box box_local[b] of handle box_inst[b] (CTAs of inactive handles return).
+template <int PREC>
+__global__ void __launch_bounds__(512) k_ras_factor_batch(const FactorParams *__restrict__ inst,
+                                                          const int *__restrict__ box_inst,
+                                                          const int *__restrict__ box_local,
+                                                          const unsigned char *__restrict__ active) {
+    const int h = box_inst[blockIdx.x];
+    if (!active[h]) return;
+    ras_factor_box<PREC>(inst[h], box_local[blockIdx.x]);
+}
+
 // ---------------------------------------------------------------------------
 // host set-up
 // ---------------------------------------------------------------------------
@@ -662,8 +670,10 @@ template <int PREC, int NBUF>
 static int set_apply_attr(size_t) {
     RAS_CK(cudaFuncSetAttribute(k_ras_apply<PREC, NBUF>,
                                 cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
-    RAS_CK(cudaFuncSetAttribute(k_ras_apply_batch<PREC, NBUF>,
-                                cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_OPTIN));
+    cudaFuncAttributes fa{};   // the persistent batch kernel has a little static shared memory
+    RAS_CK(cudaFuncGetAttributes(&fa, k_ras_apply_batch<PREC, NBUF>));
+    RAS_CK(cudaFuncSetAttribute(k_ras_apply_batch<PREC, NBUF>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_OPTIN - (int)fa.sharedSizeBytes));
     return RAS_OK;
 }
 template <int PREC>
@@ -674,6 +684,8 @@ static int set_pipe_attr() {
 template <int PREC>
 static int set_factor_attr(size_t) {
     RAS_CK(cudaFuncSetAttribute(k_ras_factor<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                SMEM_OPTIN));
+    RAS_CK(cudaFuncSetAttribute(k_ras_factor_batch<PREC>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                 SMEM_OPTIN));
     return RAS_OK;
 }
@@ -990,6 +1002,22 @@ int ras1_factor(Ras1 &R, const Stencil7 &A, cudaStream_t st) {
     if (R.prec == 64) k_ras_factor<64><<<R.nsub, block, R.smem_factor, st>>>(P);
     else if (R.prec == 32) k_ras_factor<32><<<R.nsub, block, R.smem_factor, st>>>(P);
     else k_ras_factor<16><<<R.nsub, block, R.smem_factor, st>>>(P);
+    RAS_LAUNCHED();
+    return RAS_OK;
+}
+
+void ras1_factor_params(const Ras1 &R, const Stencil7 &A, FactorParams &P) {
+    P.subs = R.d_subs; P.shapes = R.d_shapes; P.lvl = R.d_lvl; P.cells = R.d_cells;
+    P.A = A; P.fwd = R.d_fwd; P.bwd = R.d_bwd;
+    P.nx = R.nx; P.ny = R.ny; P.nz = R.nz; P.err = R.d_err;
+}
+
+int ras1_factor_batch(const FactorParams *d_inst, const int *d_box_inst, const int *d_box_local,
+                      const unsigned char *d_active, int nbox, int prec, int block, size_t smem, cudaStream_t st) {
+    if (nbox <= 0) return RAS_OK;
+    if (prec == 64) k_ras_factor_batch<64><<<nbox, block, smem, st>>>(d_inst, d_box_inst, d_box_local, d_active);
+    else if (prec == 32) k_ras_factor_batch<32><<<nbox, block, smem, st>>>(d_inst, d_box_inst, d_box_local, d_active);
+    else k_ras_factor_batch<16><<<nbox, block, smem, st>>>(d_inst, d_box_inst, d_box_local, d_active);
     RAS_LAUNCHED();
     return RAS_OK;
 }

@@ -129,6 +129,23 @@ struct BatchApply {
     int *qcount;                      // device work counter, cleared before each launch
 };
 void ras1_apply_params(const Ras1 &R, ApplyParams &P);
+// parameters of one handle's ILU(0) factorisation kernel on operator A
+struct FactorParams {
+    const SubInfo *subs;
+    const ShapeInfo *shapes;
+    const int *lvl;
+    const unsigned *cells;
+    Stencil7 A;
+    void *fwd, *bwd;
+    int nx, ny, nz;
+    int *err;
+};
+void ras1_factor_params(const Ras1 &R, const Stencil7 &A, FactorParams &P);
+// the ILU(0) factorisations of several handles in one launch: CTA b factors box
+// d_box_local[b] of handle d_box_inst[b] (d_inst: device copies of the handles'
+// parameters); no synchronisation (each handle's ras1_check reads its pivot flag)
+int ras1_factor_batch(const FactorParams *d_inst, const int *d_box_inst, const int *d_box_local,
+                      const unsigned char *d_active, int nbox, int prec, int block, size_t smem, cudaStream_t st);
 // persistent launch of `grid` CTAs over the B.nitems boxes of the work queue
 int ras1_apply_batch(const BatchApply &B, int grid, int prec, int block, size_t smem, cudaStream_t st);
 // CTAs of the batched solve that are co-resident on the device (its persistent grid)
