@@ -316,6 +316,7 @@ struct ras_batch {
     double *d_lastg = nullptr;
     cudaGraphExec_t cycle_exec = nullptr;    // the m Arnoldi steps of a cycle, captured
     int cycle_m = 0;                         // m of the captured cycle
+    long long cycle_polls = 0;               // coarse barrier poll limit captured in it
     long long cycle_launches = 0;            // kernels in it (counted at every replay)
     bool graph_off = false;                  // capture failed or disabled: direct launches
     cudaStream_t gstream = nullptr;          // the graph's own stream (joined to the caller's by events)
@@ -521,7 +522,8 @@ static int b_run_cycle(ras_batch *B, int m, cudaStream_t st) {
         }
     }
     if (!use_graph) return b_cycle(B, m, st);
-    if (!B->cycle_exec || B->cycle_m != m) {
+    const long long polls = B->twolevel ? coarse_barrier_polls() : 0;
+    if (!B->cycle_exec || B->cycle_m != m || B->cycle_polls != polls) {
         if (B->cycle_exec) {
             cudaGraphExecDestroy(B->cycle_exec);
             B->cycle_exec = nullptr;
@@ -546,6 +548,7 @@ static int b_run_cycle(ras_batch *B, int m, cudaStream_t st) {
         }
         cudaGraphDestroy(graph);
         B->cycle_m = m;
+        B->cycle_polls = polls;
         B->cycle_launches = g_launches.load() - n0;
         g_launches.store(n0);
     }

@@ -1622,6 +1622,8 @@ static long long barrier_polls() {
     return polls;
 }
 
+long long coarse_barrier_polls() { return barrier_polls(); }
+
 static int reset_bar(Coarse *c, cudaStream_t st) {
     k_reset_bars<<<1, 32, 0, st>>>(c->d_bar, 1, barrier_polls());
     RAS_LAUNCHED();

@@ -16,6 +16,10 @@ int coarse_factor(Coarse *c, const Stencil7 &A, cudaStream_t st);
 int coarse_factor125(Coarse *c, const double *Af, cudaStream_t st);
 // reads and clears the coarse pivot / layout flag (synchronises)
 int coarse_check(Coarse *c, cudaStream_t st);
+// The poll limit the coarse kernels' grid barriers take at their next launch
+// (RAS_BARRIER_POLLS; 0: the default). A captured launch keeps the value it was
+// captured with, so a graph holding one is captured again when this changes.
+long long coarse_barrier_polls();
 // bytes of the dense block factors read by one coarse solve
 double coarse_bytes(const Coarse *c);
 // ec = A_c^{-1} R t, then z (+)= P ec  (accumulate selects += )
