@@ -561,13 +561,32 @@ static int b_run_cycle(ras_batch *B, int m, cudaStream_t st) {
     return RAS_OK;
 }
 
+// Reads and clears the deferred error words of every selected reservoir (the
+// fine factors' and the coarse level's after a factorisation, the
+// preconditioner's after a solve), so that an error of one launch is not left
+// set for a later call; returns the first error found.
+static int drain_checks(ras_batch *B, const std::vector<unsigned char> &sel, bool factor, cudaStream_t st) {
+    int first = RAS_OK;
+    auto keep = [&](int rc) { if (rc != RAS_OK && first == RAS_OK) first = rc; };
+    for (int i = 0; i < B->n; ++i) {
+        if (!sel[i]) continue;
+        if (factor) {
+            keep(ras1_check(B->pc[i]->fine, st));
+            if (B->twolevel) keep(coarse_check(B->pc[i]->coarse, st));
+        } else {
+            keep(precond_check(B->pc[i], st));
+        }
+    }
+    return first;
+}
+
 // Batched right-preconditioned FGMRES(m) (the steps of the single-reservoir
 // routine, per reservoir) on B->b -> B->x for the reservoirs with want[i];
 // operators in B->ops (uploaded by the caller). The Arnoldi scalars of every
 // reservoir are updated on the device, so a restart cycle runs without the host
 // (one CUDA graph); the host reads the cycle's outcome once per restart.
-static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const ras_krylov_opts &o,
-                   ras_krylov_stats *stats, cudaStream_t st) {
+static int bfgmres_run(ras_batch *B, const std::vector<unsigned char> &want, const ras_krylov_opts &o,
+                       ras_krylov_stats *stats, cudaStream_t st) {
     const int n = B->n, m = o.restart;
     if (m < 1 || m > MAX_MDOT - 1 || o.maxit < 1) return RAS_EINVAL;
     RAS_TRY(ensure_krylov_b(B, m));
@@ -645,8 +664,7 @@ static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const r
             if (!conv[i] && it[i] < o.maxit) push(i, beta[i]);
         }
     }
-    for (int i = 0; i < n; ++i)
-        if (want[i]) RAS_TRY(precond_check(B->pc[i], st));
+    RAS_TRY(drain_checks(B, want, false, st));
     int status = RAS_OK;
     for (int i = 0; i < n; ++i) {
         if (!want[i]) continue;
@@ -659,6 +677,17 @@ static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const r
         if (!conv[i]) status = RAS_GMRES_MAXIT;
     }
     return status;
+}
+
+// The batched FGMRES; on an early error return (a non-finite value after a coarse
+// solve whose barrier wait ran out, say) the deferred error words are still read
+// and cleared, and the device error, which explains the other, is reported.
+static int bfgmres(ras_batch *B, const std::vector<unsigned char> &want, const ras_krylov_opts &o,
+                   ras_krylov_stats *stats, cudaStream_t st) {
+    const int rc = bfgmres_run(B, want, o, stats, st);
+    if (rc >= 0) return rc;
+    const int d = drain_checks(B, want, false, st);
+    return d != RAS_OK ? d : rc;
 }
 
 static void set_ops(ras_batch *B, int i, double *const *J) {
@@ -724,12 +753,7 @@ static int b_factor(ras_batch *B, const std::vector<int> &cur, const std::vector
                 if (live[i]) RAS_TRY(coarse_factor_blocks(B->pc[i]->coarse, st));
         }
     }
-    for (int i = 0; i < n; ++i) {
-        if (!live[i]) continue;
-        RAS_TRY(ras1_check(B->pc[i]->fine, st));
-        if (B->twolevel) RAS_TRY(coarse_check(B->pc[i]->coarse, st));
-    }
-    return RAS_OK;
+    return drain_checks(B, live, true, st);
 }
 
 // One implicit step of every reservoir (the single-reservoir Newton driver's

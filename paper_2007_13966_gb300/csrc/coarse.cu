@@ -41,13 +41,10 @@ constexpr int FWAVE_CTAS = 16;   // least CTAs per handle in a batched block eli
 constexpr int ERR_PIVOT = 1, ERR_ELL = 2, ERR_TIMEOUT = 7;
 constexpr long long BAR_POLLS = 1LL << 22;   // ~1-2 s of polling before a barrier gives up
 
-// arrival counter and release word on separate 128-byte lines (the waiting CTAs
-// poll `gen`, not the line the arrivals add to)
+// arrival counter on a 128-byte line of its own, and the launch's poll limit
 struct GridBar {
     unsigned count;
     unsigned pad0[31];
-    unsigned gen;
-    unsigned pad1[31];
     long long polls;   // poll limit of this launch (<= 0: BAR_POLLS)
 };
 
@@ -80,6 +77,11 @@ struct Coarse {
     int fac_grid = 0, sol_grid = 0;
     int sol_npf = 0;                // rows per warp prefetched by the solve
     int use_tc = 0;                 // FP32 inverses: trailing updates on the tcgen05 tensor cores
+    int cr = 0;                     // cyclic reduction instead of the two-ended elimination
+    int *d_crf = nullptr, *d_crs = nullptr;   // its factorisation and solve schedules
+    void *W = nullptr;              // its dense couplings and products [nslot][T][T]
+    int cr_maxE = 0;                // most blocks it inverts concurrently
+    long long cr_mats = 0;          // T x T matrices one of its solves reads
 };
 
 // ---------------------------------------------------------------------------
@@ -393,6 +395,28 @@ __global__ void k_ell(const AT *__restrict__ Ac, const int *__restrict__ pos,
     }
 }
 
+// Dense copies of the off-diagonal blocks for the first round of the cyclic
+// reduction (edges oriented pivot e -> target e + 1): L(e + 1) = A(e + 1, e) from
+// the row-wise couplings, U(e) = A(e, e + 1) from the column-wise ones. Lc and Uc
+// are [nb][T][T] and zero on entry.
+template <typename AT>
+__global__ void k_cr_couplings(const int *__restrict__ lo_q, const AT *__restrict__ lo_v,
+                               const int *__restrict__ lo_n, const int *__restrict__ up_q,
+                               const AT *__restrict__ up_v, const int *__restrict__ up_n, int T, int nb,
+                               AT *__restrict__ Lc, AT *__restrict__ Uc) {
+    const long long tot = (long long)(nb - 1) * T, bsz = (long long)T * T;
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < tot;
+         p += (long long)gridDim.x * blockDim.x) {
+        const int e = (int)(p / T), r = (int)(p % T);
+        AT *Lr = Lc + (e + 1) * bsz + (long long)r * T;
+        for (int m = 0; m < lo_n[p]; ++m) Lr[lo_q[p * ELLW + m]] = lo_v[p * ELLW + m];
+        for (int m = 0; m < up_n[p]; ++m) {
+            const long long u = (long long)e * ELLW * T + (long long)m * T + r;
+            Uc[e * bsz + (long long)up_q[u] * T + r] = up_v[u];
+        }
+    }
+}
+
 // ---------------------------------------------------------------------------
 // bounded grid barrier (all CTAs are co-resident: cooperative launch)
 // ---------------------------------------------------------------------------
@@ -403,26 +427,24 @@ __device__ __forceinline__ unsigned ld_acquire(const unsigned *p) {
     return v;
 }
 
-__device__ __forceinline__ void st_release(unsigned *p, unsigned v) {
-    asm volatile("st.release.gpu.global.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
-}
-__device__ __forceinline__ unsigned atom_add_acq_rel(unsigned *p, unsigned v) {
-    unsigned old;
-    asm volatile("atom.add.acq_rel.gpu.global.u32 %0, [%1], %2;" : "=r"(old) : "l"(p), "r"(v) : "memory");
-    return old;
+__device__ __forceinline__ void red_add_release(unsigned *p, unsigned v) {
+    asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
 }
 
 // Grid barrier on a monotonically increasing arrival counter: barrier number e
-// (1, 2, ...) of a launch is complete when the counter reaches e * gridDim.x. Each
-// CTA arrives with one atomic add (acquire-release: the CTA whose add completes the
-// count has then acquired every arrival) and that CTA publishes e in `gen`
-// (release); the others poll `gen` (acquire), at most the launch's poll
-// limit. `epoch` is the caller's count of barriers passed (same in every thread);
-// counter and gen are reset to zero before every launch. The error word is read at
-// entry without waiting for it (its value is consulted after the barrier) and every
-// 1024 polls. G: the number of CTAs that take part (default: the grid; a group of
-// co-resident CTAs with a barrier word of its own). Returns false if this or any
-// CTA has flagged an error or the wait ran out (ERR_TIMEOUT is then set).
+// (1, 2, ...) of a launch is complete when the counter reaches e * G. After the
+// CTA's threads meet, one thread adds its arrival with a release reduction (its
+// CTA's earlier writes become visible with it) and polls the counter with acquire
+// loads, at most the launch's poll limit; a second CTA barrier releases the
+// other threads. The counter is reset to zero before every launch. (Measured on
+// GB300 with 304 co-resident CTAs: 1.6 us per barrier, against 2.5 us for an
+// atomic arrival whose last arriver publishes a separate release word between
+// two full fences, and 2.0-2.7 us for two-level arrival trees.) The error word is
+// read at entry without waiting for it (its value is consulted after the
+// barrier) and every 1024 polls. G: the number of CTAs that take part (default:
+// the grid; a group of co-resident CTAs with a barrier word of its own). Returns
+// false if this or any CTA has flagged an error or the wait ran out (ERR_TIMEOUT
+// is then set).
 __device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch, unsigned G = 0) {
     __shared__ int s_ok;
     ++epoch;
@@ -431,19 +453,14 @@ __device__ bool grid_barrier(GridBar *bar, int *err, unsigned &epoch, unsigned G
         const unsigned e0 = *reinterpret_cast<volatile const unsigned *>(err);
         int ok = 1;
         const long long lim = bar->polls > 0 ? bar->polls : BAR_POLLS;
-        __threadfence();
         const unsigned target = epoch * (G ? G : gridDim.x);
-        if (atom_add_acq_rel(&bar->count, 1u) == target - 1) {
-            st_release(&bar->gen, epoch);
-        } else {
-            long long it = 0;
-            while (ld_acquire(&bar->gen) < epoch) {
-                if (++it > lim) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
-                if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
-            }
+        red_add_release(&bar->count, 1u);
+        long long it = 0;
+        while (ld_acquire(&bar->count) < target) {
+            if (++it > lim) { atomicExch(err, ERR_TIMEOUT); ok = 0; break; }
+            if ((it & 1023) == 0 && ld_acquire((const unsigned *)err) != 0) { ok = 0; break; }
         }
         if (e0 != 0) ok = 0;
-        __threadfence();
         s_ok = ok;
     }
     __syncthreads();
@@ -903,6 +920,142 @@ __device__ void tc_pair_update(TcSmem &ts, TcState &st, float *M, int T, int i0,
     __syncthreads();   // the smem overlay and the accumulator are free again
 }
 
+// Out[0 .. nrows) x [0 .. 64) (=, +=) sign (A1 B1 [+ A2 B2]) for FP32 row-major
+// operands with one leading dimension ld: A1 points at its first row and chunk,
+// B1 at its first chunk row and column, the products run over nk1 (nk2) chunks of
+// 64 along k on tcgen05 (M = 128, N = 64, K = 8, the three-term TF32 split of
+// tc_pair_update) and accumulate in tensor memory; the next chunk's global loads
+// are issued before the wait for the current chunk's MMAs. nrows is 64 or 128
+// (rows past it enter as zeros and are not written). All 256 threads; the CTA's
+// shared-memory overlay is free on entry and on return.
+__device__ void tc_gemm_core(TcSmem &ts, TcState &st, float *Out, const float *A1, const float *B1, int nk1,
+                             const float *A2, const float *B2, int nk2, int ld, int nrows, bool acc, float sign,
+                             int *err) {
+    const int tid = threadIdx.x, nch = nk1 + (A2 ? nk2 : 0);
+    const int xr = tid >> 1, xk0 = (tid & 1) * 32;        // A chunk: row, k half
+    const int yk = tid >> 2, yn0 = (tid & 3) * 16;        // B chunk: k, 16 columns
+    float4 vx[8], vy[4];
+    auto load = [&](int ch) {
+        const float *A = ch < nk1 ? A1 : A2, *B = ch < nk1 ? B1 : B2;
+        const int kc = (ch < nk1 ? ch : ch - nk1) * TILE;
+        if (xr < nrows) {
+            const float4 *src = reinterpret_cast<const float4 *>(A + (long long)xr * ld + kc + xk0);
+#pragma unroll
+            for (int q = 0; q < 8; ++q) vx[q] = __ldcg(src + q);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 8; ++q) vx[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
+        const float4 *srcy = reinterpret_cast<const float4 *>(B + (long long)(kc + yk) * ld + yn0);
+#pragma unroll
+        for (int q = 0; q < 4; ++q) vy[q] = __ldcg(srcy + q);
+    };
+    auto wait_mma = [&]() {
+        const unsigned a = (unsigned)__cvta_generic_to_shared(st.mbar), par = st.phase & 1;
+        bool done = false;
+        for (long long it = 0; it < TC_POLLS && !done; ++it) {
+            unsigned ok;
+            asm volatile(
+                "{\n.reg .pred pp;\n"
+                "mbarrier.try_wait.parity.shared::cta.b64 pp, [%1], %2;\n"
+                "selp.u32 %0, 1, 0, pp;\n}\n"
+                : "=r"(ok) : "r"(a), "r"(par) : "memory");
+            done = ok != 0;
+        }
+        if (!done) atomicExch(err, ERR_TIMEOUT);
+        ++st.phase;
+    };
+    load(0);
+    for (int ch = 0; ch < nch; ++ch) {
+        if (ch > 0) wait_mma();                             // the MMAs of the previous chunk are done
+#pragma unroll
+        for (int q = 0; q < 8; ++q) {
+            const float *e = reinterpret_cast<const float *>(&vx[q]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tc_put(ts.xh, ts.xl, tc_off(xr, xk0 + 4 * q + u), e[u]);
+        }
+#pragma unroll
+        for (int q = 0; q < 4; ++q) {
+            const float *e = reinterpret_cast<const float *>(&vy[q]);
+#pragma unroll
+            for (int u = 0; u < 4; ++u) tc_put(ts.yh, ts.yl, tc_off(yn0 + 4 * q + u, yk), e[u]);
+        }
+        asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+        __syncthreads();
+        if (tid == 0) {
+            asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+            const unsigned xh = (unsigned)__cvta_generic_to_shared(ts.xh), xl = (unsigned)__cvta_generic_to_shared(ts.xl);
+            const unsigned yh = (unsigned)__cvta_generic_to_shared(ts.yh), yl = (unsigned)__cvta_generic_to_shared(ts.yl);
+#pragma unroll
+            for (int s = 0; s < 8; ++s) {
+                const unsigned o = s * 2 * TC_LBO;
+                const unsigned long long d[3][2] = {{tc_desc(xl + o), tc_desc(yh + o)},
+                                                    {tc_desc(xh + o), tc_desc(yl + o)},
+                                                    {tc_desc(xh + o), tc_desc(yh + o)}};
+#pragma unroll
+                for (int t3 = 0; t3 < 3; ++t3) {
+                    const unsigned accum = (ch > 0 || s > 0 || t3 > 0) ? 1u : 0u;
+                    asm volatile(
+                        "{\n.reg .pred pp;\n"
+                        "setp.ne.b32 pp, %4, 0;\n"
+                        "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, pp;\n}\n"
+                        ::"r"(st.tmem), "l"(d[t3][0]), "l"(d[t3][1]), "r"(TC_IDESC), "r"(accum) : "memory");
+                }
+            }
+            asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];"
+                         ::"r"((unsigned)__cvta_generic_to_shared(st.mbar)) : "memory");
+        }
+        if (ch + 1 < nch) load(ch + 1);
+    }
+    wait_mma();
+    asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+    {   // warp w: rows 32 (w % 4) + lane, columns 32 (w / 4) .. + 31
+        const int w = tid >> 5, lane = tid & 31, q = w & 3, h = w >> 2;
+        unsigned r[32];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
+            "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
+            "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
+            : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+              "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+              "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
+              "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
+              "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+            : "r"(st.tmem + ((unsigned)(32 * q) << 16) + 32u * h));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        const int row = 32 * q + lane;
+        if (row < nrows) {
+            float *out = Out + (long long)row * ld + 32 * h;
+            float4 prev[8];
+#pragma unroll
+            for (int u = 0; u < 8; ++u)
+                prev[u] = acc ? __ldcg(reinterpret_cast<const float4 *>(out) + u) : make_float4(0.f, 0.f, 0.f, 0.f);
+#pragma unroll
+            for (int u = 0; u < 8; ++u) {
+                float4 o = prev[u];
+                o.x += sign * __uint_as_float(r[4 * u]);
+                o.y += sign * __uint_as_float(r[4 * u + 1]);
+                o.z += sign * __uint_as_float(r[4 * u + 2]);
+                o.w += sign * __uint_as_float(r[4 * u + 3]);
+                reinterpret_cast<float4 *>(out)[u] = o;
+            }
+        }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+    __syncthreads();   // the smem overlay and the accumulator are free again
+}
+
+// Out(tile rows 2 pr, 2 pr + 1, the second only if it exists; tile column j)
+// (=, +=) sign (A1 B1 [+ A2 B2]) for T x T blocks, over the full inner dimension.
+__device__ __forceinline__ void tc_gemm_pair(TcSmem &ts, TcState &st, float *Out, int T, int pr, int j,
+                                             const float *A1, const float *B1, const float *A2,
+                                             const float *B2, bool acc, float sign, int *err) {
+    const int nk = T / TILE;
+    const long long r0 = (long long)2 * pr * TILE * T;
+    tc_gemm_core(ts, st, Out + r0 + j * TILE, A1 + r0, B1 + j * TILE, nk, A2 ? A2 + r0 : nullptr,
+                 B2 ? B2 + j * TILE : nullptr, nk, T, 2 * pr + 1 < nk ? 128 : 64, acc, sign, err);
+}
+
 // ---------------------------------------------------------------------------
 // cooperative factorisation: block Thomas with in-place Gauss-Jordan inverses
 // ---------------------------------------------------------------------------
@@ -916,6 +1069,9 @@ struct FacArgs {
     int T, nt, nb, mid;
     GridBar *bar;
     int *err;
+    int cr;            // cyclic reduction (FP32, tensor cores) instead of the two-ended elimination
+    const int *crs;    // its schedule
+    AT *W;             // its dense couplings and products, [slot - nb][T][T]
 };
 
 // Out[r0+i][c] (=, -=) sum_e M[r0+i][uq[c][e]] uv[c][e] for a chunk of FROWS rows.
@@ -1112,7 +1268,17 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
             }
         };
         auto special = [&](int c) {
-            update(c, dpiv);
+            bool done = false;
+            if constexpr (sizeof(AT) == 4) {
+                if (tcs.on) {   // tile (p + 1, p + 1) -= D_{p+1,p} D_{p,p+1}, one MMA group
+                    AT *Dk = a.D + blk[c] * bsz;
+                    const long long r1 = (long long)(p + 1) * TILE * T, r0 = (long long)p * TILE * T;
+                    tc_gemm_core(*reinterpret_cast<TcSmem *>(&ts), tcs, Dk + r1 + (p + 1) * TILE, Dk + r1 + p * TILE,
+                                 Dk + r0 + (p + 1) * TILE, 1, nullptr, nullptr, 0, T, TILE, true, -1.0f, a.err);
+                    done = true;
+                }
+            }
+            if (!done) update(c, dpiv);
             __syncthreads();
             tile_invert(ts, a.D + blk[c] * bsz, T, p + 1, a.err);
         };
@@ -1165,8 +1331,86 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
 // last.
 // The factorisation of one handle by a group of G co-resident CTAs (b: this CTA's
 // index in the group).
+// ---------------------------------------------------------------------------
+// cyclic reduction of the block tridiagonal system (FP32 on the tensor cores)
+// ---------------------------------------------------------------------------
+//
+// Round r takes the active blocks L_r (initially all, in order) and eliminates
+// those at odd positions; their inverses are computed concurrently (the same
+// in-place Gauss-Jordan as above, one chain per block). With L(k), U(k) the
+// couplings of active block k to its previous / next active block (the
+// off-diagonal blocks of the operator in the first round), every kept block e
+// between eliminated neighbours om, op receives
+//     X_e = L(e) Inv_om,  Y_e = U(e) Inv_op,
+//     D_e -= X_e U(om) + Y_e L(op),  L(e) <- -X_e L(om),  U(e) <- -Y_e U(op),
+// and every eliminated block o keeps V_o = Inv_o L(o), W_o = Inv_o U(o). The last
+// active block is inverted at the end. Solve: per round, x_o = Inv_o g_o and
+// g_e -= X_e g_om + Y_e g_op; x_last = Inv_last g_last; then back through the
+// rounds, x_o -= V_o x_prev + W_o x_next. The depth is ceil(log2(nb)) + 1 block
+// inversions instead of about nb / 2 + 1, at the price of dense T x T products
+// (all of them on tcgen05), which is why only the FP32 form with the tensor path
+// takes it. Every product is one task of the schedule, computed as items of a
+// 128-row pair of tiles and a tile column.
+//
+// Schedule (ints): nround, last; per round: nE, E[nE]; then two phases of
+// products, each ntask followed by ntask records CrTask. A block slot s < nb is
+// diagonal block s (D, inverted in place when eliminated), s >= nb is
+// W + (s - nb) T^2: the dense couplings L(k) at slot nb + k, U(k) at 2 nb + k,
+// then the products.
+struct CrTask {
+    int out, acc, sign, a1, b1, a2, b2, pad;   // Out (=, +=) sign (A1 B1 [+ A2 B2]); a2 < 0: one term
+};
+
+template <typename AT>
+__device__ __forceinline__ AT *cr_slot(const FacArgs<AT> &a, int s) {
+    const long long bsz = (long long)a.T * a.T;
+    return s < a.nb ? a.D + s * bsz : a.W + (long long)(s - a.nb) * bsz;
+}
+
+template <typename AT>
+__device__ void cr_factor_body(const FacArgs<AT> &a, int b, int G, TcState &tcs) {
+    if constexpr (sizeof(AT) == 4) {
+        extern __shared__ __align__(16) unsigned char smem_raw[];
+        TileSmem<AT> &ts = *reinterpret_cast<TileSmem<AT> *>(smem_raw);
+        TcSmem &tsm = *reinterpret_cast<TcSmem *>(smem_raw);
+        const int nt = a.nt, per = ((nt + 1) / 2) * nt;   // items of one product
+        if (!tcs.on) {                     // the reduction needs the tensor path
+            if (threadIdx.x == 0) atomicExch(a.err, ERR_ELL);
+            return;
+        }
+        const int *s = a.crs;
+        const int nround = s[0];
+        const int *last = s + 1;
+        s += 2;
+        unsigned epoch = 0;
+        for (int r = 0; r < nround; ++r) {
+            const int nE = s[0];
+            if (!invert_blocks(a, ts, s + 1, nE, epoch, b, G, tcs)) return;
+            s += 1 + nE;
+            for (int ph = 0; ph < 2; ++ph) {
+                const int n = s[0];
+                const CrTask *tk = reinterpret_cast<const CrTask *>(s + 1);
+                for (int it = b; it < n * per; it += G) {
+                    const CrTask t = tk[it / per];
+                    const int q = it % per, pr = q / nt, j = q % nt;
+                    tc_gemm_pair(tsm, tcs, cr_slot(a, t.out), a.T, pr, j, cr_slot(a, t.a1), cr_slot(a, t.b1),
+                                 t.a2 >= 0 ? cr_slot(a, t.a2) : nullptr, t.a2 >= 0 ? cr_slot(a, t.b2) : nullptr,
+                                 t.acc != 0, (float)t.sign, a.err);
+                }
+                s += 1 + 8 * n;
+                if (!grid_barrier(a.bar, a.err, epoch, G)) return;
+            }
+        }
+        invert_blocks(a, ts, last, 1, epoch, b, G, tcs);
+    }
+}
+
 template <typename AT>
 __device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, int G, TcState &tcs) {
+    if (a.cr) {
+        cr_factor_body(a, b, G, tcs);
+        return;
+    }
     extern __shared__ __align__(16) unsigned char smem_raw[];
     TileSmem<AT> &ts = *reinterpret_cast<TileSmem<AT> *>(smem_raw);
     AT *rows = reinterpret_cast<AT *>(smem_raw);
@@ -1264,12 +1508,14 @@ __global__ void __launch_bounds__(256) k_coarse_factor_batch(const FacArgs<AT> *
                                                              const unsigned char *active) {
     const int h = cta_inst[blockIdx.x];
     if (!active[h]) return;
+    // the two-ended eliminations keep the CUDA-core products; the cyclic
+    // reductions take the tensor path
+    __shared__ unsigned tmem_slot;
+    __shared__ unsigned long long mbar;
     TcState tcs;
-    tcs.on = false;   // the batched eliminations keep the CUDA-core products
-    tcs.tmem = 0;
-    tcs.mbar = nullptr;
-    tcs.phase = 0;
+    tc_begin<AT>(tcs, &tmem_slot, &mbar, args[h].cr != 0);
     coarse_factor_body(args[h], blockIdx.x - first[h], size[h], tcs);
+    tc_end<AT>(tcs);
 }
 
 // ---------------------------------------------------------------------------
@@ -1290,6 +1536,9 @@ struct SolArgs {
     GridBar *bar;
     int *err;
     int npf;   // matrix rows per warp prefetched into shared memory per stage (0..2)
+    int cr;            // cyclic reduction: the block sweeps follow its solve schedule
+    const int *crs;
+    const AT *W;
 };
 
 __device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
@@ -1369,6 +1618,42 @@ __device__ void stage_vector(const AT *xsrc, AT *xs, int T) {
 
 // The coarse correction of one handle by a group of ng co-resident CTAs (b: this
 // CTA's index in the group); t: fine residual, z: fine correction.
+// Block sweeps of the cyclic reduction: phases separated by grid barriers, each a
+// list of tasks out (=, -=) M1 v1 [+ M2 v2] over the T rows of a block, one warp
+// per row (matrix rows from HBM, vectors through L2). Schedule: nphase, then per
+// phase ntask and ntask records {out, 0, sub, m1, v1, m2, v2, 0}; a vector is
+// (0 for g, 1 for x) << 16 | block, a matrix a block slot as in the factorisation
+// (m2 < 0: one term).
+template <typename AT>
+__device__ bool cr_sweeps(const SolArgs<AT> &a, int b, int ng, unsigned &epoch) {
+    const int T = a.G.T, nb = a.G.nb, lane = threadIdx.x & 31, wpb = blockDim.x / 32;
+    const int wg = b * wpb + (threadIdx.x >> 5), nwt = ng * wpb;
+    const long long bsz = (long long)T * T;
+    auto mat = [&](int q) -> const AT * { return q < nb ? a.E + q * bsz : a.W + (long long)(q - nb) * bsz; };
+    auto vec = [&](int v) -> AT * { return ((v >> 16) ? a.x : a.g) + (long long)(v & 0xffff) * T; };
+    const int *s = a.crs;
+    const int nph = *s++;
+    for (int ph = 0; ph < nph; ++ph) {
+        const int n = *s++;
+        const int *tk = s;
+        s += 8 * n;
+        for (int r = wg; r < n * T; r += nwt) {
+            const int *t = tk + 8 * (r / T);
+            const int i = r % T;
+            AT acc = 0;
+#pragma unroll 1
+            for (int m = 0; m < 2 && t[3 + 2 * m] >= 0; ++m)
+                acc += row_dot<AT, true>(mat(t[3 + 2 * m]) + (long long)i * T, vec(t[4 + 2 * m]), T, lane);
+            if (lane == 0) {
+                AT *y = vec(t[0]) + i;
+                *y = t[2] ? __ldcg(y) - acc : acc;
+            }
+        }
+        if (!grid_barrier(a.bar, a.err, epoch, ng)) return false;
+    }
+    return true;
+}
+
 template <typename AT>
 __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, int ng, const double *t, double *z) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1461,7 +1746,8 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
         a.g[a.pos[I]] = acc;
     }
     if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
-    for (int st = 0; st < nstage; ++st) {
+    if (a.cr && !cr_sweeps(a, b, ng, epoch)) { cp_async_wait_all(); return; }
+    for (int st = 0; st < (a.cr ? 0 : nstage); ++st) {
         int edg[2];
         const int ne = edges_of(st, edg);
         if (st < nsteps)
@@ -1603,7 +1889,7 @@ static void interp_axis(int n, int r, std::vector<int> &ia, std::vector<int> &ib
     }
 }
 
-// Zero the grid barriers of a cooperative launch (counter and release word of n
+// Zero the grid barriers of a cooperative launch (the arrival counters of n
 // barrier words) and set their poll limit, by a kernel rather than a host copy so
 // that the reset can be captured in a graph. RAS_BARRIER_POLLS (environment, read
 // at every launch) shortens the bounded wait, so that a test can make it run out
@@ -1611,7 +1897,6 @@ static void interp_axis(int n, int r, std::vector<int> &ia, std::vector<int> &ib
 __global__ void k_reset_bars(GridBar *bars, int n, long long polls) {
     for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         bars[i].count = 0;
-        bars[i].gen = 0;
         bars[i].polls = polls;
     }
 }
@@ -1648,6 +1933,94 @@ static CGeom geom_of(const Coarse *c) {
     return G;
 }
 
+// Schedules of the cyclic reduction of nb blocks (layout at cr_factor_body and
+// cr_sweeps).
+struct CrPlan {
+    std::vector<int> fac, sol;
+    int nslot = 0;        // W slots: the dense couplings (2 nb) and the products
+    int maxE = 1;         // most blocks inverted concurrently
+    long long mats = 0;   // T x T matrices one solve reads
+};
+static void cr_plan(int nb, CrPlan &P) {
+    const int LC = nb, UC = 2 * nb, GV = 0, XV = 1 << 16;
+    int next = 3 * nb;
+    std::vector<int> L(nb);
+    std::iota(L.begin(), L.end(), 0);
+    P.fac = {0, 0};
+    std::vector<std::vector<int>> fwd, bwd;
+    auto task = [](std::vector<int> &v, int out, int acc, int sign, int a1, int b1, int a2, int b2) {
+        v.insert(v.end(), {out, acc, sign, a1, b1, a2, b2, 0});
+    };
+    auto stask = [&](std::vector<int> &v, int out, int sub, int m1, int v1, int m2, int v2) {
+        v.insert(v.end(), {out, 0, sub, m1, v1, m2, v2, 0});
+        P.mats += m2 >= 0 ? 2 : 1;
+    };
+    int nround = 0;
+    while (L.size() > 1) {
+        const int n = (int)L.size();
+        std::vector<int> E, K, f2, f3, sf, sb;
+        for (int i = 1; i < n; i += 2) E.push_back(L[i]);
+        P.maxE = std::max(P.maxE, (int)E.size());
+        for (int i = 0; i < n; ++i) {
+            const int k = L[i];
+            const int prev = i > 0 ? L[i - 1] : -1, nxt = i + 1 < n ? L[i + 1] : -1;
+            if (i & 1) {                       // eliminated: V = Inv L(k), W = Inv U(k)
+                const int vs = next++;
+                task(f2, vs, 0, 1, k, LC + k, -1, -1);
+                int ws = -1;
+                if (nxt >= 0) {
+                    ws = next++;
+                    task(f2, ws, 0, 1, k, UC + k, -1, -1);
+                }
+                stask(sf, XV | k, 0, k, GV | k, -1, 0);                            // x_k = Inv g_k
+                stask(sb, XV | k, 1, vs, XV | prev, ws, ws >= 0 ? (XV | nxt) : 0);  // x_k -= V x_prev + W x_next
+            } else {                           // kept: X = L(k) Inv_prev, Y = U(k) Inv_next
+                int xs = -1, ys = -1;
+                if (prev >= 0) {
+                    xs = next++;
+                    task(f2, xs, 0, 1, LC + k, prev, -1, -1);
+                }
+                if (nxt >= 0) {
+                    ys = next++;
+                    task(f2, ys, 0, 1, UC + k, nxt, -1, -1);
+                }
+                if (xs >= 0 || ys >= 0) {      // D_k -= X U(prev) + Y L(next); g_k -= X g_prev + Y g_next
+                    const int a1 = xs >= 0 ? xs : ys, b1 = xs >= 0 ? UC + prev : LC + nxt;
+                    const int a2 = xs >= 0 && ys >= 0 ? ys : -1, b2 = a2 >= 0 ? LC + nxt : -1;
+                    task(f3, k, 1, -1, a1, b1, a2, b2);
+                    stask(sf, GV | k, 1, a1, GV | (xs >= 0 ? prev : nxt), a2, a2 >= 0 ? (GV | nxt) : 0);
+                }
+                if (xs >= 0 && i >= 2) task(f3, LC + k, 0, -1, xs, LC + prev, -1, -1);    // L(k) <- -X L(prev)
+                if (ys >= 0 && i + 2 < n) task(f3, UC + k, 0, -1, ys, UC + nxt, -1, -1);  // U(k) <- -Y U(next)
+                K.push_back(k);
+            }
+        }
+        P.fac.push_back((int)E.size());
+        P.fac.insert(P.fac.end(), E.begin(), E.end());
+        P.fac.push_back((int)f2.size() / 8);
+        P.fac.insert(P.fac.end(), f2.begin(), f2.end());
+        P.fac.push_back((int)f3.size() / 8);
+        P.fac.insert(P.fac.end(), f3.begin(), f3.end());
+        fwd.push_back(sf);
+        bwd.push_back(sb);
+        L = K;
+        ++nround;
+    }
+    P.fac[0] = nround;
+    P.fac[1] = L[0];
+    std::vector<int> fin;
+    stask(fin, XV | L[0], 0, L[0], GV | L[0], -1, 0);                              // x_last = Inv g_last
+    std::vector<std::vector<int>> phases(fwd.begin(), fwd.end());
+    phases.push_back(fin);
+    for (int r = nround - 1; r >= 0; --r) phases.push_back(bwd[r]);
+    P.sol = {(int)phases.size()};
+    for (const auto &ph : phases) {
+        P.sol.push_back((int)ph.size() / 8);
+        P.sol.insert(P.sol.end(), ph.begin(), ph.end());
+    }
+    P.nslot = next - nb;
+}
+
 template <typename AT>
 static int configure_t(Coarse *c) {
     // dynamic opt-in well above any need here and below the per-block limit
@@ -1674,8 +2047,17 @@ static int configure_t(Coarse *c) {
     c->use_tc = sizeof(AT) == 4 ? 1 : 0;
     if (const char *e = getenv("RAS_COARSE_TC")) c->use_tc = c->use_tc && atoi(e) != 0;
     if (c->use_tc) c->fac_smem = std::max(c->fac_smem, sizeof(TcSmem));
+    // RAS_COARSE_CR=1 at set-up (FP32 with the tensor path, at least three
+    // blocks): cyclic reduction instead of the two-ended elimination. Not the
+    // default: on the 1M-cell workload it takes 9.8 ms per factorisation against
+    // 5.3 ms and its solve reads half as many bytes again (the dense products of
+    // its rounds outweigh the shorter chain of inversions).
+    c->cr = 0;
+    if (const char *e = getenv("RAS_COARSE_CR"))
+        c->cr = sizeof(AT) == 4 && c->use_tc && c->nb >= 3 && atoi(e) != 0 ? 1 : 0;
     // the solve prefetches up to two (FP32) or one (FP64) matrix rows per warp
-    c->sol_npf = sizeof(AT) == 4 ? 2 : 1;
+    // (the reduction's sweeps read theirs directly)
+    c->sol_npf = c->cr ? 0 : (sizeof(AT) == 4 ? 2 : 1);
     while (c->sol_npf > 0 && sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T > (size_t)big) --c->sol_npf;
     c->sol_smem = sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T;
     if (c->rap_smem > (size_t)big || c->rap125_smem > (size_t)big || c->fac_smem > (size_t)big ||
@@ -1763,6 +2145,16 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
     c->nb = (ns + planes - 1) / planes;
     c->mid = c->nb == 1 ? 0 : (c->nb + 1) / 2;   // the two chains differ in length
     if ((long long)c->T * c->T * c->nb * c->esz > (8LL << 30)) return fail(RAS_EINVAL);
+    int rc = c->prec == 64 ? configure_t<double>(c) : configure_t<float>(c);
+    if (rc) return fail(rc);
+    CrPlan plan;
+    if (c->cr) {
+        c->mid = c->nb - 1;              // every edge oriented pivot e -> target e + 1
+        cr_plan(c->nb, plan);
+        c->cr_maxE = plan.maxE;
+        c->cr_mats = plan.mats;
+        if ((long long)c->T * c->T * (plan.nslot + c->nb) * c->esz > (16LL << 30)) return fail(RAS_EINVAL);
+    }
     std::vector<int> pos(c->Nc), cell((size_t)c->nb * c->T, -1);
     for (int z = 0; z < c->c[2]; ++z)
         for (int y = 0; y < c->c[1]; ++y)
@@ -1776,14 +2168,24 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
                 cell[pos[I]] = I;
             }
     const size_t bsz = (size_t)c->T * c->T;
-    int rc = 0;
     if ((rc = dalloc(&c->d_pos, pos.size())) || (rc = dalloc(&c->d_cell, cell.size())) ||
         (rc = dalloc(&c->d_err, 1)) || (rc = dalloc(&c->d_bar, 1)))
         return fail(rc);
-    unsigned char *p_ac, *p_d, *p_c, *p_f, *p_lv, *p_uv, *p_g, *p_x;
+    unsigned char *p_ac, *p_d, *p_c = nullptr, *p_f = nullptr, *p_lv, *p_uv, *p_g, *p_x;
     const size_t nbm1 = (size_t)std::max(c->nb - 1, 1);
+    if (c->cr) {                         // the reduction's buffers instead of C and F
+        unsigned char *p_w = nullptr;
+        if ((rc = dalloc(&p_w, (size_t)plan.nslot * bsz * c->esz)) ||
+            (rc = dalloc(&c->d_crf, plan.fac.size())) || (rc = dalloc(&c->d_crs, plan.sol.size())))
+            return fail(rc);
+        c->W = p_w;
+        if (cudaMemcpy(c->d_crf, plan.fac.data(), plan.fac.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess ||
+            cudaMemcpy(c->d_crs, plan.sol.data(), plan.sol.size() * 4, cudaMemcpyHostToDevice) != cudaSuccess)
+            return fail(RAS_ECUDA);
+    } else if ((rc = dalloc(&p_c, nbm1 * bsz * c->esz)) || (rc = dalloc(&p_f, nbm1 * bsz * c->esz))) {
+        return fail(rc);
+    }
     if ((rc = dalloc(&p_ac, (size_t)125 * c->Nc * c->esz)) || (rc = dalloc(&p_d, c->nb * bsz * c->esz)) ||
-        (rc = dalloc(&p_c, nbm1 * bsz * c->esz)) || (rc = dalloc(&p_f, nbm1 * bsz * c->esz)) ||
         (rc = dalloc(&c->lo_q, nbm1 * c->T * ELLW)) || (rc = dalloc(&c->up_q, nbm1 * c->T * ELLW)) ||
         (rc = dalloc(&c->lo_n, nbm1 * c->T)) || (rc = dalloc(&c->up_n, nbm1 * c->T)) ||
         (rc = dalloc(&p_lv, nbm1 * c->T * ELLW * c->esz)) ||
@@ -1793,7 +2195,8 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
         return fail(rc);
     {
         unsigned char *p_z = nullptr, *p_rx = nullptr, *p_ry = nullptr;
-        if ((rc = dalloc(&p_z, (size_t)2 * TILE * c->T * c->esz))) return fail(rc);
+        const size_t nz = (size_t)std::max(2, c->cr_maxE);   // one scratch strip per concurrent inversion
+        if ((rc = dalloc(&p_z, nz * TILE * c->T * c->esz))) return fail(rc);
         c->Zs = p_z;
         if ((rc = dalloc(&p_rx, (size_t)c->c[0] * c->n[1] * c->n[2] * c->esz))) return fail(rc);
         c->rx = p_rx;
@@ -1813,8 +2216,6 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
         cudaMemset(c->lo_n, 0, nbm1 * c->T * sizeof(int)) != cudaSuccess ||
         cudaMemset(c->up_n, 0, nbm1 * c->T * sizeof(int)) != cudaSuccess)
         return fail(RAS_ECUDA);
-    rc = c->prec == 64 ? configure_t<double>(c) : configure_t<float>(c);
-    if (rc) return fail(rc);
     *out = c;
     return RAS_OK;
 }
@@ -1826,8 +2227,8 @@ void coarse_free(Coarse *c) {
         dfree(c->d_lo[a]); dfree(c->d_hi[a]);
     }
     dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err); dfree(c->d_bar);
-    dfree(c->lo_q); dfree(c->up_q); dfree(c->lo_n); dfree(c->up_n);
-    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs, c->rx, c->ry})
+    dfree(c->lo_q); dfree(c->up_q); dfree(c->lo_n); dfree(c->up_n); dfree(c->d_crf); dfree(c->d_crs);
+    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs, c->rx, c->ry, c->W})
         if (p) cudaFree(p);
     delete c;
 }
@@ -1847,13 +2248,28 @@ static int assemble_blocks_t(Coarse *c, cudaStream_t st) {
             c->up_n, c->d_err);
         RAS_LAUNCHED();
     }
+    if (c->cr) {   // the first round's couplings, dense (slots nb + k and 2 nb + k)
+        AT *Lc = (AT *)c->W, *Uc = Lc + c->nb * bsz;
+        RAS_CK(cudaMemsetAsync(Lc, 0, 2 * c->nb * bsz * sizeof(AT), st));
+        k_cr_couplings<AT><<<grid_of((long long)(c->nb - 1) * c->T), 256, 0, st>>>(
+            c->lo_q, (const AT *)c->lo_v, c->lo_n, c->up_q, (const AT *)c->up_v, c->up_n, c->T, c->nb, Lc, Uc);
+        RAS_LAUNCHED();
+    }
     return RAS_OK;
 }
 
 template <typename AT>
 static FacArgs<AT> fac_args(Coarse *c, GridBar *bar) {
     return FacArgs<AT>{(AT *)c->D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n,
-                       (const AT *)c->lo_v, (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, bar, c->d_err};
+                       (const AT *)c->lo_v, (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, bar, c->d_err,
+                       c->cr, c->d_crf, (AT *)c->W};
+}
+
+template <typename AT>
+static SolArgs<AT> sol_args(Coarse *c, GridBar *bar, const double *t, double *z, int accumulate) {
+    return SolArgs<AT>{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
+                       (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
+                       (AT *)c->ry, bar, c->d_err, c->sol_npf, c->cr, c->d_crs, (const AT *)c->W};
 }
 
 template <typename AT>
@@ -1933,9 +2349,7 @@ int coarse_check(Coarse *c, cudaStream_t st) {
 template <typename AT>
 static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st) {
     RAS_TRY(reset_bar(c, st));
-    SolArgs<AT> sa{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
-                   (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
-                   (AT *)c->ry, c->d_bar, c->d_err, c->sol_npf};
+    SolArgs<AT> sa = sol_args<AT>(c, c->d_bar, t, z, accumulate);
     void *args[] = {&sa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve<AT>, dim3(c->sol_grid),
                                        dim3(256), args, c->sol_smem, st));
@@ -2045,9 +2459,7 @@ static int batch_setup_t(Coarse *const *cs, int n, CoarseBatch *cb) {
     RAS_TRY(dalloc(&cb->d_bars, n));
     for (int i = 0; i < n; ++i) {
         Coarse *c = cs[i];
-        args[i] = SolArgs<AT>{nullptr, nullptr, 1, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
-                              (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
-                              (AT *)c->ry, cb->d_bars + i, c->d_err, c->sol_npf};
+        args[i] = sol_args<AT>(c, cb->d_bars + i, nullptr, nullptr, 1);
         fargs[i] = fac_args<AT>(c, cb->d_bars + i);
     }
     RAS_CK(cudaMalloc(&cb->d_args, n * sizeof(SolArgs<AT>)));
@@ -2135,7 +2547,8 @@ int coarse_correct(Coarse *c, const double *t, double *z, int accumulate, cudaSt
 }
 
 double coarse_bytes(const Coarse *c) {
-    // E, C, F read once per solve
+    // E, C, F read once per solve; the reduction's matrices as its schedule reads them
+    if (c->cr) return (double)c->esz * c->T * c->T * c->cr_mats;
     return (double)c->esz * c->T * c->T * (c->nb + 2.0 * (c->nb - 1));
 }
 
