@@ -56,6 +56,7 @@ struct Coarse {
     int *d_ia[3] = {}, *d_ib[3] = {};
     double *d_wa[3] = {}, *d_wb[3] = {};
     int *d_lo[3] = {}, *d_hi[3] = {};
+    double *d_wt[3] = {};           // per coarse index: the weights of its fine support (w1's values)
     int af, am, as;                 // axis order: fastest, middle, slowest
     int T = 0, nb = 0;              // block size (multiple of TILE), number of blocks
     int mid = 0;                    // middle block of the two-ended elimination
@@ -67,6 +68,7 @@ struct Coarse {
     int *lo_n = nullptr, *up_n = nullptr;            // ELL entries used per row / column
     void *lo_v = nullptr, *up_v = nullptr;           // ELL values
     void *g = nullptr, *x = nullptr;                 // [nb*T]
+    void *xn = nullptr;                              // [Nc] the coarse solution in natural order
     void *Zs = nullptr;                              // scratch tile strips [2][TILE][T]
     void *rx = nullptr, *ry = nullptr;               // restriction passes [cx][ny][nz], [cx][cy][nz]
     int *d_err = nullptr;
@@ -92,6 +94,8 @@ struct Interp {
     const int *ia[3], *ib[3];
     const double *wa[3], *wb[3];
     const int *lo[3], *hi[3];
+    const double *wt[3];   // [I][m]: P(lo[I] + m, I), m < W (the same values as w1)
+    int W[3];
 };
 
 // P(a, I) along one axis (ia == ib only where the second weight is zero, so
@@ -920,35 +924,48 @@ __device__ void tc_pair_update(TcSmem &ts, TcState &st, float *M, int T, int i0,
     __syncthreads();   // the smem overlay and the accumulator are free again
 }
 
-// Out[0 .. nrows) x [0 .. 64) (=, +=) sign (A1 B1 [+ A2 B2]) for FP32 row-major
-// operands with one leading dimension ld: A1 points at its first row and chunk,
-// B1 at its first chunk row and column, the products run over nk1 (nk2) chunks of
-// 64 along k on tcgen05 (M = 128, N = 64, K = 8, the three-term TF32 split of
-// tc_pair_update) and accumulate in tensor memory; the next chunk's global loads
-// are issued before the wait for the current chunk's MMAs. nrows is 64 or 128
-// (rows past it enter as zeros and are not written). All 256 threads; the CTA's
-// shared-memory overlay is free on entry and on return.
-__device__ void tc_gemm_core(TcSmem &ts, TcState &st, float *Out, const float *A1, const float *B1, int nk1,
-                             const float *A2, const float *B2, int nk2, int ld, int nrows, bool acc, float sign,
-                             int *err) {
-    const int tid = threadIdx.x, nch = nk1 + (A2 ? nk2 : 0);
+// One product of tc_gemm_core: A (its first row and chunk; leading dimension
+// lda) times B (its first chunk row and column; leading dimension ldb) over nk
+// chunks of 64 along k. With bidx, row k of B is row bidx[k] of B (negative: a
+// zero row), so that B can be a gathered set of rows.
+struct TcOp {
+    const float *A, *B;
+    int lda, ldb, nk;
+    const int *bidx;
+};
+
+// Out[0 .. nrows) x [0 .. 64) (leading dimension ldo) (=, +=) sign (o1 [+ o2]) for
+// FP32 row-major operands, on tcgen05 (M = 128, N = 64, K = 8, the three-term TF32
+// split of tc_pair_update), accumulated in tensor memory; the next chunk's global
+// loads are issued before the wait for the current chunk's MMAs. nrows is 64 or
+// 128 (rows past it enter as zeros and are not written). All 256 threads; the
+// CTA's shared-memory overlay is free on entry and on return.
+__device__ void tc_gemm_core(TcSmem &ts, TcState &st, float *Out, int ldo, int nrows, const TcOp &o1,
+                             const TcOp *o2, bool acc, float sign, int *err) {
+    const int tid = threadIdx.x, nk1 = o1.nk, nch = nk1 + (o2 ? o2->nk : 0);
     const int xr = tid >> 1, xk0 = (tid & 1) * 32;        // A chunk: row, k half
     const int yk = tid >> 2, yn0 = (tid & 3) * 16;        // B chunk: k, 16 columns
     float4 vx[8], vy[4];
     auto load = [&](int ch) {
-        const float *A = ch < nk1 ? A1 : A2, *B = ch < nk1 ? B1 : B2;
+        const TcOp &o = ch < nk1 ? o1 : *o2;
         const int kc = (ch < nk1 ? ch : ch - nk1) * TILE;
         if (xr < nrows) {
-            const float4 *src = reinterpret_cast<const float4 *>(A + (long long)xr * ld + kc + xk0);
+            const float4 *src = reinterpret_cast<const float4 *>(o.A + (long long)xr * o.lda + kc + xk0);
 #pragma unroll
             for (int q = 0; q < 8; ++q) vx[q] = __ldcg(src + q);
         } else {
 #pragma unroll
             for (int q = 0; q < 8; ++q) vx[q] = make_float4(0.f, 0.f, 0.f, 0.f);
         }
-        const float4 *srcy = reinterpret_cast<const float4 *>(B + (long long)(kc + yk) * ld + yn0);
+        const long long br = o.bidx ? (long long)o.bidx[kc + yk] : (long long)(kc + yk);
+        if (br >= 0) {
+            const float4 *srcy = reinterpret_cast<const float4 *>(o.B + br * o.ldb + yn0);
 #pragma unroll
-        for (int q = 0; q < 4; ++q) vy[q] = __ldcg(srcy + q);
+            for (int q = 0; q < 4; ++q) vy[q] = __ldcg(srcy + q);
+        } else {
+#pragma unroll
+            for (int q = 0; q < 4; ++q) vy[q] = make_float4(0.f, 0.f, 0.f, 0.f);
+        }
     };
     auto wait_mma = [&]() {
         const unsigned a = (unsigned)__cvta_generic_to_shared(st.mbar), par = st.phase & 1;
@@ -1025,7 +1042,7 @@ __device__ void tc_gemm_core(TcSmem &ts, TcState &st, float *Out, const float *A
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
         const int row = 32 * q + lane;
         if (row < nrows) {
-            float *out = Out + (long long)row * ld + 32 * h;
+            float *out = Out + (long long)row * ldo + 32 * h;
             float4 prev[8];
 #pragma unroll
             for (int u = 0; u < 8; ++u)
@@ -1052,8 +1069,10 @@ __device__ __forceinline__ void tc_gemm_pair(TcSmem &ts, TcState &st, float *Out
                                              const float *B2, bool acc, float sign, int *err) {
     const int nk = T / TILE;
     const long long r0 = (long long)2 * pr * TILE * T;
-    tc_gemm_core(ts, st, Out + r0 + j * TILE, A1 + r0, B1 + j * TILE, nk, A2 ? A2 + r0 : nullptr,
-                 B2 ? B2 + j * TILE : nullptr, nk, T, 2 * pr + 1 < nk ? 128 : 64, acc, sign, err);
+    const TcOp o1{A1 + r0, B1 + j * TILE, T, T, nk, nullptr};
+    const TcOp o2{A2 ? A2 + r0 : nullptr, B2 ? B2 + j * TILE : nullptr, T, T, nk, nullptr};
+    tc_gemm_core(ts, st, Out + r0 + j * TILE, T, 2 * pr + 1 < nk ? 128 : 64, o1, A2 ? &o2 : nullptr, acc, sign,
+                 err);
 }
 
 // ---------------------------------------------------------------------------
@@ -1268,17 +1287,7 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
             }
         };
         auto special = [&](int c) {
-            bool done = false;
-            if constexpr (sizeof(AT) == 4) {
-                if (tcs.on) {   // tile (p + 1, p + 1) -= D_{p+1,p} D_{p,p+1}, one MMA group
-                    AT *Dk = a.D + blk[c] * bsz;
-                    const long long r1 = (long long)(p + 1) * TILE * T, r0 = (long long)p * TILE * T;
-                    tc_gemm_core(*reinterpret_cast<TcSmem *>(&ts), tcs, Dk + r1 + (p + 1) * TILE, Dk + r1 + p * TILE,
-                                 Dk + r0 + (p + 1) * TILE, 1, nullptr, nullptr, 0, T, TILE, true, -1.0f, a.err);
-                    done = true;
-                }
-            }
-            if (!done) update(c, dpiv);
+            update(c, dpiv);
             __syncthreads();
             tile_invert(ts, a.D + blk[c] * bsz, T, p + 1, a.err);
         };
@@ -1539,6 +1548,9 @@ struct SolArgs {
     int cr;            // cyclic reduction: the block sweeps follow its solve schedule
     const int *crs;
     const AT *W;
+    AT *xn;            // the coarse solution in natural order (written with its final values)
+    const int *cell;   // block position -> natural coarse index or -1
+    int prolong;       // 1: the cooperative kernel ends with z (+)= P x; 0: k_coarse_prolong does it
 };
 
 __device__ __forceinline__ void cp_async16_cg(void *smem, const void *gmem) {
@@ -1654,6 +1666,51 @@ __device__ bool cr_sweeps(const SolArgs<AT> &a, int b, int ng, unsigned &epoch) 
     return true;
 }
 
+// z (+)= P x for the fine cells p0, p0 + stride, ..., four at a time with their loads
+// in flight together; the coarse values from the natural-order copy (the cyclic
+// reduction's sweeps leave x in block order only)
+template <typename AT>
+__device__ __forceinline__ void coarse_prolong_range(const SolArgs<AT> &a, double *z, long long start,
+                                                     long long stride) {
+    const CGeom &G = a.G;
+    const Interp &P = a.P;
+    const long long N = (long long)G.nx * G.ny * G.nz;
+    for (long long p0 = start; p0 < N; p0 += 4 * stride) {
+        AT sv[4];
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const long long p = p0 + m * stride;
+            sv[m] = 0;
+            if (p >= N) continue;
+            const int ax = (int)(p % G.nx), ay = (int)((p / G.nx) % G.ny),
+                      az = (int)(p / ((long long)G.nx * G.ny));
+            const int Ix[2] = {P.ia[0][ax], P.ib[0][ax]};
+            const int Iy[2] = {P.ia[1][ay], P.ib[1][ay]};
+            const int Iz[2] = {P.ia[2][az], P.ib[2][az]};
+            const AT Wx[2] = {(AT)P.wa[0][ax], (AT)P.wb[0][ax]};
+            const AT Wy[2] = {(AT)P.wa[1][ay], (AT)P.wb[1][ay]};
+            const AT Wz[2] = {(AT)P.wa[2][az], (AT)P.wb[2][az]};
+            AT s = 0;
+#pragma unroll
+            for (int u = 0; u < 2; ++u)
+#pragma unroll
+                for (int v = 0; v < 2; ++v)
+#pragma unroll
+                    for (int w = 0; w < 2; ++w) {
+                        const AT wt = Wx[w] * Wy[v] * Wz[u];
+                        const int I = Ix[w] + G.cx * (Iy[v] + G.cy * Iz[u]);
+                        if (wt != (AT)0) s += wt * (a.cr ? __ldcg(a.x + a.pos[I]) : __ldcg(a.xn + I));
+                    }
+            sv[m] = s;
+        }
+#pragma unroll
+        for (int m = 0; m < 4; ++m) {
+            const long long p = p0 + m * stride;
+            if (p < N) { if (a.accumulate) z[p] += (double)sv[m]; else z[p] = (double)sv[m]; }
+        }
+    }
+}
+
 template <typename AT>
 __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, int ng, const double *t, double *z) {
     extern __shared__ __align__(16) unsigned char smem_raw[];
@@ -1716,13 +1773,25 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
     const long long gtid = b * (long long)blockDim.x + threadIdx.x;
     const long long gstride = (long long)ng * blockDim.x;
     const long long n1 = (long long)G.cx * G.ny * G.nz;
+    // (each pass: the support's weights from the per-axis table and its values
+    // loaded in batches of 8 before any is used; terms summed in index order)
     for (long long e = gtid; e < n1; e += gstride) {          // x pass
         const int Ix = (int)(e % G.cx);
         const long long yz = e / G.cx;
-        const double *src = t + yz * G.nx;
+        const int x0 = P.lo[0][Ix], nw = P.hi[0][Ix] - x0;
+        const double *src = t + yz * G.nx + x0, *wt = P.wt[0] + (long long)Ix * P.W[0];
         AT acc = 0;
-        const int x0 = P.lo[0][Ix], x1 = P.hi[0][Ix];
-        for (int ax = x0; ax < x1; ++ax) acc += (AT)w1(P, 0, ax, Ix) * (AT)__ldg(src + ax);
+        for (int m0 = 0; m0 < nw; m0 += 8) {
+            double tv[8], wv[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                tv[m] = m0 + m < nw ? __ldg(src + m0 + m) : 0.0;
+                wv[m] = m0 + m < nw ? __ldg(wt + m0 + m) : 0.0;
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m0 + m < nw) acc += (AT)wv[m] * (AT)tv[m];
+        }
         a.rx[e] = acc;
     }
     if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
@@ -1730,20 +1799,46 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
     for (long long e = gtid; e < n2; e += gstride) {          // y pass
         const int Ix = (int)(e % G.cx), Iy = (int)((e / G.cx) % G.cy);
         const long long az = e / ((long long)G.cx * G.cy);
+        const int y0 = P.lo[1][Iy], nw = P.hi[1][Iy] - y0;
+        const AT *src = a.rx + Ix + (long long)G.cx * (y0 + (long long)G.ny * az);
+        const double *wt = P.wt[1] + (long long)Iy * P.W[1];
         AT acc = 0;
-        const int y0 = P.lo[1][Iy], y1 = P.hi[1][Iy];
-        for (int ay = y0; ay < y1; ++ay)
-            acc += (AT)w1(P, 1, ay, Iy) * __ldcg(a.rx + Ix + (long long)G.cx * (ay + (long long)G.ny * az));
+        for (int m0 = 0; m0 < nw; m0 += 8) {
+            AT v[8];
+            double wv[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                v[m] = m0 + m < nw ? __ldcg(src + (long long)G.cx * (m0 + m)) : (AT)0;
+                wv[m] = m0 + m < nw ? __ldg(wt + m0 + m) : 0.0;
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m0 + m < nw) acc += (AT)wv[m] * v[m];
+        }
         a.ry[e] = acc;
     }
     if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     for (long long I = gtid; I < G.Nc; I += gstride) {         // z pass
         const int Ix = (int)(I % G.cx), Iy = (int)((I / G.cx) % G.cy), Iz = (int)(I / ((long long)G.cx * G.cy));
+        const int z0 = P.lo[2][Iz], nw = P.hi[2][Iz] - z0;
+        const long long cxy = (long long)G.cx * G.cy;
+        const AT *src = a.ry + Ix + (long long)G.cx * Iy + cxy * z0;
+        const double *wt = P.wt[2] + (long long)Iz * P.W[2];
+        const int dst = a.pos[I];
         AT acc = 0;
-        const int z0 = P.lo[2][Iz], z1 = P.hi[2][Iz];
-        for (int az = z0; az < z1; ++az)
-            acc += (AT)w1(P, 2, az, Iz) * __ldcg(a.ry + Ix + (long long)G.cx * (Iy + (long long)G.cy * az));
-        a.g[a.pos[I]] = acc;
+        for (int m0 = 0; m0 < nw; m0 += 8) {
+            AT v[8];
+            double wv[8];
+#pragma unroll
+            for (int m = 0; m < 8; ++m) {
+                v[m] = m0 + m < nw ? __ldcg(src + cxy * (m0 + m)) : (AT)0;
+                wv[m] = m0 + m < nw ? __ldg(wt + m0 + m) : 0.0;
+            }
+#pragma unroll
+            for (int m = 0; m < 8; ++m)
+                if (m0 + m < nw) acc += (AT)wv[m] * v[m];
+        }
+        a.g[dst] = acc;
     }
     if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     if (a.cr && !cr_sweeps(a, b, ng, epoch)) { cp_async_wait_all(); return; }
@@ -1763,6 +1858,12 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
         const int nr = nrows_of(st, ne);
         int k = 0;
         for (int r = wg; r < nr; r += nwt, ++k) {
+            // the natural index of a row whose x value becomes final in this stage
+            // (the middle block, and the pivot blocks on the way back)
+            long long qf = -1;
+            if (st == nsteps) qf = (long long)mid * T + r;
+            else if (st > nsteps) qf = (long long)edge_pivot(edg[r / T], mid) * T + (r % T);
+            const int cf = lane == 0 && qf >= 0 ? a.cell[qf] : -1;
             const AT *xv = xs + (long long)(st < nsteps ? r / (2 * T) : (st == nsteps ? 0 : r / T)) * T;
             const AT acc = k < a.npf ? row_dot_s(rbuf + (long long)k * T, xv, T, lane)
                                      : row_dot(row_ptr(st, edg, r), xv, T, lane);
@@ -1777,9 +1878,12 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
                     }
                 } else if (st == nsteps) {
                     a.x[(long long)mid * T + r] = acc;
+                    if (cf >= 0) a.xn[cf] = acc;
                 } else {
                     AT *y = a.x + (long long)edge_pivot(edg[r / T], mid) * T + (r % T);
-                    *y = __ldcg(y) - acc;
+                    const AT v = __ldcg(y) - acc;
+                    *y = v;
+                    if (cf >= 0) a.xn[cf] = v;
                 }
             }
         }
@@ -1787,47 +1891,21 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
         prefetch(st + 1);
         if (!grid_barrier(a.bar, a.err, epoch, ng)) { cp_async_wait_all(); return; }
     }
-    // z (+)= P x, four fine cells per thread with their loads in flight together
-    const long long N = (long long)G.nx * G.ny * G.nz;
-    for (long long p0 = gtid; p0 < N; p0 += 4 * gstride) {
-        AT sv[4];
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const long long p = p0 + m * gstride;
-            sv[m] = 0;
-            if (p >= N) continue;
-            const int ax = (int)(p % G.nx), ay = (int)((p / G.nx) % G.ny),
-                      az = (int)(p / ((long long)G.nx * G.ny));
-            const int Ix[2] = {P.ia[0][ax], P.ib[0][ax]};
-            const int Iy[2] = {P.ia[1][ay], P.ib[1][ay]};
-            const int Iz[2] = {P.ia[2][az], P.ib[2][az]};
-            const AT Wx[2] = {(AT)P.wa[0][ax], (AT)P.wb[0][ax]};
-            const AT Wy[2] = {(AT)P.wa[1][ay], (AT)P.wb[1][ay]};
-            const AT Wz[2] = {(AT)P.wa[2][az], (AT)P.wb[2][az]};
-            AT s = 0;
-#pragma unroll
-            for (int u = 0; u < 2; ++u)
-#pragma unroll
-                for (int v = 0; v < 2; ++v)
-#pragma unroll
-                    for (int w = 0; w < 2; ++w) {
-                        const AT wt = Wx[w] * Wy[v] * Wz[u];
-                        const int I = Ix[w] + G.cx * (Iy[v] + G.cy * Iz[u]);
-                        if (wt != (AT)0) s += wt * __ldcg(a.x + a.pos[I]);
-                    }
-            sv[m] = s;
-        }
-#pragma unroll
-        for (int m = 0; m < 4; ++m) {
-            const long long p = p0 + m * gstride;
-            if (p < N) { if (a.accumulate) z[p] += (double)sv[m]; else z[p] = (double)sv[m]; }
-        }
-    }
+    if (a.prolong) coarse_prolong_range(a, z, gtid, gstride);
 }
 
 template <typename AT>
-__global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
+__global__ void __launch_bounds__(256, 2) k_coarse_solve(SolArgs<AT> a) {
     coarse_solve_body(a, blockIdx.x, gridDim.x, a.t, a.z);
+}
+
+// The prolongation of a single coarse correction as a kernel of its own (full
+// occupancy: the loop is bound by the latency of its table and coarse loads, which
+// the cooperative kernel's two CTAs per SM do not hide)
+template <typename AT>
+__global__ void __launch_bounds__(256) k_coarse_prolong(SolArgs<AT> a) {
+    coarse_prolong_range(a, a.z, blockIdx.x * (long long)blockDim.x + threadIdx.x,
+                         (long long)gridDim.x * blockDim.x);
 }
 
 // The coarse corrections of several handles in one cooperative launch: handle h
@@ -1835,7 +1913,7 @@ __global__ void __launch_bounds__(256) k_coarse_solve(SolArgs<AT> a) {
 // are the handles' fine vectors concatenated at off[h]; a handle switched off in
 // `active` returns at once (all its CTAs).
 template <typename AT>
-__global__ void __launch_bounds__(256) k_coarse_solve_batch(const SolArgs<AT> *args, const int *cta_inst,
+__global__ void __launch_bounds__(256, 2) k_coarse_solve_batch(const SolArgs<AT> *args, const int *cta_inst,
                                                             const int *first, const int *size,
                                                             const long long *off, const unsigned char *active,
                                                             const double *t, double *z) {
@@ -1921,6 +1999,7 @@ static Interp interp_of(const Coarse *c) {
         P.ia[a] = c->d_ia[a]; P.ib[a] = c->d_ib[a];
         P.wa[a] = c->d_wa[a]; P.wb[a] = c->d_wb[a];
         P.lo[a] = c->d_lo[a]; P.hi[a] = c->d_hi[a];
+        P.wt[a] = c->d_wt[a]; P.W[a] = c->wmax[a];
     }
     return P;
 }
@@ -2086,12 +2165,19 @@ static int configure_t(Coarse *c) {
 
 // interpolation tables of one axis on the device
 static int upload_axis(int n, int r, int order, int *&d_ia, int *&d_ib, double *&d_wa, double *&d_wb, int *&d_lo,
-                       int *&d_hi, int &nc, int &wmax) {
+                       int *&d_hi, double *&d_wt, int &nc, int &wmax) {
     std::vector<int> ia, ib, lo, hi;
     std::vector<double> wa, wb;
     interp_axis(n, r, ia, ib, wa, wb, lo, hi, nc, order);
     wmax = 1;
     for (size_t I = 0; I < lo.size(); ++I) wmax = std::max(wmax, hi[I] - lo[I]);
+    // wt[I][m] = P(lo[I] + m, I) by w1's selection (zero past hi[I])
+    std::vector<double> wt((size_t)nc * wmax, 0.0);
+    for (int I = 0; I < nc; ++I)
+        for (int a = lo[I]; a < hi[I]; ++a)
+            wt[(size_t)I * wmax + (a - lo[I])] = ia[a] == I ? wa[a] : (ib[a] == I ? wb[a] : 0.0);
+    RAS_TRY(dalloc(&d_wt, wt.size()));
+    RAS_CK(cudaMemcpy(d_wt, wt.data(), wt.size() * 8, cudaMemcpyHostToDevice));
     RAS_TRY(dalloc(&d_ia, ia.size()));
     RAS_TRY(dalloc(&d_ib, ib.size()));
     RAS_TRY(dalloc(&d_wa, wa.size()));
@@ -2130,7 +2216,7 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
     for (int a = 0; a < 3; ++a) {
         c->r[a] = o.coarsen[a];
         const int rc = upload_axis(c->n[a], c->r[a], o.interp_order, c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
-                                   c->d_lo[a], c->d_hi[a], c->c[a], c->wmax[a]);
+                                   c->d_lo[a], c->d_hi[a], c->d_wt[a], c->c[a], c->wmax[a]);
         if (rc) return fail(rc);
     }
     c->Nc = c->c[0] * c->c[1] * c->c[2];
@@ -2202,6 +2288,9 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
         c->rx = p_rx;
         if ((rc = dalloc(&p_ry, (size_t)c->c[0] * c->c[1] * c->n[2] * c->esz))) return fail(rc);
         c->ry = p_ry;
+        unsigned char *p_xn = nullptr;
+        if ((rc = dalloc(&p_xn, (size_t)c->Nc * c->esz))) return fail(rc);
+        c->xn = p_xn;
     }
     c->Ac = p_ac; c->D = p_d; c->C = p_c; c->F = p_f; c->lo_v = p_lv; c->up_v = p_uv;
     c->g = p_g; c->x = p_x;
@@ -2224,11 +2313,11 @@ void coarse_free(Coarse *c) {
     if (!c) return;
     for (int a = 0; a < 3; ++a) {
         dfree(c->d_ia[a]); dfree(c->d_ib[a]); dfree(c->d_wa[a]); dfree(c->d_wb[a]);
-        dfree(c->d_lo[a]); dfree(c->d_hi[a]);
+        dfree(c->d_lo[a]); dfree(c->d_hi[a]); dfree(c->d_wt[a]);
     }
     dfree(c->d_pos); dfree(c->d_cell); dfree(c->d_err); dfree(c->d_bar);
     dfree(c->lo_q); dfree(c->up_q); dfree(c->lo_n); dfree(c->up_n); dfree(c->d_crf); dfree(c->d_crs);
-    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs, c->rx, c->ry, c->W})
+    for (void *p : {c->Ac, c->D, c->C, c->F, c->lo_v, c->up_v, c->g, c->x, c->Zs, c->rx, c->ry, c->W, c->xn})
         if (p) cudaFree(p);
     delete c;
 }
@@ -2269,7 +2358,8 @@ template <typename AT>
 static SolArgs<AT> sol_args(Coarse *c, GridBar *bar, const double *t, double *z, int accumulate) {
     return SolArgs<AT>{t, z, accumulate, interp_of(c), geom_of(c), c->d_pos, (const AT *)c->D,
                        (const AT *)c->C, (const AT *)c->F, (AT *)c->g, (AT *)c->x, (AT *)c->rx,
-                       (AT *)c->ry, bar, c->d_err, c->sol_npf, c->cr, c->d_crs, (const AT *)c->W};
+                       (AT *)c->ry, bar, c->d_err, c->sol_npf, c->cr, c->d_crs, (const AT *)c->W,
+                       (AT *)c->xn, c->d_cell, 1};
 }
 
 template <typename AT>
@@ -2350,9 +2440,12 @@ template <typename AT>
 static int correct_t(Coarse *c, const double *t, double *z, int accumulate, cudaStream_t st) {
     RAS_TRY(reset_bar(c, st));
     SolArgs<AT> sa = sol_args<AT>(c, c->d_bar, t, z, accumulate);
+    sa.prolong = 0;
     void *args[] = {&sa};
     RAS_CK(cudaLaunchCooperativeKernel((const void *)k_coarse_solve<AT>, dim3(c->sol_grid),
                                        dim3(256), args, c->sol_smem, st));
+    RAS_LAUNCHED();
+    k_coarse_prolong<AT><<<grid_of((long long)c->N), 256, 0, st>>>(sa);
     RAS_LAUNCHED();
     return RAS_OK;
 }
@@ -2621,7 +2714,7 @@ int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3], i
     for (int a = 0; a < 3; ++a) {
         c->r[a] = ratio[a];
         const int rc = upload_axis(c->n[a], c->r[a], order, c->d_ia[a], c->d_ib[a], c->d_wa[a], c->d_wb[a],
-                                   c->d_lo[a], c->d_hi[a], c->c[a], c->wmax[a]);
+                                   c->d_lo[a], c->d_hi[a], c->d_wt[a], c->c[a], c->wmax[a]);
         if (rc) { transfer_free(t); return rc; }
     }
     c->Nc = c->c[0] * c->c[1] * c->c[2];
@@ -2646,7 +2739,7 @@ void transfer_free(Transfer *t) {
     Coarse *c = &t->geo;
     for (int a = 0; a < 3; ++a) {
         dfree(c->d_ia[a]); dfree(c->d_ib[a]); dfree(c->d_wa[a]); dfree(c->d_wb[a]);
-        dfree(c->d_lo[a]); dfree(c->d_hi[a]);
+        dfree(c->d_lo[a]); dfree(c->d_hi[a]); dfree(c->d_wt[a]);
     }
     delete t;
 }

@@ -51,22 +51,23 @@ __global__ void __launch_bounds__(RED_THREADS) k_mdot(const double *__restrict__
     }
 }
 
+// Sums the per-block partials of nvec reductions, one CTA per reduction (grid =
+// nvec), each in a fixed order: strided per thread, a warp tree, then the warps in
+// order; the square root of the last when sqrt_last.
 __global__ void k_finalize_rows(const double *__restrict__ partials, int nvec,
                                 double *__restrict__ out, int slot0, int sqrt_last) {
     __shared__ double sh[RED_THREADS / 32];
-    for (int v = 0; v < nvec; ++v) {
-        double acc = 0.0;
-        for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) acc += partials[v * RED_BLOCKS + i];
+    const int v = blockIdx.x;
+    double acc = 0.0;
+    for (int i = threadIdx.x; i < RED_BLOCKS; i += blockDim.x) acc += partials[v * RED_BLOCKS + i];
 #pragma unroll
-        for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
-        if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
-        __syncthreads();
-        if (threadIdx.x == 0) {
-            double s = 0.0;
-            for (int q = 0; q < RED_THREADS / 32; ++q) s += sh[q];
-            out[slot0 + v] = (sqrt_last && v == nvec - 1) ? sqrt(s) : s;
-        }
-        __syncthreads();
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
+    if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = acc;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double s = 0.0;
+        for (int q = 0; q < RED_THREADS / 32; ++q) s += sh[q];
+        out[slot0 + v] = (sqrt_last && v == nvec - 1) ? sqrt(s) : s;
     }
 }
 
@@ -205,12 +206,12 @@ static int fgmres_core(int N, double *V, double *Z, double *w, double *r, Reduce
             RAS_TRY(apply_A(Zj, w));
             // CGS pass 1 (+ ||w||^2 before orthogonalisation)
             RAS_TRY(launch_mdot(V, ld, k, 1, w, N, red.partials, st));
-            k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, k + 1, red.out, 0, 0);
+            k_finalize_rows<<<k + 1, RED_THREADS, 0, st>>>(red.partials, k + 1, red.out, 0, 0);
             RAS_LAUNCHED();
             RAS_TRY(launch_update<false>(V, ld, k, red.out, w, N, nullptr, st));
             // CGS pass 2
             RAS_TRY(launch_mdot(V, ld, k, 0, w, N, red.partials, st));
-            k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, k, red.out, k + 1, 0);
+            k_finalize_rows<<<k, RED_THREADS, 0, st>>>(red.partials, k, red.out, k + 1, 0);
             RAS_LAUNCHED();
             RAS_TRY(launch_update<true>(V, ld, k, red.out + k + 1, w, N, red.partials, st));
             k_finalize_rows<<<1, RED_THREADS, 0, st>>>(red.partials, 1, red.out, 2 * k + 1, 1);

@@ -37,10 +37,25 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
             pc->A.c[s] = pc->Acopy[s];
         }
     }
+    // two levels with the exact coarse solve: the fine factors run on a side stream
+    // while the Galerkin product and the block assembly run on st; st waits for
+    // them before the cooperative block elimination, which needs every SM
+    const bool overlap = pc->coarse && !pc->xfer && !pc->use125;
+    if (overlap && !pc->side) {
+        if (cudaStreamCreateWithFlags(&pc->side, cudaStreamNonBlocking) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pc->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+            cudaEventCreateWithFlags(&pc->ev_join, cudaEventDisableTiming) != cudaSuccess)
+            return RAS_ECUDA;
+    }
     if (pc->use125) {
         const ras_problem *P = pc->prob;
         RAS_TRY(embed7(A, P->nx, P->ny, P->nz, pc->A125, st));
         RAS_TRY(ras125_factor(pc->fine125, pc->A125, st));
+    } else if (overlap) {
+        RAS_CK(cudaEventRecord(pc->ev_fork, st));
+        RAS_CK(cudaStreamWaitEvent(pc->side, pc->ev_fork, 0));
+        RAS_TRY(ras1_factor(pc->fine, A, pc->side));
+        RAS_CK(cudaEventRecord(pc->ev_join, pc->side));
     } else {
         RAS_TRY(ras1_factor(pc->fine, A, st));
     }
@@ -50,6 +65,10 @@ int precond_factor(ras_precond *pc, const ras_stencil *J, cudaStream_t st) {
         RAS_TRY(transfer_galerkin7(pc->xfer, A, pc->A1, pc->A1f, st));
         RAS_TRY(ras125_factor(pc->mid, pc->A1, st));
         RAS_TRY(coarse_factor125(pc->coarse, pc->A1, st));
+    } else if (overlap) {
+        RAS_TRY(coarse_factor_prepare(pc->coarse, A, st));
+        RAS_CK(cudaStreamWaitEvent(st, pc->ev_join, 0));
+        RAS_TRY(coarse_factor_blocks(pc->coarse, st));
     } else if (pc->coarse) {
         RAS_TRY(coarse_factor(pc->coarse, A, st));
     } else if (pc->icoarse) {
@@ -210,6 +229,9 @@ extern "C" void ras_precond_destroy(ras_precond *pc) {
     dfree(pc->t1); dfree(pc->t2); dfree(pc->t3);
     for (int s = 0; s < 7; ++s) dfree(pc->Acopy[s]);
     for (auto e : pc->ev) cudaEventDestroy(e);
+    if (pc->ev_fork) cudaEventDestroy(pc->ev_fork);
+    if (pc->ev_join) cudaEventDestroy(pc->ev_join);
+    if (pc->side) cudaStreamDestroy(pc->side);
     delete pc;
 }
 

@@ -86,6 +86,9 @@ struct ras_precond {
     float *A1f = nullptr;                // FP32 scratch of A1 (reduced-precision factors)
     ras::Ras125 mid;                     // RAS(ILU(0)) smoother of level 1
     double *b1 = nullptr, *x1 = nullptr, *r1 = nullptr;  // level-1 vectors [N1]
+    // factorisation: the fine factors on a side stream next to the Galerkin product
+    cudaStream_t side = nullptr;
+    cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
     bool timing = false;
     std::vector<cudaEvent_t> ev;
     size_t ev_used = 0;
