@@ -321,7 +321,7 @@ __global__ void k_widen(const float *__restrict__ src, double *__restrict__ dst,
 }
 
 // natural coarse index -> neighbour at offset o (or -1)
-__device__ __forceinline__ int nbr_index(const CGeom &G, int I, int o) {
+__host__ __device__ __forceinline__ int nbr_index(const CGeom &G, int I, int o) {
     const int dx = o % 5 - 2, dy = (o / 5) % 5 - 2, dz = o / 25 - 2;
     const int x = I % G.cx + dx, y = (I / G.cx) % G.cy + dy, z = I / (G.cx * G.cy) + dz;
     if (x < 0 || x >= G.cx || y < 0 || y >= G.cy || z < 0 || z >= G.cz) return -1;
@@ -1440,18 +1440,19 @@ __device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, 
         if (s == nsteps) break;
         const long long ell = (long long)T * ELLW;
         const int nchunk = T / FROWS;
-        const int nE = T + nchunk;
+        const int nC = T;                                   // C_e: one item per row
+        const int nE = nC + nchunk;
         for (int it2 = b; it2 < ne * nE; it2 += G) {
             const int e = edg[it2 / nE], it = it2 % nE;
             const AT *Inv = a.D + edge_pivot(e, mid) * bsz;
-            if (it < T) {                                   // C_e row = A(target, pivot) row * Inv
+            if (it < nC) {                                  // C_e row = A(target, pivot) row * Inv
                 const int r = it;
                 const long long at = e * ell + (long long)r * ELLW;
                 sparse_row_times(Inv, a.lo_q + at, a.lo_v + at, a.lo_n[(long long)e * T + r],
                                  a.C + e * bsz + (long long)r * T, T, smem_raw);
             } else {                                        // F_e = Inv A(pivot, target)
                 rows_times_up(rows, Inv, a.F + e * bsz, a.up_q + e * ell, a.up_v + e * ell,
-                              a.up_n + (long long)e * T, T, (it - T) * FROWS, false);
+                              a.up_n + (long long)e * T, T, (it - nC) * FROWS, false);
             }
         }
         if (!grid_barrier(a.bar, a.err, epoch, G)) return;
@@ -1858,33 +1859,33 @@ __device__ __forceinline__ void coarse_solve_body(const SolArgs<AT> &a, int b, i
         const int nr = nrows_of(st, ne);
         int k = 0;
         for (int r = wg; r < nr; r += nwt, ++k) {
-            // the natural index of a row whose x value becomes final in this stage
-            // (the middle block, and the pivot blocks on the way back)
+            // lane 0 first reads what the row updates (the target entry of g, or the
+            // pivot entry of x on the way back) and the natural index of a row whose x
+            // value becomes final in this stage (the middle block, and the pivot blocks
+            // on the way back), so that those loads overlap the dot product
+            AT *y = nullptr;
             long long qf = -1;
-            if (st == nsteps) qf = (long long)mid * T + r;
-            else if (st > nsteps) qf = (long long)edge_pivot(edg[r / T], mid) * T + (r % T);
+            if (st < nsteps) {
+                const int c = r / (2 * T), rr = r % (2 * T), e = edg[c];
+                y = rr < T ? a.x + (long long)edge_pivot(e, mid) * T + rr
+                           : a.g + (long long)edge_target(e, mid) * T + (rr - T);
+            } else if (st == nsteps) {
+                qf = (long long)mid * T + r;
+                y = a.x + qf;
+            } else {
+                qf = (long long)edge_pivot(edg[r / T], mid) * T + (r % T);
+                y = a.x + qf;
+            }
+            const bool rmw = st > nsteps || (st < nsteps && r % (2 * T) >= T);   // y -= acc
+            const AT prev = lane == 0 && rmw ? __ldcg(y) : (AT)0;
             const int cf = lane == 0 && qf >= 0 ? a.cell[qf] : -1;
             const AT *xv = xs + (long long)(st < nsteps ? r / (2 * T) : (st == nsteps ? 0 : r / T)) * T;
             const AT acc = k < a.npf ? row_dot_s(rbuf + (long long)k * T, xv, T, lane)
                                      : row_dot(row_ptr(st, edg, r), xv, T, lane);
             if (lane == 0) {
-                if (st < nsteps) {
-                    const int c = r / (2 * T), rr = r % (2 * T), e = edg[c];
-                    if (rr < T) {
-                        a.x[(long long)edge_pivot(e, mid) * T + rr] = acc;
-                    } else {
-                        AT *y = a.g + (long long)edge_target(e, mid) * T + (rr - T);
-                        *y = __ldcg(y) - acc;
-                    }
-                } else if (st == nsteps) {
-                    a.x[(long long)mid * T + r] = acc;
-                    if (cf >= 0) a.xn[cf] = acc;
-                } else {
-                    AT *y = a.x + (long long)edge_pivot(edg[r / T], mid) * T + (r % T);
-                    const AT v = __ldcg(y) - acc;
-                    *y = v;
-                    if (cf >= 0) a.xn[cf] = v;
-                }
+                const AT v = rmw ? prev - acc : acc;
+                *y = v;
+                if (cf >= 0) a.xn[cf] = v;
             }
         }
         __syncwarp();                      // this warp's reads of its row buffer are done
