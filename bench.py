@@ -148,6 +148,13 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append(line.strip())
 
+    def wait_ready(self, timeout=5.0):
+        """Block until the sampler has printed its first sample (nvidia-smi's start-up,
+        which initialises NVML, then falls before the timed region, not inside it)."""
+        t0 = time.time()
+        while self.proc is not None and not self.lines and time.time() - t0 < timeout:
+            time.sleep(0.01)
+
     def stop(self):
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
@@ -288,6 +295,7 @@ def gb300_arm(args):
     # timed region: K implicit steps on resident state (no per-launch events inside)
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_ready()
     n0 = ras.kernel_launches()
     t, outs = timed(lambda: run_steps(gp, pc, res, state, args.steps, torch), torch, dist_on)
     launches = ras.kernel_launches() - n0
@@ -589,6 +597,7 @@ def c4_arm(args):
     b.advance(max(args.warmup, 1))
     sampler = ClockSampler(local)
     sampler.start()
+    sampler.wait_ready()
     from paper_2007_13966_gb300 import ras
     n0 = ras.kernel_launches()
     t, _ = timed(lambda: b.advance(args.steps), torch, dist_on)
