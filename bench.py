@@ -65,9 +65,9 @@ def parse():
                     help="c2: 128x128x64 two-level (default); c3: 60x220x85 three-level; "
                          "c4: 64 independent reservoirs of 32^3..96^3 solved concurrently")
     ap.add_argument("--cpu-sample", action="store_true", help=argparse.SUPPRESS)
-    ap.add_argument("--kernel", choices=["ras_apply", "vcycle"], default=None,
-                    help="kernel-only mode: factor once, then time REPS applications "
-                         "(used for the ncu captures)")
+    ap.add_argument("--kernel", choices=["ras_apply", "vcycle", "factor"], default=None,
+                    help="kernel-only mode: factor once, then time REPS applications, or "
+                         "(factor) REPS factorisations (used for the ncu captures)")
     ap.add_argument("--reps", type=int, default=20)
     ap.add_argument("--apply-kernel", type=int, choices=[0, 1], default=None,
                     help="fine subdomain-solve kernel: 0 level-scheduled, 1 pipelined "
@@ -548,6 +548,15 @@ def kernel_mode(args):
     F = torch.zeros(N, dtype=torch.float64, device="cuda")
     gp.residual_eval(p, p0, p0, res.dt, 1, F, gp.J)
     pc.factor(gp.J)
+    if args.kernel == "factor":
+        # ras_factor: fine ILU(0) factors (own stream), Galerkin product, block
+        # assembly and the coarse block elimination; CUDA events, median of REPS
+        for _ in range(2):
+            pc.factor(gp.J)
+        ts = sorted(timed(lambda: pc.factor(gp.J), torch, False)[0] for _ in range(args.reps))
+        print(json.dumps({"kernel": "factor", "reps": args.reps, "factor_ms_median": ts[len(ts) // 2] * 1e3,
+                          "factor_ms_min": ts[0] * 1e3}))
+        return
     r = torch.randn(N, dtype=torch.float64, device="cuda")
     z = torch.zeros_like(r)
     for _ in range(3):
