@@ -1568,12 +1568,14 @@ __device__ __forceinline__ AT row_dot_s(const AT *row, const AT *xs, int T, int 
     constexpr int VEC = 16 / sizeof(AT);
     using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
     const V16 *rv = reinterpret_cast<const V16 *>(row);
+    const V16 *xv = reinterpret_cast<const V16 *>(xs);   // 16-byte reads: no bank conflicts
     AT acc = 0;
     for (int v = lane; v < T / VEC; v += 32) {
-        const V16 b = rv[v];
+        const V16 b = rv[v], x = xv[v];
         const AT *w = reinterpret_cast<const AT *>(&b);
+        const AT *y = reinterpret_cast<const AT *>(&x);
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) acc += w[q] * xs[v * VEC + q];
+        for (int q = 0; q < VEC; ++q) acc += w[q] * y[q];
     }
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_down_sync(0xffffffffu, acc, o);
@@ -1586,10 +1588,10 @@ __device__ __forceinline__ AT row_dot_s(const AT *row, const AT *xs, int T, int 
 template <typename AT, bool GX = false>
 __device__ __forceinline__ AT row_dot(const AT *row, const AT *xs, int T, int lane) {
     AT acc = 0;
-    auto X = [&](int c) { return GX ? __ldcg(xs + c) : xs[c]; };
     constexpr int VEC = 16 / sizeof(AT);
     using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
-    const V16 *rv = reinterpret_cast<const V16 *>(row);
+    const V16 *rv = reinterpret_cast<const V16 *>(row), *xv = reinterpret_cast<const V16 *>(xs);
+    auto X = [&](int i) { return GX ? __ldcg(xv + i) : xv[i]; };   // 16-byte reads
     const int nv = T / VEC;
     for (int base = lane; base < nv; base += 32 * 8) {
         V16 buf[8];
@@ -1599,10 +1601,11 @@ __device__ __forceinline__ AT row_dot(const AT *row, const AT *xs, int T, int la
 #pragma unroll
         for (int m = 0; m < 8; ++m)
             if (base + 32 * m < nv) {
-                const int c = (base + 32 * m) * VEC;
+                const V16 xq = X(base + 32 * m);
                 const AT *v = reinterpret_cast<const AT *>(&buf[m]);
+                const AT *y = reinterpret_cast<const AT *>(&xq);
 #pragma unroll
-                for (int q = 0; q < VEC; ++q) acc += v[q] * X(c + q);
+                for (int q = 0; q < VEC; ++q) acc += v[q] * y[q];
             }
     }
 #pragma unroll
