@@ -25,6 +25,7 @@ namespace ras {
 
 constexpr int BCH = 2048;               // cells per CTA of the batched vector kernels
 constexpr int OST = 2 * MAX_MDOT + 8;   // device results per reservoir
+constexpr int CYC_CHUNK = 2;            // Arnoldi steps per replayed graph (mask read between chunks)
 
 struct BOp {                    // one reservoir's 7-point operator
     const double *c[7];
@@ -314,10 +315,11 @@ struct ras_batch {
     int Km = 0;                              // m the device scalars were sized for
     unsigned char *d_cyc = nullptr;          // reservoirs of the current cycle
     double *d_lastg = nullptr;
-    cudaGraphExec_t cycle_exec = nullptr;    // the m Arnoldi steps of a cycle, captured
+    std::vector<cudaGraphExec_t> cycle_exec; // the cycle's Arnoldi steps, CYC_CHUNK per graph
+    std::vector<long long> cycle_launches;   // kernels in each (counted at every replay)
     int cycle_m = 0;                         // m of the captured cycle
     long long cycle_polls = 0;               // coarse barrier poll limit captured in it
-    long long cycle_launches = 0;            // kernels in it (counted at every replay)
+    unsigned char *h_act = nullptr;          // pinned host copy of the mask (between chunks)
     bool graph_off = false;                  // capture failed or disabled: direct launches
     cudaStream_t gstream = nullptr;          // the graph's own stream (joined to the caller's by events)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
@@ -339,7 +341,9 @@ static void batch_free(ras_batch *B) {
     dfree(B->V); dfree(B->Z); dfree(B->w); dfree(B->r); dfree(B->b); dfree(B->x); dfree(B->tmp);
     dfree(B->K.H); dfree(B->K.cs); dfree(B->K.sn); dfree(B->K.g); dfree(B->K.tol); dfree(B->K.res);
     dfree(B->K.it); dfree(B->K.jend); dfree(B->K.bad); dfree(B->d_cyc); dfree(B->d_lastg);
-    if (B->cycle_exec) cudaGraphExecDestroy(B->cycle_exec);
+    for (auto g : B->cycle_exec)
+        if (g) cudaGraphExecDestroy(g);
+    if (B->h_act) cudaFreeHost(B->h_act);
     if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     if (B->ev_join) cudaEventDestroy(B->ev_join);
     if (B->gstream) cudaStreamDestroy(B->gstream);
@@ -472,11 +476,11 @@ static int ensure_krylov_dev(ras_batch *B, int m) {
     if (!B->d_lastg) RAS_TRY(dalloc(&B->d_lastg, n));
     K.m = m;
     B->Km = m;
-    if (B->cycle_exec) {   // a captured cycle of another m is stale
-        cudaGraphExecDestroy(B->cycle_exec);
-        B->cycle_exec = nullptr;
-        B->cycle_m = 0;
+    for (auto &g : B->cycle_exec) {   // a captured cycle of another m is stale
+        if (g) cudaGraphExecDestroy(g);
+        g = nullptr;
     }
+    B->cycle_m = 0;
     return RAS_OK;
 }
 
@@ -484,9 +488,9 @@ static int ensure_krylov_dev(ras_batch *B, int m) {
 // preconditioner, operator, two CGS passes with their norms, the next basis vector,
 // and the device-side Hessenberg / Givens step that switches a stopping reservoir off.
 // No host data enters: the same launches serve every cycle.
-static int b_cycle(ras_batch *B, int m, cudaStream_t st) {
+static int b_cycle(ras_batch *B, int j0, int j1, cudaStream_t st) {
     const long long Nt = B->Ntot;
-    for (int j = 0; j < m; ++j) {
+    for (int j = j0; j < j1; ++j) {
         const int k = j + 1;
         double *Vj = B->V + (size_t)j * Nt, *Zj = B->Z + (size_t)j * Nt;
         RAS_TRY(b_precond(B, Vj, Zj, st));
@@ -505,10 +509,13 @@ static int b_cycle(ras_batch *B, int m, cudaStream_t st) {
     return RAS_OK;
 }
 
-// Runs the cycle: replays its CUDA graph (captured on the first cycle of this m) on
-// the batch's own stream, joined to the caller's stream by events; or launches it
-// directly (RAS_BATCH_GRAPH=0, a batch whose coarse corrections are launched per
-// reservoir from host state, or a capture that failed).
+// Runs the cycle in chunks of CYC_CHUNK Arnoldi steps: each chunk's launches are
+// captured once (per m and coarse poll limit) as a CUDA graph on the batch's own
+// stream, joined to the caller's stream by events, and replayed; between chunks the
+// host reads the device mask and ends the cycle once no reservoir is active (the
+// remaining steps would change nothing). With RAS_BATCH_GRAPH=0, for a batch whose
+// coarse corrections are launched per reservoir from host state, or after a capture
+// failed, the same chunks are launched directly.
 static int b_run_cycle(ras_batch *B, int m, cudaStream_t st) {
     bool use_graph = !B->graph_off && (!B->twolevel || B->cb);
     if (const char *e = getenv("RAS_BATCH_GRAPH")) use_graph = use_graph && atoi(e) != 0;
@@ -521,43 +528,59 @@ static int b_run_cycle(ras_batch *B, int m, cudaStream_t st) {
             use_graph = false;
         }
     }
-    if (!use_graph) return b_cycle(B, m, st);
+    const int nchk = (m + CYC_CHUNK - 1) / CYC_CHUNK;
     const long long polls = B->twolevel ? coarse_barrier_polls() : 0;
-    if (!B->cycle_exec || B->cycle_m != m || B->cycle_polls != polls) {
-        if (B->cycle_exec) {
-            cudaGraphExecDestroy(B->cycle_exec);
-            B->cycle_exec = nullptr;
-        }
-        const long long n0 = g_launches.load();
-        cudaGraph_t graph = nullptr;
-        if (cudaStreamBeginCapture(B->gstream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-            cudaGetLastError();
-            B->graph_off = true;
-            return b_cycle(B, m, st);
-        }
-        const int rc = b_cycle(B, m, B->gstream);
-        const cudaError_t ec = cudaStreamEndCapture(B->gstream, &graph);
-        if (rc < 0 || ec != cudaSuccess || !graph ||
-            cudaGraphInstantiate(&B->cycle_exec, graph, 0) != cudaSuccess) {
-            if (graph) cudaGraphDestroy(graph);
-            cudaGetLastError();
-            B->cycle_exec = nullptr;
-            B->graph_off = true;
-            g_launches.store(n0);
-            return b_cycle(B, m, st);   // nothing ran during the capture: run the cycle now
-        }
-        cudaGraphDestroy(graph);
+    if (use_graph && (B->cycle_m != m || B->cycle_polls != polls || (int)B->cycle_exec.size() != nchk)) {
+        for (auto &g : B->cycle_exec)
+            if (g) cudaGraphExecDestroy(g);
+        B->cycle_exec.assign(nchk, nullptr);
+        B->cycle_launches.assign(nchk, 0);
         B->cycle_m = m;
         B->cycle_polls = polls;
-        B->cycle_launches = g_launches.load() - n0;
-        g_launches.store(n0);
     }
-    RAS_CK(cudaEventRecord(B->ev_fork, st));
-    RAS_CK(cudaStreamWaitEvent(B->gstream, B->ev_fork, 0));
-    RAS_CK(cudaGraphLaunch(B->cycle_exec, B->gstream));
-    RAS_CK(cudaEventRecord(B->ev_join, B->gstream));
-    RAS_CK(cudaStreamWaitEvent(st, B->ev_join, 0));
-    g_launches.fetch_add(B->cycle_launches, std::memory_order_relaxed);
+    for (int c = 0; c < nchk; ++c) {
+        const int j0 = c * CYC_CHUNK, j1 = std::min(m, j0 + CYC_CHUNK);
+        if (use_graph && !B->cycle_exec[c]) {
+            const long long n0 = g_launches.load();
+            cudaGraph_t graph = nullptr;
+            bool ok = cudaStreamBeginCapture(B->gstream, cudaStreamCaptureModeThreadLocal) == cudaSuccess;
+            long long cnt = 0;
+            if (ok) {
+                const int rc = b_cycle(B, j0, j1, B->gstream);
+                cnt = g_launches.load() - n0;
+                const cudaError_t ec = cudaStreamEndCapture(B->gstream, &graph);
+                ok = rc >= 0 && ec == cudaSuccess && graph &&
+                     cudaGraphInstantiate(&B->cycle_exec[c], graph, 0) == cudaSuccess;
+            }
+            if (graph) cudaGraphDestroy(graph);
+            g_launches.store(n0);
+            if (!ok) {                   // nothing ran during the capture: launch directly from now on
+                cudaGetLastError();
+                B->cycle_exec[c] = nullptr;
+                B->graph_off = true;
+                use_graph = false;
+            } else {
+                B->cycle_launches[c] = cnt;
+            }
+        }
+        if (use_graph) {
+            RAS_CK(cudaEventRecord(B->ev_fork, st));
+            RAS_CK(cudaStreamWaitEvent(B->gstream, B->ev_fork, 0));
+            RAS_CK(cudaGraphLaunch(B->cycle_exec[c], B->gstream));
+            RAS_CK(cudaEventRecord(B->ev_join, B->gstream));
+            RAS_CK(cudaStreamWaitEvent(st, B->ev_join, 0));
+            g_launches.fetch_add(B->cycle_launches[c], std::memory_order_relaxed);
+        } else {
+            RAS_TRY(b_cycle(B, j0, j1, st));
+        }
+        if (j1 < m) {                    // any reservoir still active in this cycle?
+            RAS_CK(cudaMemcpyAsync(B->h_act, B->d_act, (size_t)B->n, cudaMemcpyDeviceToHost, st));
+            RAS_CK(cudaStreamSynchronize(st));
+            bool any = false;
+            for (int i = 0; i < B->n && !any; ++i) any = B->h_act[i] != 0;
+            if (!any) break;
+        }
+    }
     return RAS_OK;
 }
 
@@ -960,6 +983,10 @@ static int batch_create(int n, ras_problem *const *probs, ras_precond *const *pc
         return fail(rc);
     if (cudaMallocHost((void **)&B->h_out, (size_t)n * OST * sizeof(double)) != cudaSuccess) {
         B->h_out = nullptr;
+        return fail(RAS_ENOMEM);
+    }
+    if (cudaMallocHost((void **)&B->h_act, (size_t)n) != cudaSuccess) {
+        B->h_act = nullptr;
         return fail(RAS_ENOMEM);
     }
     auto up = [&](void *d, const void *h, size_t bytes) {

@@ -1091,6 +1091,7 @@ struct FacArgs {
     int cr;            // cyclic reduction (FP32, tensor cores) instead of the two-ended elimination
     const int *crs;    // its schedule
     AT *W;             // its dense couplings and products, [slot - nb][T][T]
+    int tc;            // FP32 products on the tensor cores (the handle's set-up choice)
 };
 
 // Out[r0+i][c] (=, -=) sum_e M[r0+i][uq[c][e]] uv[c][e] for a chunk of FROWS rows.
@@ -1518,12 +1519,12 @@ __global__ void __launch_bounds__(256) k_coarse_factor_batch(const FacArgs<AT> *
                                                              const unsigned char *active) {
     const int h = cta_inst[blockIdx.x];
     if (!active[h]) return;
-    // the two-ended eliminations keep the CUDA-core products; the cyclic
-    // reductions take the tensor path
+    // the handle's products on the tensor cores when its set-up chose them (FP32),
+    // as in its single factorisation
     __shared__ unsigned tmem_slot;
     __shared__ unsigned long long mbar;
     TcState tcs;
-    tc_begin<AT>(tcs, &tmem_slot, &mbar, args[h].cr != 0);
+    tc_begin<AT>(tcs, &tmem_slot, &mbar, args[h].tc != 0 || args[h].cr != 0);
     coarse_factor_body(args[h], blockIdx.x - first[h], size[h], tcs);
     tc_end<AT>(tcs);
 }
@@ -2355,7 +2356,7 @@ template <typename AT>
 static FacArgs<AT> fac_args(Coarse *c, GridBar *bar) {
     return FacArgs<AT>{(AT *)c->D, (AT *)c->C, (AT *)c->F, (AT *)c->Zs, c->lo_q, c->up_q, c->lo_n, c->up_n,
                        (const AT *)c->lo_v, (const AT *)c->up_v, c->T, c->T / TILE, c->nb, c->mid, bar, c->d_err,
-                       c->cr, c->d_crf, (AT *)c->W};
+                       c->cr, c->d_crf, (AT *)c->W, c->use_tc};
 }
 
 template <typename AT>
