@@ -1174,43 +1174,113 @@ __device__ void rows_times_up(AT *rows, const AT *M, AT *Out, const int *uq, con
     __syncthreads();
 }
 
-// out[c] = sum_e lv[e] Inv[lq[e]][c] for one row (c < T): the row's couplings are
-// staged in shared memory, then every thread keeps NB 16-byte loads of Inv rows in
-// flight (terms summed in entry order).
+constexpr int ERG = 8;     // rows of C_e per item of the gathered sparse product
+
+// Shared memory of sparse_rows_times for block size T.
+__host__ __device__ constexpr size_t edge_rows_smem(int T, size_t esz) {
+    return (size_t)(T / 32 + 32) * sizeof(int) + (size_t)ERG * ELLW * sizeof(int) +
+           (size_t)ERG * ERG * ELLW * esz + 16;
+}
+
+// out[r][c] = sum_e lv[r][e] Inv[lq[r][e]][c] for the ERG consecutive rows r of one
+// item (row-wise ELL, ELLW entries per row, ln[r] used): the rows' coupled
+// positions are merged into one sorted list U (a bitmap and its ranks), their
+// values scattered into a dense ERG x |U| block in shared memory, and every row of
+// Inv in U is read once per item for all ERG outputs (neighbouring rows couple to
+// nearly the same cells), with NB 16-byte loads in flight per thread. Terms are
+// summed in the order of U.
 template <typename AT>
-__device__ void sparse_row_times(const AT *Inv, const int *lq, const AT *lv, int nel, AT *out, int T,
-                                 unsigned char *smem) {
-    int *sq = reinterpret_cast<int *>(smem);
-    AT *sv = reinterpret_cast<AT *>(smem + ELLW * sizeof(int));
-    __syncthreads();                      // the shared memory of the previous item is free
-    for (int m = threadIdx.x; m < nel; m += blockDim.x) { sq[m] = lq[m]; sv[m] = lv[m]; }
-    __syncthreads();
-    constexpr int VEC = 16 / sizeof(AT), NB = 16;
+__device__ void sparse_rows_times(const AT *Inv, const int *lq, const AT *lv, const int *ln, AT *out, int T,
+                                  unsigned char *smem) {
+    constexpr int VEC = 16 / sizeof(AT), NB = 8;
     using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    const int nw = T / 32;
+    unsigned *bits = reinterpret_cast<unsigned *>(smem);               // [nw]
+    int *wpre = reinterpret_cast<int *>(bits + nw);                     // [32] per-lane prefix scratch
+    int *U = wpre + 32;                                                 // [ERG * ELLW]
+    AT *coef = reinterpret_cast<AT *>(                                  // [ERG][ERG * ELLW]
+        (reinterpret_cast<uintptr_t>(U + ERG * ELLW) + 15) & ~(uintptr_t)15);
+    __shared__ int s_k;
+    __syncthreads();                      // the shared memory of the previous item is free
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) bits[w] = 0u;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ERG * ELLW; t += blockDim.x) {
+        const int r = t / ELLW, e = t % ELLW;
+        if (e < ln[r]) {
+            const int q = lq[(long long)r * ELLW + e];
+            atomicOr(&bits[q >> 5], 1u << (q & 31));
+        }
+    }
+    __syncthreads();
+    if (threadIdx.x < 32) {               // exclusive prefix of the words' bit counts
+        const int lane = threadIdx.x, per = (nw + 31) / 32;
+        int c = 0;
+        for (int w = lane * per; w < min(nw, lane * per + per); ++w) c += __popc(bits[w]);
+        int inc = c;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const int v = __shfl_up_sync(0xffffffffu, inc, o);
+            if (lane >= o) inc += v;
+        }
+        wpre[lane] = inc - c;
+        if (lane == 31) s_k = inc;
+    }
+    __syncthreads();
+    const int K = s_k, per = (nw + 31) / 32;
+    auto rank = [&](int q) {              // position of q in U
+        const int w = q >> 5, l = w / per;
+        int rk = wpre[l];
+        for (int x = l * per; x < w; ++x) rk += __popc(bits[x]);
+        return rk + __popc(bits[w] & ((1u << (q & 31)) - 1u));
+    };
+    for (int w = threadIdx.x; w < nw; w += blockDim.x) {
+        unsigned m = bits[w];
+        while (m) {
+            const int b = __ffs(m) - 1;
+            m &= m - 1;
+            const int q = 32 * w + b;
+            U[rank(q)] = q;
+        }
+    }
+    for (int t = threadIdx.x; t < ERG * K; t += blockDim.x) coef[t] = (AT)0;
+    __syncthreads();
+    for (int t = threadIdx.x; t < ERG * ELLW; t += blockDim.x) {
+        const int r = t / ELLW, e = t % ELLW;
+        if (e < ln[r]) coef[r * K + rank(lq[(long long)r * ELLW + e])] = lv[(long long)r * ELLW + e];
+    }
+    __syncthreads();
     const int ng = T / VEC;
     for (int g = threadIdx.x; g < ng; g += blockDim.x) {
-        AT acc[VEC];
+        AT acc[ERG][VEC];
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) acc[q] = (AT)0;
-        for (int e0 = 0; e0 < nel; e0 += NB) {
+        for (int r = 0; r < ERG; ++r)
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) acc[r][q] = (AT)0;
+        for (int k0 = 0; k0 < K; k0 += NB) {
             V16 buf[NB];
 #pragma unroll
             for (int m = 0; m < NB; ++m)
-                if (e0 + m < nel) buf[m] = __ldcg(reinterpret_cast<const V16 *>(Inv + (long long)sq[e0 + m] * T) + g);
+                if (k0 + m < K) buf[m] = __ldcg(reinterpret_cast<const V16 *>(Inv + (long long)U[k0 + m] * T) + g);
 #pragma unroll
             for (int m = 0; m < NB; ++m)
-                if (e0 + m < nel) {
-                    const AT w = sv[e0 + m];
+                if (k0 + m < K) {
                     const AT *v = reinterpret_cast<const AT *>(&buf[m]);
 #pragma unroll
-                    for (int q = 0; q < VEC; ++q) acc[q] += w * v[q];
+                    for (int r = 0; r < ERG; ++r) {
+                        const AT w = coef[r * K + k0 + m];
+#pragma unroll
+                        for (int q = 0; q < VEC; ++q) acc[r][q] += w * v[q];
+                    }
                 }
         }
-        V16 o;
-        AT *ov = reinterpret_cast<AT *>(&o);
 #pragma unroll
-        for (int q = 0; q < VEC; ++q) ov[q] = acc[q];
-        reinterpret_cast<V16 *>(out)[g] = o;
+        for (int r = 0; r < ERG; ++r) {
+            V16 o;
+            AT *ov = reinterpret_cast<AT *>(&o);
+#pragma unroll
+            for (int q = 0; q < VEC; ++q) ov[q] = acc[r][q];
+            reinterpret_cast<V16 *>(out + (long long)r * T)[g] = o;
+        }
     }
     __syncthreads();                      // the next item may overwrite the staged couplings
 }
@@ -1441,16 +1511,16 @@ __device__ __forceinline__ void coarse_factor_body(const FacArgs<AT> &a, int b, 
         if (s == nsteps) break;
         const long long ell = (long long)T * ELLW;
         const int nchunk = T / FROWS;
-        const int nC = T;                                   // C_e: one item per row
+        const int nC = T / ERG;                             // C_e: ERG rows per item
         const int nE = nC + nchunk;
         for (int it2 = b; it2 < ne * nE; it2 += G) {
             const int e = edg[it2 / nE], it = it2 % nE;
             const AT *Inv = a.D + edge_pivot(e, mid) * bsz;
-            if (it < nC) {                                  // C_e row = A(target, pivot) row * Inv
-                const int r = it;
-                const long long at = e * ell + (long long)r * ELLW;
-                sparse_row_times(Inv, a.lo_q + at, a.lo_v + at, a.lo_n[(long long)e * T + r],
-                                 a.C + e * bsz + (long long)r * T, T, smem_raw);
+            if (it < nC) {                                  // C_e rows = A(target, pivot) rows * Inv
+                const int r0 = it * ERG;
+                const long long at = e * ell + (long long)r0 * ELLW;
+                sparse_rows_times(Inv, a.lo_q + at, a.lo_v + at, a.lo_n + (long long)e * T + r0,
+                                  a.C + e * bsz + (long long)r0 * T, T, smem_raw);
             } else {                                        // F_e = Inv A(pivot, target)
                 rows_times_up(rows, Inv, a.F + e * bsz, a.up_q + e * ell, a.up_v + e * ell,
                               a.up_n + (long long)e * T, T, (it - nC) * FROWS, false);
@@ -2127,6 +2197,7 @@ static int configure_t(Coarse *c) {
         if (c->rap125_smem <= (size_t)big || c->rap125_ng == 1) break;
     }
     c->fac_smem = std::max(sizeof(TileSmem<AT>), sizeof(AT) * (size_t)FROWS * c->T);
+    c->fac_smem = std::max(c->fac_smem, edge_rows_smem(c->T, sizeof(AT)));
     // FP32: trailing updates of the inverses on the tensor cores (RAS_COARSE_TC=0: CUDA cores)
     c->use_tc = sizeof(AT) == 4 ? 1 : 0;
     if (const char *e = getenv("RAS_COARSE_TC")) c->use_tc = c->use_tc && atoi(e) != 0;
