@@ -515,6 +515,57 @@ __device__ __forceinline__ bool invert4(AT P[4][4]) {
     return ok;
 }
 
+// a[u][v] (rows tr + u, columns tc + v of a tile) -= X Y for 64 x 64 tiles X, Y of
+// row stride ld, staged in shared memory: the arithmetic of subtile_product (the same
+// k order, out = prev + (-1) acc), so that a tile update followed by its inverse needs
+// no store and reload of the tile.
+template <typename AT>
+__device__ __forceinline__ void tile_pre_update(TileSmem<AT> &sm, AT (&a)[4][4], const AT *X, const AT *Y,
+                                                int ld, int tr, int tc) {
+    constexpr int VEC = 16 / sizeof(AT);
+    using V16 = typename std::conditional<sizeof(AT) == 4, float4, double2>::type;
+    constexpr int NV = TILE * TILE / VEC / 256;
+    V16 bx[NV], by[NV];
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        const int e = threadIdx.x + 256 * m, r = e / (TILE / VEC), k = (e % (TILE / VEC)) * VEC;
+        bx[m] = __ldcg(reinterpret_cast<const V16 *>(X + (long long)r * ld + k));
+        by[m] = __ldcg(reinterpret_cast<const V16 *>(Y + (long long)r * ld + k));
+    }
+#pragma unroll
+    for (int m = 0; m < NV; ++m) {
+        const int e = threadIdx.x + 256 * m, r = e / (TILE / VEC), k = (e % (TILE / VEC)) * VEC;
+        const AT *vx = reinterpret_cast<const AT *>(&bx[m]), *vy = reinterpret_cast<const AT *>(&by[m]);
+#pragma unroll
+        for (int q = 0; q < VEC; ++q) {
+            sm.X[r][k + q] = vx[q];
+            sm.Y[r][k + q] = vy[q];
+        }
+    }
+    __syncthreads();
+    AT acc[4][4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) acc[u][v] = 0;
+#pragma unroll 4
+    for (int k = 0; k < TILE; ++k) {
+        AT xa[4], yb[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) xa[u] = sm.X[tr + u][k];
+#pragma unroll
+        for (int v = 0; v < 4; ++v) yb[v] = sm.Y[k][tc + v];
+#pragma unroll
+        for (int u = 0; u < 4; ++u)
+#pragma unroll
+            for (int v = 0; v < 4; ++v) acc[u][v] += xa[u] * yb[v];
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+#pragma unroll
+        for (int v = 0; v < 4; ++v) a[u][v] = a[u][v] + (AT)(-1) * acc[u][v];
+}
+
 // In-place Gauss-Jordan inverse of tile (ti, ti) of M without pivoting, four
 // pivots per step (block column K = kb..kb+3, Pi = A_KK^{-1}):
 //     A_Kj <- Pi A_Kj,  A_ij <- A_ij - A_iK (Pi A_Kj),  A_iK <- -A_iK Pi,  A_KK <- Pi.
@@ -525,7 +576,8 @@ __device__ __forceinline__ bool invert4(AT P[4][4]) {
 // own update is done and publishes Pi for the next step (barrier). The 4 x 4
 // inverse takes approximate reciprocals (FP32 preconditioner factors).
 template <typename AT>
-__device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
+__device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err, const AT *X = nullptr,
+                               const AT *Y = nullptr) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
     AT a[4][4];
 #pragma unroll
@@ -533,6 +585,7 @@ __device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err
 #pragma unroll
         for (int v = 0; v < 4; ++v)
             a[u][v] = __ldcg(M + (long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v);
+    if (X) tile_pre_update(sm, a, X, Y, ld, tr, tc);   // the tile's last update first
     auto invert_publish = [&](int par) {
         AT P[4][4];
 #pragma unroll
@@ -627,7 +680,8 @@ __device__ void tile_invert_b4(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err
 // Scalar Gauss-Jordan (one pivot per barrier): fewest operations, used for
 // FP64 where the arithmetic pipe, not the barrier, bounds the tile inverse.
 template <typename AT>
-__device__ void tile_invert_s(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
+__device__ void tile_invert_s(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err, const AT *X = nullptr,
+                              const AT *Y = nullptr) {
     const int tr = (threadIdx.x / 16) * 4, tc = (threadIdx.x % 16) * 4;
     AT a[4][4];
 #pragma unroll
@@ -635,6 +689,7 @@ __device__ void tile_invert_s(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err)
 #pragma unroll
         for (int v = 0; v < 4; ++v)
             a[u][v] = __ldcg(M + (long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v);
+    if (X) tile_pre_update(sm, a, X, Y, ld, tr, tc);   // the tile's last update first
     for (int kk = 0; kk < TILE; ++kk) {
         const int par = kk & 1;
         if (tr <= kk && kk < tr + 4) {
@@ -677,10 +732,12 @@ __device__ void tile_invert_s(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err)
             M[(long long)(ti * TILE + tr + u) * ld + ti * TILE + tc + v] = a[u][v];
 }
 
+// (X, Y: tiles whose product the tile receives first, tile -= X Y; null: none)
 template <typename AT>
-__device__ __forceinline__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err) {
-    if constexpr (sizeof(AT) == 8) tile_invert_s(sm, M, ld, ti, err);
-    else tile_invert_b4(sm, M, ld, ti, err);
+__device__ __forceinline__ void tile_invert(TileSmem<AT> &sm, AT *M, int ld, int ti, int *err,
+                                            const AT *X = nullptr, const AT *Y = nullptr) {
+    if constexpr (sizeof(AT) == 8) tile_invert_s(sm, M, ld, ti, err, X, Y);
+    else tile_invert_b4(sm, M, ld, ti, err, X, Y);
 }
 
 // Sub-tile product: rows [r0, r0 + RR) and columns [c0, c0 + CC) of
@@ -1357,10 +1414,10 @@ __device__ __forceinline__ bool invert_blocks(const FacArgs<AT> &a, TileSmem<AT>
                 }
             }
         };
-        auto special = [&](int c) {
-            update(c, dpiv);
-            __syncthreads();
-            tile_invert(ts, a.D + blk[c] * bsz, T, p + 1, a.err);
+        auto special = [&](int c) {         // tile (p+1, p+1) -= D_{p+1,p} D_{p,p+1}, then inverted
+            AT *Dk = a.D + blk[c] * bsz;
+            tile_invert(ts, Dk, T, p + 1, a.err, Dk + (long long)(p + 1) * TILE * T + p * TILE,
+                        Dk + (long long)p * TILE * T + (p + 1) * TILE);
         };
         if (nxt && own) {
             if (b < nblk) special(b);
