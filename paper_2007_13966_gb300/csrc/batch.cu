@@ -1,10 +1,12 @@
 // Many independent reservoirs advanced together on one GPU: a batched inexact
 // Newton step (Section 2) whose FGMRES iterations run each operation for every
 // reservoir in one launch -- the left-RAS subdomain solves of all reservoirs'
-// boxes (Eq. equ:as-left), their 7-point operators, the Arnoldi dot products and
-// updates -- while the scalar logic of each reservoir (Givens rotations, stop
-// tests, cubic backtracking) stays on the host. One host synchronisation per
-// Arnoldi step serves the whole batch. With two-level V-cycle preconditioners
+// boxes (Eq. equ:as-left; a persistent kernel over a largest-first work queue),
+// their 7-point operators, the Arnoldi dot products and updates. Each reservoir's
+// Arnoldi scalars (Hessenberg column, Givens rotations, residual estimate, stop
+// test) are updated on the device, so a restart cycle replays as CUDA graphs of a
+// few Arnoldi steps with the host reading the mask only between them; the cubic
+// backtracking stays on the host. With two-level V-cycle preconditioners
 // (Eq. equ:v-cycle) the fine-level solves and residuals are batched the same way,
 // the exact coarse corrections of all reservoirs run in one cooperative launch (a
 // group of CTAs and a barrier word per reservoir), and their coarse block

@@ -24,6 +24,10 @@
 // The factorisation and the solve each run as ONE cooperative persistent
 // kernel whose phases are separated by a grid barrier; the barrier gives up
 // after a bounded number of polls and reports RAS_ETIMEOUT instead of hanging.
+// The solve of a single handle hands the prolongation z (+)= P x to a separate
+// full-occupancy kernel (k_coarse_prolong) that reads the coarse solution in
+// natural order; FP32 handles may take the cyclic reduction of the block
+// tridiagonal system instead of the two-ended elimination (RAS_COARSE_CR=1).
 #include "precond.cuh"
 
 #include <algorithm>
