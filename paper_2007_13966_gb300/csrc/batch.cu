@@ -28,6 +28,7 @@ namespace ras {
 constexpr int BCH = 2048;               // cells per CTA of the batched vector kernels
 constexpr int OST = 2 * MAX_MDOT + 8;   // device results per reservoir
 constexpr int CYC_CHUNK = 2;            // Arnoldi steps per replayed graph (mask read between chunks)
+constexpr int NPOOL = 8;                // streams for independent per-reservoir launches
 
 struct BOp {                    // one reservoir's 7-point operator
     const double *c[7];
@@ -325,6 +326,10 @@ struct ras_batch {
     bool graph_off = false;                  // capture failed or disabled: direct launches
     cudaStream_t gstream = nullptr;          // the graph's own stream (joined to the caller's by events)
     cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
+    // streams for the independent per-reservoir launches (Galerkin products and
+    // block assembly, residual evaluations), forked from and joined to the caller's
+    cudaStream_t pool[NPOOL] = {};
+    cudaEvent_t pool_fork_ev = nullptr, pool_join_ev[NPOOL] = {};
     // Krylov and batch vectors
     int m = 0;
     double *V = nullptr, *Z = nullptr, *w = nullptr, *r = nullptr, *b = nullptr, *x = nullptr,
@@ -349,7 +354,36 @@ static void batch_free(ras_batch *B) {
     if (B->ev_fork) cudaEventDestroy(B->ev_fork);
     if (B->ev_join) cudaEventDestroy(B->ev_join);
     if (B->gstream) cudaStreamDestroy(B->gstream);
+    if (B->pool_fork_ev) cudaEventDestroy(B->pool_fork_ev);
+    for (int k = 0; k < NPOOL; ++k) {
+        if (B->pool_join_ev[k]) cudaEventDestroy(B->pool_join_ev[k]);
+        if (B->pool[k]) cudaStreamDestroy(B->pool[k]);
+    }
     delete B;
+}
+
+// Fork: every pool stream waits for the work issued so far on st (streams and
+// events made on first use). pool_stream(B, q) is the stream of the q-th
+// reservoir's launches; join: st waits for everything issued on the pool.
+static int pool_fork(ras_batch *B, cudaStream_t st) {
+    if (!B->pool_fork_ev) {
+        if (cudaEventCreateWithFlags(&B->pool_fork_ev, cudaEventDisableTiming) != cudaSuccess) return RAS_ECUDA;
+        for (int k = 0; k < NPOOL; ++k)
+            if (cudaStreamCreateWithFlags(&B->pool[k], cudaStreamNonBlocking) != cudaSuccess ||
+                cudaEventCreateWithFlags(&B->pool_join_ev[k], cudaEventDisableTiming) != cudaSuccess)
+                return RAS_ECUDA;
+    }
+    RAS_CK(cudaEventRecord(B->pool_fork_ev, st));
+    for (int k = 0; k < NPOOL; ++k) RAS_CK(cudaStreamWaitEvent(B->pool[k], B->pool_fork_ev, 0));
+    return RAS_OK;
+}
+static cudaStream_t pool_stream(ras_batch *B, int q) { return B->pool[q % NPOOL]; }
+static int pool_join(ras_batch *B, cudaStream_t st) {
+    for (int k = 0; k < NPOOL; ++k) {
+        RAS_CK(cudaEventRecord(B->pool_join_ev[k], B->pool[k]));
+        RAS_CK(cudaStreamWaitEvent(st, B->pool_join_ev[k], 0));
+    }
+    return RAS_OK;
 }
 
 static int upload_mask(ras_batch *B, cudaStream_t st) {
@@ -768,9 +802,11 @@ static int b_factor(ras_batch *B, const std::vector<int> &cur, const std::vector
     RAS_TRY(upload_mask(B, st));
     RAS_TRY(ras1_factor_batch(B->d_fp, B->d_box_inst, B->d_box_local, B->d_act, B->nbox, B->prec, fblock, fsmem,
                               st));
-    if (B->twolevel) {
-        for (int i = 0; i < n; ++i)
-            if (live[i]) RAS_TRY(coarse_factor_prepare(B->pc[i]->coarse, B->pc[i]->A, st));
+    if (B->twolevel) {   // each reservoir's Galerkin product and block assembly on a pool stream
+        RAS_TRY(pool_fork(B, st));
+        for (int i = 0, q = 0; i < n; ++i)
+            if (live[i]) RAS_TRY(coarse_factor_prepare(B->pc[i]->coarse, B->pc[i]->A, pool_stream(B, q++)));
+        RAS_TRY(pool_join(B, st));
         if (B->cb) {
             RAS_TRY(coarse_factor_batch(B->cb, B->d_act, st));
         } else {
@@ -788,14 +824,17 @@ static int bnewton(ras_batch *B, double *const *p, const double *const *pl, cons
                    cudaStream_t st) {
     const int n = B->n;
     std::vector<int> cur(n, 0), k(n, 0), nres(n, 0), lin_total(n, 0), status(n, RAS_OK);
+    RAS_TRY(pool_fork(B, st));   // the reservoirs' residual evaluations on the pool streams
     for (int i = 0; i < n; ++i) {
         ras_problem *P = B->P[i];
+        const cudaStream_t sq = pool_stream(B, i);
         RAS_TRY(ensure_newton(P));
-        RAS_TRY(vec_copy(P->nX[0], p[i], P->N, st));
+        RAS_TRY(vec_copy(P->nX[0], p[i], P->N, sq));
         RAS_TRY(residual_eval_impl(P, P->nX[0], pl[i], order == 2 ? plm1[i] : nullptr, dt[i], order, P->nF[0],
-                                   P->nJ[0], st));
+                                   P->nJ[0], sq));
         ++nres[i];
     }
+    RAS_TRY(pool_join(B, st));
     std::vector<unsigned char> all(n, 1), live(n, 0);
     std::vector<const double *> vecs(n);
     std::vector<double> fnorm(n, 0.0), f0(n, 0.0), tol(n, 0.0), ft(n, 0.0);
@@ -859,17 +898,20 @@ static int bnewton(ras_batch *B, double *const *p, const double *const *pl, cons
             bool anys = false;
             for (int i = 0; i < n; ++i) anys = anys || search[i];
             if (!anys) break;
-            for (int i = 0; i < n; ++i) {
+            RAS_TRY(pool_fork(B, st));   // the trial residuals on the pool streams
+            for (int i = 0, q = 0; i < n; ++i) {
                 if (!search[i]) continue;
                 ras_problem *P = B->P[i];
                 const int nxt = 1 - cur[i];
-                RAS_TRY(vec_copy(P->nX[nxt], P->nX[cur[i]], P->N, st));
-                RAS_TRY(vec_axpby(P->nX[nxt], lam[i], B->x + B->off[i], 1.0, P->N, st));
+                const cudaStream_t sq = pool_stream(B, q++);
+                RAS_TRY(vec_copy(P->nX[nxt], P->nX[cur[i]], P->N, sq));
+                RAS_TRY(vec_axpby(P->nX[nxt], lam[i], B->x + B->off[i], 1.0, P->N, sq));
                 RAS_TRY(residual_eval_impl(P, P->nX[nxt], pl[i], order == 2 ? plm1[i] : nullptr, dt[i], order,
-                                           P->nF[nxt], P->nJ[nxt], st));
+                                           P->nF[nxt], P->nJ[nxt], sq));
                 ++nres[i];
                 vecs[i] = P->nF[nxt];
             }
+            RAS_TRY(pool_join(B, st));
             RAS_TRY(b_norms_of(B, vecs, search, ft, st));
             for (int i = 0; i < n; ++i) {
                 if (!search[i]) continue;
