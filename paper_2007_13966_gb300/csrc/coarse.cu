@@ -901,6 +901,15 @@ __device__ __forceinline__ void tc_put(unsigned char *h, unsigned char *l, int o
 // row-major block M. All 256 threads; the CTA's smem overlay is free on entry.
 __device__ void tc_pair_update(TcSmem &ts, TcState &st, float *M, int T, int i0, int p, int j, int *err) {
     const int tid = threadIdx.x;
+    // the updated tiles (rows 64 i0 .. + 127, column tile j) are read together with the
+    // operands: no other item of the phase writes them, and they overlap neither X
+    // (column tile p) nor Y (row tile p); warp w: rows 32 (w % 4) + lane, columns
+    // 32 (w / 4) .. + 31
+    const int w = tid >> 5, lane = tid & 31, wq = w & 3, wh = w >> 2;
+    float *out = M + (long long)(i0 * TILE + 32 * wq + lane) * T + j * TILE + 32 * wh;
+    float4 prev[8];
+#pragma unroll
+    for (int u = 0; u < 8; ++u) prev[u] = __ldcg(reinterpret_cast<const float4 *>(out) + u);
     {   // X: rows 64 i0 .. + 127, columns 64 p .. + 63; thread t: row t / 2, k half (t & 1)
         const int r = tid >> 1, k0 = (tid & 1) * 32;
         const float4 *src = reinterpret_cast<const float4 *>(M + (long long)(i0 * TILE + r) * T + p * TILE + k0);
@@ -968,8 +977,7 @@ __device__ void tc_pair_update(TcSmem &ts, TcState &st, float *M, int T, int i0,
         ++st.phase;
     }
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
-    {   // warp w: rows 32 (w % 4) + lane, columns 32 (w / 4) .. + 31
-        const int w = tid >> 5, lane = tid & 31, q = w & 3, h = w >> 2;
+    {
         unsigned r[32];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
@@ -980,12 +988,8 @@ __device__ void tc_pair_update(TcSmem &ts, TcState &st, float *M, int T, int i0,
               "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]),
               "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]),
               "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
-            : "r"(st.tmem + ((unsigned)(32 * q) << 16) + 32u * h));
+            : "r"(st.tmem + ((unsigned)(32 * wq) << 16) + 32u * wh));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        float *out = M + (long long)(i0 * TILE + 32 * q + lane) * T + j * TILE + 32 * h;
-        float4 prev[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) prev[u] = __ldcg(reinterpret_cast<const float4 *>(out) + u);
 #pragma unroll
         for (int u = 0; u < 8; ++u) {
             float4 o = prev[u];
@@ -2680,8 +2684,16 @@ static int batch_setup_t(Coarse *const *cs, int n, CoarseBatch *cb) {
     // The block elimination is a chain of latency-bound panel steps whose trailing
     // work needs CTAs: handles are factored in waves (largest first) of at most
     // total / FWAVE_CTAS handles, so every handle gets at least FWAVE_CTAS CTAs.
+    // On 64 reservoirs of 32^3 to 96^3 cells 16 is the best of 1 to 48: fewer
+    // leave each handle's trailing updates too few CTAs, more make more waves,
+    // each paying its handles' pivot chains.
     const int ftotal = sms * std::min(bf, 2);
-    const int per = std::max(1, ftotal / FWAVE_CTAS);
+    int wave_ctas = FWAVE_CTAS;
+    if (const char *e = getenv("RAS_COARSE_WAVE_CTAS")) {   // tuning knob
+        const int v = atoi(e);
+        if (v >= 1) wave_ctas = v;
+    }
+    const int per = std::max(1, ftotal / wave_ctas);
     std::vector<int> order(n);
     for (int i = 0; i < n; ++i) order[i] = i;
     std::stable_sort(order.begin(), order.end(), [&](int x, int y) { return wf[x] > wf[y]; });

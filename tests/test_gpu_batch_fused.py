@@ -119,6 +119,44 @@ def test_newton_steps_match_single_and_oracle(ras, nlevels):
         plm1, pl = pl, ps
 
 
+def _two_steps(ras, env):
+    """Two batched implicit steps (BDF1, BDF2) of the three reservoirs, two-level FP32,
+    with the batch handle created under env."""
+    import os
+    res = reservoirs()
+    probs = [ras.Problem(r) for r in res]
+    pcs = [make_pc(ras, gp, 32, 2) for gp in probs]
+    old = {k: os.environ.get(k) for k in env}
+    os.environ.update(env)
+    try:
+        bs = ras.BatchSolver(probs, pcs)
+    finally:
+        for k, v in old.items():
+            if v is None:
+                del os.environ[k]
+            else:
+                os.environ[k] = v
+    pl = [torch.full((r.grid.n,), r.p0, dtype=torch.float64, device="cuda") for r in res]
+    plm1 = [p.clone() for p in pl]
+    for step in range(2):
+        order = 1 if step == 0 else 2
+        ps = [p.clone() for p in pl]
+        st, _ = bs.newton_step(ps, pl, plm1 if order == 2 else None, [r.dt for r in res], order)
+        assert st == 0
+        plm1, pl = pl, ps
+    return pl
+
+
+def test_elimination_waves_do_not_change_bits(ras):
+    """The batched block eliminations give the same states whether the reservoirs share
+    one cooperative launch (the default for three reservoirs) or each takes a launch of
+    its own with every CTA (RAS_COARSE_WAVE_CTAS larger than the grid)."""
+    a = _two_steps(ras, {})
+    b = _two_steps(ras, {"RAS_COARSE_WAVE_CTAS": "100000"})
+    for x, y in zip(a, b):
+        assert torch.equal(x, y)
+
+
 def test_batch_handle_checks(ras):
     res = reservoirs()[:2]
     probs = [ras.Problem(r) for r in res]

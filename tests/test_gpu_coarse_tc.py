@@ -5,7 +5,7 @@ the coarse correction agrees with the CUDA-core form to FP32 rounding and with
 the FP64 oracle to the FP32 tolerance, on block sizes with several 128-row tile
 pairs and an odd tile count. The same for the cyclic reduction of the block
 tridiagonal system (RAS_COARSE_CR=1 at set-up: its dense products on tcgen05),
-single and batched."""
+single and batched. The elimination's bits do not depend on its grid size."""
 import os
 
 import numpy as np
@@ -78,6 +78,36 @@ def test_tensor_core_inverses_match(ras, dims, parts, ov, ratios):
     ref = ml.TwoLevel(A, schwarz.Schwarz(A, dims, parts, ov), P, ml.DenseCoarse(ml.galerkin(A, P)),
                       ml.COARSE_ONLY)(host(r))
     assert rel_err(host(z[True]), ref) < 5e-3
+
+
+@pytest.mark.parametrize("prec", [32, 64])
+@pytest.mark.parametrize("dims", [(24, 20, 28), (40, 24, 24)])   # 7 blocks of T = 192, 10 of T = 320
+def test_factor_grid_size_does_not_change_bits(ras, prec, dims):
+    """The block elimination strides its items over the CTAs the cooperative launch
+    has: 1, 2 and 3 CTAs (no more than the two chains, so the next pivot tiles are
+    inverted by CTAs that also take trailing updates) give the default grid's bits,
+    on the tensor path (FP32) and the CUDA-core path (FP64)."""
+    nx, ny, nz = dims
+    res = syn.small_3d(nx, ny, nz, seed=8)
+    prob = disc.Problem(res)
+    p = syn.random_pressure(res, 8)
+    _, J = disc.residual(prob, p, 0.98 * p, 0.97 * p, res.dt, 2, want_jac=True)
+    gp = ras.Problem(res)
+    Jd = j_to_dev(J)
+    r = dev(syn.random_vector(res.grid.n, 4))
+    outs = []
+    for ctas in (None, "1", "2", "3"):
+        env = {} if ctas is None else {"RAS_COARSE_FACTOR_CTAS": ctas}
+        pc = _with_env(env, lambda: ras.Precond(gp, (2, 2, 2), 1, factor_prec=prec, nlevels=2,
+                                                coarsen=(2, 2, 2), mlevel_type=4, coarse_prec=prec))
+        pc.factor(Jd)
+        z = torch.zeros_like(r)
+        pc.apply(r, z)
+        outs.append(z)
+        del pc
+    assert torch.isfinite(outs[0]).all()
+    for z in outs[1:]:
+        assert torch.equal(z, outs[0])
 
 
 @pytest.mark.parametrize("dims,parts,ov,ratios", [
