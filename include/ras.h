@@ -113,7 +113,13 @@ typedef struct {
                               solves; 16 = BF16-stored factors, FP32 solves          */
     int nlevels;           /* 1 = one-level; 2 = two-level (Eq. equ:v-cycle);
                               3 = three-level V-cycle (Algorithm 1, mu = nu = 1)     */
-    int coarsen[3];        /* coarse:fine ratio per axis of each coarsening (Table 7) */
+    int coarsen[3];        /* coarse:fine ratio per axis of each coarsening (Table 7:
+                              2 to 16). A coarse cell's interpolation support is
+                              about 2 r fine cells per axis; the Galerkin product
+                              stages it in shared memory whole or in slabs of
+                              z-planes, and set-up returns RAS_EINVAL when even one
+                              x-y plane of it does not fit (x and y ratios beyond
+                              about 25 with FP64 coarse arithmetic, 31 with FP32) */
     int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second; 1 = nearest
                               coarse centre, Eq. equ:inter-frist (order 3 couples
                               coarse cells three apart: not supported)            */

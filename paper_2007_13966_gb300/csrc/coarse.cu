@@ -79,6 +79,8 @@ struct Coarse {
     GridBar *d_bar = nullptr;
     size_t esz = 8;
     size_t rap_smem = 0, rap125_smem = 0, fac_smem = 0, sol_smem = 0;
+    int rap_zs = 0;                 // 0: k_rap (whole support boxes); > 0: k_rap_slab, slabs of rap_zs planes
+    int need125 = 0;                // the handle's operator is 125-point (three levels): k_rap125 must fit
     int rap125_ng = 25;             // offsets staged per round in k_rap125
     int fac_grid = 0, sol_grid = 0;
     int sol_npf = 0;                // rows per warp prefetched by the solve
@@ -126,27 +128,11 @@ struct RapDims {
     int wx, wy, wz;   // maximum support widths (shared-memory capacity)
 };
 
-// The three sum-factorised contractions of one fine-operator term for one
-// coarse row (z, then y, then x):
-//   U[dz][ay][ax] = sum_az Wz[dz][az] A[az][ay][ax],
-//   V[dz][dy][ax] = sum_ay Wy[dy][ay] U[dz][ay][ax],
-//   out[dz][dy][dx] += sum_ax Wx[dx][ax] V[dz][dy][ax].
-// uix / vix hold the index decomposition of the first two passes (computed once
-// per coarse row: dz << 16 | ay * WX + ax, and dz << 16 | dy << 8 | ax).
+// The second and third contractions (y, then x) of a term whose U is complete.
 template <typename AT>
-__device__ __forceinline__ void rap_term(const AT *Ab, const AT *Wz, const AT *Wy, const AT *Wx,
-                                         int dstride, AT *U, AT *V, AT *out, const int *uix,
-                                         const int *vix, int wx, int wy, int wz, int WX, int WY) {
-    const int nU = 5 * wy * wx, nV = 25 * wx, plane = WY * WX;
-    for (int e = threadIdx.x; e < nU; e += blockDim.x) {
-        const int code = uix[e];
-        const int dz = code >> 16, ab = code & 0xffff;
-        const AT *wz_ = Wz + dz * dstride;
-        AT acc = 0;
-        for (int az = 0; az < wz; ++az) acc += wz_[az] * Ab[az * plane + ab];
-        U[dz * plane + ab] = acc;
-    }
-    __syncthreads();
+__device__ __forceinline__ void rap_yx(const AT *Wy, const AT *Wx, int dstride, const AT *U, AT *V, AT *out,
+                                       const int *vix, int wx, int wy, int WX, int WY) {
+    const int nV = 25 * wx, plane = WY * WX;
     for (int e = threadIdx.x; e < nV; e += blockDim.x) {
         const int code = vix[e];
         const int dz = code >> 16, dy = (code >> 8) & 0xff, ax = code & 0xff;
@@ -166,6 +152,30 @@ __device__ __forceinline__ void rap_term(const AT *Ab, const AT *Wz, const AT *W
         out[e] += acc;
     }
     __syncthreads();
+}
+
+// The three sum-factorised contractions of one fine-operator term for one
+// coarse row (z, then y, then x):
+//   U[dz][ay][ax] = sum_az Wz[dz][az] A[az][ay][ax],
+//   V[dz][dy][ax] = sum_ay Wy[dy][ay] U[dz][ay][ax],
+//   out[dz][dy][dx] += sum_ax Wx[dx][ax] V[dz][dy][ax].
+// uix / vix hold the index decomposition of the first two passes (computed once
+// per coarse row: dz << 16 | ay * WX + ax, and dz << 16 | dy << 8 | ax).
+template <typename AT>
+__device__ __forceinline__ void rap_term(const AT *Ab, const AT *Wz, const AT *Wy, const AT *Wx,
+                                         int dstride, AT *U, AT *V, AT *out, const int *uix,
+                                         const int *vix, int wx, int wy, int wz, int WX, int WY) {
+    const int nU = 5 * wy * wx, plane = WY * WX;
+    for (int e = threadIdx.x; e < nU; e += blockDim.x) {
+        const int code = uix[e];
+        const int dz = code >> 16, ab = code & 0xffff;
+        const AT *wz_ = Wz + dz * dstride;
+        AT acc = 0;
+        for (int az = 0; az < wz; ++az) acc += wz_[az] * Ab[az * plane + ab];
+        U[dz * plane + ab] = acc;
+    }
+    __syncthreads();
+    rap_yx(Wy, Wx, dstride, U, V, out, vix, wx, wy, WX, WY);
 }
 
 // the index tables of rap_term for a coarse row with supports wx, wy
@@ -241,6 +251,110 @@ __global__ void __launch_bounds__(256) k_rap(Stencil7 A, Interp P, CGeom G, RapD
         rap_term(As, Wz, Wy, Wx, 3 * WM, U, V, out, uix, vix, wx, wy, wz, WX, WY);
     }
     if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
+}
+
+// The same product for support boxes too large to stage whole (large
+// coarse-to-fine ratios: a box is 2r cells wide per axis for linear
+// interpolation): the seven terms one at a time, each term's box streamed
+// through shared memory in slabs of ZS fine planes along z. U carries the z
+// contraction from slab to slab and adds the planes in rap_term's order, in
+// the same precision, so the result has k_rap's bits.
+template <typename AT>
+__global__ void __launch_bounds__(256) k_rap_slab(Stencil7 A, Interp P, CGeom G, RapDims W, int ZS,
+                                                  AT *__restrict__ Ac) {
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    AT *sm = reinterpret_cast<AT *>(smem_raw);
+    const int WX = W.wx, WY = W.wy, WZ = W.wz;
+    const int WM = max(WX, max(WY, WZ));
+    const int plane = WY * WX;
+    AT *slab = sm;                              // [ZS][WY][WX]
+    AT *Wt = slab + ZS * plane;                 // [3][5][3][WM]
+    AT *U = Wt + 45 * WM;                       // [5][WY][WX]
+    AT *V = U + 5 * plane;                      // [25][WX]
+    AT *out = V + 25 * WX;                      // [125]
+    int *uix = reinterpret_cast<int *>(out + 128);   // [5][WY][WX]
+    int *vix = uix + 5 * plane;                      // [25][WX]
+
+    const int I = blockIdx.x;
+    const int Ic[3] = {I % G.cx, (I / G.cx) % G.cy, I / (G.cx * G.cy)};
+    const int cdim[3] = {G.cx, G.cy, G.cz};
+    const int ndim[3] = {G.nx, G.ny, G.nz};
+    const int lo[3] = {P.lo[0][Ic[0]], P.lo[1][Ic[1]], P.lo[2][Ic[2]]};
+    const int wx = P.hi[0][Ic[0]] - lo[0], wy = P.hi[1][Ic[1]] - lo[1], wz = P.hi[2][Ic[2]] - lo[2];
+    const int sbox = wx * wy, nU = 5 * wy * wx;
+    const long long nxy = (long long)G.nx * G.ny;
+    rap_tables(uix, vix, wx, wy, WX);
+    for (int e = threadIdx.x; e < 45 * WM; e += blockDim.x) {   // pair weights, as in k_rap
+        const int q = e % WM, si = (e / WM) % 3, d = (e / (3 * WM)) % 5, axis = e / (15 * WM);
+        const int wa = axis == 0 ? wx : (axis == 1 ? wy : wz);
+        double w = 0.0;
+        if (q < wa) {
+            const int a = lo[axis] + q, as = a + si - 1, J = Ic[axis] + d - 2;
+            if (J >= 0 && J < cdim[axis] && as >= 0 && as < ndim[axis])
+                w = w1(P, axis, a, Ic[axis]) * w1(P, axis, as, J);
+        }
+        Wt[e] = (AT)w;
+    }
+    if (threadIdx.x < 125) out[threadIdx.x] = 0;
+    __syncthreads();
+
+    for (int s = 0; s < 7; ++s) {
+        const int sgn = (s & 1) ? -1 : 1;
+        const int sx = (s == 1 || s == 2) ? sgn : 0;
+        const int sy = (s == 3 || s == 4) ? sgn : 0;
+        const int sz = (s == 5 || s == 6) ? sgn : 0;
+        const AT *Wz = Wt + (2 * 15) * WM + (sz + 1) * WM;
+        const AT *Wy = Wt + (1 * 15) * WM + (sy + 1) * WM;
+        const AT *Wx = Wt + (0 * 15) * WM + (sx + 1) * WM;
+        const double *src = s == 0 ? A.c[0] : s == 1 ? A.c[1] : s == 2 ? A.c[2] : s == 3 ? A.c[3]
+                          : s == 4 ? A.c[4] : s == 5 ? A.c[5] : A.c[6];   // no indexed parameter copy
+        for (int z0 = 0; z0 < wz; z0 += ZS) {
+            const int zn = min(ZS, wz - z0);
+            for (int e = threadIdx.x; e < zn * sbox; e += blockDim.x) {
+                const int ax = e % wx, ay = (e / wx) % wy, az = e / sbox;
+                const long long g = (lo[0] + ax) + (long long)G.nx * (lo[1] + ay) + nxy * (lo[2] + z0 + az);
+                slab[(az * WY + ay) * WX + ax] = (AT)src[g];
+            }
+            __syncthreads();
+            for (int e = threadIdx.x; e < nU; e += blockDim.x) {
+                const int code = uix[e];
+                const int dz = code >> 16, ab = code & 0xffff;
+                const AT *wz_ = Wz + dz * 3 * WM + z0;
+                AT acc = z0 == 0 ? (AT)0 : U[dz * plane + ab];
+                for (int az = 0; az < zn; ++az) acc += wz_[az] * slab[az * plane + ab];
+                U[dz * plane + ab] = acc;
+            }
+            __syncthreads();
+        }
+        rap_yx(Wy, Wx, 3 * WM, U, V, out, vix, wx, wy, WX, WY);
+    }
+    if (threadIdx.x < 125) Ac[(long long)threadIdx.x * G.Nc + I] = out[threadIdx.x];
+}
+
+// Shared memory of the Galerkin kernels of the 7-point operator for support
+// widths w (elements of esz bytes): k_rap (zs = 0: the seven terms' whole boxes)
+// or k_rap_slab (slabs of zs planes).
+static size_t rap_smem_of(const int w[3], int zs, size_t esz) {
+    const size_t WX = w[0], WY = w[1], WZ = w[2], WM = std::max(WX, std::max(WY, WZ));
+    const size_t box = zs == 0 ? 7 * WX * WY * WZ : (size_t)zs * WX * WY;
+    return esz * (box + 45 * WM + 5 * WY * WX + 25 * WX + 128) + sizeof(int) * (5 * WY * WX + 25 * WX);
+}
+
+// The form that fits in cap bytes: whole boxes when they fit, else the tallest
+// slab that does (RAS_RAP_SLAB=n at set-up, a test knob, asks for slabs of at
+// most n planes); RAS_EINVAL when not even one plane fits.
+static int rap_plan(const int w[3], size_t esz, size_t cap, int &zs, size_t &smem) {
+    int force = 0;
+    if (const char *e = getenv("RAS_RAP_SLAB")) force = atoi(e);
+    zs = 0;
+    smem = rap_smem_of(w, 0, esz);
+    if (force < 1 && smem <= cap) return RAS_OK;
+    for (zs = force >= 1 ? std::min(force, w[2]) : w[2]; zs >= 1; --zs) {
+        smem = rap_smem_of(w, zs, esz);
+        if (smem <= cap) return RAS_OK;
+    }
+    zs = 0;
+    return RAS_EINVAL;
 }
 
 // Galerkin product of a 125-point level operator A (the coarse operator of
@@ -2261,6 +2375,7 @@ static int configure_t(Coarse *c) {
     // minus the kernels' static shared memory
     const int big = 200 * 1024;
     RAS_CK(cudaFuncSetAttribute(k_rap<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
+    RAS_CK(cudaFuncSetAttribute(k_rap_slab<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_rap125<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_factor<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
     RAS_CK(cudaFuncSetAttribute(k_coarse_factor_batch<AT>, cudaFuncAttributeMaxDynamicSharedMemorySize, big));
@@ -2269,7 +2384,7 @@ static int configure_t(Coarse *c) {
     const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
     const int WM = std::max(WX, std::max(WY, WZ));
     const size_t tables = sizeof(int) * (size_t)(5 * WY * WX + 25 * WX);
-    c->rap_smem = sizeof(AT) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 128) + tables;
+    if (rap_plan(c->wmax, sizeof(AT), big, c->rap_zs, c->rap_smem)) return RAS_EINVAL;
     // offsets staged per round: 25 (one plane of offsets) when it fits, else fewer
     for (c->rap125_ng = 25;; c->rap125_ng = c->rap125_ng > 5 ? 5 : 1) {
         c->rap125_smem = sizeof(AT) * (size_t)(c->rap125_ng * WX * WY * WZ + 75 * WM + 5 * WY * WX +
@@ -2295,7 +2410,7 @@ static int configure_t(Coarse *c) {
     c->sol_npf = c->cr ? 0 : (sizeof(AT) == 4 ? 2 : 1);
     while (c->sol_npf > 0 && sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T > (size_t)big) --c->sol_npf;
     c->sol_smem = sizeof(AT) * (size_t)(2 + 8 * c->sol_npf) * c->T;
-    if (c->rap_smem > (size_t)big || c->rap125_smem > (size_t)big || c->fac_smem > (size_t)big ||
+    if (c->rap_smem > (size_t)big || (c->need125 && c->rap125_smem > (size_t)big) || c->fac_smem > (size_t)big ||
         c->sol_smem > (size_t)big)
         return RAS_EINVAL;
     int dev = 0, sms = 0, bf = 0, bs = 0;
@@ -2387,6 +2502,7 @@ int coarse_setup_grid(Coarse **out, int fnx, int fny, int fnz, const ras_opts &o
     c->nb = (ns + planes - 1) / planes;
     c->mid = c->nb == 1 ? 0 : (c->nb + 1) / 2;   // the two chains differ in length
     if ((long long)c->T * c->T * c->nb * c->esz > (8LL << 30)) return fail(RAS_EINVAL);
+    c->need125 = o.nlevels == 3 ? 1 : 0;
     int rc = c->prec == 64 ? configure_t<double>(c) : configure_t<float>(c);
     if (rc) return fail(rc);
     CrPlan plan;
@@ -2540,10 +2656,17 @@ static int eliminate_t(Coarse *c, cudaStream_t st) {
     return RAS_OK;
 }
 
+// the Galerkin product of the 7-point operator in the form of the handle's plan
+template <typename AT>
+static void rap_launch(const Coarse *c, int zs, size_t smem, const Stencil7 &A, AT *Ac, cudaStream_t st) {
+    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
+    if (zs == 0) k_rap<AT><<<c->Nc, 256, smem, st>>>(A, interp_of(c), geom_of(c), W, Ac);
+    else k_rap_slab<AT><<<c->Nc, 256, smem, st>>>(A, interp_of(c), geom_of(c), W, zs, Ac);
+}
+
 template <typename AT>
 static int factor_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
-    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
-    k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, (AT *)c->Ac);
+    rap_launch<AT>(c, c->rap_zs, c->rap_smem, A, (AT *)c->Ac, st);
     RAS_LAUNCHED();
     return factor_blocks_t<AT>(c, st);
 }
@@ -2563,8 +2686,7 @@ int coarse_factor(Coarse *c, const Stencil7 &A, cudaStream_t st) {
 
 template <typename AT>
 static int prepare_t(Coarse *c, const Stencil7 &A, cudaStream_t st) {
-    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
-    k_rap<AT><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, (AT *)c->Ac);
+    rap_launch<AT>(c, c->rap_zs, c->rap_smem, A, (AT *)c->Ac, st);
     RAS_LAUNCHED();
     return assemble_blocks_t<AT>(c, st);
 }
@@ -2817,6 +2939,8 @@ double coarse_bytes(const Coarse *c) {
 
 struct Transfer {
     Coarse geo;        // interpolation tables and grid sizes only (no factors)
+    int zs32 = 0;      // the FP32 Galerkin kernel's form and shared memory (geo holds FP64's)
+    size_t smem32 = 0;
 };
 
 // tc[I] = sum_a P(a, I) t[a] over the fine support box of I (FP64)
@@ -2882,14 +3006,18 @@ int transfer_setup(Transfer **out, int nx, int ny, int nz, const int ratio[3], i
         if (rc) { transfer_free(t); return rc; }
     }
     c->Nc = c->c[0] * c->c[1] * c->c[2];
-    const int WX = c->wmax[0], WY = c->wmax[1], WZ = c->wmax[2];
-    const int WM = std::max(WX, std::max(WY, WZ));
-    c->rap_smem = sizeof(double) * (size_t)(7 * WX * WY * WZ + 45 * WM + 5 * WY * WX + 25 * WX + 128) +
-                  sizeof(int) * (size_t)(5 * WY * WX + 25 * WX);
-    if (c->rap_smem > (size_t)200 * 1024) { transfer_free(t); return RAS_EINVAL; }
+    if (rap_plan(c->wmax, sizeof(double), 200 * 1024, c->rap_zs, c->rap_smem) ||
+        rap_plan(c->wmax, sizeof(float), 200 * 1024, t->zs32, t->smem32)) {
+        transfer_free(t);
+        return RAS_EINVAL;
+    }
     if (cudaFuncSetAttribute(k_rap<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
             cudaSuccess ||
         cudaFuncSetAttribute(k_rap<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_rap_slab<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(k_rap_slab<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024) !=
             cudaSuccess) {
         transfer_free(t);
         return RAS_ECUDA;
@@ -2914,17 +3042,12 @@ void transfer_dims(const Transfer *t, int c[3]) {
 
 int transfer_galerkin7(Transfer *t, const Stencil7 &A, double *Ac, float *scratch, cudaStream_t st) {
     const Coarse *c = &t->geo;
-    RapDims W{c->wmax[0], c->wmax[1], c->wmax[2]};
     if (!scratch) {
-        k_rap<double><<<c->Nc, 256, c->rap_smem, st>>>(A, interp_of(c), geom_of(c), W, Ac);
+        rap_launch<double>(c, c->rap_zs, c->rap_smem, A, Ac, st);
         RAS_LAUNCHED();
         return RAS_OK;
     }
-    const size_t smem32 = sizeof(float) * (size_t)(7 * c->wmax[0] * c->wmax[1] * c->wmax[2] +
-                                                   45 * std::max(c->wmax[0], std::max(c->wmax[1], c->wmax[2])) +
-                                                   5 * c->wmax[1] * c->wmax[0] + 25 * c->wmax[0] + 128) +
-                          sizeof(int) * (size_t)(5 * c->wmax[1] * c->wmax[0] + 25 * c->wmax[0]);
-    k_rap<float><<<c->Nc, 256, smem32, st>>>(A, interp_of(c), geom_of(c), W, scratch);
+    rap_launch<float>(c, t->zs32, t->smem32, A, scratch, st);
     RAS_LAUNCHED();
     k_widen<<<grid_of(125LL * c->Nc), 256, 0, st>>>(scratch, Ac, 125LL * c->Nc);
     RAS_LAUNCHED();
