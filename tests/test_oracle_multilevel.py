@@ -114,3 +114,37 @@ def test_coarse_only_is_weaker_than_vcycle():
         _, info = krylov.fgmres(lambda v: A @ v, T, b, rtol=1e-8, restart=30, maxit=300)
         its[kind] = info["iters"]
     assert its[ml.COARSE_ONLY] > 3 * its[ml.VCYCLE]
+
+
+def test_ratio_and_order_trends_of_table_7():
+    """Table 7's orderings on a small 2D system (V-cycle, FGMRES(30) to 1e-6): for every
+    interpolation order the iterations do not fall as the coarse-to-fine ratio grows
+    from 2 to 16; at every ratio first order needs at least as many as second order
+    and third order at most as many; every two-level count stays far below
+    one-level RAS's. (The table's slow growth for the higher orders needs its far
+    larger grids and is not asserted.)"""
+    from oracle import krylov
+    nx = ny = 64
+    res = syn.small_3d(nx, ny, 1, seed=2)
+    prob = disc.Problem(res)
+    p = syn.random_pressure(res, 2)
+    _, J = disc.residual(prob, p, 0.98 * p, 0.97 * p, 8640.0, 2, want_jac=True)
+    A = disc.jacobian_csr(res.grid, J)
+    dims = (nx, ny, 1)
+    M = schwarz.Schwarz(A, dims, (4, 4, 1), 1)
+    b = syn.random_vector(A.shape[0], 4)
+    its = {}
+    for order in (1, 2, 3):
+        for r in (2, 4, 8, 16):
+            P = ml.interpolation(dims, (r, r, 1), order)
+            T = ml.TwoLevel(A, M, P, ml.DenseCoarse(ml.galerkin(A, P)), ml.VCYCLE)
+            _, info = krylov.fgmres(lambda v: A @ v, T, b, rtol=1e-6, restart=30, maxit=500)
+            its[order, r] = info["iters"]
+    _, info = krylov.fgmres(lambda v: A @ v, M, b, rtol=1e-6, restart=30, maxit=2000)
+    one_level = info["iters"]
+    for order in (1, 2, 3):
+        seq = [its[order, r] for r in (2, 4, 8, 16)]
+        assert seq == sorted(seq), (order, seq)
+    for r in (2, 4, 8, 16):
+        assert its[1, r] >= its[2, r] >= its[3, r], (r, its)
+    assert max(its.values()) * 4 < one_level
