@@ -148,3 +148,34 @@ def test_ratio_and_order_trends_of_table_7():
     for r in (2, 4, 8, 16):
         assert its[1, r] >= its[2, r] >= its[3, r], (r, its)
     assert max(its.values()) * 4 < one_level
+
+
+def test_two_level_type_and_order_trends_of_table_6():
+    """Table 6's orderings at ratio 2 as a trend check (FGMRES(30) to 1e-6): for every
+    interpolation order V-cycle <= left-Kaskade <= right-Kaskade <= additive, the
+    V-cycle strictly below additive; for every type first order >= second >= third."""
+    from oracle import krylov
+    nx = ny = 64
+    res = syn.small_3d(nx, ny, 1, seed=2)
+    prob = disc.Problem(res)
+    p = syn.random_pressure(res, 2)
+    _, J = disc.residual(prob, p, 0.98 * p, 0.97 * p, 8640.0, 2, want_jac=True)
+    A = disc.jacobian_csr(res.grid, J)
+    dims = (nx, ny, 1)
+    M = schwarz.Schwarz(A, dims, (4, 4, 1), 1)
+    b = syn.random_vector(A.shape[0], 4)
+    kinds = (ml.VCYCLE, ml.LEFT_KASKADE, ml.RIGHT_KASKADE, ml.ADDITIVE)
+    its = {}
+    for order in (1, 2, 3):
+        P = ml.interpolation(dims, (2, 2, 1), order)
+        Ac = ml.galerkin(A, P)
+        for kind in kinds:
+            T = ml.TwoLevel(A, M, P, ml.DenseCoarse(Ac), kind)
+            _, info = krylov.fgmres(lambda v: A @ v, T, b, rtol=1e-6, restart=30, maxit=1000)
+            its[order, kind] = info["iters"]
+    for order in (1, 2, 3):
+        seq = [its[order, k] for k in kinds]
+        assert seq == sorted(seq), (order, seq)
+        assert its[order, ml.VCYCLE] < its[order, ml.ADDITIVE]
+    for kind in kinds:
+        assert its[1, kind] >= its[2, kind] >= its[3, kind], (kind, its)

@@ -147,3 +147,23 @@ def test_reduced_precision_factors_close_to_fp64(prec):
     err = np.abs(zlo - z64).max() / np.abs(z64).max()
     assert err < (1e-5 if prec == 32 else 3e-2)
     assert err > 0
+
+
+def test_restricted_variants_beat_classical_as_table_5():
+    """Table 5's orderings as a trend check (FGMRES(30) to 1e-6, 4 x 4 subdomains):
+    at every overlap 1 to 3 left- and right-RAS need fewer iterations than
+    classical AS, and a wider overlap does not make RAS worse than overlap 1."""
+    from oracle import krylov
+    A, dims = jac(32, 32, 1, seed=2)
+    b = syn.random_vector(A.shape[0], 4)
+    its = {}
+    for kind in (schwarz.AS, schwarz.LEFT_RAS, schwarz.RIGHT_RAS):
+        for d in (1, 2, 3):
+            M = schwarz.Schwarz(A, dims, (4, 4, 1), d, kind=kind)
+            _, info = krylov.fgmres(lambda v: A @ v, M, b, rtol=1e-6, restart=30, maxit=3000)
+            its[kind, d] = info["iters"]
+    for d in (1, 2, 3):
+        assert its[schwarz.LEFT_RAS, d] < its[schwarz.AS, d], its
+        assert its[schwarz.RIGHT_RAS, d] < its[schwarz.AS, d], its
+    for kind in (schwarz.LEFT_RAS, schwarz.RIGHT_RAS):
+        assert max(its[kind, 2], its[kind, 3]) <= its[kind, 1], its
