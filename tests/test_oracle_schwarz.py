@@ -167,3 +167,18 @@ def test_restricted_variants_beat_classical_as_table_5():
         assert its[schwarz.RIGHT_RAS, d] < its[schwarz.AS, d], its
     for kind in (schwarz.LEFT_RAS, schwarz.RIGHT_RAS):
         assert max(its[kind, 2], its[kind, 3]) <= its[kind, 1], its
+
+
+@pytest.mark.parametrize("dims,parts,seed", [((32, 32, 1), (4, 4, 1), 2), ((16, 16, 8), (2, 2, 2), 3)])
+def test_more_fill_fewer_iterations_table_3(dims, parts, seed):
+    """Table 3's ordering as a trend check (classical AS, overlap 1, FGMRES(30) to
+    1e-6): ILU(0) > ILU(1) > ILU(2) > ILU(4) > exact LU in iterations, in 2D and 3D."""
+    from oracle import krylov
+    A, dims = jac(*dims, seed=seed)
+    b = syn.random_vector(A.shape[0], 4)
+    its = []
+    for sub, k in (("ilu", 0), ("ilu", 1), ("ilu", 2), ("ilu", 4), ("lu", 0)):
+        M = schwarz.Schwarz(A, dims, parts, 1, kind=schwarz.AS, sub=sub, ilu_k=k)
+        _, info = krylov.fgmres(lambda v: A @ v, M, b, rtol=1e-6, restart=30, maxit=3000)
+        its.append(info["iters"])
+    assert all(a > b_ for a, b_ in zip(its, its[1:])), its
