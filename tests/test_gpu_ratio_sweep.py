@@ -108,3 +108,40 @@ def test_support_beyond_one_plane_slabs_is_refused(ras):
     _precond(ras, gp, (16, 16, 1), 64)          # 32 x 32 supports: accepted
     with pytest.raises(ras.RasError):
         _precond(ras, gp, (32, 32, 1), 64)
+
+
+def test_vcycle_fgmres_matches_oracle_across_ratios(ras):
+    """FGMRES(30) to 1e-8 with the two-level V-cycle (FP64 factors and coarse LU) on a
+    32 x 32 x 16 system at ratios 2, 4 and 8 (the last through the slab form): at every
+    ratio the GPU takes the oracle's iterations (within one) along the same residual
+    history, and the counts grow with the ratio as in Table 7."""
+    from oracle import krylov, schwarz
+    dims, parts = (32, 32, 16), (2, 2, 2)
+    res = syn.small_3d(*dims, seed=9)
+    prob = disc.Problem(res)
+    p = syn.random_pressure(res, 9)
+    F, J = disc.residual(prob, p, 0.98 * p, 0.97 * p, res.dt, 2, want_jac=True)
+    A = disc.jacobian_csr(res.grid, J)
+    M = schwarz.Schwarz(A, dims, parts, 1)
+    gp = ras.Problem(res)
+    Jd = j_to_dev(J)
+    counts = []
+    for r in (2, 4, 8):
+        P = ml.interpolation(dims, (r, r, r), 2)
+        T = ml.TwoLevel(A, M, P, ml.DenseCoarse(ml.galerkin(A, P)), ml.VCYCLE)
+        hist = []
+        x_ref, info = krylov.fgmres(lambda v: A @ v, T, -F, rtol=1e-8, atol=0.0, restart=30, maxit=500,
+                                    history=hist)
+        pc = ras.Precond(gp, parts, 1, factor_prec=64, nlevels=2, coarsen=(r, r, r), mlevel_type=0,
+                         coarse_prec=64)
+        pc.factor(Jd)
+        x = torch.zeros(res.grid.n, dtype=torch.float64, device="cuda")
+        out = gp.gmres_solve(Jd, pc, dev(-F), x, restart=30, maxit=500, rtol=1e-8, atol=0.0)
+        assert abs(out["iters"] - info["iters"]) <= 1, (r, out["iters"], info["iters"])
+        h = np.array(out["history"])
+        m = min(h.size, len(hist))
+        assert np.max(np.abs(h[:m] - np.array(hist[:m]))) <= 1e-8 * hist[0]
+        assert rel_err(host(x), x_ref) < 1e-6
+        counts.append(out["iters"])
+        del pc
+    assert counts == sorted(counts) and counts[0] < counts[-1], counts
