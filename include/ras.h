@@ -438,6 +438,26 @@ int ras_gemm_f32(int m, int n, int k, float alpha, const float *A, int lda, cons
                  float beta, float *C, int ldc, void *stream);
 int ras_get_apply_kernel(const ras_precond *pc, int *kernel);
 
+/* The cyclic-reduction schedule of the coarse block-tridiagonal system (the opt-in
+ * elimination order of the exact coarse solve, Section 3.2, RAS_COARSE_CR=1 at
+ * set-up) as the library builds it for nb diagonal blocks, for inspection and
+ * host-side checks: host only, no CUDA call. Matrix slots: s < nb is diagonal
+ * block s (inverted in place when eliminated); nb + k and 2 nb + k hold the
+ * couplings L(k) = A(k, k-1) and U(k) = A(k, k+1); higher slots are products
+ * (*nslot slots beyond the nb diagonal blocks). fac: nround, last; then per round
+ * nE and the nE blocks it inverts, followed by two phases, each a task count n and
+ * n tasks of 8 ints {out, acc, sign, a1, b1, a2, b2, 0} meaning
+ * out = (acc ? out : 0) + sign (a1 b1 [+ a2 b2]) (a2 < 0: one term); after the
+ * rounds block `last` is inverted. sol: a phase count, then per phase a task count
+ * n and n tasks of 8 ints {out, 0, sub, m1, v1, m2, v2, 0} on block vectors (bit
+ * 16 set: the solution x, clear: the right-hand side g; low 16 bits: the block)
+ * meaning out = (sub ? out - t : t), t = m1 v1 [+ m2 v2] (m2 < 0: one term). The
+ * tasks of one phase are independent of each other. The lengths go to *fac_len and
+ * *sol_len even when fac_cap or sol_cap is too small (then RAS_EINVAL); RAS_EINVAL
+ * also for nb < 1, nb > 65535 or a NULL pointer. */
+int ras_coarse_cr_schedule(int nb, int *fac, int fac_cap, int *sol, int sol_cap, int *fac_len, int *sol_len,
+                           int *nslot);
+
 #ifdef __cplusplus
 }
 #endif

@@ -3069,3 +3069,19 @@ int transfer_prolong(Transfer *t, const double *xc, double *x, cudaStream_t st) 
 }
 
 }  // namespace ras
+
+// The cyclic-reduction schedule for nb blocks, copied out for inspection (host
+// only: the plan is the one coarse set-up builds).
+extern "C" int ras_coarse_cr_schedule(int nb, int *fac, int fac_cap, int *sol, int sol_cap, int *fac_len,
+                                      int *sol_len, int *nslot) {
+    if (nb < 1 || nb > 0xffff || !fac_len || !sol_len || !nslot) return RAS_EINVAL;
+    ras::CrPlan P;
+    ras::cr_plan(nb, P);
+    *fac_len = (int)P.fac.size();
+    *sol_len = (int)P.sol.size();
+    *nslot = P.nslot;
+    if (!fac || !sol || fac_cap < *fac_len || sol_cap < *sol_len) return RAS_EINVAL;
+    std::copy(P.fac.begin(), P.fac.end(), fac);
+    std::copy(P.sol.begin(), P.sol.end(), sol);
+    return RAS_OK;
+}

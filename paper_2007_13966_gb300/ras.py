@@ -26,7 +26,8 @@ EXPORTED = ["ras_problem_create", "ras_problem_destroy", "residual_eval", "ras_s
             "ras_timing_enable", "ras_timing_read", "ras_apply_bytes", "ras_norm2_noalloc",
             "ras_stencil_transpose", "ras_adjoint_rhs", "ras_grad_logk", "ras_batch_create",
             "ras_batch_destroy", "ras_batch_gmres", "ras_batch_newton_step", "ras_set_apply_schedule",
-            "ras_get_apply_schedule", "ras_set_apply_kernel", "ras_get_apply_kernel", "ras_gemm_f32"]
+            "ras_get_apply_schedule", "ras_set_apply_kernel", "ras_get_apply_kernel", "ras_gemm_f32",
+            "ras_coarse_cr_schedule"]
 
 
 class Grid(C.Structure):
@@ -122,6 +123,8 @@ def lib():
             "ras_set_apply_kernel": (i, [vp, i]),
             "ras_get_apply_kernel": (i, [vp, C.POINTER(i)]),
             "ras_gemm_f32": (i, [i, i, i, C.c_float, vp, i, vp, i, C.c_float, vp, i, vp]),
+            "ras_coarse_cr_schedule": (i, [i, C.POINTER(i), i, C.POINTER(i), i, C.POINTER(i), C.POINTER(i),
+                                           C.POINTER(i)]),
             "ras_batch_create": (i, [i, vp, vp, C.POINTER(vp)]),
             "ras_batch_destroy": (None, [vp]),
             "ras_batch_gmres": (i, [vp, vp, vp, vp, C.POINTER(KrylovOpts), vp, vp]),
@@ -185,6 +188,16 @@ def gemm_f32(A, B, C, alpha=1.0, beta=0.0, stream=None):
     n = B.shape[1]
     check(lib().ras_gemm_f32(m, n, k, float(alpha), _ptr(A), A.stride(0), _ptr(B), B.stride(0),
                              float(beta), _ptr(C), C.stride(0), _stream(stream)), "ras_gemm_f32")
+
+
+def coarse_cr_schedule(nb):
+    """(fac, sol, nslot): the cyclic-reduction schedules for nb coarse blocks (host only)."""
+    fl, sl, ns = C.c_int(0), C.c_int(0), C.c_int(0)
+    lib().ras_coarse_cr_schedule(nb, None, 0, None, 0, C.byref(fl), C.byref(sl), C.byref(ns))
+    fac, sol = (C.c_int * max(fl.value, 1))(), (C.c_int * max(sl.value, 1))()
+    check(lib().ras_coarse_cr_schedule(nb, fac, fl.value, sol, sl.value, C.byref(fl), C.byref(sl), C.byref(ns)),
+          "ras_coarse_cr_schedule")
+    return list(fac[:fl.value]), list(sol[:sl.value]), ns.value
 
 
 def kernel_launches() -> int:
