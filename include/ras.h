@@ -122,7 +122,8 @@ typedef struct {
                               about 25 with FP64 coarse arithmetic, 31 with FP32) */
     int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second; 1 = nearest
                               coarse centre, Eq. equ:inter-frist (order 3 couples
-                              coarse cells three apart: not supported)            */
+                              coarse cells up to four apart, beyond the 125-point
+                              coarse operator: not supported)                     */
     int mlevel_type;       /* 0 = V-cycle, 1 = left-Kaskade, 2 = right-Kaskade,
                               3 = additive, 4 = coarse-only (Eqs. equ:v-cycle ..
                               equ:coarse-level)                                      */
