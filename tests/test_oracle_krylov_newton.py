@@ -118,3 +118,24 @@ def test_step_mass_balance_at_convergence():
     Q = disc.connection_flux(prob, p).sum()
     scale = np.abs(disc.storage(prob, p, p0, p0, 8640.0, 1)).sum()
     assert abs(S + Q) <= 1e-8 * scale
+
+
+
+@pytest.mark.parametrize("dims,parts", [((24, 24, 1), (2, 2, 1)), ((12, 12, 6), (2, 2, 1))])
+def test_larger_time_steps_need_more_iterations_table_2(dims, parts):
+    """Table 2's trend as a check (one-level left-RAS): one BDF1 step from the same
+    state (after two 0.1-day steps) with a time step of 0.05 to 0.8 day converges
+    every time, its Newton iterations do not fall and its total FGMRES iterations
+    rise as the step grows."""
+    res = syn.small_3d(*dims, seed=3)
+    prob = disc.Problem(res)
+    fac = lambda A, J: schwarz.Schwarz(A, dims, parts, 1)
+    states, _ = newton.simulate(prob, fac, 2, dt=0.1 * 86400.0)
+    nits, lits = [], []
+    for days in (0.05, 0.1, 0.2, 0.4, 0.8):
+        _, info = newton.newton_solve(prob, fac, states[-1], states[-2], days * 86400.0, 1)
+        assert info["status"] == 0
+        nits.append(info["newton_iters"])
+        lits.append(sum(info["lin_iters"]))
+    assert nits == sorted(nits), nits
+    assert all(a < b for a, b in zip(lits, lits[1:])), lits
