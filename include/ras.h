@@ -119,7 +119,8 @@ typedef struct {
                               stages it in shared memory whole or in slabs of
                               z-planes, and set-up returns RAS_EINVAL when even one
                               x-y plane of it does not fit (x and y ratios beyond
-                              about 25 with FP64 coarse arithmetic, 31 with FP32) */
+                              about 25 with FP64 coarse arithmetic, 31 with FP32)
+                              or its x extent reaches 256 cells (x ratio > 127)   */
     int interp_order;      /* 2 = (bi/tri)linear, Eq. equ:inter-second; 1 = nearest
                               coarse centre, Eq. equ:inter-frist (order 3 couples
                               coarse cells up to four apart, beyond the 125-point

@@ -342,8 +342,12 @@ static size_t rap_smem_of(const int w[3], int zs, size_t esz) {
 
 // The form that fits in cap bytes: whole boxes when they fit, else the tallest
 // slab that does (RAS_RAP_SLAB=n at set-up, a test knob, asks for slabs of at
-// most n planes); RAS_EINVAL when not even one plane fits.
+// most n planes); RAS_EINVAL when not even one plane fits, or when the support
+// is wider than rap_tables' packed indices hold (x < 256, one x-y plane < 2^16).
 static int rap_plan(const int w[3], size_t esz, size_t cap, int &zs, size_t &smem) {
+    zs = 0;
+    smem = 0;
+    if (w[0] > 255 || (long long)w[0] * w[1] > 0xffff) return RAS_EINVAL;
     int force = 0;
     if (const char *e = getenv("RAS_RAP_SLAB")) force = atoi(e);
     zs = 0;
