@@ -43,8 +43,9 @@ def test_perturbation_scales_connections():
     th = np.linspace(-0.5, 0.5, res.grid.n)
     r2 = adj.perturbed(res, th)
     e = np.exp(th)
-    assert np.allclose(r2.kx, res.kx * e) and np.allclose(r2.kz, res.kz * e)
-    assert np.allclose(r2.conns.T, res.conns.T * e[res.conns.cell])
+    assert np.allclose(r2.kx, res.kx * e, rtol=1e-14, atol=0)
+    assert np.allclose(r2.kz, res.kz * e, rtol=1e-14, atol=0)
+    assert np.allclose(r2.conns.T, res.conns.T * e[res.conns.cell], rtol=1e-14, atol=0)
 
 
 @pytest.mark.parametrize("options", [{"conservative": True}, {"gravity": 50 * 9.80665, "upwind": True}])

@@ -134,6 +134,21 @@ def test_transmissibility_uniform_equals_kA_over_h():
     k = np.full(res.grid.n, 2e-13)
     Tx, Ty, Tz = disc.face_transmissibilities(res.grid, k, k, k)
     g = res.grid
-    assert np.allclose(Tx.reshape(g.nz, g.ny, g.nx)[:, :, :-1], 2e-13 * g.hy * g.hz / g.hx, rtol=1e-15)
+    assert np.allclose(Tx.reshape(g.nz, g.ny, g.nx)[:, :, :-1], 2e-13 * g.hy * g.hz / g.hx, rtol=1e-15, atol=0)
     assert np.all(Tx.reshape(g.nz, g.ny, g.nx)[:, :, -1] == 0)
-    assert np.allclose(Tz.reshape(g.nz, g.ny, g.nx)[:-1], 2e-13 * g.hx * g.hy / g.hz, rtol=1e-15)
+    assert np.allclose(Tz.reshape(g.nz, g.ny, g.nx)[:-1], 2e-13 * g.hx * g.hy / g.hz, rtol=1e-15, atol=0)
+
+
+def test_bdf_terms_exact_on_polynomials_in_time():
+    """Eqs. implicit-method-bdf1 / -bdf2 in closed form: BDF1 gives the exact time
+    derivative of a pressure linear in time, BDF2 that of one quadratic in time,
+    and the derivative terms are 1/dt and 3/(2 dt)."""
+    dt, t = 7.5, 40.0
+    for c0, c1, c2 in ((2.0e6, 3.0e3, 0.0), (1.0e5, -2.0e2, 5.0)):
+        p = lambda s: c0 + c1 * s + c2 * s * s
+        dp = c1 + 2.0 * c2 * t
+        D2, d2 = disc.bdf_terms(p(t), p(t - dt), p(t - 2 * dt), dt, 2)
+        assert D2 == pytest.approx(dp, rel=1e-12) and d2 == pytest.approx(1.5 / dt, rel=1e-15)
+        if c2 == 0.0:
+            D1, d1 = disc.bdf_terms(p(t), p(t - dt), None, dt, 1)
+            assert D1 == pytest.approx(dp, rel=1e-12) and d1 == pytest.approx(1.0 / dt, rel=1e-15)
