@@ -120,3 +120,32 @@ def test_left_ras_combined_as_classical_as(monkeypatch):
             self.kind = schwarz.LEFT_RAS
     monkeypatch.setattr(schwarz.Schwarz, "apply", bad)
     _fails(T_sch.test_left_ras_transpose_is_right_ras_of_transpose)
+
+
+def test_keys_kernel_with_another_parameter(monkeypatch):
+    def bad(s):                  # cubic convolution with a = -3/4 instead of -1/2
+        s = abs(s)
+        if s < 1.0:
+            return 1.25 * s ** 3 - 2.25 * s ** 2 + 1.0
+        if s < 2.0:
+            return -0.75 * s ** 3 + 3.75 * s ** 2 - 6.0 * s + 3.0
+        return 0.0
+    monkeypatch.setattr(ml, "keys_w", bad)
+    _fails(T_ml.test_polynomial_reproduction, 32, 4)
+
+
+def test_dz_dp_with_the_wrong_sign(monkeypatch):
+    orig = eos.dz_dp_paper
+    monkeypatch.setattr(eos, "dz_dp_paper", lambda *a: -orig(*a))
+    _fails(T_eos.test_dz_dp_closed_form, syn.Fluid())
+
+
+def test_gravity_term_with_the_wrong_sign(monkeypatch):
+    import test_oracle_gravity as T_grav
+    orig = disc.Problem.__init__
+
+    def bad(self, res):
+        orig(self, res)
+        self.gravity = -self.gravity
+    monkeypatch.setattr(disc.Problem, "__init__", bad)
+    _fails(T_grav.test_closed_column_settles_to_the_hydrostatic_profile)
