@@ -30,12 +30,12 @@ Readings (the paper defers CCFD details to its references):
   Darcy velocity v into the domain through boundary faces of total area A of a cell
   carries (p/Z) v A of the equation's transported quantity (Eq. gover_sys divided by
   W / (RT)), the cell's own p/Z for the injected gas: F_i -= mu m(p_i) Q_i with
-  Q_i = v A (Reservoir.rate_Q, m^3/s per cell; positive into the cell). Oracle only;
+  Q_i = v A (Reservoir.rate_Q, m^3/s per cell; positive into the cell);
 * Reservoir.conservative = True takes the accumulation in conservative form,
   V phi D_t (p/Z) (the time derivative of Eq. mass conservation's phi rho, divided by
   W / (RT)), instead of Eq. gover_sys's V phi c(p) D_t p; the two agree for an ideal
   gas (Z = 1) and differ at O(dt) otherwise; the conservative form keeps the discrete
-  mass of a closed domain exactly. Oracle only.
+  mass of a closed domain exactly.
 The source term -qRT/W of Eq. gover_sys is carried by the connections.
 
 Jacobian storage: seven arrays (centre, -x, +x, -y, +y, -z, +z) of length N,

@@ -149,3 +149,33 @@ def test_gravity_term_with_the_wrong_sign(monkeypatch):
         self.gravity = -self.gravity
     monkeypatch.setattr(disc.Problem, "__init__", bad)
     _fails(T_grav.test_closed_column_settles_to_the_hydrostatic_profile)
+
+
+def test_vcycle_without_post_smoothing(monkeypatch):
+    orig = ml.TwoLevel.apply
+
+    def bad(self, r):
+        if self.kind != ml.VCYCLE:
+            return orig(self, r)
+        e1 = self.M(r)
+        return e1 + self.coarse(r - self.A @ e1)
+    monkeypatch.setattr(ml.TwoLevel, "apply", bad)
+    _fails(T_ml.test_vcycle_three_steps_equal_closed_form)
+
+
+def test_ilu_lower_factor_off_by_a_percent(monkeypatch):
+    orig = schwarz.ilu_numeric
+    monkeypatch.setattr(schwarz, "ilu_numeric", lambda A, pat: (lambda LU: (1.01 * LU[0], LU[1]))(orig(A, pat)))
+    _fails(T_sch.test_ilu0_tridiagonal_is_exact_lu)
+
+
+def test_rate_inflow_with_the_wrong_sign(monkeypatch):
+    import test_oracle_rates as T_rates
+    orig = disc.Problem.__init__
+
+    def bad(self, res):
+        orig(self, res)
+        if self.rate_Q is not None:
+            self.rate_Q = -self.rate_Q
+    monkeypatch.setattr(disc.Problem, "__init__", bad)
+    _fails(T_rates.test_steady_rate_inlet_matches_the_closed_form)
