@@ -19,8 +19,8 @@ def test_interp_rows_sum_to_one(order, n, r):
 def test_ratio_two_linear_weights():
     P = ml.interp_1d(16, 2, 2)
     # interior fine cells sit at 1/4 and 3/4 between coarse centres
-    assert np.allclose(P[3, 1:3], [0.75, 0.25])
-    assert np.allclose(P[4, 1:3], [0.25, 0.75])
+    assert np.allclose(P[3, 1:3], [0.75, 0.25], rtol=0, atol=1e-15)
+    assert np.allclose(P[4, 1:3], [0.25, 0.75], rtol=0, atol=1e-15)
 
 
 @pytest.mark.parametrize("n,r", [(32, 4), (24, 2), (40, 8)])
@@ -29,7 +29,7 @@ def test_polynomial_reproduction(n, r):
     x = np.arange(n) + 0.5
     inside = (x >= xc[0]) & (x <= xc[-1])
     P1, P2, P3 = (ml.interp_1d(n, r, o) for o in (1, 2, 3))
-    assert np.allclose(P1 @ np.full(xc.size, 3.0), 3.0)
+    assert np.allclose(P1 @ np.full(xc.size, 3.0), 3.0, rtol=0, atol=1e-14)
     lin = lambda t: 2.0 * t - 1.0
     assert np.allclose((P2 @ lin(xc))[inside], lin(x)[inside], atol=1e-12)
     # cubic convolution (a = -1/2) reproduces quadratics away from the clamped ends
