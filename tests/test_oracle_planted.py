@@ -179,3 +179,44 @@ def test_rate_inflow_with_the_wrong_sign(monkeypatch):
             self.rate_Q = -self.rate_Q
     monkeypatch.setattr(disc.Problem, "__init__", bad)
     _fails(T_rates.test_steady_rate_inlet_matches_the_closed_form)
+
+
+def test_algorithm1_without_presmoothing(monkeypatch):
+    orig = ml.MultiLevel.__init__
+
+    def bad(self, *a, **k):
+        orig(self, *a, **k)
+        self.mu = 0
+    monkeypatch.setattr(ml.MultiLevel, "__init__", bad)
+    _fails(T_ml.test_algorithm1_two_levels_equals_vcycle)
+
+
+def test_adjoint_parameter_derivative_with_the_wrong_sign(monkeypatch):
+    from oracle import adjoint
+    import test_oracle_adjoint as T_adj
+    orig = adjoint.dF_dtheta_T
+    monkeypatch.setattr(adjoint, "dF_dtheta_T", lambda *a: -orig(*a))
+    _fails(T_adj.test_adjoint_gradient_matches_finite_differences, (5, 4, 2), 1)
+
+
+def test_conservative_option_ignored(monkeypatch):
+    import test_oracle_conservative as T_cons
+    orig = disc.Problem.__init__
+
+    def bad(self, res):
+        orig(self, res)
+        self.conservative = False
+    monkeypatch.setattr(disc.Problem, "__init__", bad)
+    _fails(T_cons.test_closed_domain_keeps_its_mass_only_in_conservative_form)
+
+
+def test_upwind_option_ignored(monkeypatch):
+    import test_oracle_upwind as T_up
+    orig = disc.Problem.__init__
+
+    def bad(self, res):
+        orig(self, res)
+        self.upwind = False
+    monkeypatch.setattr(disc.Problem, "__init__", bad)
+    _fails(T_up.test_upwind_telescopes_and_differs_from_the_mean)
+    _fails(T_up.test_steady_flow_converges_at_first_order_from_below)
