@@ -213,7 +213,9 @@ int residual_eval(ras_problem *prob, const double *p, const double *p_l, const d
                   void *stream);
 
 /* y = J x for a 7-point operator (the Jacobian-vector product of the Krylov
- * solve, Eq. jacobian). x, y: device [N], must not alias. */
+ * solve, Eq. jacobian). x, y: device [N], must not alias; J's seven arrays are
+ * read, not kept. Asynchronous on `stream`. RAS_EINVAL for a NULL pointer or
+ * array, or x == y. */
 int ras_stencil_matvec(const ras_problem *prob, const ras_stencil *J, const double *x,
                        double *y, void *stream);
 
@@ -365,7 +367,11 @@ int ras_stencil_transpose(const ras_problem *prob, const ras_stencil *J, ras_ste
                           void *stream);
 
 /* rhs = -dphi + c1 s(p1) lam1 + c2 s(p2) lam2, s(p) = V phi c(p) per cell; a
- * term whose state (p1 or p2) is NULL is absent, dphi NULL reads as 0. */
+ * term whose state (p1 or p2) is NULL is absent, dphi NULL reads as 0. In the
+ * backward sweep over a BDF2 time loop (Eq. implicit-method-bdf2) c1 = 2/dt and
+ * c2 = -1/(2 dt), the weights with which p^l enters the residuals of steps l+1
+ * and l+2; p1, p2 are the states where those residuals take s (p^{l+1}, p^{l+2},
+ * or p^l itself in the conservative form). */
 int ras_adjoint_rhs(const ras_problem *prob, const double *dphi, const double *p1,
                     const double *lam1, double c1, const double *p2, const double *lam2,
                     double c2, double *rhs, void *stream);
@@ -426,6 +432,8 @@ int ras_get_apply_schedule(const ras_precond *pc, int *chunk_cells, int *threads
  * final. Allowed for left-RAS (ras_type 1) ILU(0) with FP32 or BF16 factors when
  * no overlapped box has more than 1024 x-pencils (RAS_EINVAL otherwise). */
 int ras_set_apply_kernel(ras_precond *pc, int kernel);
+/* The current kernel of the subdomain solves (0 or 1, as above). */
+int ras_get_apply_kernel(const ras_precond *pc, int *kernel);
 
 /* Dense FP32 product C = alpha A B + beta C on the tcgen05 tensor cores, the
  * building block of the dense coarse-level block elimination (Section 3.2: the
@@ -438,7 +446,6 @@ int ras_set_apply_kernel(ras_precond *pc, int kernel);
  * bounded wait for the tensor core gave up. */
 int ras_gemm_f32(int m, int n, int k, float alpha, const float *A, int lda, const float *B, int ldb,
                  float beta, float *C, int ldc, void *stream);
-int ras_get_apply_kernel(const ras_precond *pc, int *kernel);
 
 /* The cyclic-reduction schedule of the coarse block-tridiagonal system (the opt-in
  * elimination order of the exact coarse solve, Section 3.2, RAS_COARSE_CR=1 at
